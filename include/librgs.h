@@ -1,0 +1,200 @@
+/*
+ * librgs -- randomized Gram-Schmidt (RGS) and RGS-GMRES on one NVIDIA GB300 GPU.
+ *
+ * Method: L. Balabanov and L. Grigori, "Randomized Gram-Schmidt process with
+ * application to GMRES" (arXiv 2011.05090).  Every entry point below cites the
+ * section, algorithm or equation whose operation it performs.
+ *
+ * Conventions shared by all entry points
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *  - Array arguments are device pointers owned by the caller unless a function
+ *    says otherwise; the library never frees them.  rgs_qr additionally accepts
+ *    host pointers (pinned or pageable) and stages them through device memory.
+ *  - Work is issued on the stream bound to the handle (rgs_create /
+ *    rgs_set_stream).  Functions that return device-computed status (breakdown,
+ *    convergence, timeouts) synchronise that stream before returning.
+ *  - Errors are reported by return value, never by aborting; a human-readable
+ *    message for the last error on a handle is available from rgs_last_error.
+ *  - Workspaces (sketch tables, Householder factors, partial sketches) belong
+ *    to the handle or to the object that needs them and are freed with it.
+ *  - Random sketches are drawn from Philox4x32-10 (Salmon et al., SC'11) with
+ *    key = (seed mod 2^32, seed div 2^32) and these counter streams:
+ *      Gaussian entry (l, c): counter (c, l>>1, 0, 0); Box-Muller on the two
+ *        53-bit midpoint uniforms of words (x0,x1) and (x2,x3); cosine for even
+ *        l, sine for odd l; scaled by 1/sqrt(k).
+ *      SRHT sign of column c: bit (c mod 128) of the words at (c>>7, 0, 0, 1).
+ *      SRHT sample: the k indices c < s with the smallest (x0*2^32+x1, c) at
+ *        counter (c, 0, 0, 2), in ascending order.
+ */
+#ifndef LIBRGS_H
+#define LIBRGS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RGS_API __attribute__((visibility("default")))
+#else
+#define RGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RGS_OK = 0,
+    RGS_ERR_INVALID_ARG = 1,     /* shape, pointer, alignment or option rejected */
+    RGS_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+    RGS_ERR_ALLOC = 3,           /* device or host allocation failed */
+    RGS_ERR_BREAKDOWN = 4,       /* r_ii <= 16 u ||p_i||: column i depends on the previous ones */
+    RGS_ERR_NOT_CONVERGED = 5,   /* solver stopped at max_cycles above the tolerance; x is the last iterate */
+    RGS_ERR_TIMEOUT = 6,         /* a device-side grid barrier gave up waiting */
+    RGS_ERR_NONFINITE = 7,       /* NaN or Inf met in a sketched norm */
+    RGS_ERR_NOT_IMPLEMENTED = 8
+} rgs_status;
+
+typedef enum { RGS_F64 = 0, RGS_F32 = 1, RGS_BF16 = 2 } rgs_dtype;
+
+typedef enum { RGS_SKETCH_GAUSSIAN = 0, RGS_SKETCH_SRHT = 1 } rgs_sketch_kind;
+
+typedef struct rgs_context* rgs_handle;
+typedef struct rgs_sketch_obj* rgs_sketch;
+typedef struct rgs_arnoldi_obj* rgs_arnoldi;
+
+/* Library handle on the current CUDA device.  stream: a cudaStream_t, or NULL
+ * for the default stream.  Returns RGS_ERR_CUDA if no device is usable. */
+RGS_API rgs_status rgs_create(rgs_handle* out, void* stream);
+RGS_API rgs_status rgs_destroy(rgs_handle h);
+RGS_API rgs_status rgs_set_stream(rgs_handle h, void* stream);
+RGS_API const char* rgs_status_string(rgs_status s);
+RGS_API const char* rgs_last_error(rgs_handle h);
+
+/* ---------------------------------------------------------------- sketches
+ * Sec. 2.1: Theta (k x n) is either Gaussian with N(0, 1/k) entries or the
+ * partial SRHT -- the first n columns of (1/sqrt(k)) P H_s D with s the power of
+ * two n <= s < 2n, D random signs, H_s the +-1 Walsh-Hadamard matrix and P a
+ * uniform sample of k rows.  Both are fully determined by (kind, n, k, seed).
+ * Requires 1 <= k; SRHT requires k <= s; Gaussian stores Theta in device memory
+ * (8 k n bytes).  The object holds device tables until rgs_sketch_destroy. */
+RGS_API rgs_status rgs_sketch_create(rgs_handle h, rgs_sketch_kind kind, int64_t n, int32_t k,
+                             uint64_t seed, rgs_sketch* out);
+RGS_API rgs_status rgs_sketch_destroy(rgs_sketch s);
+
+/* Y (k x ncols, ldy >= k) = Theta X (n x ncols, ldx >= n), FP64, device pointers.
+ * The sketch of Alg. 2 step 1 / step 4 applied to a block of vectors. */
+RGS_API rgs_status rgs_sketch_apply(rgs_handle h, rgs_sketch s, int32_t ncols, const double* X, int64_t ldx,
+                            double* Y, int64_t ldy);
+
+/* ---------------------------------------------------------------- RGS QR
+ * Alg. 2: given W (n x m, FP64) and Theta with m <= k, computes Q (n x m) and
+ * the upper-triangular R (m x m, FP64, positive diagonal) with W = Q R and
+ * Theta Q orthonormal.  Step 2 uses a Householder QR of S_{i-1} (Sec. 5),
+ * step 3 runs in the storage precision qtype (FP64, or FP32 accumulation for
+ * RGS_F32 / RGS_BF16 storage: the working precision u_crs), steps 1, 4-8 run
+ * in FP64 (u_fine).
+ *   Q      n x m in qtype, ldq >= n.  If qscale is non-NULL, Q receives the
+ *          unnormalised q'_i and qscale[i] = 1/r_ii (FP64), so the basis is
+ *          Q diag(qscale) exactly (the Step 7 division is never rounded to
+ *          qtype).  If qscale is NULL, Q is scaled in place at the end.
+ *   R      m x m, ldr >= m (strictly lower part set to 0).
+ *   S      optional (NULL): k x m, lds >= k, receives S = Theta Q (FP64).
+ *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings.
+ *   info   optional host struct: step-8 certificates and breakdown column.
+ * W, Q, R, S, qscale may be all device or all host pointers.  Returns
+ * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
+#define RGS_QR_NO_CERTIFICATES 1
+#define RGS_QR_TIMINGS 2         /* bit 1: time each phase with CUDA events (fills the *_ms fields) */
+typedef struct {
+    double delta;          /* Delta_m  = ||I - S^T S||_F            (Alg. 2 step 8) */
+    double delta_tilde;    /* Delta~_m = ||P - S R||_F / ||P||_F    (Alg. 2 step 8) */
+    int32_t breakdown_col; /* -1, or the column at which r_ii vanished */
+    int32_t launches;      /* kernels this call launched */
+    double sketch_ms;      /* step 1 for all columns (P = Theta W), with RGS_QR_TIMINGS */
+    double update_ms;      /* fused steps 3-4 over all columns, with RGS_QR_TIMINGS */
+    double ls_ms;          /* steps 2, 5, 6 over all columns, with RGS_QR_TIMINGS */
+} rgs_qr_info;
+
+RGS_API rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double* W, int64_t ldw,
+                  void* Q, rgs_dtype qtype, int64_t ldq, double* qscale, double* R, int64_t ldr,
+                  double* S, int64_t lds, int32_t flags, rgs_qr_info* info);
+
+/* ---------------------------------------------------------------- sparse operator */
+typedef struct {
+    int64_t n;              /* rows = columns */
+    int64_t nnz;
+    const int32_t* rowptr;  /* n + 1 entries, device */
+    const int32_t* colind;  /* nnz entries, device, ascending within a row */
+    const double* val;      /* nnz entries, device */
+} rgs_csr;
+
+/* ---------------------------------------------------------------- RGS-Arnoldi
+ * Alg. 3: builds Q_j (Theta-orthonormal Krylov basis) and R_j one column at a
+ * time; H_j = R_j(1:j, 2:j) (Sec. 4.1).  The object owns the basis (n x mmax in
+ * qtype, stored as q'_i with scale 1/r_ii), S, R, the Householder factors of S
+ * and a work vector.
+ *   rgs_arnoldi_start: iteration 1 with w_1 (device FP64, n).
+ *   rgs_arnoldi_step:  next iteration with w_i = A q_{i-1} (A given, FP64 SpMV),
+ *                      or with the caller's w (device FP64) when A is NULL.
+ *   rgs_arnoldi_get:   number of columns, and copies of R (ncols x ncols, ldr)
+ *                      and qscale (ncols) to host memory; Q stays in the object
+ *                      and rgs_arnoldi_basis returns its device pointer and ld.
+ * A step after a breakdown returns RGS_ERR_BREAKDOWN (happy breakdown in
+ * GMRES terms). */
+RGS_API rgs_status rgs_arnoldi_create(rgs_handle h, rgs_sketch s, int64_t n, int32_t mmax, rgs_dtype qtype,
+                              rgs_arnoldi* out);
+RGS_API rgs_status rgs_arnoldi_destroy(rgs_arnoldi a);
+RGS_API rgs_status rgs_arnoldi_start(rgs_handle h, rgs_arnoldi a, const double* w1);
+RGS_API rgs_status rgs_arnoldi_step(rgs_handle h, rgs_arnoldi a, const rgs_csr* A, const double* w);
+RGS_API rgs_status rgs_arnoldi_get(rgs_handle h, rgs_arnoldi a, int32_t* ncols, double* R_host, int64_t ldr,
+                           double* qscale_host);
+RGS_API rgs_status rgs_arnoldi_basis(rgs_arnoldi a, void** Q, int64_t* ldq);
+
+/* ---------------------------------------------------------------- GMRES
+ * rgmres_solve: restarted randomized GMRES (Sec. 4.2, Eq. hls) on A x = b with
+ * the RGS-Arnoldi basis; in each cycle y = argmin ||H z - r_11 e_1|| by Givens
+ * rotations in FP64, x += Q y, and the true residual b - A x is recomputed in
+ * FP64 (restarting is not in the paper, which runs one cycle).
+ * cgs2_gmres_solve: the same restarted GMRES with an l2-orthonormal FP64 basis
+ * built by CGS2 (projector (I - Q Q^T)^2, Sec. 1.2): the comparator.
+ * b, x: device FP64 (x holds x0 on entry, the solution on exit).
+ * Returns RGS_OK on convergence, RGS_ERR_NOT_CONVERGED otherwise. */
+typedef struct {
+    int32_t restart;        /* Arnoldi steps (products with A) per cycle */
+    int32_t max_cycles;
+    double rtol;            /* stop when ||b - A x|| <= rtol ||b|| */
+    double inner_factor;    /* cycle ends when the Givens residual <= inner_factor * rtol * ||Theta b|| */
+    rgs_dtype qtype;        /* basis storage (RGS only) */
+    int32_t fixed_steps;    /* 1: always run `restart` steps per cycle */
+    int32_t reserved;
+} rgmres_opts;
+
+typedef struct {
+    int32_t cycles;
+    int32_t total_steps;
+    int32_t converged;
+    int32_t status;
+    double rel_residual;    /* final ||b - A x|| / ||b|| in FP64 */
+    double* history;        /* optional host array (max_cycles + 1): residual after each cycle */
+} rgmres_info;
+
+RGS_API rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const double* b, double* x,
+                        const rgmres_opts* opts, rgmres_info* info);
+RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, double* x,
+                            const rgmres_opts* opts, rgmres_info* info);
+
+/* Batched solves (one persistent launch) and the learned preconditioner are
+ * declared for interface stability; they return RGS_ERR_NOT_IMPLEMENTED until
+ * built.  Right preconditioning follows Sec. 5.3 (A M, x = M y); kind 1 is the
+ * Jacobi preconditioner diag(A)^-1. */
+typedef enum { RGS_PRECOND_NONE = 0, RGS_PRECOND_JACOBI = 1, RGS_PRECOND_LEARNED_CONV = 2 } rgs_precond_kind;
+RGS_API rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void* params,
+                                     int32_t flexible);
+RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_sketch* sketches,
+                                const rgs_csr* A, const double* const* b, double* const* x,
+                                const rgmres_opts* opts, rgmres_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBRGS_H */

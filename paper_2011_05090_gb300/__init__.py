@@ -1,0 +1,226 @@
+"""Python binding of librgs: randomized Gram-Schmidt and RGS-GMRES on the GPU.
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+``lib/librgs.so`` (built from ``csrc/`` by ``build.py``).  If the library is
+missing, importing a function raises immediately; there is no fallback.
+
+Matrices are torch tensors in column-major layout: an n x m matrix is a tensor
+of shape (n, m) with stride (1, ld), e.g. ``torch.empty(m, n).T``.  Functions
+keep the names of the C entry points in ``include/librgs.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librgs.so")
+
+RGS_OK = 0
+RGS_ERR_INVALID_ARG = 1
+RGS_ERR_CUDA = 2
+RGS_ERR_ALLOC = 3
+RGS_ERR_BREAKDOWN = 4
+RGS_ERR_NOT_CONVERGED = 5
+RGS_ERR_TIMEOUT = 6
+RGS_ERR_NONFINITE = 7
+RGS_ERR_NOT_IMPLEMENTED = 8
+
+RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
+RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
+RGS_QR_NO_CERTIFICATES = 1
+RGS_QR_TIMINGS = 2
+RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
+
+_DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF16}
+_KIND = {"gaussian": RGS_SKETCH_GAUSSIAN, "srht": RGS_SKETCH_SRHT}
+
+EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", "rgs_last_error",
+            "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_qr",
+            "rgs_arnoldi_create", "rgs_arnoldi_destroy", "rgs_arnoldi_start", "rgs_arnoldi_step",
+            "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgmres_solve", "cgs2_gmres_solve",
+            "rgmres_set_preconditioner", "rgmres_solve_batched"]
+
+
+class RgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"librgs status {status}: {msg}")
+        self.status = status
+
+
+class QRInfo(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("delta_tilde", ctypes.c_double),
+                ("breakdown_col", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("sketch_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("ls_ms", ctypes.c_double)]
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("inner_factor", ctypes.c_double), ("qtype", ctypes.c_int32), ("fixed_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int32), ("total_steps", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def load():
+    """Load librgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2011_05090_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "rgs_create": [ctypes.POINTER(P), P],
+        "rgs_destroy": [P],
+        "rgs_set_stream": [P, P],
+        "rgs_status_string": [ctypes.c_int],
+        "rgs_last_error": [P],
+        "rgs_sketch_create": [P, ctypes.c_int, I64, I32, ctypes.c_uint64, ctypes.POINTER(P)],
+        "rgs_sketch_destroy": [P],
+        "rgs_sketch_apply": [P, P, I32, P, I64, P, I64],
+        "rgs_qr": [P, P, I64, I32, P, I64, P, ctypes.c_int, I64, P, P, I64, P, I64, I32, ctypes.POINTER(QRInfo)],
+        "rgs_arnoldi_create": [P, P, I64, I32, ctypes.c_int, ctypes.POINTER(P)],
+        "rgs_arnoldi_destroy": [P],
+        "rgs_arnoldi_start": [P, P, P],
+        "rgs_arnoldi_step": [P, P, ctypes.POINTER(CSR), P],
+        "rgs_arnoldi_get": [P, P, ctypes.POINTER(I32), P, I64, P],
+        "rgs_arnoldi_basis": [P, ctypes.POINTER(P), ctypes.POINTER(I64)],
+        "rgmres_solve": [P, P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+        "cgs2_gmres_solve": [P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+        "rgmres_set_preconditioner": [P, ctypes.c_int, P, I32],
+        "rgmres_solve_batched": [P, I32, P, P, P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name in ("rgs_status_string", "rgs_last_error") else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, handle=None):
+    if status != RGS_OK:
+        L = load()
+        msg = L.rgs_status_string(status).decode()
+        if handle is not None and handle.ptr:
+            detail = L.rgs_last_error(handle.ptr).decode()
+            if detail:
+                msg += f" ({detail})"
+        raise RgsError(status, msg)
+
+
+def _colmajor(t, rows=None, cols=None):
+    """(pointer, ld) of a column-major 2-D tensor of shape (rows, cols)."""
+    if t.dim() == 1:
+        t = t[:, None]
+    if rows is not None and t.shape[0] != rows or cols is not None and t.shape[1] != cols:
+        raise ValueError(f"shape {tuple(t.shape)} != ({rows}, {cols})")
+    if t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1)")
+    ld = t.stride(1) if t.shape[1] > 1 else max(t.shape[0], 1)
+    return t.data_ptr(), ld
+
+
+def colmajor_empty(rows, cols, dtype=torch.float64, device="cuda", pin=False):
+    """An uninitialised column-major (rows x cols) tensor."""
+    if pin:
+        return torch.empty(cols, rows, dtype=dtype, pin_memory=True).T
+    return torch.empty(cols, rows, dtype=dtype, device=device).T
+
+
+class Handle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.rgs_destroy(self.ptr)
+            self.ptr = None
+
+
+class Sketch:
+    def __init__(self, ptr, handle, kind, n, k, seed):
+        self.ptr, self.handle, self.kind, self.n, self.k, self.seed = ptr, handle, kind, n, k, seed
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.rgs_sketch_destroy(self.ptr)
+            self.ptr = None
+
+
+def rgs_create(stream=None):
+    """Handle bound to ``stream`` (default: torch's current CUDA stream)."""
+    L = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_void_p()
+    _check(L.rgs_create(ctypes.byref(out), ctypes.c_void_p(stream.cuda_stream)))
+    return Handle(out.value)
+
+
+def rgs_set_stream(h, stream):
+    _check(load().rgs_set_stream(h.ptr, ctypes.c_void_p(stream.cuda_stream)), h)
+
+
+def rgs_sketch_create(h, kind, n, k, seed):
+    out = ctypes.c_void_p()
+    _check(load().rgs_sketch_create(h.ptr, _KIND[kind], int(n), int(k), int(seed), ctypes.byref(out)), h)
+    return Sketch(out.value, h, kind, int(n), int(k), int(seed))
+
+
+def rgs_sketch_apply(h, sk, X, Y=None):
+    """Y (k x ncols) = Theta X for a column-major FP64 X (n x ncols) on the GPU."""
+    if X.dim() == 1:
+        X = X[:, None]
+    ncols = X.shape[1]
+    if Y is None:
+        Y = colmajor_empty(sk.k, ncols, device=X.device)
+    px, ldx = _colmajor(X, sk.n, ncols)
+    py, ldy = _colmajor(Y, sk.k, ncols)
+    _check(load().rgs_sketch_apply(h.ptr, sk.ptr, ncols, px, ldx, py, ldy), h)
+    return Y
+
+
+def rgs_qr(h, sk, W, Q, R, qscale=None, S=None, flags=0):
+    """Alg. 2 on W (n x m, FP64).  Fills Q (n x m, FP64/FP32/BF16), R (m x m) and optionally
+    qscale (m) and S (k x m); returns the step-8 certificates as a dict."""
+    n, m = W.shape
+    pw, ldw = _colmajor(W, n, m)
+    pq, ldq = _colmajor(Q, n, m)
+    pr, ldr = _colmajor(R, m, m)
+    ps, lds = (_colmajor(S, sk.k, m) if S is not None else (None, sk.k))
+    info = QRInfo()
+    st = load().rgs_qr(h.ptr, sk.ptr, n, m, pw, ldw, pq, _DTYPE[Q.dtype], ldq,
+                       qscale.data_ptr() if qscale is not None else None, pr, ldr, ps, lds, flags,
+                       ctypes.byref(info))
+    res = {"delta": info.delta, "delta_tilde": info.delta_tilde, "breakdown_col": info.breakdown_col,
+           "launches": info.launches, "sketch_ms": info.sketch_ms, "update_ms": info.update_ms,
+           "ls_ms": info.ls_ms}
+    if st != RGS_OK:
+        try:
+            _check(st, h)
+        except RgsError as e:
+            e.info = res
+            raise
+    return res
+
+
+def csr_struct(rowptr, colind, val):
+    n = rowptr.numel() - 1
+    return CSR(n, colind.numel(), rowptr.data_ptr(), colind.data_ptr(), val.data_ptr())

@@ -1,0 +1,271 @@
+// Internal definitions shared by the librgs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/librgs.h"
+
+// ---------------------------------------------------------------- error plumbing
+struct RgsError {
+    rgs_status status;
+    std::string msg;
+};
+
+#define RGS_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            throw RgsError{RGS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define RGS_REQUIRE(cond, what)                                                         \
+    do {                                                                                \
+        if (!(cond)) throw RgsError{RGS_ERR_INVALID_ARG, what};                         \
+    } while (0)
+
+// ---------------------------------------------------------------- device workspace
+// A growable device buffer owned by a handle or an object.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    void ensure(size_t want) {
+        if (want <= bytes) return;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&ptr, want) != cudaSuccess) {
+            ptr = nullptr;
+            throw RgsError{RGS_ERR_ALLOC, "cudaMalloc of " + std::to_string(want) + " bytes failed"};
+        }
+        bytes = want;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(ptr); }
+    ~DevBuf() { if (ptr) cudaFree(ptr); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Device status words: [0] status code, [1] detail (column), [2..3] grid barrier count/generation.
+struct rgs_context {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    DevBuf ctl;            // int[8]: status, detail, barrier count, barrier generation, ...
+    DevBuf partials;       // per-CTA partial sketches
+    DevBuf scratch;        // staging for host-pointer calls
+    DevBuf lsbuf;          // Householder factors and vectors of the least-squares engine
+    DevBuf work;           // P = Theta W, certificates
+    int upd_blocks_per_sm = 4;
+    int ls_blocks = 0;     // cooperative grid of the least-squares kernel
+    int precond_kind = 0;
+    int launches = 0;      // kernels launched by the current call
+    std::vector<cudaEvent_t> events;   // pool for per-phase timings
+    ~rgs_context() { for (auto e : events) cudaEventDestroy(e); }
+};
+
+// Accumulates the device time of repeated phases from pairs of events.
+struct PhaseTimer {
+    rgs_context* ctx;
+    bool on;
+    std::vector<std::pair<int, int>> marks[3];   // per phase: (start event, stop event)
+    int next = 0;
+    PhaseTimer(rgs_context* c, bool enabled) : ctx(c), on(enabled) {}
+    int ev() {
+        if (next >= (int)ctx->events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) throw RgsError{RGS_ERR_CUDA, "cudaEventCreate failed"};
+            ctx->events.push_back(e);
+        }
+        return next++;
+    }
+    int start(int phase) {
+        if (!on) return -1;
+        int a = ev();
+        cudaEventRecord(ctx->events[a], ctx->stream);
+        marks[phase].push_back({a, -1});
+        return a;
+    }
+    void stop(int phase) {
+        if (!on) return;
+        int b = ev();
+        cudaEventRecord(ctx->events[b], ctx->stream);
+        marks[phase].back().second = b;
+    }
+    double total_ms(int phase) const {
+        double t = 0.0;
+        for (auto& m : marks[phase]) {
+            float ms = 0.f;
+            if (m.second >= 0 && cudaEventElapsedTime(&ms, ctx->events[m.first], ctx->events[m.second]) == cudaSuccess)
+                t += ms;
+        }
+        return t;
+    }
+};
+
+struct rgs_sketch_obj {
+    rgs_handle h = nullptr;
+    int kind = 0;
+    int64_t n = 0, s = 0;
+    int k = 0;
+    uint64_t seed = 0;
+    DevBuf theta;          // Gaussian: k x n FP64, column-major (ld k)
+    DevBuf signbits;       // SRHT: ceil(n/32) words, bit set => -1
+    DevBuf rows;           // SRHT: k int32 sample rows (ascending)
+};
+
+// ---------------------------------------------------------------- device helpers
+namespace rgsdev {
+
+constexpr int kStatusWord = 0;
+constexpr int kDetailWord = 1;
+constexpr int kBarCount = 2;
+constexpr int kBarGen = 3;
+constexpr int kAbortWord = 4;
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies.
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = (uint32_t)p1;
+        c[2] = n2;
+        c[3] = (uint32_t)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__host__ __device__ inline double u53(uint32_t hi, uint32_t lo) {
+    uint64_t v = (((uint64_t)hi << 32) | lo) >> 11;
+    return ((double)v + 0.5) * 0x1p-53;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, result valid in every thread (fixed order: deterministic).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sm /* NT/32 doubles */) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += sm[i];
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
+// about two seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word
+// and returns false, and every other CTA then leaves at its next barrier.
+__device__ __forceinline__ bool grid_barrier(int* ctl) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile int* vctl = ctl;
+        unsigned* count = reinterpret_cast<unsigned*>(ctl + kBarCount);
+        unsigned* gen = reinterpret_cast<unsigned*>(ctl + kBarGen);
+        unsigned g = *reinterpret_cast<volatile unsigned*>(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long start = clock64();
+            unsigned spins = 0;
+            while (*reinterpret_cast<volatile unsigned*>(gen) == g) {
+                if (vctl[kAbortWord] != 0) { ok = 0; break; }
+                if ((++spins & 255u) == 0 && clock64() - start > 4000000000LL) {
+                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                    atomicExch(ctl + kAbortWord, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+}  // namespace rgsdev
+
+// ---------------------------------------------------------------- launchers (host side)
+// update.cu
+struct UpdateLaunch {
+    int64_t n;
+    int ncols;              // prior basis columns used by the update
+    const void* Q;          // basis (qtype), ld ldq
+    int64_t ldq;
+    int qtype;
+    const double* w;        // input column(s), FP64, ld ldw between columns
+    int64_t ldw;
+    int wcols;              // number of input columns (batched sketches; no update when > 1)
+    const double* wscale;   // optional device scalar multiplying w
+    const double* coef;     // ncols FP64 coefficients (device)
+    void* qout;             // optional stored result column (qtype)
+};
+// Number of partial sketches (per input column) the next update/sketch launch will write.
+int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols);
+int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L,
+                             double* partials, int* nparts, const int* ctl);
+void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols,
+                                double scale, double* Y, int64_t ldy);
+void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed);
+
+// ls.cu: Householder (compact-WY) least-squares engine for the sketched problems.
+struct LSState {
+    int k, mmax;
+    double *V, *T, *TT, *RinvT, *S;
+    double *sbuf, *pbuf, *ys, *yp;
+    double *us, *up, *u2s, *u2p, *z;
+    double *ypart;          // 2 * max_chunks * k
+    double *blk;            // 4 * grid
+    double *sigma, *pnorm, *coef;
+    double *R;
+    int64_t ldr;
+    int max_chunks;
+    int* ctl;
+};
+struct LSStep {
+    int i;                  // reflectors already in the factorisation
+    int append;             // append s_i (reduced from s_part) as column i
+    int solve;              // solve for p and write x to R(:, xcol), coef
+    int xcol;
+    const double* s_part;
+    int s_nparts;
+    double s_scale;
+    const double* p_vec;    // p given directly (scaled by p_scale), or
+    const double* p_part;   // reduced from partials
+    int p_nparts;
+    double p_scale;
+    int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
+    int pnorm_idx;          // where to record ||p||
+};
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, LSState* st);
+void rgs_ls_reset(rgs_context* ctx, const LSState& st);
+void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a);
+int rgs_ls_max_blocks(int num_sms);
+void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
+                             const double* P, double* out2 /* device: delta, delta_tilde */, double* work);

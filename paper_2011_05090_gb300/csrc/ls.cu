@@ -1,0 +1,346 @@
+// Alg. 2 steps 2, 5, 6 on the GPU in FP64: the sketched least-squares problem
+// argmin_y ||S_{i-1} y - p_i|| solved through a Householder QR of S (the solver
+// of the paper's experiments, Sec. 5), kept incrementally in compact-WY form
+//     H_0 H_1 ... H_{i-1} = I - V T V^T,    S_i = (H_0 ... H_{i-1}) [R_S; 0],
+// together with R_S^{-1}.  With that form every phase is a parallel matrix-vector
+// product spread over the whole GPU instead of i dependent reflector applications:
+//   y  = (I - V T^T V^T) [s, p]          (apply the i existing reflectors)
+//   new reflector H_i from y_s(i:k)      (appends s_i, column i of R_S = [y_s(0:i); beta])
+//   x  = R_S^{-1} (H_i y_p)(0:i+1)       (the least-squares solution)
+//   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta.
+// One cooperative launch per column; phases are separated by bounded grid barriers.
+#include "common.cuh"
+
+#include <algorithm>
+
+using namespace rgsdev;
+
+namespace {
+
+constexpr int LT = 256;      // threads per CTA
+constexpr int NW = LT / 32;  // warps per CTA
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// Deterministic total of per-CTA values blk[b*stride + off] (same order in every CTA).
+__device__ double grid_total(const double* blk, int stride, int off, double* sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += LT) v += ldcg(blk + (size_t)b * stride + off);
+    return block_sum<LT>(v, sh);
+}
+
+__global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
+    __shared__ double sh[NW];
+    __shared__ double sc[8];
+    int* ctl = st.ctl;
+    if (ctl[kStatusWord] != 0) return;
+    const int k = st.k, mm = st.mmax, i = a.i;
+    const int nthreads = gridDim.x * LT;
+    const int gtid = blockIdx.x * LT + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = gtid >> 5, nwarps = nthreads >> 5;
+    const bool app = a.append != 0, sol = a.solve != 0;
+
+    // ---- phase 0: reduce the partial sketches into s' and p
+    double ss = 0.0, pp = 0.0;
+    for (int l = gtid; l < k; l += nthreads) {
+        if (app) {
+            double v = 0.0;
+            for (int b = 0; b < a.s_nparts; ++b) v += a.s_part[(size_t)b * k + l];
+            v *= a.s_scale;
+            st.sbuf[l] = v;
+            ss += v * v;
+        }
+        if (sol) {
+            double v;
+            if (a.p_vec) {
+                v = a.p_vec[l];
+            } else {
+                v = 0.0;
+                for (int b = 0; b < a.p_nparts; ++b) v += a.p_part[(size_t)b * k + l];
+            }
+            v *= a.p_scale;
+            st.pbuf[l] = v;
+            pp += v * v;
+        }
+    }
+    ss = block_sum<LT>(ss, sh);
+    pp = block_sum<LT>(pp, sh);
+    if (threadIdx.x == 0) { st.blk[blockIdx.x * 4 + 0] = ss; st.blk[blockIdx.x * 4 + 1] = pp; }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p]
+    const double r = sqrt(grid_total(st.blk, 4, 0, sh));
+    const double pn = sqrt(grid_total(st.blk, 4, 1, sh));
+    double inv_r = 1.0, pmul = 1.0;
+    if (app) {
+        const double pref = st.pnorm[i];
+        if (!isfinite(r)) {
+            if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_NONFINITE); ctl[kDetailWord] = i; }
+            return;
+        }
+        if (!(r > 16.0 * 0x1p-53 * pref)) {
+            if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
+            return;
+        }
+        inv_r = 1.0 / r;
+        if (a.p_lag) pmul = inv_r;
+        if (gtid == 0) {
+            st.R[(size_t)i * st.ldr + i] = r;
+            st.sigma[i] = inv_r;
+        }
+        for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
+    }
+    if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
+    for (int j = gwarp; j < i; j += nwarps) {
+        const double* v = st.V + (size_t)j * k;
+        double ds = 0.0, dp = 0.0;
+        for (int l = j + lane; l < k; l += 32) {
+            const double vv = v[l];
+            if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
+            if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
+        }
+        ds = warp_sum(ds);
+        dp = warp_sum(dp);
+        if (lane == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 2: u2 = T(0:i, 0:i)^T u   (column j of T is its upper part)
+    for (int j = gwarp; j < i; j += nwarps) {
+        const double* t = st.T + (size_t)j * mm;
+        double ds = 0.0, dp = 0.0;
+        for (int l = lane; l <= j; l += 32) {
+            const double tv = t[l];
+            if (app) ds = fma(tv, ldcg(st.us + l), ds);
+            if (sol) dp = fma(tv, ldcg(st.up + l), dp);
+        }
+        ds = warp_sum(ds);
+        dp = warp_sum(dp);
+        if (lane == 0) { st.u2s[j] = ds; st.u2p[j] = dp; }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 3: partial sums of V(:, 0:i) u2 over column chunks
+    // rows needed: all k when appending; only 0..i-1 for a pure solve
+    const int krows = app ? k : i;
+    const int nrb = (krows + LT - 1) / LT;
+    int cj = 8;
+    if (i > 0) cj = std::max(8, (i * nrb + 2 * (int)gridDim.x - 1) / (2 * (int)gridDim.x));
+    int nch = i > 0 ? (i + cj - 1) / cj : 0;
+    if (nch > st.max_chunks) { cj = (i + st.max_chunks - 1) / st.max_chunks; nch = (i + cj - 1) / cj; }
+    for (int item = blockIdx.x; item < nrb * nch; item += gridDim.x) {
+        const int rb = item % nrb, c = item / nrb;
+        const int l = rb * LT + threadIdx.x;
+        const int j0 = c * cj, j1 = min(i, j0 + cj);
+        if (l < krows) {
+            double as = 0.0, ap = 0.0;
+            for (int j = j0; j < j1 && j <= l; ++j) {
+                const double vv = st.V[(size_t)j * k + l];
+                if (app) as = fma(vv, ldcg(st.u2s + j), as);
+                if (sol) ap = fma(vv, ldcg(st.u2p + j), ap);
+            }
+            st.ypart[(size_t)c * k + l] = as;
+            st.ypart[(size_t)(st.max_chunks + c) * k + l] = ap;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 3b: y = [s, p] - V u2; sums for the new reflector
+    double sg = 0.0, cr = 0.0;
+    for (int l = gtid; l < krows; l += nthreads) {
+        double ysl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
+        double ypl = sol ? ldcg(st.pbuf + l) * pmul : 0.0;
+        for (int c = 0; c < nch; ++c) {
+            ysl -= ldcg(st.ypart + (size_t)c * k + l);
+            ypl -= ldcg(st.ypart + (size_t)(st.max_chunks + c) * k + l);
+        }
+        st.ys[l] = ysl;
+        st.yp[l] = ypl;
+        if (app && l > i) { sg = fma(ysl, ysl, sg); cr = fma(ysl, ypl, cr); }
+    }
+    sg = block_sum<LT>(sg, sh);
+    cr = block_sum<LT>(cr, sh);
+    if (threadIdx.x == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
+    if (!grid_barrier(ctl)) return;
+
+    if (!app) {
+        // pure solve: x = R_S^{-1} y(0:i); row j of R_S^{-1} is column j of RinvT
+        for (int j = gwarp; j < i; j += nwarps) {
+            const double* rr = st.RinvT + (size_t)j * mm;
+            double d = 0.0;
+            for (int l = j + lane; l < i; l += 32) d = fma(rr[l], ldcg(st.yp + l), d);
+            d = warp_sum(d);
+            if (lane == 0) {
+                st.R[(size_t)a.xcol * st.ldr + j] = d;
+                st.coef[j] = d * st.sigma[j];
+            }
+        }
+        return;
+    }
+
+    // ---- phase 4: the new reflector H_i, V(:, i), z = V^T v_i, R_S^{-1} column, x
+    const double SG = grid_total(st.blk, 4, 2, sh);
+    const double CR = grid_total(st.blk, 4, 3, sh);
+    if (threadIdx.x == 0) {
+        const double alpha = ldcg(st.ys + i);
+        double beta, tau, vs;
+        if (SG == 0.0) {
+            beta = alpha; tau = 0.0; vs = 0.0;
+        } else {
+            const double nrm = sqrt(alpha * alpha + SG);
+            beta = alpha >= 0.0 ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            vs = 1.0 / (alpha - beta);
+        }
+        sc[0] = beta; sc[1] = tau; sc[2] = vs;
+        sc[3] = sol ? ldcg(st.yp + i) - tau * (ldcg(st.yp + i) + CR * vs) : 0.0;
+    }
+    __syncthreads();
+    const double beta = sc[0], tau = sc[1], vs = sc[2], ypi = sc[3];
+    if (beta == 0.0) {
+        if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
+        return;
+    }
+    for (int l = gtid; l < k; l += nthreads)
+        st.V[(size_t)i * k + l] = l < i ? 0.0 : (l == i ? 1.0 : ldcg(st.ys + l) * vs);
+    if (gtid == 0) {
+        st.T[(size_t)i * mm + i] = tau;
+        st.TT[(size_t)i * mm + i] = tau;
+        st.RinvT[(size_t)i * mm + i] = 1.0 / beta;
+        if (sol) {
+            const double xi = ypi / beta;
+            st.R[(size_t)a.xcol * st.ldr + i] = xi;
+            st.coef[i] = xi * inv_r;
+        }
+    }
+    for (int j = gwarp; j < i; j += nwarps) {
+        const double* v = st.V + (size_t)j * k;
+        double zz = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) zz = fma(v[l], ldcg(st.ys + l), zz);
+        zz = warp_sum(zz);
+        const double* rr = st.RinvT + (size_t)j * mm;     // row j of R_S^{-1}
+        double d1 = 0.0, d2 = 0.0;
+        for (int l = j + lane; l < i; l += 32) {
+            const double rv = rr[l];
+            d1 = fma(rv, ldcg(st.ys + l), d1);
+            if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
+        }
+        d1 = warp_sum(d1);
+        d2 = warp_sum(d2);
+        if (lane == 0) {
+            st.z[j] = v[i] + vs * zz;
+            const double cnew = -d1 / beta;                 // R_S^{-1}(j, i)
+            st.RinvT[(size_t)j * mm + i] = cnew;
+            if (sol) {
+                const double xj = d2 + cnew * ypi;
+                st.R[(size_t)a.xcol * st.ldr + j] = xj;
+                st.coef[j] = xj * st.sigma[j];
+            }
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 5: T(0:i, i) = -tau T(0:i, 0:i) z  (row j of T is column j of TT)
+    for (int j = gwarp; j < i; j += nwarps) {
+        const double* tr = st.TT + (size_t)j * mm;
+        double d = 0.0;
+        for (int l = j + lane; l < i; l += 32) d = fma(tr[l], ldcg(st.z + l), d);
+        d = warp_sum(d);
+        if (lane == 0) {
+            const double t = -tau * d;
+            st.T[(size_t)i * mm + j] = t;
+            st.TT[(size_t)j * mm + i] = t;
+        }
+    }
+}
+
+// Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
+// Block b handles column b: sums of squares of (I - S^T S)(0:m, b) and (P - S R)(:, b).
+__global__ void __launch_bounds__(256) cert_kernel(const double* S, int k, int m, const double* R, int64_t ldr,
+                                                   const double* P, double* work) {
+    __shared__ double sh[8];
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double g2 = 0.0;
+    for (int a = w; a < m; a += 8) {
+        double d = 0.0;
+        for (int l = lane; l < k; l += 32) d = fma(S[(size_t)a * k + l], S[(size_t)b * k + l], d);
+        d = warp_sum(d);
+        const double e = (a == b ? 1.0 : 0.0) - d;
+        g2 += lane == 0 ? e * e : 0.0;
+    }
+    double e2 = 0.0, p2 = 0.0;
+    for (int l = threadIdx.x; l < k; l += 256) {
+        double v = P[(size_t)b * k + l];
+        p2 += v * v;
+        for (int j = 0; j <= b; ++j) v = fma(-S[(size_t)j * k + l], R[(size_t)b * ldr + j], v);
+        e2 += v * v;
+    }
+    g2 = block_sum<256>(g2, sh);
+    e2 = block_sum<256>(e2, sh);
+    p2 = block_sum<256>(p2, sh);
+    if (threadIdx.x == 0) { work[3 * b] = g2; work[3 * b + 1] = e2; work[3 * b + 2] = p2; }
+}
+
+__global__ void cert_final_kernel(const double* work, int m, double* out) {
+    __shared__ double sh[8];
+    double g = 0.0, e = 0.0, p = 0.0;
+    for (int b = threadIdx.x; b < m; b += 256) { g += work[3 * b]; e += work[3 * b + 1]; p += work[3 * b + 2]; }
+    g = block_sum<256>(g, sh);
+    e = block_sum<256>(e, sh);
+    p = block_sum<256>(p, sh);
+    if (threadIdx.x == 0) { out[0] = sqrt(g); out[1] = sqrt(e / p); }
+}
+
+}  // namespace
+
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, LSState* st) {
+    const int max_chunks = std::max(1, (mmax + 7) / 8);
+    size_t n = 0;
+    auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
+    const size_t oV = take((size_t)k * mmax), oT = take((size_t)mmax * mmax), oTT = take((size_t)mmax * mmax),
+                 oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax), osb = take(k), opb = take(k),
+                 oys = take(k), oyp = take(k), ous = take(mmax), oup = take(mmax), ou2s = take(mmax),
+                 ou2p = take(mmax), oz = take(mmax), oyr = take((size_t)2 * max_chunks * k), oblk = take((size_t)4 * grid),
+                 osg = take(mmax + 1), opn = take(mmax + 2), oco = take(mmax + 1);
+    buf.ensure(n * sizeof(double));
+    double* b = buf.as<double>();
+    st->k = k; st->mmax = mmax; st->max_chunks = max_chunks;
+    st->V = b + oV; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
+    st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
+    st->us = b + ous; st->up = b + oup; st->u2s = b + ou2s; st->u2p = b + ou2p; st->z = b + oz;
+    st->ypart = b + oyr; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn; st->coef = b + oco;
+}
+
+// Zero the factorisation (V must be zero above each reflector's diagonal; T, R_S^{-1} upper parts).
+void rgs_ls_reset(rgs_context* ctx, const LSState& st) {
+    RGS_CUDA(cudaMemsetAsync(st.V, 0, sizeof(double) * (size_t)st.k * st.mmax, ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.T, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.TT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.RinvT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.pnorm, 0, sizeof(double) * (size_t)(st.mmax + 2), ctx->stream));
+}
+
+void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
+    LSState s = st;
+    LSStep p = a;
+    void* args[] = {&s, &p};
+    RGS_CUDA(cudaLaunchCooperativeKernel((const void*)ls_kernel, dim3(ctx->ls_blocks), dim3(LT), args, 0, ctx->stream));
+    ctx->launches++;
+}
+
+int rgs_ls_max_blocks(int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ls_kernel, LT, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return num_sms * std::min(per_sm, 2);
+}
+
+void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
+                             const double* P, double* out2, double* work) {
+    cert_kernel<<<m, 256, 0, ctx->stream>>>(S, k, m, R, ldr, P, work);
+    RGS_CUDA(cudaGetLastError());
+    cert_final_kernel<<<1, 256, 0, ctx->stream>>>(work, m, out2);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+}

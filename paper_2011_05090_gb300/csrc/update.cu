@@ -1,0 +1,419 @@
+// Fused RGS step 3 + step 4 (Alg. 2): q'_i = w_i - Q'_{i-1} c, rounded to the
+// storage type and written once, then sketched from the stored values without
+// re-reading them.  The SRHT sketch is applied per tile of 1024 rows: signs,
+// an in-register / warp-shuffle / shared-memory Walsh-Hadamard transform of
+// the tile, and the tile's contribution to each sampled output row
+// (H_s = H_{s/1024} (x) H_1024, so output row a*1024+b gets
+// (-1)^popcount(a & t) * (H_1024 z_t)[b] from tile t).  Per-CTA partial
+// k-vectors are summed later in a fixed order (deterministic).
+#include "common.cuh"
+
+#include <algorithm>
+
+using namespace rgsdev;
+
+namespace {
+
+constexpr int TILE = 1024;
+constexpr int LOG_TILE = 10;
+constexpr int UT = 256;      // threads per CTA, 4 consecutive rows each
+constexpr int UNROLL = 8;    // basis columns loaded ahead
+
+template <typename TQ> struct QIO;
+
+template <> struct QIO<double> {
+    using Acc = double;
+    __device__ static void load4(const double* p, double v[4]) {
+        double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ static void store4(double* p, const double v[4]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+    __device__ static double load1(const double* p) { return __ldg(p); }
+    __device__ static void store1(double* p, double v) { *p = v; }
+    __device__ static double to_storage(double v) { return v; }
+};
+
+template <> struct QIO<float> {
+    using Acc = float;
+    __device__ static void load4(const float* p, float v[4]) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    __device__ static void store4(float* p, const float v[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ static float load1(const float* p) { return __ldg(p); }
+    __device__ static void store1(float* p, float v) { *p = v; }
+    __device__ static float to_storage(float v) { return v; }
+};
+
+template <> struct QIO<__nv_bfloat16> {
+    using Acc = float;
+    __device__ static void load4(const __nv_bfloat16* p, float v[4]) {
+        uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+        __nv_bfloat162 x = *reinterpret_cast<__nv_bfloat162*>(&a.x);
+        __nv_bfloat162 y = *reinterpret_cast<__nv_bfloat162*>(&a.y);
+        float2 fx = __bfloat1622float2(x), fy = __bfloat1622float2(y);
+        v[0] = fx.x; v[1] = fx.y; v[2] = fy.x; v[3] = fy.y;
+    }
+    __device__ static void store4(__nv_bfloat16* p, const float v[4]) {
+        __nv_bfloat162 x = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 y = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 a;
+        a.x = *reinterpret_cast<uint32_t*>(&x);
+        a.y = *reinterpret_cast<uint32_t*>(&y);
+        *reinterpret_cast<uint2*>(p) = a;
+    }
+    __device__ static float load1(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
+    __device__ static void store1(__nv_bfloat16* p, float v) { p[0] = __float2bfloat16_rn(v); }
+    // value actually stored, back in float
+    __device__ static float to_storage(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+};
+
+struct UpdParams {
+    int64_t n;
+    int ncols;
+    const void* Q;
+    int64_t ldq;
+    const double* w;
+    int64_t ldw;
+    const double* wscale;
+    const double* coef;
+    void* qout;
+    const uint32_t* signbits;
+    const int32_t* rows;
+    int k;
+    int ntiles;
+    int vec;
+    double* partials;
+    const int* ctl;
+};
+
+// Walsh-Hadamard transform of the CTA's 1024-element tile.  Element b = 4*tid + e:
+// bits 0-1 in registers, bits 2-6 across the warp, bits 7-9 through shared memory.
+// On return zt[b] holds (H_1024 z)[b] for every b.
+__device__ __forceinline__ void fwht_tile(double z[4], double* zt) {
+    double a0 = z[0] + z[1], a1 = z[0] - z[1], a2 = z[2] + z[3], a3 = z[2] - z[3];
+    z[0] = a0 + a2; z[1] = a1 + a3; z[2] = a0 - a2; z[3] = a1 - a3;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int m = 1 << s;
+        const bool upper = (lane & m) != 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            double o = __shfl_xor_sync(0xffffffffu, z[e], m);
+            z[e] = upper ? (o - z[e]) : (z[e] + o);
+        }
+    }
+    __syncthreads();                               // previous readers of zt are done
+    reinterpret_cast<double2*>(zt)[threadIdx.x * 2] = make_double2(z[0], z[1]);
+    reinterpret_cast<double2*>(zt)[threadIdx.x * 2 + 1] = make_double2(z[2], z[3]);
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int g = threadIdx.x;
+        double v[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v[w] = zt[g + 128 * w];
+#pragma unroll
+        for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+            for (int a = 0; a < 8; a += 2 * h)
+#pragma unroll
+                for (int b = a; b < a + h; ++b) {
+                    double u = v[b], t = v[b + h];
+                    v[b] = u + t;
+                    v[b + h] = u - t;
+                }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) zt[g + 128 * w] = v[w];
+    }
+    __syncthreads();
+}
+
+template <typename TQ, bool SRHT>
+__global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
+    using IO = QIO<TQ>;
+    using Acc = typename IO::Acc;
+    extern __shared__ __align__(16) double smem[];
+    double* zt = smem;                                   // TILE
+    double* part = zt + TILE;                            // k
+    int32_t* srow = reinterpret_cast<int32_t*>(part + (SRHT ? p.k : 0));     // k
+    Acc* sc = reinterpret_cast<Acc*>(srow + (SRHT ? ((p.k + 3) & ~3) : 0));   // ncols
+
+    if (p.ctl != nullptr && p.ctl[kStatusWord] != 0) return;   // an earlier step failed or broke down
+    const int col = blockIdx.y;
+    const double* w = p.w + (int64_t)col * p.ldw;
+    const double wmul = p.wscale ? *p.wscale : 1.0;
+    const TQ* Q = reinterpret_cast<const TQ*>(p.Q);
+    TQ* qout = reinterpret_cast<TQ*>(p.qout);
+    const int64_t n = p.n;
+
+    for (int j = threadIdx.x; j < p.ncols; j += UT) sc[j] = (Acc)p.coef[j];
+    if (SRHT)
+        for (int j = threadIdx.x; j < p.k; j += UT) { srow[j] = p.rows[j]; part[j] = 0.0; }
+    __syncthreads();
+
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const int64_t r0 = (int64_t)tile * TILE + threadIdx.x * 4;
+        const bool full = p.vec && (r0 + 4 <= n);
+        Acc acc[4];
+        if (full) {
+            double2 a = __ldg(reinterpret_cast<const double2*>(w + r0));
+            double2 b = __ldg(reinterpret_cast<const double2*>(w + r0 + 2));
+            acc[0] = (Acc)(a.x * wmul); acc[1] = (Acc)(a.y * wmul);
+            acc[2] = (Acc)(b.x * wmul); acc[3] = (Acc)(b.y * wmul);
+            int j = 0;
+            for (; j + UNROLL <= p.ncols; j += UNROLL) {
+                Acc q[UNROLL][4];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) IO::load4(Q + (int64_t)(j + u) * p.ldq + r0, q[u]);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const Acc c = sc[j + u];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[e] = fma(-c, q[u][e], acc[e]);
+                }
+            }
+            for (; j < p.ncols; ++j) {
+                Acc q[4];
+                IO::load4(Q + (int64_t)j * p.ldq + r0, q);
+                const Acc c = sc[j];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] = fma(-c, q[e], acc[e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] = (r0 + e < n) ? (Acc)(w[r0 + e] * wmul) : (Acc)0;
+            for (int j = 0; j < p.ncols; ++j) {
+                const Acc c = sc[j];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (r0 + e < n) acc[e] = fma(-c, IO::load1(Q + (int64_t)j * p.ldq + r0 + e), acc[e]);
+            }
+        }
+        double z[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            acc[e] = IO::to_storage(acc[e]);
+            z[e] = (r0 + e < n) ? (double)acc[e] : 0.0;
+        }
+        if (qout != nullptr) {
+            if (full) {
+                IO::store4(qout + r0, acc);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (r0 + e < n) IO::store1(qout + r0 + e, acc[e]);
+            }
+        }
+        if (SRHT) {
+            if (r0 < n) {
+                const uint32_t bits = __ldg(p.signbits + (r0 >> 5)) >> (r0 & 31);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((bits >> e) & 1u) z[e] = -z[e];
+            }
+            fwht_tile(z, zt);
+            for (int j = threadIdx.x; j < p.k; j += UT) {
+                const int r = srow[j];
+                const double v = zt[r & (TILE - 1)];
+                part[j] += (__popc((r >> LOG_TILE) & tile) & 1) ? -v : v;
+            }
+        }
+    }
+    if (SRHT) {
+        __syncthreads();
+        double* out = p.partials + ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
+        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = part[j];
+    }
+}
+
+// Gaussian sketch partials: partial_b = Theta[:, rows of block b] x[rows of block b].
+template <typename TX>
+__global__ void __launch_bounds__(256) gauss_sketch_kernel(const double* __restrict__ theta, int k, int64_t n,
+                                                           const TX* __restrict__ x, int64_t ldx,
+                                                           double* __restrict__ partials, const int* ctl) {
+    constexpr int CH = 256;
+    __shared__ double xs[CH];
+    if (ctl != nullptr && ctl[kStatusWord] != 0) return;
+    const int col = blockIdx.y;
+    x += (int64_t)col * ldx;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per;
+    const int64_t c1 = min(n, c0 + per);
+    double* out = partials + ((int64_t)col * gridDim.x + blockIdx.x) * k;
+    for (int lb = 0; lb < k; lb += 1024) {           // rows lb + threadIdx.x + 256 t of Theta
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t cb = c0; cb < c1; cb += CH) {
+            const int len = (int)min((int64_t)CH, c1 - cb);
+            __syncthreads();
+            if (threadIdx.x < len) {
+                if constexpr (sizeof(TX) == 2) xs[threadIdx.x] = (double)__bfloat162float(x[cb + threadIdx.x]);
+                else xs[threadIdx.x] = (double)x[cb + threadIdx.x];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int l = lb + threadIdx.x + 256 * t;
+                if (l < k) {
+                    const double* th = theta + cb * k + l;
+                    double a = acc[t];
+                    for (int c = 0; c < len; ++c) a = fma(__ldg(th + (int64_t)c * k), xs[c], a);
+                    acc[t] = a;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int l = lb + threadIdx.x + 256 * t;
+            if (l < k) out[l] = acc[t];
+        }
+    }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partials, int nparts, int k, double scale,
+                                       double* __restrict__ Y, int64_t ldy) {
+    const int col = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= k) return;
+    const double* src = partials + (int64_t)col * nparts * k + l;
+    double v = 0.0;
+    for (int b = 0; b < nparts; ++b) v += src[(int64_t)b * k];
+    Y[(int64_t)col * ldy + l] = v * scale;
+}
+
+__global__ void gaussian_theta_kernel(double* theta, int k, int64_t n, uint32_t key0, uint32_t key1) {
+    const int pairs = (k + 1) / 2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)pairs * n) return;
+    const int64_t c = idx / pairs;
+    const int pr = (int)(idx - c * pairs);
+    uint32_t ctr[4] = {(uint32_t)c, (uint32_t)pr, 0u, 0u};
+    philox4x32_10(ctr, key0, key1);
+    const double u1 = u53(ctr[0], ctr[1]), u2 = u53(ctr[2], ctr[3]);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincos(2.0 * M_PI * u2, &sn, &cs);
+    const double scale = 1.0 / sqrt((double)k);
+    theta[c * k + 2 * pr] = rad * cs * scale;
+    if (2 * pr + 1 < k) theta[c * k + 2 * pr + 1] = rad * sn * scale;
+}
+
+template <typename TQ, bool SRHT>
+void launch_update_t(rgs_context* ctx, const UpdParams& p, int gx, int gy, size_t smem) {
+    auto kern = update_sketch_kernel<TQ, SRHT>;
+    if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(gx, gy), UT, smem, ctx->stream>>>(p);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+template <typename TX>
+void launch_gauss_t(rgs_context* ctx, const double* theta, int k, int64_t n, const void* x, int64_t ldx, int cols,
+                    double* partials, int gx, const int* ctl) {
+    gauss_sketch_kernel<TX><<<dim3(gx, cols), 256, 0, ctx->stream>>>(theta, k, n, reinterpret_cast<const TX*>(x),
+                                                                       ldx, partials, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols) {
+    const int ntiles = (int)((n + TILE - 1) / TILE);
+    if (sk->kind != RGS_SKETCH_SRHT) return std::max(1, std::min((int)((n + 255) / 256), ctx->num_sms * 2));
+    const int slots = ctx->num_sms * ctx->upd_blocks_per_sm;
+    if (wcols <= 1) return std::max(1, std::min(ntiles, slots));
+    return std::max(1, std::min(ntiles, std::max(4, 8 * slots / wcols)));
+}
+
+// Launch the fused update (optional) + sketch.  Writes partial sketches for each
+// input column to `partials` ([col][nparts][k]) and returns nparts through *nparts.
+int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L, double* partials,
+                             int* nparts, const int* ctl) {
+    const int64_t n = L.n;
+    const int ntiles = (int)((n + TILE - 1) / TILE);
+    const size_t esz = L.qtype == RGS_F64 ? 8 : (L.qtype == RGS_F32 ? 4 : 2);
+    UpdParams p{};
+    p.n = n;
+    p.ncols = L.ncols;
+    p.Q = L.Q;
+    p.ldq = L.ldq;
+    p.w = L.w;
+    p.ldw = L.ldw;
+    p.wscale = L.wscale;
+    p.coef = L.coef;
+    p.qout = L.qout;
+    p.ntiles = ntiles;
+    p.ctl = ctl;
+    p.k = sk->k;
+    // vector path: every 4-row group of w, Q and q_out starts on a 16-byte (bf16: 8-byte) boundary
+    bool vec = aligned16(L.w) && (L.wcols == 1 || L.ldw % 2 == 0);
+    if (L.ncols > 0) vec = vec && aligned16(L.Q) && (L.ldq % 4 == 0);
+    if (L.qout) vec = vec && ((uintptr_t)L.qout % (4 * esz) == 0 || aligned16(L.qout)) && (L.ldq % 4 == 0);
+    p.vec = vec ? 1 : 0;
+    const bool srht = sk->kind == RGS_SKETCH_SRHT;
+    const int gx = srht ? rgs_update_nparts(ctx, sk, n, L.wcols)
+                        : std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+    if (srht) {
+        p.signbits = sk->signbits.as<uint32_t>();
+        p.rows = sk->rows.as<int32_t>();
+        p.partials = partials;
+    }
+    size_t accsz = (L.qtype == RGS_F64) ? 8 : 4;
+    size_t smem = TILE * 8 + (srht ? (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 : 0) + (size_t)L.ncols * accsz + 16;
+    if (L.ncols > 0 || L.qout || srht) {
+        const int gy = L.wcols;
+        if (srht) {
+            switch (L.qtype) {
+                case RGS_F64: launch_update_t<double, true>(ctx, p, gx, gy, smem); break;
+                case RGS_F32: launch_update_t<float, true>(ctx, p, gx, gy, smem); break;
+                default: launch_update_t<__nv_bfloat16, true>(ctx, p, gx, gy, smem); break;
+            }
+        } else {
+            switch (L.qtype) {
+                case RGS_F64: launch_update_t<double, false>(ctx, p, gx, gy, smem); break;
+                case RGS_F32: launch_update_t<float, false>(ctx, p, gx, gy, smem); break;
+                default: launch_update_t<__nv_bfloat16, false>(ctx, p, gx, gy, smem); break;
+            }
+        }
+    }
+    if (srht) {
+        *nparts = gx;
+        return gx;
+    }
+    // Gaussian: sketch the stored column (or the input columns when nothing is stored)
+    const int gg = rgs_update_nparts(ctx, sk, n, L.wcols);
+    if (L.qout) {
+        switch (L.qtype) {
+            case RGS_F64: launch_gauss_t<double>(ctx, sk->theta.as<double>(), sk->k, n, L.qout, L.ldq, 1, partials, gg, ctl); break;
+            case RGS_F32: launch_gauss_t<float>(ctx, sk->theta.as<double>(), sk->k, n, L.qout, L.ldq, 1, partials, gg, ctl); break;
+            default: launch_gauss_t<__nv_bfloat16>(ctx, sk->theta.as<double>(), sk->k, n, L.qout, L.ldq, 1, partials, gg, ctl); break;
+        }
+    } else {
+        launch_gauss_t<double>(ctx, sk->theta.as<double>(), sk->k, n, L.w, L.ldw, L.wcols, partials, gg, ctl);
+    }
+    *nparts = gg;
+    return gg;
+}
+
+void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols, double scale,
+                                double* Y, int64_t ldy) {
+    reduce_partials_kernel<<<dim3((k + 255) / 256, ncols), 256, 0, ctx->stream>>>(partials, nparts, k, scale, Y, ldy);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed) {
+    const int64_t total = (int64_t)((k + 1) / 2) * n;
+    const int64_t blocks = (total + 255) / 256;
+    gaussian_theta_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(theta, k, n, (uint32_t)seed, (uint32_t)(seed >> 32));
+    RGS_CUDA(cudaGetLastError());
+}

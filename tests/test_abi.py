@@ -1,0 +1,46 @@
+"""The C-ABI library loads and exports every entry point its header declares (CPU only)."""
+import os
+import re
+
+import pytest
+
+import paper_2011_05090_gb300 as rgs
+from paper_2011_05090_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "librgs.h")).read()
+    return sorted(set(re.findall(r"^RGS_API\s+[\w\s\*]+?\b((?:rgs|rgmres|cgs2)_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return rgs.load()
+
+
+def test_header_declares_the_documented_api():
+    names = _declared()
+    for must in ("rgs_qr", "rgs_arnoldi_step", "rgmres_solve", "rgmres_solve_batched", "rgmres_set_preconditioner"):
+        assert must in names
+    assert set(names) == set(rgs.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_only_the_c_api_is_exported():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", rgs.LIB_PATH], capture_output=True, text=True).stdout
+    text_syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert text_syms == set(_declared())
+
+
+def test_status_strings(lib):
+    assert lib.rgs_status_string(rgs.RGS_OK) == b"ok"
+    assert b"breakdown" in lib.rgs_status_string(rgs.RGS_ERR_BREAKDOWN)
+    assert lib.rgs_status_string(99) == b"unknown status"

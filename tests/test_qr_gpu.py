@@ -1,0 +1,188 @@
+"""GPU parity of the sketch and of RGS QR (Alg. 2) against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2011_05090_gb300 as rgs
+import synth
+from oracle import c_oracle
+from oracle import rgs as orgs
+from oracle.sketch import Sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2011_05090_gb300 import build
+    build.build()
+    return rgs.rgs_create()
+
+
+def to_gpu(a):
+    """numpy (n, m) -> column-major CUDA tensor of shape (n, m)."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().T
+
+
+def run_qr(h, sk, W, qdtype=torch.float64, qscale=False):
+    n, m = W.shape
+    Q = rgs.colmajor_empty(n, m, dtype=qdtype)
+    R = rgs.colmajor_empty(m, m)
+    S = rgs.colmajor_empty(sk.k, m)
+    qs = torch.empty(m, dtype=torch.float64, device="cuda") if qscale else None
+    info = rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, S=S)
+    torch.cuda.synchronize()
+    out = {"Q": Q.double().cpu().numpy(), "R": R.cpu().numpy(), "S": S.cpu().numpy(), "info": info}
+    if qscale:
+        out["qscale"] = qs.cpu().numpy()
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# ------------------------------------------------------------------ sketch
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+@pytest.mark.parametrize("n,k", [(1, 1), (5, 3), (1000, 64), (1024, 300), (1025, 64), (4099, 7), (70001, 300)])
+def test_sketch_apply_matches_oracle(h, kind, n, k):
+    X = np.random.default_rng(n + k).standard_normal((n, 3))
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 17)
+    Y = rgs.rgs_sketch_apply(h, sk, to_gpu(X)).cpu().numpy()
+    ref = Sketch(kind, n, k, 17).apply(X)
+    assert np.abs(Y - ref).max() <= 1e-13 * np.linalg.norm(X, axis=0).max()
+
+
+def test_sketch_tables_match_oracle_definition(h):
+    # the SRHT applied to unit vectors reproduces P H D column by column
+    n, k = 300, 40
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 5)
+    Y = rgs.rgs_sketch_apply(h, sk, to_gpu(np.eye(n))).cpu().numpy()
+    assert np.array_equal(Y, Sketch("srht", n, k, 5).dense())
+
+
+# ------------------------------------------------------------------ QR, FP64
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+@pytest.mark.parametrize("n,m,k", [(1000, 10, 40), (4099, 33, 100), (70001, 40, 160), (2048, 64, 64)])
+def test_qr_fp64_matches_oracle(h, kind, n, m, k):
+    A = synth.gdw_matrix(n, m, 1e2, n + m).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 11)
+    g = run_qr(h, sk, to_gpu(A))
+    ref = orgs.rgs_qr(A, Sketch(kind, n, k, 11))
+    assert rel(g["R"], ref.R) <= 1e-12
+    assert rel(g["Q"], ref.Q) <= 1e-12
+    assert rel(g["S"], ref.S) <= 1e-12
+    assert np.allclose(np.tril(g["R"], -1), 0.0, atol=0) and np.all(np.diag(g["R"]) > 0)
+    assert g["info"]["delta"] <= 1e-12 and g["info"]["delta_tilde"] <= 1e-13
+    assert rel(A, g["Q"] @ g["R"]) <= 1e-13
+
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_qr_fp64_ill_conditioned_within_oracle_floor(h, kind):
+    # two correct FP64 computations differ by ~cond * u in R: the floor is 10x the A-B oracle gap
+    n, m, k = 6000, 40, 120
+    A = synth.gdw_matrix(n, m, 1e8, 4).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 2)
+    g = run_qr(h, sk, to_gpu(A))
+    ra = orgs.rgs_qr(A, Sketch(kind, n, k, 2))
+    rb = c_oracle.rgs_qr(A, c_oracle.CSketch(kind, n, k, 2))
+    floor = max(1e-12, 10 * rel(rb.R, ra.R))
+    assert rel(g["R"], ra.R) <= floor
+    assert rel(A, g["Q"] @ g["R"]) <= 1e-13
+
+
+def test_qr_config_c1_full_size(h):
+    """n = 10,000, m = 100, D from 1 to 1e-8, Gaussian k = 300, seed 0, FP64."""
+    n, m, k = 10000, 100, 300
+    A = synth.gdw_matrix(n, m, 1e8, 0).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, k, 0)
+    g = run_qr(h, sk, to_gpu(A))
+    ra = orgs.rgs_qr(A, Sketch("gaussian", n, k, 0))
+    rb = c_oracle.rgs_qr(A, c_oracle.CSketch("gaussian", n, k, 0))
+    err = rel(g["R"], ra.R)
+    print(f"C1: ||R-R_or||/||R_or|| = {err:.3e} (oracle A-B {rel(rb.R, ra.R):.3e}), "
+          f"Delta_m = {g['info']['delta']:.3e}, ||A-QR||/||A|| = {rel(A, g['Q'] @ g['R']):.3e}")
+    assert err <= max(1e-12, 10 * rel(rb.R, ra.R))
+    assert rel(A, g["Q"] @ g["R"]) <= 1e-13
+    assert abs(g["info"]["delta"] - ra.delta) <= 10 * max(ra.delta, 1e-15)
+
+
+def test_qscale_mode_returns_exact_basis(h):
+    n, m, k = 3000, 20, 60
+    A = synth.gdw_matrix(n, m, 1e3, 9).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 1)
+    a = run_qr(h, sk, to_gpu(A), qscale=True)
+    b = run_qr(h, sk, to_gpu(A))
+    assert np.array_equal(a["R"], b["R"])
+    assert np.allclose(a["Q"] * a["qscale"][None, :], b["Q"], rtol=1e-15, atol=0)
+    assert np.allclose(a["qscale"], 1.0 / np.diag(a["R"]), rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------ QR, reduced storage precision
+@pytest.mark.parametrize("qdtype,storage", [(torch.float32, "f32"), (torch.bfloat16, "bf16")])
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_qr_reduced_precision_within_emulated_oracle(h, qdtype, storage, kind):
+    n, m, k = 20000, 40, 120
+    A = synth.gdw_matrix(n, m, 1e6, 3).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 8)
+    g = run_qr(h, sk, to_gpu(A), qdtype=qdtype, qscale=True)
+    Qg = g["Q"] * g["qscale"][None, :]
+    emu = orgs.rgs_qr(A, Sketch(kind, n, k, 8), storage=storage)
+    exact = orgs.rgs_qr(A, Sketch(kind, n, k, 8))
+    e_gpu, e_emu = rel(A, Qg @ g["R"]), rel(A, emu.Q @ emu.R)
+    r_gpu, r_emu = rel(g["R"], exact.R), rel(emu.R, exact.R)
+    print(f"{storage}/{kind}: ||A-QR||/||A|| gpu {e_gpu:.3e} emulated {e_emu:.3e}; "
+          f"||R-R_fp64||/||R_fp64|| gpu {r_gpu:.3e} emulated {r_emu:.3e}; cond(Q) {np.linalg.cond(Qg):.3f}")
+    assert e_gpu <= 10 * e_emu
+    assert r_gpu <= 10 * r_emu
+    assert np.linalg.cond(Qg) <= 10 * np.linalg.cond(emu.Q)
+
+
+# ------------------------------------------------------------------ status, modes, edge cases
+def test_breakdown_reported_with_column(h):
+    n, m, k = 2000, 6, 30
+    A = synth.gdw_matrix(n, m, 10.0, 5).numpy().T.copy()
+    A[:, 4] = 2.0 * A[:, 1] - A[:, 0]
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, k, 3)
+    with pytest.raises(rgs.RgsError) as e:
+        run_qr(h, sk, to_gpu(A))
+    assert e.value.status == rgs.RGS_ERR_BREAKDOWN
+    assert e.value.info["breakdown_col"] == 4
+    # the handle stays usable afterwards
+    A[:, 4] = np.random.default_rng(0).standard_normal(n)
+    run_qr(h, sk, to_gpu(A))
+
+
+def test_host_pointers_match_device_path(h):
+    n, m, k = 5000, 16, 48
+    A = synth.gdw_matrix(n, m, 1e4, 6).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 4)
+    d = run_qr(h, sk, to_gpu(A))
+    Wh = torch.from_numpy(A.T.copy()).pin_memory().T
+    Qh = rgs.colmajor_empty(n, m, pin=True)
+    Rh = rgs.colmajor_empty(m, m, pin=True)
+    rgs.rgs_qr(h, sk, Wh, Qh, Rh)
+    assert np.array_equal(Rh.numpy(), d["R"]) and np.array_equal(Qh.numpy(), d["Q"])
+
+
+def test_deterministic_reruns(h):
+    n, m, k = 9000, 30, 90
+    A = to_gpu(synth.gdw_matrix(n, m, 1e5, 7).numpy().T.copy())
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 6)
+    a, b = run_qr(h, sk, A, torch.float32), run_qr(h, sk, A, torch.float32)
+    assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["Q"], b["Q"])
+
+
+def test_invalid_arguments_rejected(h):
+    n, m = 500, 10
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, 8, 1)           # k < m
+    W = rgs.colmajor_empty(n, m)
+    with pytest.raises(rgs.RgsError) as e:
+        rgs.rgs_qr(h, sk, W, rgs.colmajor_empty(n, m), rgs.colmajor_empty(m, m))
+    assert e.value.status == rgs.RGS_ERR_INVALID_ARG
+    with pytest.raises(rgs.RgsError) as e:
+        rgs.rgs_sketch_create(h, "srht", 100, 129, 1)            # k > s = 128
+    assert e.value.status == rgs.RGS_ERR_INVALID_ARG
