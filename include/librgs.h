@@ -91,19 +91,23 @@ RGS_API rgs_status rgs_sketch_apply(rgs_handle h, rgs_sketch s, int32_t ncols, c
  * Theta Q orthonormal.  Step 2 uses a Householder QR of S_{i-1} (Sec. 5),
  * step 3 runs in the storage precision qtype (FP64, or FP32 accumulation for
  * RGS_F32 / RGS_BF16 storage: the working precision u_crs), steps 1, 4-8 run
- * in FP64 (u_fine).
+ * in FP64 (u_fine).  With FP32 / BF16 storage the SRHT's Walsh-Hadamard sums
+ * use double-float arithmetic (about 2^-48 relative error, against 2^-24 for
+ * u_crs) unless RGS_QR_FP64_SKETCH is set; everything after them is FP64.
  *   Q      n x m in qtype, ldq >= n.  If qscale is non-NULL, Q receives the
  *          unnormalised q'_i and qscale[i] = 1/r_ii (FP64), so the basis is
  *          Q diag(qscale) exactly (the Step 7 division is never rounded to
  *          qtype).  If qscale is NULL, Q is scaled in place at the end.
  *   R      m x m, ldr >= m (strictly lower part set to 0).
  *   S      optional (NULL): k x m, lds >= k, receives S = Theta Q (FP64).
- *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings.
+ *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings;
+ *          RGS_QR_FP64_SKETCH: FP64 transform sums in every storage mode.
  *   info   optional host struct: step-8 certificates and breakdown column.
  * W, Q, R, S, qscale may be all device or all host pointers.  Returns
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
 #define RGS_QR_NO_CERTIFICATES 1
 #define RGS_QR_TIMINGS 2         /* bit 1: time each phase with CUDA events (fills the *_ms fields) */
+#define RGS_QR_FP64_SKETCH 4     /* bit 2: FP64 Walsh-Hadamard sums also for FP32/BF16 storage */
 typedef struct {
     double delta;          /* Delta_m  = ||I - S^T S||_F            (Alg. 2 step 8) */
     double delta_tilde;    /* Delta~_m = ||P - S R||_F / ||P||_F    (Alg. 2 step 8) */

@@ -32,6 +32,7 @@ RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
 RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
 RGS_QR_NO_CERTIFICATES = 1
 RGS_QR_TIMINGS = 2
+RGS_QR_FP64_SKETCH = 4
 RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
 
 _DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF16}

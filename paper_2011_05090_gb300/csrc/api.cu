@@ -77,7 +77,7 @@ void reset_ctl(rgs_context* ctx) {
 
 // Y (k x ncols) = Theta X, in column batches whose partial sketches fit a fixed budget.
 void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const double* X, int64_t ldx, double* Y,
-                  int64_t ldy) {
+                  int64_t ldy, bool df = false) {
     const int k = sk->k;
     const double scale = sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)k) : 1.0;
     const size_t budget = (size_t)256 << 20;
@@ -94,6 +94,7 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
         L.w = X + (int64_t)c0 * ldx;
         L.ldw = ldx;
         L.wcols = nc;
+        L.df_sketch = df ? 1 : 0;
         int nparts = 0;
         rgs_launch_update_sketch(ctx, sk, L, ctx->partials.as<double>(), &nparts, nullptr);
         rgs_launch_reduce_partials(ctx, ctx->partials.as<double>(), nparts, k, nc, scale, Y + (int64_t)c0 * ldy, ldy);
@@ -279,7 +280,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
 
         // workspaces: Householder engine, P = Theta W, partial sketches, certificates
         LSState ls{};
-        rgs_ls_alloc(h->lsbuf, k, m, h->ls_blocks, &ls);
+        rgs_ls_alloc(h->lsbuf, k, m, h->ls_blocks, h->num_sms * h->upd_blocks_per_sm, &ls);
         ls.ctl = h->ctl.as<int>();
         ls.R = dR;
         ls.ldr = dldr;
@@ -298,7 +299,8 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
 
         // step 1 for all columns at once: P = Theta W (one pass over W)
         timer.start(0);
-        sketch_block(h, s, m, dW, dldw, P, k);
+        const bool df = qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH);
+        sketch_block(h, s, m, dW, dldw, P, k, df);
         timer.stop(0);
         h->partials.ensure(sizeof(double) * (size_t)np1 * k);
 
@@ -315,6 +317,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             L.wcols = 1;
             L.coef = ls.coef;
             L.qout = static_cast<char*>(dQ) + esz * (size_t)i * dldq;
+            L.df_sketch = df ? 1 : 0;
             int nparts = 0;
             timer.start(1);
             rgs_launch_update_sketch(h, s, L, h->partials.as<double>(), &nparts, ls.ctl);   // steps 3, 4

@@ -128,6 +128,7 @@ constexpr int kDetailWord = 1;
 constexpr int kBarCount = 2;
 constexpr int kBarGen = 3;
 constexpr int kAbortWord = 4;
+constexpr int kStopWord = 5;     // an Arnoldi cycle ended early (convergence or happy breakdown)
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies.
 __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -225,6 +226,7 @@ struct UpdateLaunch {
     const double* wscale;   // optional device scalar multiplying w
     const double* coef;     // ncols FP64 coefficients (device)
     void* qout;             // optional stored result column (qtype)
+    int df_sketch;          // SRHT transform in double-float (FP32 pairs) instead of FP64
 };
 // Number of partial sketches (per input column) the next update/sketch launch will write.
 int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols);
@@ -239,13 +241,15 @@ struct LSState {
     int k, mmax;
     double *V, *T, *TT, *RinvT, *S;
     double *sbuf, *pbuf, *ys, *yp;
-    double *us, *up, *u2s, *u2p, *z;
-    double *ypart;          // 2 * max_chunks * k
+    double *us, *up, *u2s, *u2p;
+    double *zp, *d1, *d2;   // per-column dots of phase 4
+    double *ypart;          // 2 * NCH_MAX * k
+    double *red;            // first-level sums of partial sketches
     double *blk;            // 4 * grid
     double *sigma, *pnorm, *coef;
     double *R;
     int64_t ldr;
-    int max_chunks;
+    int max_parts;
     int* ctl;
 };
 struct LSStep {
@@ -263,7 +267,7 @@ struct LSStep {
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
     int pnorm_idx;          // where to record ||p||
 };
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, LSState* st);
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a);
 int rgs_ls_max_blocks(int num_sms);

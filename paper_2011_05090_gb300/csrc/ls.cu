@@ -17,8 +17,10 @@ using namespace rgsdev;
 
 namespace {
 
-constexpr int LT = 256;      // threads per CTA
-constexpr int NW = LT / 32;  // warps per CTA
+constexpr int LT = 512;        // threads per CTA (one CTA per SM)
+constexpr int NW = LT / 32;    // warps per CTA
+constexpr int GS = 32;         // partial sketches summed per warp in the first reduction level
+constexpr int NCH_MAX = 16;    // column chunks of the V u2 product
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
@@ -29,47 +31,67 @@ __device__ double grid_total(const double* blk, int stride, int off, double* sh)
     return block_sum<LT>(v, sh);
 }
 
-__global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
+__global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     __shared__ double sh[NW];
     __shared__ double sc[8];
     int* ctl = st.ctl;
-    if (ctl[kStatusWord] != 0) return;
+    if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
     const int k = st.k, mm = st.mmax, i = a.i;
-    const int nthreads = gridDim.x * LT;
-    const int gtid = blockIdx.x * LT + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nthreads = G * LT, gtid = blockIdx.x * LT + tid;
     const int gwarp = gtid >> 5, nwarps = nthreads >> 5;
     const bool app = a.append != 0, sol = a.solve != 0;
+    const bool p_parts = sol && a.p_vec == nullptr;
 
-    // ---- phase 0: reduce the partial sketches into s' and p
+    // ---- phase 0a: first reduction level of the partial sketches (warp per 32 rows x GS partials)
+    const int nseg = (k + 31) / 32;
+    const int sgroups = app ? (a.s_nparts + GS - 1) / GS : 0;
+    const int pgroups = p_parts ? (a.p_nparts + GS - 1) / GS : 0;
+    for (int it = gwarp; it < nseg * (sgroups + pgroups); it += nwarps) {
+        const int seg = it % nseg, g = it / nseg;
+        const bool is_s = g < sgroups;
+        const int gg = is_s ? g : g - sgroups;
+        const double* src = is_s ? a.s_part : a.p_part;
+        const int np = is_s ? a.s_nparts : a.p_nparts;
+        const int l = seg * 32 + lane;
+        if (l < k) {
+            const int b0 = gg * GS, b1 = min(np, b0 + GS);
+            double v = 0.0;
+#pragma unroll 8
+            for (int b = b0; b < b1; ++b) v += src[(size_t)b * k + l];
+            st.red[(size_t)g * k + l] = v;
+        }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 0b: second level (warp per row, lanes over groups): s', p and their norms
     double ss = 0.0, pp = 0.0;
-    for (int l = gtid; l < k; l += nthreads) {
+    for (int l = gwarp; l < k; l += nwarps) {
         if (app) {
             double v = 0.0;
-            for (int b = 0; b < a.s_nparts; ++b) v += a.s_part[(size_t)b * k + l];
-            v *= a.s_scale;
-            st.sbuf[l] = v;
-            ss += v * v;
+            for (int g = lane; g < sgroups; g += 32) v += ldcg(st.red + (size_t)g * k + l);
+            v = warp_sum(v) * a.s_scale;
+            if (lane == 0) { st.sbuf[l] = v; ss = fma(v, v, ss); }
         }
         if (sol) {
-            double v;
-            if (a.p_vec) {
-                v = a.p_vec[l];
+            double v = 0.0;
+            if (p_parts) {
+                for (int g = lane; g < pgroups; g += 32) v += ldcg(st.red + (size_t)(sgroups + g) * k + l);
+                v = warp_sum(v);
             } else {
-                v = 0.0;
-                for (int b = 0; b < a.p_nparts; ++b) v += a.p_part[(size_t)b * k + l];
+                v = a.p_vec[l];
             }
             v *= a.p_scale;
-            st.pbuf[l] = v;
-            pp += v * v;
+            if (lane == 0) { st.pbuf[l] = v; pp = fma(v, v, pp); }
         }
     }
     ss = block_sum<LT>(ss, sh);
     pp = block_sum<LT>(pp, sh);
-    if (threadIdx.x == 0) { st.blk[blockIdx.x * 4 + 0] = ss; st.blk[blockIdx.x * 4 + 1] = pp; }
+    if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = ss; st.blk[blockIdx.x * 4 + 1] = pp; }
     if (!grid_barrier(ctl)) return;
 
-    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p]
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (CTA per column)
     const double r = sqrt(grid_total(st.blk, 4, 0, sh));
     const double pn = sqrt(grid_total(st.blk, 4, 1, sh));
     double inv_r = 1.0, pmul = 1.0;
@@ -92,21 +114,21 @@ __global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
         for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
-    for (int j = gwarp; j < i; j += nwarps) {
+    for (int j = blockIdx.x; j < i; j += G) {
         const double* v = st.V + (size_t)j * k;
         double ds = 0.0, dp = 0.0;
-        for (int l = j + lane; l < k; l += 32) {
+        for (int l = j + tid; l < k; l += LT) {
             const double vv = v[l];
             if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
             if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
         }
-        ds = warp_sum(ds);
-        dp = warp_sum(dp);
-        if (lane == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
+        ds = block_sum<LT>(ds, sh);
+        dp = block_sum<LT>(dp, sh);
+        if (tid == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
     }
     if (!grid_barrier(ctl)) return;
 
-    // ---- phase 2: u2 = T(0:i, 0:i)^T u   (column j of T is its upper part)
+    // ---- phase 2: u2 = T(0:i, 0:i)^T u   (warp per column of T)
     for (int j = gwarp; j < i; j += nwarps) {
         const double* t = st.T + (size_t)j * mm;
         double ds = 0.0, dp = 0.0;
@@ -121,47 +143,41 @@ __global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
     }
     if (!grid_barrier(ctl)) return;
 
-    // ---- phase 3: partial sums of V(:, 0:i) u2 over column chunks
-    // rows needed: all k when appending; only 0..i-1 for a pure solve
-    const int krows = app ? k : i;
+    // ---- phase 3: partial sums of V(:, 0:i) u2 over at most NCH_MAX column chunks
+    const int krows = app ? k : i;                 // a pure solve needs rows 0..i-1 only
     const int nrb = (krows + LT - 1) / LT;
-    int cj = 8;
-    if (i > 0) cj = std::max(8, (i * nrb + 2 * (int)gridDim.x - 1) / (2 * (int)gridDim.x));
-    int nch = i > 0 ? (i + cj - 1) / cj : 0;
-    if (nch > st.max_chunks) { cj = (i + st.max_chunks - 1) / st.max_chunks; nch = (i + cj - 1) / cj; }
-    for (int item = blockIdx.x; item < nrb * nch; item += gridDim.x) {
+    const int cj = i > 0 ? max(8, (i + NCH_MAX - 1) / NCH_MAX) : 8;
+    const int nch = i > 0 ? (i + cj - 1) / cj : 0;
+    for (int item = blockIdx.x; item < nrb * nch; item += G) {
         const int rb = item % nrb, c = item / nrb;
-        const int l = rb * LT + threadIdx.x;
+        const int l = rb * LT + tid;
         const int j0 = c * cj, j1 = min(i, j0 + cj);
         if (l < krows) {
             double as = 0.0, ap = 0.0;
-            for (int j = j0; j < j1 && j <= l; ++j) {
+            const int jend = min(j1, l + 1);
+#pragma unroll 4
+            for (int j = j0; j < jend; ++j) {
                 const double vv = st.V[(size_t)j * k + l];
                 if (app) as = fma(vv, ldcg(st.u2s + j), as);
                 if (sol) ap = fma(vv, ldcg(st.u2p + j), ap);
             }
             st.ypart[(size_t)c * k + l] = as;
-            st.ypart[(size_t)(st.max_chunks + c) * k + l] = ap;
+            st.ypart[(size_t)(NCH_MAX + c) * k + l] = ap;
         }
     }
     if (!grid_barrier(ctl)) return;
 
-    // ---- phase 3b: y = [s, p] - V u2; sums for the new reflector
-    double sg = 0.0, cr = 0.0;
+    // ---- phase 3b: y = [s, p] - V u2 (the i existing reflectors applied)
     for (int l = gtid; l < krows; l += nthreads) {
         double ysl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
         double ypl = sol ? ldcg(st.pbuf + l) * pmul : 0.0;
         for (int c = 0; c < nch; ++c) {
             ysl -= ldcg(st.ypart + (size_t)c * k + l);
-            ypl -= ldcg(st.ypart + (size_t)(st.max_chunks + c) * k + l);
+            ypl -= ldcg(st.ypart + (size_t)(NCH_MAX + c) * k + l);
         }
         st.ys[l] = ysl;
         st.yp[l] = ypl;
-        if (app && l > i) { sg = fma(ysl, ysl, sg); cr = fma(ysl, ypl, cr); }
     }
-    sg = block_sum<LT>(sg, sh);
-    cr = block_sum<LT>(cr, sh);
-    if (threadIdx.x == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
     if (!grid_barrier(ctl)) return;
 
     if (!app) {
@@ -179,10 +195,40 @@ __global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
         return;
     }
 
-    // ---- phase 4: the new reflector H_i, V(:, i), z = V^T v_i, R_S^{-1} column, x
+    // ---- phase 4: everything the new reflector needs that does not depend on beta
+    //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp,
+    //   and the global sums sg = sum_{l>i} ys_l^2, cr = sum_{l>i} ys_l yp_l
+    double sg = 0.0, cr = 0.0;
+    for (int l = i + 1 + gtid; l < k; l += nthreads) {
+        const double y = ldcg(st.ys + l);
+        sg = fma(y, y, sg);
+        if (sol) cr = fma(y, ldcg(st.yp + l), cr);
+    }
+    sg = block_sum<LT>(sg, sh);
+    cr = block_sum<LT>(cr, sh);
+    if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
+    for (int j = blockIdx.x; j < i; j += G) {
+        const double* v = st.V + (size_t)j * k;
+        double zz = 0.0;
+        for (int l = i + 1 + tid; l < k; l += LT) zz = fma(v[l], ldcg(st.ys + l), zz);
+        const double* rr = st.RinvT + (size_t)j * mm;
+        double d1 = 0.0, d2 = 0.0;
+        for (int l = j + tid; l < i; l += LT) {
+            const double rv = rr[l];
+            d1 = fma(rv, ldcg(st.ys + l), d1);
+            if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
+        }
+        zz = block_sum<LT>(zz, sh);
+        d1 = block_sum<LT>(d1, sh);
+        d2 = block_sum<LT>(d2, sh);
+        if (tid == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
+    }
+    if (!grid_barrier(ctl)) return;
+
+    // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
     const double SG = grid_total(st.blk, 4, 2, sh);
     const double CR = grid_total(st.blk, 4, 3, sh);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         const double alpha = ldcg(st.ys + i);
         double beta, tau, vs;
         if (SG == 0.0) {
@@ -215,42 +261,23 @@ __global__ void __launch_bounds__(LT) ls_kernel(LSState st, LSStep a) {
         }
     }
     for (int j = gwarp; j < i; j += nwarps) {
-        const double* v = st.V + (size_t)j * k;
-        double zz = 0.0;
-        for (int l = i + 1 + lane; l < k; l += 32) zz = fma(v[l], ldcg(st.ys + l), zz);
-        zz = warp_sum(zz);
-        const double* rr = st.RinvT + (size_t)j * mm;     // row j of R_S^{-1}
-        double d1 = 0.0, d2 = 0.0;
-        for (int l = j + lane; l < i; l += 32) {
-            const double rv = rr[l];
-            d1 = fma(rv, ldcg(st.ys + l), d1);
-            if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
-        }
-        d1 = warp_sum(d1);
-        d2 = warp_sum(d2);
-        if (lane == 0) {
-            st.z[j] = v[i] + vs * zz;
-            const double cnew = -d1 / beta;                 // R_S^{-1}(j, i)
-            st.RinvT[(size_t)j * mm + i] = cnew;
-            if (sol) {
-                const double xj = d2 + cnew * ypi;
-                st.R[(size_t)a.xcol * st.ldr + j] = xj;
-                st.coef[j] = xj * st.sigma[j];
-            }
-        }
-    }
-    if (!grid_barrier(ctl)) return;
-
-    // ---- phase 5: T(0:i, i) = -tau T(0:i, 0:i) z  (row j of T is column j of TT)
-    for (int j = gwarp; j < i; j += nwarps) {
+        // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
         const double* tr = st.TT + (size_t)j * mm;
         double d = 0.0;
-        for (int l = j + lane; l < i; l += 32) d = fma(tr[l], ldcg(st.z + l), d);
+        for (int l = j + lane; l < i; l += 32)
+            d = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), d);
         d = warp_sum(d);
         if (lane == 0) {
             const double t = -tau * d;
             st.T[(size_t)i * mm + j] = t;
             st.TT[(size_t)j * mm + i] = t;
+            const double cnew = -ldcg(st.d1 + j) / beta;       // R_S^{-1}(j, i)
+            st.RinvT[(size_t)j * mm + i] = cnew;
+            if (sol) {
+                const double xj = ldcg(st.d2 + j) + cnew * ypi;
+                st.R[(size_t)a.xcol * st.ldr + j] = xj;
+                st.coef[j] = xj * st.sigma[j];
+            }
         }
     }
 }
@@ -295,22 +322,25 @@ __global__ void cert_final_kernel(const double* work, int m, double* out) {
 
 }  // namespace
 
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, LSState* st) {
-    const int max_chunks = std::max(1, (mmax + 7) / 8);
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st) {
+    const int groups = 2 * ((std::max(max_parts, 1) + GS - 1) / GS);
     size_t n = 0;
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
     const size_t oV = take((size_t)k * mmax), oT = take((size_t)mmax * mmax), oTT = take((size_t)mmax * mmax),
                  oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax), osb = take(k), opb = take(k),
                  oys = take(k), oyp = take(k), ous = take(mmax), oup = take(mmax), ou2s = take(mmax),
-                 ou2p = take(mmax), oz = take(mmax), oyr = take((size_t)2 * max_chunks * k), oblk = take((size_t)4 * grid),
+                 ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
+                 oyr = take((size_t)2 * NCH_MAX * k), ored = take((size_t)groups * k), oblk = take((size_t)4 * grid),
                  osg = take(mmax + 1), opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
     double* b = buf.as<double>();
-    st->k = k; st->mmax = mmax; st->max_chunks = max_chunks;
+    st->k = k; st->mmax = mmax; st->max_parts = max_parts;
     st->V = b + oV; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
-    st->us = b + ous; st->up = b + oup; st->u2s = b + ou2s; st->u2p = b + ou2p; st->z = b + oz;
-    st->ypart = b + oyr; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn; st->coef = b + oco;
+    st->us = b + ous; st->up = b + oup; st->u2s = b + ou2s; st->u2p = b + ou2p;
+    st->zp = b + ozp; st->d1 = b + od1; st->d2 = b + od2;
+    st->ypart = b + oyr; st->red = b + ored; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
+    st->coef = b + oco;
 }
 
 // Zero the factorisation (V must be zero above each reflector's diagonal; T, R_S^{-1} upper parts).
@@ -323,6 +353,7 @@ void rgs_ls_reset(rgs_context* ctx, const LSState& st) {
 }
 
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
+    RGS_REQUIRE(a.s_nparts <= st.max_parts && a.p_nparts <= st.max_parts, "too many partial sketches");
     LSState s = st;
     LSStep p = a;
     void* args[] = {&s, &p};
@@ -333,7 +364,7 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
 int rgs_ls_max_blocks(int num_sms) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ls_kernel, LT, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    return num_sms * std::min(per_sm, 2);
+    return num_sms;   // one CTA of LT threads per SM
 }
 
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,

@@ -9,6 +9,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 using namespace rgsdev;
 
@@ -93,12 +94,58 @@ struct UpdParams {
     const int* ctl;
 };
 
+// Double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2): the compensated
+// arithmetic used for the sketches of FP32 / BF16 bases.  Addition is Knuth's
+// error-free TwoSum of the high words, the low words added to its error, and a
+// final Dekker FastTwoSum renormalisation (about 2^-48 relative error per add).
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.h + b.h;
+    const float bv = s - a.h;
+    float e = (a.h - (s - bv)) + (b.h - bv);
+    e += a.l + b.l;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+
+// Arithmetic of the transform for the two value types.
+template <typename V> struct FW;
+template <> struct FW<double> {
+    __device__ static double add(double a, double b) { return a + b; }
+    __device__ static double sub(double a, double b) { return a - b; }
+    __device__ static double neg(double a) { return -a; }
+    __device__ static double shfl(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+    __device__ static double from(double x) { return x; }
+    __device__ static double to_double(double a) { return a; }
+    __device__ static double zero() { return 0.0; }
+};
+template <> struct FW<df> {
+    __device__ static df add(df a, df b) { return df_add(a, b); }
+    __device__ static df sub(df a, df b) { return df_add(a, df_neg(b)); }
+    __device__ static df neg(df a) { return df_neg(a); }
+    __device__ static df shfl(df a, int m) {
+        return {__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+    }
+    __device__ static df from(double x) {
+        const float h = __double2float_rn(x);
+        return {h, __double2float_rn(x - (double)h)};
+    }
+    __device__ static double to_double(df a) { return (double)a.h + (double)a.l; }
+    __device__ static df zero() { return {0.f, 0.f}; }
+};
+
 // Walsh-Hadamard transform of the CTA's 1024-element tile.  Element b = 4*tid + e:
 // bits 0-1 in registers, bits 2-6 across the warp, bits 7-9 through shared memory.
 // On return zt[b] holds (H_1024 z)[b] for every b.
-__device__ __forceinline__ void fwht_tile(double z[4], double* zt) {
-    double a0 = z[0] + z[1], a1 = z[0] - z[1], a2 = z[2] + z[3], a3 = z[2] - z[3];
-    z[0] = a0 + a2; z[1] = a1 + a3; z[2] = a0 - a2; z[3] = a1 - a3;
+template <typename V>
+__device__ __forceinline__ void fwht_tile(V z[4], V* zt) {
+    using F = FW<V>;
+    V a0 = F::add(z[0], z[1]), a1 = F::sub(z[0], z[1]), a2 = F::add(z[2], z[3]), a3 = F::sub(z[2], z[3]);
+    z[0] = F::add(a0, a2); z[1] = F::add(a1, a3); z[2] = F::sub(a0, a2); z[3] = F::sub(a1, a3);
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
@@ -106,17 +153,17 @@ __device__ __forceinline__ void fwht_tile(double z[4], double* zt) {
         const bool upper = (lane & m) != 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            double o = __shfl_xor_sync(0xffffffffu, z[e], m);
-            z[e] = upper ? (o - z[e]) : (z[e] + o);
+            const V o = F::shfl(z[e], m);
+            z[e] = upper ? F::sub(o, z[e]) : F::add(z[e], o);
         }
     }
     __syncthreads();                               // previous readers of zt are done
-    reinterpret_cast<double2*>(zt)[threadIdx.x * 2] = make_double2(z[0], z[1]);
-    reinterpret_cast<double2*>(zt)[threadIdx.x * 2 + 1] = make_double2(z[2], z[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) zt[threadIdx.x * 4 + e] = z[e];
     __syncthreads();
     if (threadIdx.x < 128) {
         const int g = threadIdx.x;
-        double v[8];
+        V v[8];
 #pragma unroll
         for (int w = 0; w < 8; ++w) v[w] = zt[g + 128 * w];
 #pragma unroll
@@ -125,9 +172,9 @@ __device__ __forceinline__ void fwht_tile(double z[4], double* zt) {
             for (int a = 0; a < 8; a += 2 * h)
 #pragma unroll
                 for (int b = a; b < a + h; ++b) {
-                    double u = v[b], t = v[b + h];
-                    v[b] = u + t;
-                    v[b + h] = u - t;
+                    const V u = v[b], t = v[b + h];
+                    v[b] = F::add(u, t);
+                    v[b + h] = F::sub(u, t);
                 }
 #pragma unroll
         for (int w = 0; w < 8; ++w) zt[g + 128 * w] = v[w];
@@ -135,13 +182,15 @@ __device__ __forceinline__ void fwht_tile(double z[4], double* zt) {
     __syncthreads();
 }
 
-template <typename TQ, bool SRHT>
+template <typename TQ, bool SRHT, bool DF>
 __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     using IO = QIO<TQ>;
     using Acc = typename IO::Acc;
+    using V = typename std::conditional<DF, df, double>::type;     // transform arithmetic
+    using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
-    double* zt = smem;                                   // TILE
-    double* part = zt + TILE;                            // k
+    V* zt = reinterpret_cast<V*>(smem);                  // TILE
+    V* part = zt + TILE;                                 // k
     int32_t* srow = reinterpret_cast<int32_t*>(part + (SRHT ? p.k : 0));     // k
     Acc* sc = reinterpret_cast<Acc*>(srow + (SRHT ? ((p.k + 3) & ~3) : 0));   // ncols
 
@@ -155,7 +204,7 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
 
     for (int j = threadIdx.x; j < p.ncols; j += UT) sc[j] = (Acc)p.coef[j];
     if (SRHT)
-        for (int j = threadIdx.x; j < p.k; j += UT) { srow[j] = p.rows[j]; part[j] = 0.0; }
+        for (int j = threadIdx.x; j < p.k; j += UT) { srow[j] = p.rows[j]; part[j] = F::zero(); }
     __syncthreads();
 
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
@@ -196,11 +245,11 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
                     if (r0 + e < n) acc[e] = fma(-c, IO::load1(Q + (int64_t)j * p.ldq + r0 + e), acc[e]);
             }
         }
-        double z[4];
+        V z[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             acc[e] = IO::to_storage(acc[e]);
-            z[e] = (r0 + e < n) ? (double)acc[e] : 0.0;
+            z[e] = F::from((r0 + e < n) ? (double)acc[e] : 0.0);
         }
         if (qout != nullptr) {
             if (full) {
@@ -216,20 +265,20 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
                 const uint32_t bits = __ldg(p.signbits + (r0 >> 5)) >> (r0 & 31);
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if ((bits >> e) & 1u) z[e] = -z[e];
+                    if ((bits >> e) & 1u) z[e] = F::neg(z[e]);
             }
-            fwht_tile(z, zt);
+            fwht_tile<V>(z, zt);
             for (int j = threadIdx.x; j < p.k; j += UT) {
                 const int r = srow[j];
-                const double v = zt[r & (TILE - 1)];
-                part[j] += (__popc((r >> LOG_TILE) & tile) & 1) ? -v : v;
+                const V v = zt[r & (TILE - 1)];
+                part[j] = (__popc((r >> LOG_TILE) & tile) & 1) ? F::sub(part[j], v) : F::add(part[j], v);
             }
         }
     }
     if (SRHT) {
         __syncthreads();
         double* out = p.partials + ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
-        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = part[j];
+        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = F::to_double(part[j]);
     }
 }
 
@@ -304,9 +353,9 @@ __global__ void gaussian_theta_kernel(double* theta, int k, int64_t n, uint32_t 
     if (2 * pr + 1 < k) theta[c * k + 2 * pr + 1] = rad * sn * scale;
 }
 
-template <typename TQ, bool SRHT>
+template <typename TQ, bool SRHT, bool DF = false>
 void launch_update_t(rgs_context* ctx, const UpdParams& p, int gx, int gy, size_t smem) {
-    auto kern = update_sketch_kernel<TQ, SRHT>;
+    auto kern = update_sketch_kernel<TQ, SRHT, DF>;
     if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(gx, gy), UT, smem, ctx->stream>>>(p);
     RGS_CUDA(cudaGetLastError());
@@ -371,7 +420,13 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     size_t smem = TILE * 8 + (srht ? (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 : 0) + (size_t)L.ncols * accsz + 16;
     if (L.ncols > 0 || L.qout || srht) {
         const int gy = L.wcols;
-        if (srht) {
+        if (srht && L.df_sketch) {
+            switch (L.qtype) {
+                case RGS_F64: launch_update_t<double, true, true>(ctx, p, gx, gy, smem); break;
+                case RGS_F32: launch_update_t<float, true, true>(ctx, p, gx, gy, smem); break;
+                default: launch_update_t<__nv_bfloat16, true, true>(ctx, p, gx, gy, smem); break;
+            }
+        } else if (srht) {
             switch (L.qtype) {
                 case RGS_F64: launch_update_t<double, true>(ctx, p, gx, gy, smem); break;
                 case RGS_F32: launch_update_t<float, true>(ctx, p, gx, gy, smem); break;

@@ -186,3 +186,29 @@ def test_invalid_arguments_rejected(h):
     with pytest.raises(rgs.RgsError) as e:
         rgs.rgs_sketch_create(h, "srht", 100, 129, 1)            # k > s = 128
     assert e.value.status == rgs.RGS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("qdtype", [torch.float32, torch.bfloat16])
+def test_double_float_sketch_accuracy(h, qdtype):
+    """S must equal Theta applied to the stored basis: the double-float transform's error, stated."""
+    n, m, k = 50000, 24, 96
+    A = synth.gdw_matrix(n, m, 1e4, 12).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 3)
+    g = run_qr(h, sk, to_gpu(A), qdtype=qdtype, qscale=True)
+    Qrep = g["Q"] * g["qscale"][None, :]                   # the represented basis Q' diag(sigma)
+    exact = Sketch("srht", n, k, 3).apply(Qrep)
+    err = rel(g["S"], exact)
+    print(f"double-float sketch ({qdtype}): ||S - Theta Q||/||S|| = {err:.3e}")
+    assert err <= 1e-13
+
+
+def test_fp64_sketch_flag_close_to_double_float(h):
+    n, m, k = 30000, 20, 80
+    A = to_gpu(synth.gdw_matrix(n, m, 1e3, 13).numpy().T.copy())
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 2)
+    R1, R2 = rgs.colmajor_empty(m, m), rgs.colmajor_empty(m, m)
+    rgs.rgs_qr(h, sk, A, rgs.colmajor_empty(n, m, dtype=torch.float32), R1)
+    rgs.rgs_qr(h, sk, A, rgs.colmajor_empty(n, m, dtype=torch.float32), R2, flags=rgs.RGS_QR_FP64_SKETCH)
+    d = rel(R1.cpu().numpy(), R2.cpu().numpy())
+    print(f"FP32 storage, double-float vs FP64 transform: ||dR||/||R|| = {d:.3e}")
+    assert d <= 1e-9
