@@ -150,7 +150,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    msub = 12
+    msub = 40
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     A = synth.gdw_matrix(N_ROWS, M_COLS, COND, SEED, device=dev)[:msub].cpu().numpy().T.copy()
     for _ in range(args.warmup):
@@ -191,7 +191,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
 
-    n, m, k = N_ROWS, M_COLS, K_SKETCH
+    n, m, k = N_ROWS, (args.cols or M_COLS), K_SKETCH
     W = synth.gdw_matrix(n, m, COND, SEED + rank, device="cuda").T          # (n, m) column-major
     h = rgs.rgs_create()
     sk = rgs.rgs_sketch_create(h, "srht", n, k, SEED)
@@ -262,7 +262,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        msub = 12
+        msub = 100
         v, dt, _ = cpu_sample_gbps(W[:, :msub].cpu().numpy(), n, k)
         cpu = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {msub} of {m} columns (n=2^20, SRHT k=2000, f32 storage emulation), {dt:.1f} s"}
@@ -271,7 +271,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
+               "config": {"workload": WORKLOAD if m == M_COLS else f"profiling case m={m}", "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
                           "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "phases_ms": phases,
@@ -290,6 +290,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cols", type=int, default=0, help="profiling cases only: override m (the bench line is m=500)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
