@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <utility>
@@ -72,7 +74,7 @@ bool is_host_pointer(const void* p) {
 }
 
 void reset_ctl(rgs_context* ctx) {
-    RGS_CUDA(cudaMemsetAsync(ctx->ctl.ptr, 0, 8 * sizeof(int), ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(ctx->ctl.ptr, 0, kCtlWords * sizeof(int), ctx->stream));
 }
 
 // Y (k x ncols) = Theta X, in column batches whose partial sketches fit a fixed budget.
@@ -134,8 +136,8 @@ rgs_status rgs_create(rgs_handle* out, void* stream) {
         RGS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
         RGS_REQUIRE(coop, "device does not support cooperative launches");
         ctx->stream = (cudaStream_t)stream;
-        ctx->ctl.ensure(8 * sizeof(int));
-        RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, 8 * sizeof(int)));
+        ctx->ctl.ensure(kCtlWords * sizeof(int));
+        RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, kCtlWords * sizeof(int)));
         ctx->ls_blocks = rgs_ls_max_blocks(ctx->num_sms);
     });
     if (st != RGS_OK) {
@@ -292,6 +294,9 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         h->partials.ensure(sizeof(double) * (size_t)np1 * k);
 
         PhaseTimer timer(h, (flags & RGS_QR_TIMINGS) != 0);
+        // RGS_TRACE=1 in the environment: per-phase device timestamps of the least-squares kernel
+        const bool trace = std::getenv("RGS_TRACE") != nullptr;
+        if (trace) h->trace.ensure(sizeof(unsigned long long) * 10 * (size_t)m);
         h->launches = 0;
         reset_ctl(h);
         rgs_ls_reset(h, ls);
@@ -333,6 +338,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             a.p_vec = P + (size_t)(i + 1) * k;
             a.p_scale = 1.0;
             a.pnorm_idx = i + 1;
+            a.trace = trace ? h->trace.as<unsigned long long>() + 10 * (size_t)i : nullptr;
             timer.start(2);
             rgs_launch_ls(h, ls, a);
             timer.stop(2);
@@ -369,6 +375,16 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
                 info->update_ms = timer.total_ms(1);
                 info->ls_ms = timer.total_ms(2);
             }
+        }
+        if (trace) {
+            std::vector<unsigned long long> t(10 * (size_t)m);
+            RGS_CUDA(cudaMemcpy(t.data(), h->trace.ptr, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+            double ph[8] = {0};
+            for (int i = 0; i < m; ++i)
+                for (int p = 0; p < 8; ++p) ph[p] += (double)(t[10 * (size_t)i + p + 1] - t[10 * (size_t)i + p]) * 1e-3;
+            std::fprintf(stderr, "[rgs trace] least-squares phase means (us):");
+            for (int p = 0; p < 8; ++p) std::fprintf(stderr, " %.2f", ph[p] / m);
+            std::fprintf(stderr, "\n");
         }
         if (ctl[0] != 0)
             throw RgsError{(rgs_status)ctl[0], std::string("device status ") + rgs_status_string((rgs_status)ctl[0]) +

@@ -57,7 +57,8 @@ struct rgs_context {
     int num_sms = 0;
     cudaStream_t stream = nullptr;
     std::string last_error;
-    DevBuf ctl;            // int[8]: status, detail, barrier count, barrier generation, ...
+    DevBuf ctl;            // int[kCtlWords]: status, detail, stop flag, barrier words (own lines), abort
+    DevBuf trace;          // optional per-phase timestamps of the least-squares kernel
     DevBuf partials;       // per-CTA partial sketches
     DevBuf scratch;        // staging for host-pointer calls
     DevBuf lsbuf;          // Householder factors and vectors of the least-squares engine
@@ -125,10 +126,13 @@ namespace rgsdev {
 
 constexpr int kStatusWord = 0;
 constexpr int kDetailWord = 1;
-constexpr int kBarCount = 2;
-constexpr int kBarGen = 3;
-constexpr int kAbortWord = 4;
 constexpr int kStopWord = 5;     // an Arnoldi cycle ended early (convergence or happy breakdown)
+// the grid barrier's words sit on separate 128-byte lines so that polling one
+// does not queue behind atomics on another
+constexpr int kBarCount = 32;
+constexpr int kBarGen = 64;
+constexpr int kAbortWord = 96;
+constexpr int kCtlWords = 128;
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies.
 __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -172,35 +176,44 @@ __device__ __forceinline__ double block_sum(double v, double* sm /* NT/32 double
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
+// Grid-wide barrier for a cooperative launch.  Arrival is a release-ordered atomic
+// increment; the last CTA resets the count and bumps the generation word, which the
+// others poll with acquire loads and a short back-off.  Every wait is bounded: after
 // about two seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word
 // and returns false, and every other CTA then leaves at its next barrier.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(int* ctl) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile int* vctl = ctl;
         unsigned* count = reinterpret_cast<unsigned*>(ctl + kBarCount);
         unsigned* gen = reinterpret_cast<unsigned*>(ctl + kBarGen);
-        unsigned g = *reinterpret_cast<volatile unsigned*>(gen);
+        const unsigned g = ld_acquire(gen);
         __threadfence();
         if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            atomicExch(count, 0u);
+            *count = 0u;
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
-            long long start = clock64();
+            const long long start = clock64();
             unsigned spins = 0;
-            while (*reinterpret_cast<volatile unsigned*>(gen) == g) {
-                if (vctl[kAbortWord] != 0) { ok = 0; break; }
-                if ((++spins & 255u) == 0 && clock64() - start > 4000000000LL) {
-                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
-                    atomicExch(ctl + kAbortWord, 1);
-                    ok = 0;
-                    break;
+            while (ld_acquire(gen) == g) {
+                if ((++spins & 63u) == 0) {
+                    if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
+                    if (clock64() - start > 4000000000LL) {
+                        atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                        atomicExch(ctl + kAbortWord, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(20);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -208,6 +221,12 @@ __device__ __forceinline__ bool grid_barrier(int* ctl) {
     }
     __syncthreads();
     return ok_sh != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 }  // namespace rgsdev
@@ -266,6 +285,7 @@ struct LSStep {
     double p_scale;
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
     int pnorm_idx;          // where to record ||p||
+    unsigned long long* trace;  // optional: 9 timestamps (ns) at the phase boundaries, written by CTA 0
 };
 void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);

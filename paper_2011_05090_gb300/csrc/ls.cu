@@ -43,6 +43,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const int gwarp = gtid >> 5, nwarps = nthreads >> 5;
     const bool app = a.append != 0, sol = a.solve != 0;
     const bool p_parts = sol && a.p_vec == nullptr;
+    unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
+    if (trace) trace[0] = globaltimer();
 
     // ---- phase 0a: first reduction level of the partial sketches (warp per 32 rows x GS partials)
     const int nseg = (k + 31) / 32;
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[1] = globaltimer();
 
     // ---- phase 0b: second level (warp per row, lanes over groups): s', p and their norms
     double ss = 0.0, pp = 0.0;
@@ -90,6 +93,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     pp = block_sum<LT>(pp, sh);
     if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = ss; st.blk[blockIdx.x * 4 + 1] = pp; }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[2] = globaltimer();
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (CTA per column)
     const double r = sqrt(grid_total(st.blk, 4, 0, sh));
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         if (tid == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[3] = globaltimer();
 
     // ---- phase 2: u2 = T(0:i, 0:i)^T u   (warp per column of T)
     for (int j = gwarp; j < i; j += nwarps) {
@@ -142,6 +147,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         if (lane == 0) { st.u2s[j] = ds; st.u2p[j] = dp; }
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[4] = globaltimer();
 
     // ---- phase 3: partial sums of V(:, 0:i) u2 over at most NCH_MAX column chunks
     const int krows = app ? k : i;                 // a pure solve needs rows 0..i-1 only
@@ -166,6 +172,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[5] = globaltimer();
 
     // ---- phase 3b: y = [s, p] - V u2 (the i existing reflectors applied)
     for (int l = gtid; l < krows; l += nthreads) {
@@ -179,6 +186,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         st.yp[l] = ypl;
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[6] = globaltimer();
 
     if (!app) {
         // pure solve: x = R_S^{-1} y(0:i); row j of R_S^{-1} is column j of RinvT
@@ -192,6 +200,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 st.coef[j] = d * st.sigma[j];
             }
         }
+        if (trace) trace[8] = globaltimer();
         return;
     }
 
@@ -224,6 +233,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         if (tid == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
     }
     if (!grid_barrier(ctl)) return;
+    if (trace) trace[7] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
     const double SG = grid_total(st.blk, 4, 2, sh);
@@ -280,6 +290,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
         }
     }
+    if (trace) trace[8] = globaltimer();
 }
 
 // Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
