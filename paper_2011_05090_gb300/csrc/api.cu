@@ -99,7 +99,8 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
         L.df_sketch = df ? 1 : 0;
         int nparts = 0;
         rgs_launch_update_sketch(ctx, sk, L, ctx->partials.as<double>(), &nparts, nullptr);
-        rgs_launch_reduce_partials(ctx, ctx->partials.as<double>(), nparts, k, nc, scale, Y + (int64_t)c0 * ldy, ldy);
+        rgs_launch_reduce_partials(ctx, ctx->partials.as<double>(), nparts, k, nc, scale, Y + (int64_t)c0 * ldy, ldy,
+                                   df && sk->kind == RGS_SKETCH_SRHT);
     }
 }
 
@@ -333,6 +334,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             a.s_part = h->partials.as<double>();
             a.s_nparts = nparts;
             a.s_scale = s_scale;
+            a.s_df = (df && s->kind == RGS_SKETCH_SRHT) ? 1 : 0;
             a.solve = (i + 1 < m) ? 1 : 0;                     // step 2 of the next column
             a.xcol = i + 1;
             a.p_vec = P + (size_t)(i + 1) * k;

@@ -162,19 +162,42 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum of v over the block, result valid in every thread (fixed order: deterministic).
+// Sum of v over the block, valid in every thread, in a fixed order (deterministic).
+// FP64 instructions are scarce on this GPU (about 2 lane-operations per clock per SM),
+// so the per-thread values go through shared memory and a single warp does the adds.
 template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sm /* NT/32 doubles */) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ double block_sum(double v, double* sm /* NT doubles */) {
     __syncthreads();
-    if (lane == 0) sm[w] = v;
+    sm[threadIdx.x] = v;
     __syncthreads();
-    double t = 0.0;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) t += sm[i];
-    return t;
+        for (int i = 0; i < NT / 32; ++i) t += sm[threadIdx.x + 32 * i];
+        t = warp_sum(t);
+        if (threadIdx.x == 0) sm[0] = t;
+    }
+    __syncthreads();
+    return sm[0];
 }
+
+// Double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2): the compensated
+// arithmetic used for the sketches of FP32 / BF16 bases.  Addition is Knuth's
+// error-free TwoSum of the high words, the low words added to its error, and a
+// final Dekker FastTwoSum renormalisation (about 2^-48 relative error per add).
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.h + b.h;
+    const float bv = s - a.h;
+    float e = (a.h - (s - bv)) + (b.h - bv);
+    e += a.l + b.l;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
 
 // Grid-wide barrier for a cooperative launch.  Arrival is a release-ordered atomic
 // increment; the last CTA resets the count and bumps the generation word, which the
@@ -252,7 +275,7 @@ int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t 
 int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L,
                              double* partials, int* nparts, const int* ctl);
 void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols,
-                                double scale, double* Y, int64_t ldy);
+                                double scale, double* Y, int64_t ldy, bool df = false);
 void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed);
 
 // ls.cu: Householder (compact-WY) least-squares engine for the sketched problems.
@@ -284,6 +307,7 @@ struct LSStep {
     int p_nparts;
     double p_scale;
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
+    int s_df, p_df;         // partial sketches stored as double-float pairs (float2) instead of FP64
     int pnorm_idx;          // where to record ||p||
     unsigned long long* trace;  // optional: 9 timestamps (ns) at the phase boundaries, written by CTA 0
 };

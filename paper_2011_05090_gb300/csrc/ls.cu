@@ -24,15 +24,24 @@ constexpr int NCH_MAX = 16;    // column chunks of the V u2 product
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Deterministic total of per-CTA values blk[b*stride + off] (same order in every CTA).
+// Deterministic total of per-CTA values blk[b*stride + off] (same order in every CTA);
+// one warp does the FP64 adds and broadcasts through shared memory.
 __device__ double grid_total(const double* blk, int stride, int off, double* sh) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += LT) v += ldcg(blk + (size_t)b * stride + off);
-    return block_sum<LT>(v, sh);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += ldcg(blk + (size_t)b * stride + off);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) sh[0] = v;
+    }
+    __syncthreads();
+    const double t = sh[0];
+    __syncthreads();
+    return t;
 }
 
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
-    __shared__ double sh[NW];
+    __shared__ double sh[LT];
     __shared__ double sc[8];
     int* ctl = st.ctl;
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
@@ -56,12 +65,21 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         const int gg = is_s ? g : g - sgroups;
         const double* src = is_s ? a.s_part : a.p_part;
         const int np = is_s ? a.s_nparts : a.p_nparts;
+        const bool sdf = is_s ? a.s_df != 0 : a.p_df != 0;
         const int l = seg * 32 + lane;
         if (l < k) {
             const int b0 = gg * GS, b1 = min(np, b0 + GS);
             double v = 0.0;
+            if (sdf) {       // double-float partials: summed in FP32 pairs, converted once
+                const df* d = reinterpret_cast<const df*>(src);
+                df t = {0.f, 0.f};
 #pragma unroll 8
-            for (int b = b0; b < b1; ++b) v += src[(size_t)b * k + l];
+                for (int b = b0; b < b1; ++b) t = df_add(t, d[(size_t)b * k + l]);
+                v = (double)t.h + (double)t.l;
+            } else {
+#pragma unroll 8
+                for (int b = b0; b < b1; ++b) v += src[(size_t)b * k + l];
+            }
             st.red[(size_t)g * k + l] = v;
         }
     }
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (!grid_barrier(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
-    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (CTA per column)
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (warp per column)
     const double r = sqrt(grid_total(st.blk, 4, 0, sh));
     const double pn = sqrt(grid_total(st.blk, 4, 1, sh));
     double inv_r = 1.0, pmul = 1.0;
@@ -118,17 +136,18 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
-    for (int j = blockIdx.x; j < i; j += G) {
+    for (int j = gwarp; j < i; j += nwarps) {          // warp per column of V
         const double* v = st.V + (size_t)j * k;
         double ds = 0.0, dp = 0.0;
-        for (int l = j + tid; l < k; l += LT) {
+#pragma unroll 4
+        for (int l = j + lane; l < k; l += 32) {
             const double vv = v[l];
             if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
             if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
         }
-        ds = block_sum<LT>(ds, sh);
-        dp = block_sum<LT>(dp, sh);
-        if (tid == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
+        ds = warp_sum(ds);
+        dp = warp_sum(dp);
+        if (lane == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[3] = globaltimer();
@@ -216,21 +235,22 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     sg = block_sum<LT>(sg, sh);
     cr = block_sum<LT>(cr, sh);
     if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
-    for (int j = blockIdx.x; j < i; j += G) {
+    for (int j = gwarp; j < i; j += nwarps) {          // warp per column
         const double* v = st.V + (size_t)j * k;
         double zz = 0.0;
-        for (int l = i + 1 + tid; l < k; l += LT) zz = fma(v[l], ldcg(st.ys + l), zz);
+#pragma unroll 4
+        for (int l = i + 1 + lane; l < k; l += 32) zz = fma(v[l], ldcg(st.ys + l), zz);
         const double* rr = st.RinvT + (size_t)j * mm;
         double d1 = 0.0, d2 = 0.0;
-        for (int l = j + tid; l < i; l += LT) {
+        for (int l = j + lane; l < i; l += 32) {
             const double rv = rr[l];
             d1 = fma(rv, ldcg(st.ys + l), d1);
             if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
         }
-        zz = block_sum<LT>(zz, sh);
-        d1 = block_sum<LT>(d1, sh);
-        d2 = block_sum<LT>(d2, sh);
-        if (tid == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
+        zz = warp_sum(zz);
+        d1 = warp_sum(d1);
+        if (sol) d2 = warp_sum(d2);
+        if (lane == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[7] = globaltimer();
@@ -297,7 +317,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
 // Block b handles column b: sums of squares of (I - S^T S)(0:m, b) and (P - S R)(:, b).
 __global__ void __launch_bounds__(256) cert_kernel(const double* S, int k, int m, const double* R, int64_t ldr,
                                                    const double* P, double* work) {
-    __shared__ double sh[8];
+    __shared__ double sh[256];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double g2 = 0.0;
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(256) cert_kernel(const double* S, int k, int m
 }
 
 __global__ void cert_final_kernel(const double* work, int m, double* out) {
-    __shared__ double sh[8];
+    __shared__ double sh[256];
     double g = 0.0, e = 0.0, p = 0.0;
     for (int b = threadIdx.x; b < m; b += 256) { g += work[3 * b]; e += work[3 * b + 1]; p += work[3 * b + 2]; }
     g = block_sum<256>(g, sh);

@@ -94,24 +94,6 @@ struct UpdParams {
     const int* ctl;
 };
 
-// Double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2): the compensated
-// arithmetic used for the sketches of FP32 / BF16 bases.  Addition is Knuth's
-// error-free TwoSum of the high words, the low words added to its error, and a
-// final Dekker FastTwoSum renormalisation (about 2^-48 relative error per add).
-struct df {
-    float h, l;
-};
-
-__device__ __forceinline__ df df_add(df a, df b) {
-    const float s = a.h + b.h;
-    const float bv = s - a.h;
-    float e = (a.h - (s - bv)) + (b.h - bv);
-    e += a.l + b.l;
-    const float h = s + e;
-    return {h, e - (h - s)};
-}
-__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
-
 // Arithmetic of the transform for the two value types.
 template <typename V> struct FW;
 template <> struct FW<double> {
@@ -120,6 +102,7 @@ template <> struct FW<double> {
     __device__ static double neg(double a) { return -a; }
     __device__ static double shfl(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
     __device__ static double from(double x) { return x; }
+    __device__ static double from_float(float x) { return (double)x; }
     __device__ static double to_double(double a) { return a; }
     __device__ static double zero() { return 0.0; }
 };
@@ -134,6 +117,7 @@ template <> struct FW<df> {
         const float h = __double2float_rn(x);
         return {h, __double2float_rn(x - (double)h)};
     }
+    __device__ static df from_float(float x) { return {x, 0.f}; }
     __device__ static double to_double(df a) { return (double)a.h + (double)a.l; }
     __device__ static df zero() { return {0.f, 0.f}; }
 };
@@ -214,8 +198,8 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
         if (full) {
             double2 a = __ldg(reinterpret_cast<const double2*>(w + r0));
             double2 b = __ldg(reinterpret_cast<const double2*>(w + r0 + 2));
-            acc[0] = (Acc)(a.x * wmul); acc[1] = (Acc)(a.y * wmul);
-            acc[2] = (Acc)(b.x * wmul); acc[3] = (Acc)(b.y * wmul);
+            if (p.wscale) { a.x *= wmul; a.y *= wmul; b.x *= wmul; b.y *= wmul; }
+            acc[0] = (Acc)a.x; acc[1] = (Acc)a.y; acc[2] = (Acc)b.x; acc[3] = (Acc)b.y;
             int j = 0;
             for (; j + UNROLL <= p.ncols; j += UNROLL) {
                 Acc q[UNROLL][4];
@@ -249,7 +233,8 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             acc[e] = IO::to_storage(acc[e]);
-            z[e] = F::from((r0 + e < n) ? (double)acc[e] : 0.0);
+            if constexpr (sizeof(Acc) == 4) z[e] = F::from_float((r0 + e < n) ? (float)acc[e] : 0.f);
+            else z[e] = F::from((r0 + e < n) ? (double)acc[e] : 0.0);
         }
         if (qout != nullptr) {
             if (full) {
@@ -277,8 +262,8 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     }
     if (SRHT) {
         __syncthreads();
-        double* out = p.partials + ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
-        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = F::to_double(part[j]);
+        V* out = reinterpret_cast<V*>(p.partials) + ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
+        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = part[j];
     }
 }
 
@@ -325,14 +310,23 @@ __global__ void __launch_bounds__(256) gauss_sketch_kernel(const double* __restr
     }
 }
 
+template <bool DF>
 __global__ void reduce_partials_kernel(const double* __restrict__ partials, int nparts, int k, double scale,
                                        double* __restrict__ Y, int64_t ldy) {
     const int col = blockIdx.y;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= k) return;
-    const double* src = partials + (int64_t)col * nparts * k + l;
-    double v = 0.0;
-    for (int b = 0; b < nparts; ++b) v += src[(int64_t)b * k];
+    double v;
+    if constexpr (DF) {
+        const df* src = reinterpret_cast<const df*>(partials) + (int64_t)col * nparts * k + l;
+        df t = {0.f, 0.f};
+        for (int b = 0; b < nparts; ++b) t = df_add(t, src[(int64_t)b * k]);
+        v = (double)t.h + (double)t.l;
+    } else {
+        const double* src = partials + (int64_t)col * nparts * k + l;
+        v = 0.0;
+        for (int b = 0; b < nparts; ++b) v += src[(int64_t)b * k];
+    }
     Y[(int64_t)col * ldy + l] = v * scale;
 }
 
@@ -460,8 +454,11 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
 }
 
 void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols, double scale,
-                                double* Y, int64_t ldy) {
-    reduce_partials_kernel<<<dim3((k + 255) / 256, ncols), 256, 0, ctx->stream>>>(partials, nparts, k, scale, Y, ldy);
+                                double* Y, int64_t ldy, bool df) {
+    if (df)
+        reduce_partials_kernel<true><<<dim3((k + 255) / 256, ncols), 256, 0, ctx->stream>>>(partials, nparts, k, scale, Y, ldy);
+    else
+        reduce_partials_kernel<false><<<dim3((k + 255) / 256, ncols), 256, 0, ctx->stream>>>(partials, nparts, k, scale, Y, ldy);
     RGS_CUDA(cudaGetLastError());
     ctx->launches++;
 }
