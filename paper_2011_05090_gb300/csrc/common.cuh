@@ -199,9 +199,9 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
 
-// Grid-wide barrier for a cooperative launch.  Arrival is a release-ordered atomic
-// increment; the last CTA resets the count and bumps the generation word, which the
-// others poll with acquire loads and a short back-off.  Every wait is bounded: after
+// Grid-wide barrier for a cooperative launch.  Arrival is an acquire-release atomic
+// increment; the last CTA resets the count and bumps the generation word with a
+// release reduction, which the others poll with acquire loads and a short back-off.  Every wait is bounded: after
 // about two seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word
 // and returns false, and every other CTA then leaves at its next barrier.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -210,19 +210,31 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(int* ctl) {
     __shared__ int ok_sh;
-    __syncthreads();
+    __syncthreads();                       // the CTA's writes are ordered before thread 0's release
     if (threadIdx.x == 0) {
         int ok = 1;
         unsigned* count = reinterpret_cast<unsigned*>(ctl + kBarCount);
         unsigned* gen = reinterpret_cast<unsigned*>(ctl + kBarGen);
         const unsigned g = ld_acquire(gen);
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            *count = 0u;
-            __threadfence();
-            atomicAdd(gen, 1u);
+        if (atom_add_acq_rel(count, 1u) == gridDim.x - 1) {
+            st_relaxed(count, 0u);
+            red_add_release(gen, 1u);
         } else {
             const long long start = clock64();
             unsigned spins = 0;
@@ -239,7 +251,6 @@ __device__ __forceinline__ bool grid_barrier(int* ctl) {
                 __nanosleep(32);
             }
         }
-        __threadfence();
         ok_sh = ok;
     }
     __syncthreads();

@@ -24,18 +24,22 @@ constexpr int NCH_MAX = 16;    // column chunks of the V u2 product
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Deterministic total of per-CTA values blk[b*stride + off] (same order in every CTA);
-// one warp does the FP64 adds and broadcasts through shared memory.
-__device__ double grid_total(const double* blk, int stride, int off, double* sh) {
+// Deterministic totals of the per-CTA values blk[b*stride + off] and blk[b*stride + off + 1],
+// identical in every CTA; one warp does the FP64 adds and broadcasts through shared memory.
+__device__ double2 grid_total2(const double* blk, int stride, int off, double* sh) {
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += ldcg(blk + (size_t)b * stride + off);
-        v = warp_sum(v);
-        if (threadIdx.x == 0) sh[0] = v;
+        double v0 = 0.0, v1 = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+            v0 += ldcg(blk + (size_t)b * stride + off);
+            v1 += ldcg(blk + (size_t)b * stride + off + 1);
+        }
+        v0 = warp_sum(v0);
+        v1 = warp_sum(v1);
+        if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
     }
     __syncthreads();
-    const double t = sh[0];
+    const double2 t = make_double2(sh[0], sh[1]);
     __syncthreads();
     return t;
 }
@@ -49,7 +53,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const int G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nthreads = G * LT, gtid = blockIdx.x * LT + tid;
-    const int gwarp = gtid >> 5, nwarps = nthreads >> 5;
+    // warp w of CTA b is global warp b + G*w, so consecutive items spread over all SMs
+    const int gwarp = blockIdx.x + G * (tid >> 5), nwarps = nthreads >> 5;
     const bool app = a.append != 0, sol = a.solve != 0;
     const bool p_parts = sol && a.p_vec == nullptr;
     unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
@@ -114,8 +119,9 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (trace) trace[2] = globaltimer();
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (warp per column)
-    const double r = sqrt(grid_total(st.blk, 4, 0, sh));
-    const double pn = sqrt(grid_total(st.blk, 4, 1, sh));
+    const double2 tot01 = grid_total2(st.blk, 4, 0, sh);
+    const double r = sqrt(tot01.x);
+    const double pn = sqrt(tot01.y);
     double inv_r = 1.0, pmul = 1.0;
     if (app) {
         const double pref = st.pnorm[i];
@@ -156,6 +162,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     for (int j = gwarp; j < i; j += nwarps) {
         const double* t = st.T + (size_t)j * mm;
         double ds = 0.0, dp = 0.0;
+#pragma unroll 4
         for (int l = lane; l <= j; l += 32) {
             const double tv = t[l];
             if (app) ds = fma(tv, ldcg(st.us + l), ds);
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     for (int l = gtid; l < krows; l += nthreads) {
         double ysl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
         double ypl = sol ? ldcg(st.pbuf + l) * pmul : 0.0;
+#pragma unroll 8
         for (int c = 0; c < nch; ++c) {
             ysl -= ldcg(st.ypart + (size_t)c * k + l);
             ypl -= ldcg(st.ypart + (size_t)(NCH_MAX + c) * k + l);
@@ -212,6 +220,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         for (int j = gwarp; j < i; j += nwarps) {
             const double* rr = st.RinvT + (size_t)j * mm;
             double d = 0.0;
+#pragma unroll 4
             for (int l = j + lane; l < i; l += 32) d = fma(rr[l], ldcg(st.yp + l), d);
             d = warp_sum(d);
             if (lane == 0) {
@@ -242,6 +251,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         for (int l = i + 1 + lane; l < k; l += 32) zz = fma(v[l], ldcg(st.ys + l), zz);
         const double* rr = st.RinvT + (size_t)j * mm;
         double d1 = 0.0, d2 = 0.0;
+#pragma unroll 4
         for (int l = j + lane; l < i; l += 32) {
             const double rv = rr[l];
             d1 = fma(rv, ldcg(st.ys + l), d1);
@@ -256,8 +266,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (trace) trace[7] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    const double SG = grid_total(st.blk, 4, 2, sh);
-    const double CR = grid_total(st.blk, 4, 3, sh);
+    const double2 tot23 = grid_total2(st.blk, 4, 2, sh);
+    const double SG = tot23.x, CR = tot23.y;
     if (tid == 0) {
         const double alpha = ldcg(st.ys + i);
         double beta, tau, vs;
@@ -294,6 +304,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
         const double* tr = st.TT + (size_t)j * mm;
         double d = 0.0;
+#pragma unroll 4
         for (int l = j + lane; l < i; l += 32)
             d = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), d);
         d = warp_sum(d);
