@@ -129,8 +129,8 @@ constexpr int kDetailWord = 1;
 constexpr int kStopWord = 5;     // an Arnoldi cycle ended early (convergence or happy breakdown)
 // the grid barrier's words sit on separate 128-byte lines so that polling one
 // does not queue behind atomics on another
-constexpr int kBarCount = 32;
-constexpr int kBarGen = 64;
+constexpr int kBarCount = 32;     // the barrier word
+constexpr int kBarGen = 64;       // unused (kept free)
 constexpr int kAbortWord = 96;
 constexpr int kCtlWords = 128;
 
@@ -163,22 +163,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum of v over the block, valid in every thread, in a fixed order (deterministic).
-// FP64 instructions are scarce on this GPU (about 2 lane-operations per clock per SM),
-// so the per-thread values go through shared memory and a single warp does the adds.
+// On this GPU a dependent FP64 add costs about 64 cycles, so the sum is a tree:
+// a shuffle tree inside every warp, then one warp's tree over the warp totals.
 template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sm /* NT doubles */) {
+__device__ __forceinline__ double block_sum(double v, double* sm /* >= NT/32 doubles */) {
+    v = warp_sum(v);
     __syncthreads();
-    sm[threadIdx.x] = v;
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double t = 0.0;
-#pragma unroll
-        for (int i = 0; i < NT / 32; ++i) t += sm[threadIdx.x + 32 * i];
+        double t = threadIdx.x < NT / 32 ? sm[threadIdx.x] : 0.0;
         t = warp_sum(t);
-        if (threadIdx.x == 0) sm[0] = t;
+        if (threadIdx.x == 0) sm[NT / 32] = t;
     }
     __syncthreads();
-    return sm[0];
+    return sm[NT / 32];
 }
 
 // Double-float value hi + lo (two FP32 words, |lo| <= ulp(hi)/2): the compensated
@@ -199,9 +198,9 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
 
-// Grid-wide barrier for a cooperative launch.  Arrival is an acquire-release atomic
-// increment; the last CTA resets the count and bumps the generation word with a
-// release reduction, which the others poll with acquire loads and a short back-off.  Every wait is bounded: after
+// Grid-wide barrier for a cooperative launch on one word: every CTA arrives with one
+// acquire-release atomic add and polls the word with acquire loads until its top bit
+// flips.  Every wait is bounded: after
 // about two seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word
 // and returns false, and every other CTA then leaves at its next barrier.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -229,26 +228,22 @@ __device__ __forceinline__ bool grid_barrier(int* ctl) {
     __syncthreads();                       // the CTA's writes are ordered before thread 0's release
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned* count = reinterpret_cast<unsigned*>(ctl + kBarCount);
-        unsigned* gen = reinterpret_cast<unsigned*>(ctl + kBarGen);
-        const unsigned g = ld_acquire(gen);
-        if (atom_add_acq_rel(count, 1u) == gridDim.x - 1) {
-            st_relaxed(count, 0u);
-            red_add_release(gen, 1u);
-        } else {
-            const long long start = clock64();
-            unsigned spins = 0;
-            while (ld_acquire(gen) == g) {
-                if ((++spins & 63u) == 0) {
-                    if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
-                    if (clock64() - start > 4000000000LL) {
-                        atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
-                        atomicExch(ctl + kAbortWord, 1);
-                        ok = 0;
-                        break;
-                    }
+        unsigned* word = reinterpret_cast<unsigned*>(ctl + kBarCount);
+        // CTA 0 adds 2^31 - (G-1), the others 1: the sum over one barrier is exactly 2^31,
+        // so the top bit flips once per barrier and the low bits return to their value.
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        const unsigned old = atom_add_acq_rel(word, add);
+        const long long start = clock64();
+        unsigned spins = 0;
+        while (((old ^ ld_acquire(word)) & 0x80000000u) == 0u) {
+            if ((++spins & 63u) == 0) {
+                if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
+                if (clock64() - start > 4000000000LL) {
+                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                    atomicExch(ctl + kAbortWord, 1);
+                    ok = 0;
+                    break;
                 }
-                __nanosleep(32);
             }
         }
         ok_sh = ok;

@@ -45,7 +45,7 @@ __device__ double2 grid_total2(const double* blk, int stride, int off, double* s
 }
 
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
-    __shared__ double sh[LT];
+    __shared__ double sh[NW + 2];
     __shared__ double sc[8];
     int* ctl = st.ctl;
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
@@ -77,13 +77,27 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             double v = 0.0;
             if (sdf) {       // double-float partials: summed in FP32 pairs, converted once
                 const df* d = reinterpret_cast<const df*>(src);
-                df t = {0.f, 0.f};
-#pragma unroll 8
-                for (int b = b0; b < b1; ++b) t = df_add(t, d[(size_t)b * k + l]);
-                v = (double)t.h + (double)t.l;
+                df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
+                int b = b0;
+#pragma unroll 4
+                for (; b + 1 < b1; b += 2) {
+                    t0 = df_add(t0, d[(size_t)b * k + l]);
+                    t1 = df_add(t1, d[(size_t)(b + 1) * k + l]);
+                }
+                if (b < b1) t0 = df_add(t0, d[(size_t)b * k + l]);
+                t0 = df_add(t0, t1);
+                v = (double)t0.h + (double)t0.l;
             } else {
-#pragma unroll 8
-                for (int b = b0; b < b1; ++b) v += src[(size_t)b * k + l];
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                int b = b0;
+                for (; b + 3 < b1; b += 4) {
+                    v0 += src[(size_t)b * k + l];
+                    v1 += src[(size_t)(b + 1) * k + l];
+                    v2 += src[(size_t)(b + 2) * k + l];
+                    v3 += src[(size_t)(b + 3) * k + l];
+                }
+                for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
+                v = (v0 + v1) + (v2 + v3);
             }
             st.red[(size_t)g * k + l] = v;
         }
@@ -144,16 +158,24 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
     for (int j = gwarp; j < i; j += nwarps) {          // warp per column of V
         const double* v = st.V + (size_t)j * k;
-        double ds = 0.0, dp = 0.0;
-#pragma unroll 4
-        for (int l = j + lane; l < k; l += 32) {
-            const double vv = v[l];
-            if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
-            if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
+        double ds[4] = {0.0, 0.0, 0.0, 0.0}, dp[4] = {0.0, 0.0, 0.0, 0.0};
+        int l = j + lane;
+        for (; l + 96 < k; l += 128) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double vv = v[l + 32 * q];
+                if (app) ds[q] = fma(vv, ldcg(st.sbuf + l + 32 * q), ds[q]);
+                if (sol) dp[q] = fma(vv, ldcg(st.pbuf + l + 32 * q), dp[q]);
+            }
         }
-        ds = warp_sum(ds);
-        dp = warp_sum(dp);
-        if (lane == 0) { st.us[j] = ds * inv_r; st.up[j] = dp * pmul; }
+        for (; l < k; l += 32) {
+            const double vv = v[l];
+            if (app) ds[0] = fma(vv, ldcg(st.sbuf + l), ds[0]);
+            if (sol) dp[0] = fma(vv, ldcg(st.pbuf + l), dp[0]);
+        }
+        const double s_tot = warp_sum((ds[0] + ds[1]) + (ds[2] + ds[3]));
+        const double p_tot = warp_sum((dp[0] + dp[1]) + (dp[2] + dp[3]));
+        if (lane == 0) { st.us[j] = s_tot * inv_r; st.up[j] = p_tot * pmul; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[3] = globaltimer();
@@ -161,15 +183,20 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     // ---- phase 2: u2 = T(0:i, 0:i)^T u   (warp per column of T)
     for (int j = gwarp; j < i; j += nwarps) {
         const double* t = st.T + (size_t)j * mm;
-        double ds = 0.0, dp = 0.0;
-#pragma unroll 4
-        for (int l = lane; l <= j; l += 32) {
+        double ds = 0.0, dp = 0.0, ds1 = 0.0, dp1 = 0.0;
+        int l = lane;
+        for (; l + 32 <= j; l += 64) {
+            const double t0 = t[l], t1 = t[l + 32];
+            if (app) { ds = fma(t0, ldcg(st.us + l), ds); ds1 = fma(t1, ldcg(st.us + l + 32), ds1); }
+            if (sol) { dp = fma(t0, ldcg(st.up + l), dp); dp1 = fma(t1, ldcg(st.up + l + 32), dp1); }
+        }
+        if (l <= j) {
             const double tv = t[l];
             if (app) ds = fma(tv, ldcg(st.us + l), ds);
             if (sol) dp = fma(tv, ldcg(st.up + l), dp);
         }
-        ds = warp_sum(ds);
-        dp = warp_sum(dp);
+        ds = warp_sum(ds + ds1);
+        dp = warp_sum(dp + dp1);
         if (lane == 0) { st.u2s[j] = ds; st.u2p[j] = dp; }
     }
     if (!grid_barrier(ctl)) return;
@@ -185,16 +212,24 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         const int l = rb * LT + tid;
         const int j0 = c * cj, j1 = min(i, j0 + cj);
         if (l < krows) {
-            double as = 0.0, ap = 0.0;
+            double as[4] = {0.0, 0.0, 0.0, 0.0}, ap[4] = {0.0, 0.0, 0.0, 0.0};
             const int jend = min(j1, l + 1);
-#pragma unroll 4
-            for (int j = j0; j < jend; ++j) {
-                const double vv = st.V[(size_t)j * k + l];
-                if (app) as = fma(vv, ldcg(st.u2s + j), as);
-                if (sol) ap = fma(vv, ldcg(st.u2p + j), ap);
+            int j = j0;
+            for (; j + 3 < jend; j += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double vv = st.V[(size_t)(j + q) * k + l];
+                    if (app) as[q] = fma(vv, ldcg(st.u2s + j + q), as[q]);
+                    if (sol) ap[q] = fma(vv, ldcg(st.u2p + j + q), ap[q]);
+                }
             }
-            st.ypart[(size_t)c * k + l] = as;
-            st.ypart[(size_t)(NCH_MAX + c) * k + l] = ap;
+            for (; j < jend; ++j) {
+                const double vv = st.V[(size_t)j * k + l];
+                if (app) as[0] = fma(vv, ldcg(st.u2s + j), as[0]);
+                if (sol) ap[0] = fma(vv, ldcg(st.u2p + j), ap[0]);
+            }
+            st.ypart[(size_t)c * k + l] = (as[0] + as[1]) + (as[2] + as[3]);
+            st.ypart[(size_t)(NCH_MAX + c) * k + l] = (ap[0] + ap[1]) + (ap[2] + ap[3]);
         }
     }
     if (!grid_barrier(ctl)) return;
@@ -202,15 +237,18 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
 
     // ---- phase 3b: y = [s, p] - V u2 (the i existing reflectors applied)
     for (int l = gtid; l < krows; l += nthreads) {
-        double ysl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
-        double ypl = sol ? ldcg(st.pbuf + l) * pmul : 0.0;
-#pragma unroll 8
-        for (int c = 0; c < nch; ++c) {
-            ysl -= ldcg(st.ypart + (size_t)c * k + l);
-            ypl -= ldcg(st.ypart + (size_t)(NCH_MAX + c) * k + l);
+        double cs[NCH_MAX], cp[NCH_MAX];
+#pragma unroll
+        for (int c = 0; c < NCH_MAX; ++c) {
+            cs[c] = c < nch ? ldcg(st.ypart + (size_t)c * k + l) : 0.0;
+            cp[c] = c < nch ? ldcg(st.ypart + (size_t)(NCH_MAX + c) * k + l) : 0.0;
         }
-        st.ys[l] = ysl;
-        st.yp[l] = ypl;
+#pragma unroll
+        for (int h = NCH_MAX / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int c = 0; c < h; ++c) { cs[c] += cs[c + h]; cp[c] += cp[c + h]; }
+        st.ys[l] = (app ? ldcg(st.sbuf + l) * inv_r : 0.0) - cs[0];
+        st.yp[l] = (sol ? ldcg(st.pbuf + l) * pmul : 0.0) - cp[0];
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[6] = globaltimer();
@@ -246,20 +284,28 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
     for (int j = gwarp; j < i; j += nwarps) {          // warp per column
         const double* v = st.V + (size_t)j * k;
-        double zz = 0.0;
-#pragma unroll 4
-        for (int l = i + 1 + lane; l < k; l += 32) zz = fma(v[l], ldcg(st.ys + l), zz);
+        double z4[4] = {0.0, 0.0, 0.0, 0.0};
+        int l = i + 1 + lane;
+        for (; l + 96 < k; l += 128)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) z4[q] = fma(v[l + 32 * q], ldcg(st.ys + l + 32 * q), z4[q]);
+        for (; l < k; l += 32) z4[0] = fma(v[l], ldcg(st.ys + l), z4[0]);
         const double* rr = st.RinvT + (size_t)j * mm;
-        double d1 = 0.0, d2 = 0.0;
-#pragma unroll 4
-        for (int l = j + lane; l < i; l += 32) {
-            const double rv = rr[l];
-            d1 = fma(rv, ldcg(st.ys + l), d1);
-            if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
+        double d1a = 0.0, d1b = 0.0, d2a = 0.0, d2b = 0.0;
+        l = j + lane;
+        for (; l + 32 < i; l += 64) {
+            const double r0 = rr[l], r1 = rr[l + 32];
+            d1a = fma(r0, ldcg(st.ys + l), d1a);
+            d1b = fma(r1, ldcg(st.ys + l + 32), d1b);
+            if (sol) { d2a = fma(r0, ldcg(st.yp + l), d2a); d2b = fma(r1, ldcg(st.yp + l + 32), d2b); }
         }
-        zz = warp_sum(zz);
-        d1 = warp_sum(d1);
-        if (sol) d2 = warp_sum(d2);
+        if (l < i) {
+            d1a = fma(rr[l], ldcg(st.ys + l), d1a);
+            if (sol) d2a = fma(rr[l], ldcg(st.yp + l), d2a);
+        }
+        const double zz = warp_sum((z4[0] + z4[1]) + (z4[2] + z4[3]));
+        const double d1 = warp_sum(d1a + d1b);
+        const double d2 = sol ? warp_sum(d2a + d2b) : 0.0;
         if (lane == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
     }
     if (!grid_barrier(ctl)) return;
@@ -303,11 +349,14 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     for (int j = gwarp; j < i; j += nwarps) {
         // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
         const double* tr = st.TT + (size_t)j * mm;
-        double d = 0.0;
-#pragma unroll 4
-        for (int l = j + lane; l < i; l += 32)
-            d = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), d);
-        d = warp_sum(d);
+        double da = 0.0, db = 0.0;
+        int l = j + lane;
+        for (; l + 32 < i; l += 64) {
+            da = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), da);
+            db = fma(tr[l + 32], st.V[(size_t)(l + 32) * k + i] + vs * ldcg(st.zp + l + 32), db);
+        }
+        if (l < i) da = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), da);
+        const double d = warp_sum(da + db);
         if (lane == 0) {
             const double t = -tau * d;
             st.T[(size_t)i * mm + j] = t;
