@@ -381,11 +381,11 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         if (trace) {
             std::vector<unsigned long long> t(10 * (size_t)m);
             RGS_CUDA(cudaMemcpy(t.data(), h->trace.ptr, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-            double ph[8] = {0};
+            double ph[7] = {0};
             for (int i = 0; i < m; ++i)
-                for (int p = 0; p < 8; ++p) ph[p] += (double)(t[10 * (size_t)i + p + 1] - t[10 * (size_t)i + p]) * 1e-3;
+                for (int p = 0; p < 7; ++p) ph[p] += (double)(t[10 * (size_t)i + p + 1] - t[10 * (size_t)i + p]) * 1e-3;
             std::fprintf(stderr, "[rgs trace] least-squares phase means (us):");
-            for (int p = 0; p < 8; ++p) std::fprintf(stderr, " %.2f", ph[p] / m);
+            for (int p = 0; p < 7; ++p) std::fprintf(stderr, " %.2f", ph[p] / m);
             std::fprintf(stderr, "\n");
         }
         if (ctl[0] != 0)

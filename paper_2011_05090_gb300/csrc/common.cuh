@@ -287,11 +287,10 @@ void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n
 // ls.cu: Householder (compact-WY) least-squares engine for the sketched problems.
 struct LSState {
     int k, mmax;
-    double *V, *T, *TT, *RinvT, *S;
+    double *V, *VT, *T, *TT, *RinvT, *S;   // V column-major k x mmax; VT its row-major copy (ld mmax)
     double *sbuf, *pbuf, *ys, *yp;
     double *us, *up, *u2s, *u2p;
     double *zp, *d1, *d2;   // per-column dots of phase 4
-    double *ypart;          // 2 * NCH_MAX * k
     double *red;            // first-level sums of partial sketches
     double *blk;            // 4 * grid
     double *sigma, *pnorm, *coef;
@@ -315,7 +314,7 @@ struct LSStep {
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
     int s_df, p_df;         // partial sketches stored as double-float pairs (float2) instead of FP64
     int pnorm_idx;          // where to record ||p||
-    unsigned long long* trace;  // optional: 9 timestamps (ns) at the phase boundaries, written by CTA 0
+    unsigned long long* trace;  // optional: 8 timestamps (ns) at the phase boundaries, written by CTA 0
 };
 void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);

@@ -20,19 +20,43 @@ namespace {
 constexpr int LT = 512;        // threads per CTA (one CTA per SM)
 constexpr int NW = LT / 32;    // warps per CTA
 constexpr int GS = 32;         // partial sketches summed per warp in the first reduction level
-constexpr int NCH_MAX = 16;    // column chunks of the V u2 product
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Deterministic totals of the per-CTA values blk[b*stride + off] and blk[b*stride + off + 1],
+// Block-wide sums of N values at once (trees: shuffles within warps, then one warp),
+// identical in every thread; sm holds at least N * (NW + 1) doubles.
+template <int N>
+__device__ __forceinline__ void block_sum_n(double (&v)[N], double* sm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < N; ++q) sm[q * NW + w] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double t = lane < NW ? sm[q * NW + lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) sm[N * NW + q] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
+}
+
+// Deterministic totals of the per-CTA values blk[b*4 + off] and blk[b*4 + off + 1],
 // identical in every CTA; one warp does the FP64 adds and broadcasts through shared memory.
-__device__ double2 grid_total2(const double* blk, int stride, int off, double* sh) {
+__device__ double2 grid_total2(const double* blk, int off, double* sh) {
     __syncthreads();
     if (threadIdx.x < 32) {
         double v0 = 0.0, v1 = 0.0;
         for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-            v0 += ldcg(blk + (size_t)b * stride + off);
-            v1 += ldcg(blk + (size_t)b * stride + off + 1);
+            v0 += ldcg(blk + (size_t)b * 4 + off);
+            v1 += ldcg(blk + (size_t)b * 4 + off + 1);
         }
         v0 = warp_sum(v0);
         v1 = warp_sum(v1);
@@ -44,8 +68,35 @@ __device__ double2 grid_total2(const double* blk, int stride, int off, double* s
     return t;
 }
 
+// Sum of the GS partial sketches of group g at row l (double-float or FP64 partials).
+__device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
+    if (sdf) {
+        const df* d = reinterpret_cast<const df*>(src);
+        df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
+        int b = b0;
+#pragma unroll 4
+        for (; b + 1 < b1; b += 2) {
+            t0 = df_add(t0, d[(size_t)b * k + l]);
+            t1 = df_add(t1, d[(size_t)(b + 1) * k + l]);
+        }
+        if (b < b1) t0 = df_add(t0, d[(size_t)b * k + l]);
+        t0 = df_add(t0, t1);
+        return (double)t0.h + (double)t0.l;
+    }
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int b = b0;
+    for (; b + 3 < b1; b += 4) {
+        v0 += src[(size_t)b * k + l];
+        v1 += src[(size_t)(b + 1) * k + l];
+        v2 += src[(size_t)(b + 2) * k + l];
+        v3 += src[(size_t)(b + 3) * k + l];
+    }
+    for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
+    return (v0 + v1) + (v2 + v3);
+}
+
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
-    __shared__ double sh[NW + 2];
+    __shared__ double sh[3 * (NW + 1) + 2];
     __shared__ double sc[8];
     int* ctl = st.ctl;
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
@@ -60,80 +111,65 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
     if (trace) trace[0] = globaltimer();
 
-    // ---- phase 0a: first reduction level of the partial sketches (warp per 32 rows x GS partials)
-    const int nseg = (k + 31) / 32;
+    // ---- phase 0a: with more than GS partial sketches, a first level sums groups of GS
     const int sgroups = app ? (a.s_nparts + GS - 1) / GS : 0;
     const int pgroups = p_parts ? (a.p_nparts + GS - 1) / GS : 0;
-    for (int it = gwarp; it < nseg * (sgroups + pgroups); it += nwarps) {
-        const int seg = it % nseg, g = it / nseg;
-        const bool is_s = g < sgroups;
-        const int gg = is_s ? g : g - sgroups;
-        const double* src = is_s ? a.s_part : a.p_part;
-        const int np = is_s ? a.s_nparts : a.p_nparts;
-        const bool sdf = is_s ? a.s_df != 0 : a.p_df != 0;
-        const int l = seg * 32 + lane;
-        if (l < k) {
-            const int b0 = gg * GS, b1 = min(np, b0 + GS);
-            double v = 0.0;
-            if (sdf) {       // double-float partials: summed in FP32 pairs, converted once
-                const df* d = reinterpret_cast<const df*>(src);
-                df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
-                int b = b0;
-#pragma unroll 4
-                for (; b + 1 < b1; b += 2) {
-                    t0 = df_add(t0, d[(size_t)b * k + l]);
-                    t1 = df_add(t1, d[(size_t)(b + 1) * k + l]);
-                }
-                if (b < b1) t0 = df_add(t0, d[(size_t)b * k + l]);
-                t0 = df_add(t0, t1);
-                v = (double)t0.h + (double)t0.l;
-            } else {
-                double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-                int b = b0;
-                for (; b + 3 < b1; b += 4) {
-                    v0 += src[(size_t)b * k + l];
-                    v1 += src[(size_t)(b + 1) * k + l];
-                    v2 += src[(size_t)(b + 2) * k + l];
-                    v3 += src[(size_t)(b + 3) * k + l];
-                }
-                for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
-                v = (v0 + v1) + (v2 + v3);
-            }
-            st.red[(size_t)g * k + l] = v;
+    const bool level1 = sgroups > 1 || pgroups > 1;
+    if (level1) {
+        const int nseg = (k + 31) / 32;
+        for (int it = gwarp; it < nseg * (sgroups + pgroups); it += nwarps) {
+            const int seg = it % nseg, g = it / nseg;
+            const bool is_s = g < sgroups;
+            const int gg = is_s ? g : g - sgroups;
+            const int np = is_s ? a.s_nparts : a.p_nparts;
+            const int l = seg * 32 + lane;
+            if (l < k)
+                st.red[(size_t)g * k + l] = group_sum(is_s ? a.s_part : a.p_part, is_s ? a.s_df : a.p_df,
+                                                      gg * GS, min(np, gg * GS + GS), k, l);
         }
+        if (!grid_barrier(ctl)) return;
     }
-    if (!grid_barrier(ctl)) return;
     if (trace) trace[1] = globaltimer();
 
-    // ---- phase 0b: second level (warp per row, lanes over groups): s', p and their norms
-    double ss = 0.0, pp = 0.0;
-    for (int l = gwarp; l < k; l += nwarps) {
-        if (app) {
-            double v = 0.0;
-            for (int g = lane; g < sgroups; g += 32) v += ldcg(st.red + (size_t)g * k + l);
-            v = warp_sum(v) * a.s_scale;
-            if (lane == 0) { st.sbuf[l] = v; ss = fma(v, v, ss); }
-        }
-        if (sol) {
-            double v = 0.0;
-            if (p_parts) {
-                for (int g = lane; g < pgroups; g += 32) v += ldcg(st.red + (size_t)(sgroups + g) * k + l);
-                v = warp_sum(v);
-            } else {
-                v = a.p_vec[l];
+    // ---- phase 0b: warp per row, lanes over groups (or partials): s', p and their squared norms
+    {
+        double nrm[2] = {0.0, 0.0};
+        for (int l = gwarp; l < k; l += nwarps) {
+            if (app) {
+                double v = 0.0;
+                if (level1) {
+                    for (int g = lane; g < sgroups; g += 32) v += ldcg(st.red + (size_t)g * k + l);
+                } else if (lane < a.s_nparts) {
+                    v = a.s_df ? (double)reinterpret_cast<const df*>(a.s_part)[(size_t)lane * k + l].h +
+                                     (double)reinterpret_cast<const df*>(a.s_part)[(size_t)lane * k + l].l
+                               : a.s_part[(size_t)lane * k + l];
+                }
+                v = warp_sum(v) * a.s_scale;
+                if (lane == 0) { st.sbuf[l] = v; nrm[0] = fma(v, v, nrm[0]); }
             }
-            v *= a.p_scale;
-            if (lane == 0) { st.pbuf[l] = v; pp = fma(v, v, pp); }
+            if (sol) {
+                double v = 0.0;
+                if (!p_parts) {
+                    v = lane == 0 ? a.p_vec[l] : 0.0;
+                } else if (level1) {
+                    for (int g = lane; g < pgroups; g += 32) v += ldcg(st.red + (size_t)(sgroups + g) * k + l);
+                } else if (lane < a.p_nparts) {
+                    v = a.p_df ? (double)reinterpret_cast<const df*>(a.p_part)[(size_t)lane * k + l].h +
+                                     (double)reinterpret_cast<const df*>(a.p_part)[(size_t)lane * k + l].l
+                               : a.p_part[(size_t)lane * k + l];
+                }
+                v = warp_sum(v) * a.p_scale;
+                if (lane == 0) { st.pbuf[l] = v; nrm[1] = fma(v, v, nrm[1]); }
+            }
         }
+        block_sum_n<2>(nrm, sh);
+        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm[0]; st.blk[blockIdx.x * 4 + 1] = nrm[1]; }
     }
-    ss = block_sum<LT>(ss, sh);
-    pp = block_sum<LT>(pp, sh);
-    if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = ss; st.blk[blockIdx.x * 4 + 1] = pp; }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
-    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (warp per column)
-    const double2 tot01 = grid_total2(st.blk, 4, 0, sh);
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (CTA per column)
+    const double2 tot01 = grid_total2(st.blk, 0, sh);
     const double r = sqrt(tot01.x);
     const double pn = sqrt(tot01.y);
     double inv_r = 1.0, pmul = 1.0;
@@ -156,26 +192,17 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
-    for (int j = gwarp; j < i; j += nwarps) {          // warp per column of V
+    for (int j = blockIdx.x; j < i; j += G) {
         const double* v = st.V + (size_t)j * k;
-        double ds[4] = {0.0, 0.0, 0.0, 0.0}, dp[4] = {0.0, 0.0, 0.0, 0.0};
-        int l = j + lane;
-        for (; l + 96 < k; l += 128) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const double vv = v[l + 32 * q];
-                if (app) ds[q] = fma(vv, ldcg(st.sbuf + l + 32 * q), ds[q]);
-                if (sol) dp[q] = fma(vv, ldcg(st.pbuf + l + 32 * q), dp[q]);
-            }
-        }
-        for (; l < k; l += 32) {
+        double acc[2] = {0.0, 0.0};
+#pragma unroll 4
+        for (int l = j + tid; l < k; l += LT) {
             const double vv = v[l];
-            if (app) ds[0] = fma(vv, ldcg(st.sbuf + l), ds[0]);
-            if (sol) dp[0] = fma(vv, ldcg(st.pbuf + l), dp[0]);
+            if (app) acc[0] = fma(vv, ldcg(st.sbuf + l), acc[0]);
+            if (sol) acc[1] = fma(vv, ldcg(st.pbuf + l), acc[1]);
         }
-        const double s_tot = warp_sum((ds[0] + ds[1]) + (ds[2] + ds[3]));
-        const double p_tot = warp_sum((dp[0] + dp[1]) + (dp[2] + dp[3]));
-        if (lane == 0) { st.us[j] = s_tot * inv_r; st.up[j] = p_tot * pmul; }
+        block_sum_n<2>(acc, sh);
+        if (tid == 0) { st.us[j] = acc[0] * inv_r; st.up[j] = acc[1] * pmul; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[3] = globaltimer();
@@ -202,117 +229,86 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (!grid_barrier(ctl)) return;
     if (trace) trace[4] = globaltimer();
 
-    // ---- phase 3: partial sums of V(:, 0:i) u2 over at most NCH_MAX column chunks
+    // ---- phase 3: y = [s, p] - V u2 (the i reflectors applied), warp per row using the
+    //      row-major copy VT of V; plus the sums the new reflector needs over rows > i
     const int krows = app ? k : i;                 // a pure solve needs rows 0..i-1 only
-    const int nrb = (krows + LT - 1) / LT;
-    const int cj = i > 0 ? max(8, (i + NCH_MAX - 1) / NCH_MAX) : 8;
-    const int nch = i > 0 ? (i + cj - 1) / cj : 0;
-    for (int item = blockIdx.x; item < nrb * nch; item += G) {
-        const int rb = item % nrb, c = item / nrb;
-        const int l = rb * LT + tid;
-        const int j0 = c * cj, j1 = min(i, j0 + cj);
-        if (l < krows) {
+    {
+        double sums[2] = {0.0, 0.0};
+        for (int l = gwarp; l < krows; l += nwarps) {
+            const double* vr = st.VT + (size_t)l * mm;
+            const int jend = min(i, l + 1);
             double as[4] = {0.0, 0.0, 0.0, 0.0}, ap[4] = {0.0, 0.0, 0.0, 0.0};
-            const int jend = min(j1, l + 1);
-            int j = j0;
-            for (; j + 3 < jend; j += 4) {
+            int j = lane;
+            for (; j + 96 < jend; j += 128)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const double vv = st.V[(size_t)(j + q) * k + l];
-                    if (app) as[q] = fma(vv, ldcg(st.u2s + j + q), as[q]);
-                    if (sol) ap[q] = fma(vv, ldcg(st.u2p + j + q), ap[q]);
+                    const double vv = vr[j + 32 * q];
+                    if (app) as[q] = fma(vv, ldcg(st.u2s + j + 32 * q), as[q]);
+                    if (sol) ap[q] = fma(vv, ldcg(st.u2p + j + 32 * q), ap[q]);
                 }
-            }
-            for (; j < jend; ++j) {
-                const double vv = st.V[(size_t)j * k + l];
+            for (; j < jend; j += 32) {
+                const double vv = vr[j];
                 if (app) as[0] = fma(vv, ldcg(st.u2s + j), as[0]);
                 if (sol) ap[0] = fma(vv, ldcg(st.u2p + j), ap[0]);
             }
-            st.ypart[(size_t)c * k + l] = (as[0] + as[1]) + (as[2] + as[3]);
-            st.ypart[(size_t)(NCH_MAX + c) * k + l] = (ap[0] + ap[1]) + (ap[2] + ap[3]);
+            const double ws = warp_sum((as[0] + as[1]) + (as[2] + as[3]));
+            const double wp = warp_sum((ap[0] + ap[1]) + (ap[2] + ap[3]));
+            if (lane == 0) {
+                const double ysl = app ? ldcg(st.sbuf + l) * inv_r - ws : 0.0;
+                const double ypl = sol ? ldcg(st.pbuf + l) * pmul - wp : 0.0;
+                st.ys[l] = ysl;
+                st.yp[l] = ypl;
+                if (app && l > i) { sums[0] = fma(ysl, ysl, sums[0]); sums[1] = fma(ysl, ypl, sums[1]); }
+            }
         }
+        block_sum_n<2>(sums, sh);
+        if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sums[0]; st.blk[blockIdx.x * 4 + 3] = sums[1]; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[5] = globaltimer();
-
-    // ---- phase 3b: y = [s, p] - V u2 (the i existing reflectors applied)
-    for (int l = gtid; l < krows; l += nthreads) {
-        double cs[NCH_MAX], cp[NCH_MAX];
-#pragma unroll
-        for (int c = 0; c < NCH_MAX; ++c) {
-            cs[c] = c < nch ? ldcg(st.ypart + (size_t)c * k + l) : 0.0;
-            cp[c] = c < nch ? ldcg(st.ypart + (size_t)(NCH_MAX + c) * k + l) : 0.0;
-        }
-#pragma unroll
-        for (int h = NCH_MAX / 2; h > 0; h >>= 1)
-#pragma unroll
-            for (int c = 0; c < h; ++c) { cs[c] += cs[c + h]; cp[c] += cp[c + h]; }
-        st.ys[l] = (app ? ldcg(st.sbuf + l) * inv_r : 0.0) - cs[0];
-        st.yp[l] = (sol ? ldcg(st.pbuf + l) * pmul : 0.0) - cp[0];
-    }
-    if (!grid_barrier(ctl)) return;
-    if (trace) trace[6] = globaltimer();
 
     if (!app) {
         // pure solve: x = R_S^{-1} y(0:i); row j of R_S^{-1} is column j of RinvT
         for (int j = gwarp; j < i; j += nwarps) {
             const double* rr = st.RinvT + (size_t)j * mm;
-            double d = 0.0;
-#pragma unroll 4
-            for (int l = j + lane; l < i; l += 32) d = fma(rr[l], ldcg(st.yp + l), d);
-            d = warp_sum(d);
+            double da = 0.0, db = 0.0;
+            int l = j + lane;
+            for (; l + 32 < i; l += 64) {
+                da = fma(rr[l], ldcg(st.yp + l), da);
+                db = fma(rr[l + 32], ldcg(st.yp + l + 32), db);
+            }
+            if (l < i) da = fma(rr[l], ldcg(st.yp + l), da);
+            const double d = warp_sum(da + db);
             if (lane == 0) {
                 st.R[(size_t)a.xcol * st.ldr + j] = d;
                 st.coef[j] = d * st.sigma[j];
             }
         }
-        if (trace) trace[8] = globaltimer();
+        if (trace) { trace[6] = globaltimer(); trace[7] = trace[6]; }
         return;
     }
 
-    // ---- phase 4: everything the new reflector needs that does not depend on beta
-    //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp,
-    //   and the global sums sg = sum_{l>i} ys_l^2, cr = sum_{l>i} ys_l yp_l
-    double sg = 0.0, cr = 0.0;
-    for (int l = i + 1 + gtid; l < k; l += nthreads) {
-        const double y = ldcg(st.ys + l);
-        sg = fma(y, y, sg);
-        if (sol) cr = fma(y, ldcg(st.yp + l), cr);
-    }
-    sg = block_sum<LT>(sg, sh);
-    cr = block_sum<LT>(cr, sh);
-    if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sg; st.blk[blockIdx.x * 4 + 3] = cr; }
-    for (int j = gwarp; j < i; j += nwarps) {          // warp per column
+    // ---- phase 4: per column j < i, the dots the new reflector needs that do not depend on beta:
+    //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
+    for (int j = blockIdx.x; j < i; j += G) {
         const double* v = st.V + (size_t)j * k;
-        double z4[4] = {0.0, 0.0, 0.0, 0.0};
-        int l = i + 1 + lane;
-        for (; l + 96 < k; l += 128)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) z4[q] = fma(v[l + 32 * q], ldcg(st.ys + l + 32 * q), z4[q]);
-        for (; l < k; l += 32) z4[0] = fma(v[l], ldcg(st.ys + l), z4[0]);
         const double* rr = st.RinvT + (size_t)j * mm;
-        double d1a = 0.0, d1b = 0.0, d2a = 0.0, d2b = 0.0;
-        l = j + lane;
-        for (; l + 32 < i; l += 64) {
-            const double r0 = rr[l], r1 = rr[l + 32];
-            d1a = fma(r0, ldcg(st.ys + l), d1a);
-            d1b = fma(r1, ldcg(st.ys + l + 32), d1b);
-            if (sol) { d2a = fma(r0, ldcg(st.yp + l), d2a); d2b = fma(r1, ldcg(st.yp + l + 32), d2b); }
+        double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+        for (int l = i + 1 + tid; l < k; l += LT) acc[0] = fma(v[l], ldcg(st.ys + l), acc[0]);
+        for (int l = j + tid; l < i; l += LT) {
+            const double rv = rr[l];
+            acc[1] = fma(rv, ldcg(st.ys + l), acc[1]);
+            if (sol) acc[2] = fma(rv, ldcg(st.yp + l), acc[2]);
         }
-        if (l < i) {
-            d1a = fma(rr[l], ldcg(st.ys + l), d1a);
-            if (sol) d2a = fma(rr[l], ldcg(st.yp + l), d2a);
-        }
-        const double zz = warp_sum((z4[0] + z4[1]) + (z4[2] + z4[3]));
-        const double d1 = warp_sum(d1a + d1b);
-        const double d2 = sol ? warp_sum(d2a + d2b) : 0.0;
-        if (lane == 0) { st.zp[j] = zz; st.d1[j] = d1; st.d2[j] = d2; }
+        block_sum_n<3>(acc, sh);
+        if (tid == 0) { st.zp[j] = acc[0]; st.d1[j] = acc[1]; st.d2[j] = acc[2]; }
     }
     if (!grid_barrier(ctl)) return;
-    if (trace) trace[7] = globaltimer();
+    if (trace) trace[6] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    const double2 tot23 = grid_total2(st.blk, 4, 2, sh);
+    const double2 tot23 = grid_total2(st.blk, 2, sh);
     const double SG = tot23.x, CR = tot23.y;
     if (tid == 0) {
         const double alpha = ldcg(st.ys + i);
@@ -334,8 +330,11 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
         return;
     }
-    for (int l = gtid; l < k; l += nthreads)
-        st.V[(size_t)i * k + l] = l < i ? 0.0 : (l == i ? 1.0 : ldcg(st.ys + l) * vs);
+    for (int l = gtid; l < k; l += nthreads) {
+        const double vl = l < i ? 0.0 : (l == i ? 1.0 : ldcg(st.ys + l) * vs);
+        st.V[(size_t)i * k + l] = vl;
+        if (l >= i) st.VT[(size_t)l * mm + i] = vl;
+    }
     if (gtid == 0) {
         st.T[(size_t)i * mm + i] = tau;
         st.TT[(size_t)i * mm + i] = tau;
@@ -346,16 +345,17 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             st.coef[i] = xi * inv_r;
         }
     }
+    const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
     for (int j = gwarp; j < i; j += nwarps) {
         // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
         const double* tr = st.TT + (size_t)j * mm;
         double da = 0.0, db = 0.0;
         int l = j + lane;
         for (; l + 32 < i; l += 64) {
-            da = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), da);
-            db = fma(tr[l + 32], st.V[(size_t)(l + 32) * k + i] + vs * ldcg(st.zp + l + 32), db);
+            da = fma(tr[l], vrow_i[l] + vs * ldcg(st.zp + l), da);
+            db = fma(tr[l + 32], vrow_i[l + 32] + vs * ldcg(st.zp + l + 32), db);
         }
-        if (l < i) da = fma(tr[l], st.V[(size_t)l * k + i] + vs * ldcg(st.zp + l), da);
+        if (l < i) da = fma(tr[l], vrow_i[l] + vs * ldcg(st.zp + l), da);
         const double d = warp_sum(da + db);
         if (lane == 0) {
             const double t = -tau * d;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
         }
     }
-    if (trace) trace[8] = globaltimer();
+    if (trace) trace[7] = globaltimer();
 }
 
 // Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
@@ -417,26 +417,27 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState
     const int groups = 2 * ((std::max(max_parts, 1) + GS - 1) / GS);
     size_t n = 0;
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
-    const size_t oV = take((size_t)k * mmax), oT = take((size_t)mmax * mmax), oTT = take((size_t)mmax * mmax),
-                 oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax), osb = take(k), opb = take(k),
-                 oys = take(k), oyp = take(k), ous = take(mmax), oup = take(mmax), ou2s = take(mmax),
-                 ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
-                 oyr = take((size_t)2 * NCH_MAX * k), ored = take((size_t)groups * k), oblk = take((size_t)4 * grid),
-                 osg = take(mmax + 1), opn = take(mmax + 2), oco = take(mmax + 1);
+    const size_t oV = take((size_t)k * mmax), oVT = take((size_t)k * mmax), oT = take((size_t)mmax * mmax),
+                 oTT = take((size_t)mmax * mmax), oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax),
+                 osb = take(k), opb = take(k), oys = take(k), oyp = take(k), ous = take(mmax), oup = take(mmax),
+                 ou2s = take(mmax), ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
+                 ored = take((size_t)groups * k), oblk = take((size_t)4 * grid), osg = take(mmax + 1),
+                 opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
     double* b = buf.as<double>();
     st->k = k; st->mmax = mmax; st->max_parts = max_parts;
-    st->V = b + oV; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
+    st->V = b + oV; st->VT = b + oVT; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
     st->us = b + ous; st->up = b + oup; st->u2s = b + ou2s; st->u2p = b + ou2p;
     st->zp = b + ozp; st->d1 = b + od1; st->d2 = b + od2;
-    st->ypart = b + oyr; st->red = b + ored; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
+    st->red = b + ored; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
     st->coef = b + oco;
 }
 
 // Zero the factorisation (V must be zero above each reflector's diagonal; T, R_S^{-1} upper parts).
 void rgs_ls_reset(rgs_context* ctx, const LSState& st) {
     RGS_CUDA(cudaMemsetAsync(st.V, 0, sizeof(double) * (size_t)st.k * st.mmax, ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.VT, 0, sizeof(double) * (size_t)st.k * st.mmax, ctx->stream));
     RGS_CUDA(cudaMemsetAsync(st.T, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
     RGS_CUDA(cudaMemsetAsync(st.TT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
     RGS_CUDA(cudaMemsetAsync(st.RinvT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
