@@ -20,13 +20,42 @@ constexpr int LOG_TILE = 10;
 constexpr int UT = 256;      // threads per CTA, 4 consecutive rows each
 constexpr int UNROLL = 8;    // basis columns loaded ahead
 
+// Streaming loads of the basis and of w: they are read once per column step and would
+// otherwise evict the least-squares factors (V, T, S: a few tens of MB) from L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ float4 ld_stream_f4(const void* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream_d2(const void* p, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const void* p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
 template <typename TQ> struct QIO;
 
 template <> struct QIO<double> {
     using Acc = double;
-    __device__ static void load4(const double* p, double v[4]) {
-        double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    __device__ static void load4(const double* p, double v[4], uint64_t pol) {
+        double2 a = ld_stream_d2(p, pol);
+        double2 b = ld_stream_d2(p + 2, pol);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
     __device__ static void store4(double* p, const double v[4]) {
@@ -40,8 +69,8 @@ template <> struct QIO<double> {
 
 template <> struct QIO<float> {
     using Acc = float;
-    __device__ static void load4(const float* p, float v[4]) {
-        float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    __device__ static void load4(const float* p, float v[4], uint64_t pol) {
+        float4 a = ld_stream_f4(p, pol);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
     __device__ static void store4(float* p, const float v[4]) {
@@ -54,8 +83,8 @@ template <> struct QIO<float> {
 
 template <> struct QIO<__nv_bfloat16> {
     using Acc = float;
-    __device__ static void load4(const __nv_bfloat16* p, float v[4]) {
-        uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+    __device__ static void load4(const __nv_bfloat16* p, float v[4], uint64_t pol) {
+        uint2 a = ld_stream_u2(p, pol);
         __nv_bfloat162 x = *reinterpret_cast<__nv_bfloat162*>(&a.x);
         __nv_bfloat162 y = *reinterpret_cast<__nv_bfloat162*>(&a.y);
         float2 fx = __bfloat1622float2(x), fy = __bfloat1622float2(y);
@@ -185,6 +214,7 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     const TQ* Q = reinterpret_cast<const TQ*>(p.Q);
     TQ* qout = reinterpret_cast<TQ*>(p.qout);
     const int64_t n = p.n;
+    const uint64_t pol = evict_first_policy();
 
     for (int j = threadIdx.x; j < p.ncols; j += UT) sc[j] = (Acc)p.coef[j];
     if (SRHT)
@@ -196,15 +226,15 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
         const bool full = p.vec && (r0 + 4 <= n);
         Acc acc[4];
         if (full) {
-            double2 a = __ldg(reinterpret_cast<const double2*>(w + r0));
-            double2 b = __ldg(reinterpret_cast<const double2*>(w + r0 + 2));
+            double2 a = ld_stream_d2(w + r0, pol);
+            double2 b = ld_stream_d2(w + r0 + 2, pol);
             if (p.wscale) { a.x *= wmul; a.y *= wmul; b.x *= wmul; b.y *= wmul; }
             acc[0] = (Acc)a.x; acc[1] = (Acc)a.y; acc[2] = (Acc)b.x; acc[3] = (Acc)b.y;
             int j = 0;
             for (; j + UNROLL <= p.ncols; j += UNROLL) {
                 Acc q[UNROLL][4];
 #pragma unroll
-                for (int u = 0; u < UNROLL; ++u) IO::load4(Q + (int64_t)(j + u) * p.ldq + r0, q[u]);
+                for (int u = 0; u < UNROLL; ++u) IO::load4(Q + (int64_t)(j + u) * p.ldq + r0, q[u], pol);
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
                     const Acc c = sc[j + u];
@@ -214,7 +244,7 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
             }
             for (; j < p.ncols; ++j) {
                 Acc q[4];
-                IO::load4(Q + (int64_t)j * p.ldq + r0, q);
+                IO::load4(Q + (int64_t)j * p.ldq + r0, q, pol);
                 const Acc c = sc[j];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[e] = fma(-c, q[e], acc[e]);
