@@ -48,6 +48,29 @@ __device__ __forceinline__ void block_sum_n(double (&v)[N], double* sm) {
     for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
 }
 
+// Block-wide sums of N values held by lane 0 of each warp (other lanes ignored): one warp
+// adds the NW per-warp values, so only NW/32-wide FP64 work is spent on the reduction.
+template <int N>
+__device__ __forceinline__ void block_sum_lane0(double (&v)[N], double* sm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < N; ++q) sm[q * NW + w] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            double t = lane < NW ? sm[q * NW + lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) sm[N * NW + q] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
+}
+
 // Deterministic totals of the per-CTA values blk[b*4 + off] and blk[b*4 + off + 1],
 // identical in every CTA; one warp does the FP64 adds and broadcasts through shared memory.
 __device__ double2 grid_total2(const double* blk, int off, double* sh) {
@@ -96,7 +119,7 @@ __device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0,
 }
 
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
-    __shared__ double sh[3 * (NW + 1) + 2];
+    __shared__ double sh[3 * (NW + 1) + 2 + 3 * NW];
     __shared__ double sc[8];
     int* ctl = st.ctl;
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
@@ -162,13 +185,13 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 if (lane == 0) { st.pbuf[l] = v; nrm[1] = fma(v, v, nrm[1]); }
             }
         }
-        block_sum_n<2>(nrm, sh);
+        block_sum_lane0<2>(nrm, sh);
         if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm[0]; st.blk[blockIdx.x * 4 + 1] = nrm[1]; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
-    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p] (CTA per column)
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p]
     const double2 tot01 = grid_total2(st.blk, 0, sh);
     const double r = sqrt(tot01.x);
     const double pn = sqrt(tot01.y);
@@ -192,17 +215,35 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
-    for (int j = blockIdx.x; j < i; j += G) {
-        const double* v = st.V + (size_t)j * k;
-        double acc[2] = {0.0, 0.0};
+    {
+        // a quad of warps (one per SM sub-partition) per column; each warp a quarter of the rows
+        const int quad = tid >> 7, qw = (tid >> 5) & 3;
+        double* qs = sh + 3 * (NW + 1) + 2;                // [NW/4 quads][4 warps][2]
+        for (int base = 0; base < i; base += G * (NW / 4)) {
+            const int j = base + blockIdx.x + G * quad;
+            double ds = 0.0, dp = 0.0;
+            if (j < i) {
+                const double* v = st.V + (size_t)j * k;
+                const int len = k - j, seg = (len + 3) / 4;
+                const int l0 = j + qw * seg, l1 = min(k, l0 + seg);
 #pragma unroll 4
-        for (int l = j + tid; l < k; l += LT) {
-            const double vv = v[l];
-            if (app) acc[0] = fma(vv, ldcg(st.sbuf + l), acc[0]);
-            if (sol) acc[1] = fma(vv, ldcg(st.pbuf + l), acc[1]);
+                for (int l = l0 + lane; l < l1; l += 32) {
+                    const double vv = v[l];
+                    if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
+                    if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
+                }
+                ds = warp_sum(ds);
+                dp = warp_sum(dp);
+                if (lane == 0) { qs[(quad * 4 + qw) * 2] = ds; qs[(quad * 4 + qw) * 2 + 1] = dp; }
+            }
+            __syncthreads();
+            if (j < i && qw == 0 && lane == 0) {
+                const double* q4 = qs + quad * 8;
+                st.us[j] = ((q4[0] + q4[2]) + (q4[4] + q4[6])) * inv_r;
+                st.up[j] = ((q4[1] + q4[3]) + (q4[5] + q4[7])) * pmul;
+            }
+            __syncthreads();
         }
-        block_sum_n<2>(acc, sh);
-        if (tid == 0) { st.us[j] = acc[0] * inv_r; st.up[j] = acc[1] * pmul; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[3] = globaltimer();
@@ -261,7 +302,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 if (app && l > i) { sums[0] = fma(ysl, ysl, sums[0]); sums[1] = fma(ysl, ypl, sums[1]); }
             }
         }
-        block_sum_n<2>(sums, sh);
+        block_sum_lane0<2>(sums, sh);
         if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sums[0]; st.blk[blockIdx.x * 4 + 3] = sums[1]; }
     }
     if (!grid_barrier(ctl)) return;
@@ -290,19 +331,44 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
 
     // ---- phase 4: per column j < i, the dots the new reflector needs that do not depend on beta:
     //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
-    for (int j = blockIdx.x; j < i; j += G) {
-        const double* v = st.V + (size_t)j * k;
-        const double* rr = st.RinvT + (size_t)j * mm;
-        double acc[3] = {0.0, 0.0, 0.0};
+    {
+        const int quad = tid >> 7, qw = (tid >> 5) & 3;
+        double* qs = sh + 3 * (NW + 1) + 2;                // [NW/4 quads][4 warps][3]
+        for (int base = 0; base < i; base += G * (NW / 4)) {
+            const int j = base + blockIdx.x + G * quad;
+            double z = 0.0, d1 = 0.0, d2 = 0.0;
+            if (j < i) {
+                const double* v = st.V + (size_t)j * k;
+                const int len = k - (i + 1), seg = (max(len, 0) + 3) / 4;
+                const int l0 = i + 1 + qw * seg, l1 = min(k, l0 + seg);
 #pragma unroll 4
-        for (int l = i + 1 + tid; l < k; l += LT) acc[0] = fma(v[l], ldcg(st.ys + l), acc[0]);
-        for (int l = j + tid; l < i; l += LT) {
-            const double rv = rr[l];
-            acc[1] = fma(rv, ldcg(st.ys + l), acc[1]);
-            if (sol) acc[2] = fma(rv, ldcg(st.yp + l), acc[2]);
+                for (int l = l0 + lane; l < l1; l += 32) z = fma(v[l], ldcg(st.ys + l), z);
+                const double* rr = st.RinvT + (size_t)j * mm;       // row j of R_S^{-1}
+                const int rlen = i - j, rseg = (rlen + 3) / 4;
+                const int r0 = j + qw * rseg, r1 = min(i, r0 + rseg);
+                for (int l = r0 + lane; l < r1; l += 32) {
+                    const double rv = rr[l];
+                    d1 = fma(rv, ldcg(st.ys + l), d1);
+                    if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
+                }
+                z = warp_sum(z);
+                d1 = warp_sum(d1);
+                if (sol) d2 = warp_sum(d2);
+                if (lane == 0) {
+                    qs[(quad * 4 + qw) * 3] = z;
+                    qs[(quad * 4 + qw) * 3 + 1] = d1;
+                    qs[(quad * 4 + qw) * 3 + 2] = d2;
+                }
+            }
+            __syncthreads();
+            if (j < i && qw == 0 && lane == 0) {
+                const double* q4 = qs + quad * 12;
+                st.zp[j] = (q4[0] + q4[3]) + (q4[6] + q4[9]);
+                st.d1[j] = (q4[1] + q4[4]) + (q4[7] + q4[10]);
+                st.d2[j] = (q4[2] + q4[5]) + (q4[8] + q4[11]);
+            }
+            __syncthreads();
         }
-        block_sum_n<3>(acc, sh);
-        if (tid == 0) { st.zp[j] = acc[0]; st.d1[j] = acc[1]; st.d2[j] = acc[2]; }
     }
     if (!grid_barrier(ctl)) return;
     if (trace) trace[6] = globaltimer();
