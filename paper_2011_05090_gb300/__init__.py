@@ -225,3 +225,113 @@ def rgs_qr(h, sk, W, Q, R, qscale=None, S=None, flags=0):
 def csr_struct(rowptr, colind, val):
     n = rowptr.numel() - 1
     return CSR(n, colind.numel(), rowptr.data_ptr(), colind.data_ptr(), val.data_ptr())
+
+
+class Arnoldi:
+    def __init__(self, ptr, handle, sketch, n, mmax, qdtype):
+        self.ptr, self.handle, self.sketch, self.n, self.mmax, self.qdtype = ptr, handle, sketch, n, mmax, qdtype
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.rgs_arnoldi_destroy(self.ptr)
+            self.ptr = None
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ wrapper so torch can view library-owned device memory."""
+
+    def __init__(self, ptr, shape, strides, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "strides": strides, "typestr": typestr,
+                                         "data": (ptr, False), "version": 2}
+
+
+def rgs_arnoldi_create(h, sk, n, mmax, qdtype=torch.float64):
+    out = ctypes.c_void_p()
+    _check(load().rgs_arnoldi_create(h.ptr, sk.ptr, int(n), int(mmax), _DTYPE[qdtype], ctypes.byref(out)), h)
+    return Arnoldi(out.value, h, sk, int(n), int(mmax), qdtype)
+
+
+def rgs_arnoldi_start(h, a, w1):
+    _check(load().rgs_arnoldi_start(h.ptr, a.ptr, w1.data_ptr()), h)
+
+
+def rgs_arnoldi_step(h, a, csr=None, w=None):
+    A = ctypes.byref(csr) if csr is not None else None
+    _check(load().rgs_arnoldi_step(h.ptr, a.ptr, A, w.data_ptr() if w is not None else None), h)
+
+
+def rgs_arnoldi_get(h, a):
+    """(ncols, R (ncols x ncols, numpy), qscale (ncols, numpy)) copied to the host."""
+    import numpy as np
+    nc = ctypes.c_int32()
+    _check(load().rgs_arnoldi_get(h.ptr, a.ptr, ctypes.byref(nc), None, 0, None), h)
+    m = nc.value
+    R = np.zeros((m, m), order="F")
+    qs = np.zeros(m)
+    if m:
+        _check(load().rgs_arnoldi_get(h.ptr, a.ptr, ctypes.byref(nc), R.ctypes.data_as(ctypes.c_void_p), m,
+                                      qs.ctypes.data_as(ctypes.c_void_p)), h)
+    return m, R, qs
+
+
+def rgs_arnoldi_basis(a, ncols=None):
+    """The stored basis Q' (n x ncols, column-major, in the object's dtype) as a torch view."""
+    q = ctypes.c_void_p()
+    ld = ctypes.c_int64()
+    _check(load().rgs_arnoldi_basis(a.ptr, ctypes.byref(q), ctypes.byref(ld)))
+    ncols = a.mmax if ncols is None else ncols
+    esz = {torch.float64: 8, torch.float32: 4, torch.bfloat16: 2}[a.qdtype]
+    typestr = {torch.float64: "<f8", torch.float32: "<f4", torch.bfloat16: "<V2"}[a.qdtype]
+    arr = _DeviceArray(q.value, (ncols, a.n), (ld.value * esz, esz), typestr)
+    if a.qdtype == torch.bfloat16:
+        raw = torch.as_tensor(_DeviceArray(q.value, (ncols, a.n), (ld.value * 2, 2), "<i2"), device="cuda")
+        return raw.view(torch.bfloat16).T
+    return torch.as_tensor(arr, device="cuda").T
+
+
+def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps):
+    return GmresOpts(int(restart), int(max_cycles), float(rtol), float(inner_factor), _DTYPE[qdtype],
+                     1 if fixed_steps else 0, 0)
+
+
+def _gmres_result(st, info, hist, h):
+    res = {"cycles": info.cycles, "total_steps": info.total_steps, "converged": bool(info.converged),
+           "status": info.status, "rel_residual": info.rel_residual,
+           "history": [hist[i] for i in range(info.cycles + 1)]}
+    if st not in (RGS_OK, RGS_ERR_NOT_CONVERGED):
+        try:
+            _check(st, h)
+        except RgsError as e:
+            e.info = res
+            raise
+    return res
+
+
+def rgmres_solve(h, sk, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_factor=0.5,
+                 qdtype=torch.float32, fixed_steps=False):
+    """Restarted randomized GMRES; x (FP64, CUDA) holds x0 and receives the solution."""
+    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps)
+    hist = (ctypes.c_double * (max_cycles + 2))()
+    info = GmresInfo()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    st = load().rgmres_solve(h.ptr, sk.ptr, ctypes.byref(csr), b.data_ptr(), x.data_ptr(), ctypes.byref(opts),
+                             ctypes.byref(info))
+    return _gmres_result(st, info, hist, h)
+
+
+def cgs2_gmres_solve(h, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_factor=0.5, fixed_steps=False):
+    """Restarted FP64 GMRES with a CGS2 Arnoldi basis (the comparator)."""
+    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, torch.float64, fixed_steps)
+    hist = (ctypes.c_double * (max_cycles + 2))()
+    info = GmresInfo()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    st = load().cgs2_gmres_solve(h.ptr, ctypes.byref(csr), b.data_ptr(), x.data_ptr(), ctypes.byref(opts),
+                                 ctypes.byref(info))
+    return _gmres_result(st, info, hist, h)
+
+
+def csr_to_device(rowptr, colind, val, device="cuda"):
+    """Device copies of CSR arrays (int32, int32, FP64) and the C struct pointing at them."""
+    t = (torch.as_tensor(rowptr, dtype=torch.int32).to(device), torch.as_tensor(colind, dtype=torch.int32).to(device),
+         torch.as_tensor(val, dtype=torch.float64).to(device))
+    return t, csr_struct(*t)

@@ -127,6 +127,7 @@ namespace rgsdev {
 constexpr int kStatusWord = 0;
 constexpr int kDetailWord = 1;
 constexpr int kStopWord = 5;     // an Arnoldi cycle ended early (convergence or happy breakdown)
+constexpr int kStepsWord = 6;    // Arnoldi steps of the cycle just solved
 // the grid barrier's words sit on separate 128-byte lines so that polling one
 // does not queue behind atomics on another
 constexpr int kBarCount = 32;     // the barrier word
@@ -271,7 +272,8 @@ struct UpdateLaunch {
     const double* w;        // input column(s), FP64, ld ldw between columns
     int64_t ldw;
     int wcols;              // number of input columns (batched sketches; no update when > 1)
-    const double* wscale;   // optional device scalar multiplying w
+    const double* wscale;   // optional device scalar multiplying w (FP64 w only)
+    int w_df;               // w holds double-float pairs (float2) instead of FP64
     const double* coef;     // ncols FP64 coefficients (device)
     void* qout;             // optional stored result column (qtype)
     int df_sketch;          // SRHT transform in double-float (FP32 pairs) instead of FP64
@@ -283,6 +285,25 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
 void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols,
                                 double scale, double* Y, int64_t ldy, bool df = false);
 void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed);
+
+// spmv.cu
+void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* out);
+int rgs_spmv_nparts(const rgs_context* ctx, int64_t n);
+int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
+                    const rgs_sketch_obj* sk, double* partials, const int* ctl);
+int rgs_norm_grid(const rgs_context* ctx, int64_t n);
+void rgs_launch_residual(rgs_context* ctx, const rgs_csr& A, const double* x, const double* b, double* r,
+                         double* part, double* norm_out);
+void rgs_launch_norm(rgs_context* ctx, int64_t n, const double* v, double* part, double* norm_out);
+void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype, int64_t ldq, const double* cy,
+                           double* x, const int* ctl);
+void rgs_launch_hess_solve(rgs_context* ctx, const double* Hr, int ldh, const double* g, const double* colscale,
+                           int jmax, double* y, double* cy, int* ctl);
+int rgs_multidot_grid(const rgs_context* ctx, int64_t n);
+void rgs_launch_cgs_pass(rgs_context* ctx, int64_t n, const double* Vp, int64_t ldv, int ncols, const double* sigma,
+                         double* w, double* part, double* coef, double* hacc, int accumulate, const int* ctl);
+void rgs_launch_cgs_update(rgs_context* ctx, int64_t n, const double* Vp, int64_t ldv, int ncols, const double* coef,
+                           double* w, double* out, double* part, const int* ctl);
 
 // ls.cu: Householder (compact-WY) least-squares engine for the sketched problems.
 struct LSState {
@@ -296,6 +317,7 @@ struct LSState {
     double *sigma, *pnorm, *coef;
     double *R;
     int64_t ldr;
+    double *cs, *sn, *g, *Hr;       // Givens state of the Hessenberg problem (GMRES); Hr ld mmax
     int max_parts;
     int* ctl;
 };
@@ -315,6 +337,9 @@ struct LSStep {
     int s_df, p_df;         // partial sketches stored as double-float pairs (float2) instead of FP64
     int pnorm_idx;          // where to record ||p||
     unsigned long long* trace;  // optional: 8 timestamps (ns) at the phase boundaries, written by CTA 0
+    int givens;             // GMRES: rotate H(:, i-1) = sigma_{i-1} R(0:i+1, i) once r_ii is known
+    int arnoldi;            // a vanishing r_ii ends the cycle (happy breakdown) instead of failing
+    double stop_tol;        // GMRES: stop the cycle when the rotated residual falls to this value
 };
 void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);

@@ -1,29 +1,577 @@
-// RGS-Arnoldi (Alg. 3), randomized GMRES (Sec. 4.2) and the CGS2-GMRES comparator.
+// RGS-Arnoldi (Alg. 3), restarted randomized GMRES (Sec. 4.2, Eq. hls) and the FP64
+// CGS2-GMRES comparator (projector (I - Q Q^T)^2, Sec. 1.2).
+//
+// The RGS runs on the unnormalised Krylov columns w'_1 = r, w'_{i+1} = A q'_i (q'_i the stored
+// basis vector, q_i = q'_i sigma_i with sigma_i = 1 / r_ii), so the Arnoldi relation reads
+// A Q_m = Q_{m+1} H with H(:, j) = sigma_j R'(0:j+2, j+1); nothing ever rescales a stream.
+// One Arnoldi step is three launches: the fused update + sketch of column i (Alg. 2 steps 3-4),
+// the product w'_{i+1} = A q'_i with the sketch of w'_{i+1} fused in (Alg. 3 step 3, Alg. 2
+// step 1), and the least-squares kernel (steps 2, 5, 6 plus the Givens rotation of H(:, i-1)).
+// A converged or broken-down cycle raises a stop word that turns the remaining launches of
+// the cycle into no-ops; the host reads it once per cycle with the true residual.
 #include "common.cuh"
+#include "givens.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+using namespace rgsdev;
+
+struct rgs_arnoldi_obj {
+    rgs_handle h = nullptr;
+    rgs_sketch_obj* sk = nullptr;
+    int64_t n = 0;
+    int mmax = 0;
+    int qtype = 0;
+    int64_t ldq = 0;
+    int ncols = 0;           // columns appended so far (public step-by-step interface)
+    DevBuf Q;                // n x mmax in qtype
+    DevBuf lsbuf;
+    LSState ls{};
+    DevBuf R;                // mmax x mmax
+    DevBuf gv;               // cs, sn, g, Hr, y, cy
+    DevBuf wbuf;             // w' (FP64 or double-float pairs), n
+    DevBuf spart, ppart;     // partial sketches of q'_i and of w'_{i+1}
+    DevBuf vdf;              // A's values split into double-float pairs
+    DevBuf work;             // r (n), norm partials, scalars
+};
+
+namespace {
+
+template <class F>
+rgs_status guarded(rgs_handle h, F&& f) {
+    try {
+        f();
+        if (h) h->last_error.clear();
+        return RGS_OK;
+    } catch (const RgsError& e) {
+        if (h) h->last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (h) h->last_error = "host allocation failed";
+        return RGS_ERR_ALLOC;
+    } catch (...) {
+        if (h) h->last_error = "unexpected exception";
+        return RGS_ERR_INVALID_ARG;
+    }
+}
+
+size_t dsize(int t) { return t == RGS_F64 ? 8 : (t == RGS_F32 ? 4 : 2); }
+
+void check_csr(const rgs_csr* A, int64_t n) {
+    RGS_REQUIRE(A != nullptr && A->rowptr && A->colind && A->val, "null CSR array");
+    RGS_REQUIRE(A->n == n && A->nnz >= 0, "CSR size differs from the sketch's n");
+}
+
+// Allocate everything an Arnoldi object needs for a basis of mmax columns.
+void arnoldi_alloc(rgs_arnoldi_obj* a) {
+    rgs_context* h = a->h;
+    const int k = a->sk->k, m = a->mmax;
+    a->ldq = (a->n + 7) & ~(int64_t)7;
+    a->Q.ensure(dsize(a->qtype) * (size_t)a->ldq * m);
+    rgs_ls_alloc(a->lsbuf, k, m, h->ls_blocks, h->num_sms * h->upd_blocks_per_sm, &a->ls);
+    a->R.ensure(sizeof(double) * (size_t)m * m);
+    a->gv.ensure(sizeof(double) * (4 * (size_t)m + 2 + (size_t)m * m + 2 * (size_t)m));
+    double* g = a->gv.as<double>();
+    a->ls.cs = g;
+    a->ls.sn = g + m;
+    a->ls.g = g + 2 * m;
+    a->ls.Hr = g + 3 * m + 2;
+    a->ls.R = a->R.as<double>();
+    a->ls.ldr = m;
+    a->ls.ctl = h->ctl.as<int>();
+    a->wbuf.ensure(sizeof(double) * (size_t)a->n);
+    const size_t parts = (size_t)h->num_sms * h->upd_blocks_per_sm * k * sizeof(double);
+    a->spart.ensure(parts);
+    a->ppart.ensure(parts);
+    a->work.ensure(sizeof(double) * ((size_t)a->n + 8 * (size_t)h->num_sms + 16 + (size_t)k));
+}
+
+double* y_buf(rgs_arnoldi_obj* a) { return a->ls.Hr + (size_t)a->mmax * a->mmax; }
+double* cy_buf(rgs_arnoldi_obj* a) { return y_buf(a) + a->mmax; }
+
+void reset_cycle(rgs_arnoldi_obj* a) {
+    rgs_context* h = a->h;
+    RGS_CUDA(cudaMemsetAsync(h->ctl.as<int>() + kStopWord, 0, 2 * sizeof(int), h->stream));
+    rgs_ls_reset(h, a->ls);
+    RGS_CUDA(cudaMemsetAsync(a->R.ptr, 0, a->R.bytes, h->stream));
+    RGS_CUDA(cudaMemsetAsync(a->gv.ptr, 0, a->gv.bytes, h->stream));
+}
+
+bool sketch_is_df(const rgs_arnoldi_obj* a) { return a->sk->kind == RGS_SKETCH_SRHT && a->qtype != RGS_F64; }
+
+double s_scale(const rgs_sketch_obj* sk) { return sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)sk->k) : 1.0; }
+
+// Steps 3-4 for column i from the input column w (FP64 or double-float), into spart.
+int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df) {
+    UpdateLaunch L{};
+    L.n = a->n;
+    L.ncols = i;
+    L.Q = a->Q.ptr;
+    L.ldq = a->ldq;
+    L.qtype = a->qtype;
+    L.w = reinterpret_cast<const double*>(w);
+    L.ldw = a->n;
+    L.wcols = 1;
+    L.w_df = w_df;
+    L.coef = a->ls.coef;
+    L.qout = a->Q.as<char>() + dsize(a->qtype) * (size_t)i * a->ldq;
+    L.df_sketch = sketch_is_df(a) ? 1 : 0;
+    int np = 0;
+    rgs_launch_update_sketch(a->h, a->sk, L, a->spart.as<double>(), &np, a->h->ctl.as<int>());
+    return np;
+}
+
+// w' = A q'_col (+ sketch of w' into ppart); returns the number of partial sketches.
+int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col) {
+    rgs_context* h = a->h;
+    const void* x = a->Q.as<char>() + dsize(a->qtype) * (size_t)col * a->ldq;
+    if (a->sk->kind == RGS_SKETCH_SRHT) {
+        const int dfm = sketch_is_df(a) ? 1 : 0;
+        return rgs_launch_spmv(h, A, a->vdf.ptr, x, a->qtype, a->wbuf.ptr, dfm, a->sk, a->ppart.as<double>(),
+                               h->ctl.as<int>());
+    }
+    rgs_launch_spmv(h, A, nullptr, x, a->qtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
+    UpdateLaunch L{};
+    L.n = a->n;
+    L.qtype = RGS_F64;
+    L.w = a->wbuf.as<double>();
+    L.ldw = a->n;
+    L.wcols = 1;
+    int np = 0;
+    rgs_launch_update_sketch(h, a->sk, L, a->ppart.as<double>(), &np, h->ctl.as<int>());
+    return np;
+}
+
+void launch_ls(rgs_arnoldi_obj* a, int i, int sparts, bool solve, int pparts, bool gmres, double stop_tol) {
+    LSStep s{};
+    s.i = i;
+    s.append = 1;
+    s.s_part = a->spart.as<double>();
+    s.s_nparts = sparts;
+    s.s_scale = s_scale(a->sk);
+    s.s_df = sketch_is_df(a) ? 1 : 0;
+    s.solve = solve ? 1 : 0;
+    s.xcol = i + 1;
+    s.p_part = a->ppart.as<double>();
+    s.p_nparts = pparts;
+    s.p_scale = s_scale(a->sk);
+    s.p_df = sketch_is_df(a) ? 1 : 0;
+    s.pnorm_idx = i + 1;
+    s.givens = gmres ? 1 : 0;
+    s.arnoldi = 1;
+    s.stop_tol = stop_tol;
+    rgs_launch_ls(a->h, a->ls, s);
+}
+
+struct Scalars {
+    double* r;        // n
+    double* part;     // norm partials (8 per SM)
+    double* val;      // 16 device scalars: [0] ||r||, [1] ||b||, [2] ||Theta b||
+    double* kvec;     // k entries: Theta b
+};
+
+Scalars scalars(rgs_arnoldi_obj* a) {
+    double* w = a->work.as<double>();
+    double* val = w + a->n + 8 * (size_t)a->h->num_sms;
+    return {w, w + a->n, val, val + 16};
+}
+
+__global__ void scale_vec_kernel(int64_t n, double* w, const double* scale) {
+    const double s = *scale;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] *= s;
+}
+
+}  // namespace
 
 extern "C" {
 
-rgs_status rgs_arnoldi_create(rgs_handle, rgs_sketch, int64_t, int32_t, rgs_dtype, rgs_arnoldi* out) {
-    if (out) *out = nullptr;
+rgs_status rgs_arnoldi_create(rgs_handle h, rgs_sketch s, int64_t n, int32_t mmax, rgs_dtype qtype,
+                              rgs_arnoldi* out) {
+    if (!h || !s || !out) return RGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    rgs_arnoldi_obj* a = new (std::nothrow) rgs_arnoldi_obj();
+    if (!a) return RGS_ERR_ALLOC;
+    rgs_status st = guarded(h, [&] {
+        RGS_REQUIRE(qtype == RGS_F64 || qtype == RGS_F32 || qtype == RGS_BF16, "unknown qtype");
+        RGS_REQUIRE(n == s->n, "n differs from the sketch's n");
+        RGS_REQUIRE(mmax >= 1 && mmax <= s->k && mmax <= 1024 && mmax <= n, "need 1 <= mmax <= min(k, n, 1024)");
+        a->h = h;
+        a->sk = s;
+        a->n = n;
+        a->mmax = mmax;
+        a->qtype = qtype;
+        arnoldi_alloc(a);
+    });
+    if (st != RGS_OK) {
+        delete a;
+        return st;
+    }
+    *out = a;
+    return RGS_OK;
+}
+
+rgs_status rgs_arnoldi_destroy(rgs_arnoldi a) {
+    if (!a) return RGS_ERR_INVALID_ARG;
+    if (a->h) cudaStreamSynchronize(a->h->stream);
+    delete a;
+    return RGS_OK;
+}
+
+// Alg. 3 steps 1-2: iteration 1 of Alg. 2 on w_1.
+rgs_status rgs_arnoldi_start(rgs_handle h, rgs_arnoldi a, const double* w1) {
+    if (!h || !a || !w1) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_CUDA(cudaMemsetAsync(h->ctl.ptr, 0, kCtlWords * sizeof(int), h->stream));
+        reset_cycle(a);
+        const int np = launch_update(a, 0, w1, 0);
+        LSStep s{};
+        s.i = 0;
+        s.append = 1;
+        s.s_part = a->spart.as<double>();
+        s.s_nparts = np;
+        s.s_scale = s_scale(a->sk);
+        s.s_df = sketch_is_df(a) ? 1 : 0;
+        rgs_launch_ls(h, a->ls, s);
+        a->ncols = 1;
+        int ctl[2];
+        RGS_CUDA(cudaMemcpyAsync(ctl, h->ctl.ptr, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+        if (ctl[0] != 0) throw RgsError{(rgs_status)ctl[0], "first Arnoldi column failed"};
+    });
+}
+
+// Alg. 3 steps 3-4: w_i = A q_{i-1} (or the caller's w), then iteration i of Alg. 2.
+rgs_status rgs_arnoldi_step(rgs_handle h, rgs_arnoldi a, const rgs_csr* A, const double* w) {
+    if (!h || !a) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(a->ncols >= 1, "rgs_arnoldi_start first");
+        RGS_REQUIRE(a->ncols < a->mmax, "the basis is full (mmax columns)");
+        RGS_REQUIRE(A != nullptr || w != nullptr, "need A or w");
+        const int i = a->ncols;
+        const double* wi = w;
+        if (A) {
+            // w_i = A q_{i-1} = sigma_{i-1} A q'_{i-1}: FP64 product, then scale
+            check_csr(A, a->n);
+            const void* x = a->Q.as<char>() + dsize(a->qtype) * (size_t)(i - 1) * a->ldq;
+            rgs_launch_spmv(h, *A, nullptr, x, a->qtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((a->n + 255) / 256, 4 * h->num_sms));
+            scale_vec_kernel<<<grid, 256, 0, h->stream>>>(a->n, a->wbuf.as<double>(), a->ls.sigma + (i - 1));
+            RGS_CUDA(cudaGetLastError());
+            wi = a->wbuf.as<double>();
+        }
+        // p_i = Theta w_i (FP64 sketch), then the pure least-squares solve with i reflectors
+        UpdateLaunch L{};
+        L.n = a->n;
+        L.qtype = RGS_F64;
+        L.w = wi;
+        L.ldw = a->n;
+        L.wcols = 1;
+        int pp = 0;
+        rgs_launch_update_sketch(h, a->sk, L, a->ppart.as<double>(), &pp, h->ctl.as<int>());
+        LSStep s{};
+        s.i = i;
+        s.solve = 1;
+        s.xcol = i;
+        s.p_part = a->ppart.as<double>();
+        s.p_nparts = pp;
+        s.p_scale = s_scale(a->sk);
+        s.pnorm_idx = i;
+        rgs_launch_ls(h, a->ls, s);
+        // Alg. 2 steps 3-4, then steps 5-6
+        UpdateLaunch U{};
+        U.n = a->n;
+        U.ncols = i;
+        U.Q = a->Q.ptr;
+        U.ldq = a->ldq;
+        U.qtype = a->qtype;
+        U.w = wi;
+        U.ldw = a->n;
+        U.wcols = 1;
+        U.coef = a->ls.coef;
+        U.qout = a->Q.as<char>() + dsize(a->qtype) * (size_t)i * a->ldq;
+        U.df_sketch = sketch_is_df(a) ? 1 : 0;
+        int np = 0;
+        rgs_launch_update_sketch(h, a->sk, U, a->spart.as<double>(), &np, h->ctl.as<int>());
+        LSStep t{};
+        t.i = i;
+        t.append = 1;
+        t.s_part = a->spart.as<double>();
+        t.s_nparts = np;
+        t.s_scale = s_scale(a->sk);
+        t.s_df = sketch_is_df(a) ? 1 : 0;
+        rgs_launch_ls(h, a->ls, t);
+        int ctl[2];
+        RGS_CUDA(cudaMemcpyAsync(ctl, h->ctl.ptr, sizeof(ctl), cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+        if (ctl[0] != 0) {
+            RGS_CUDA(cudaMemsetAsync(h->ctl.ptr, 0, 2 * sizeof(int), h->stream));
+            throw RgsError{(rgs_status)ctl[0], "Arnoldi step " + std::to_string(i) + ": " +
+                                                   rgs_status_string((rgs_status)ctl[0])};
+        }
+        a->ncols = i + 1;
+    });
+}
+
+rgs_status rgs_arnoldi_get(rgs_handle h, rgs_arnoldi a, int32_t* ncols, double* R_host, int64_t ldr,
+                           double* qscale_host) {
+    if (!h || !a) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        if (ncols) *ncols = a->ncols;
+        const int m = a->ncols;
+        if (R_host && m > 0) {
+            RGS_REQUIRE(ldr >= m, "ldr too small");
+            RGS_CUDA(cudaMemcpy2DAsync(R_host, sizeof(double) * ldr, a->R.ptr, sizeof(double) * a->mmax,
+                                       sizeof(double) * m, m, cudaMemcpyDeviceToHost, h->stream));
+        }
+        if (qscale_host && m > 0)
+            RGS_CUDA(cudaMemcpyAsync(qscale_host, a->ls.sigma, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+rgs_status rgs_arnoldi_basis(rgs_arnoldi a, void** Q, int64_t* ldq) {
+    if (!a || !Q || !ldq) return RGS_ERR_INVALID_ARG;
+    *Q = a->Q.ptr;
+    *ldq = a->ldq;
+    return RGS_OK;
+}
+
+rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const double* b, double* x,
+                        const rgmres_opts* opts, rgmres_info* info) {
+    if (!h || !s || !opts) return RGS_ERR_INVALID_ARG;
+    if (info) {
+        info->cycles = info->total_steps = info->converged = 0;
+        info->status = RGS_OK;
+        info->rel_residual = NAN;
+    }
+    bool converged = false;
+    rgs_status st = guarded(h, [&] {
+        check_csr(A, s->n);
+        RGS_REQUIRE(b && x, "null b or x");
+        RGS_REQUIRE(opts->restart >= 1 && opts->restart + 1 <= s->k && opts->restart < 1024,
+                    "need 1 <= restart < min(k, 1024)");
+        RGS_REQUIRE(opts->max_cycles >= 0 && opts->rtol >= 0.0, "bad max_cycles or rtol");
+        const int m = opts->restart;
+        rgs_arnoldi_obj obj;
+        obj.h = h;
+        obj.sk = s;
+        obj.n = s->n;
+        obj.mmax = m + 1;
+        obj.qtype = opts->qtype;
+        arnoldi_alloc(&obj);
+        if (sketch_is_df(&obj)) {
+            obj.vdf.ensure(8 * (size_t)std::max<int64_t>(A->nnz, 1));
+            rgs_csr_split_df(h, A->val, A->nnz, obj.vdf.ptr);
+        }
+        Scalars sc = scalars(&obj);
+        h->launches = 0;
+        RGS_CUDA(cudaMemsetAsync(h->ctl.ptr, 0, kCtlWords * sizeof(int), h->stream));
+        // ||b|| and ||Theta b|| (the inner stopping test compares the sketched residual with the latter)
+        rgs_launch_norm(h, s->n, b, sc.part, sc.val + 1);
+        {
+            UpdateLaunch L{};
+            L.n = s->n;
+            L.qtype = RGS_F64;
+            L.w = b;
+            L.ldw = s->n;
+            L.wcols = 1;
+            int np = 0;
+            rgs_launch_update_sketch(h, s, L, obj.ppart.as<double>(), &np, nullptr);
+            rgs_launch_reduce_partials(h, obj.ppart.as<double>(), np, s->k, 1, s_scale(s), sc.kvec, s->k);
+            rgs_launch_norm(h, s->k, sc.kvec, sc.part, sc.val + 2);
+        }
+        double hv[3];
+        RGS_CUDA(cudaMemcpyAsync(hv, sc.val, sizeof(hv), cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+        const double bnorm = hv[1], sbnorm = hv[2];
+        RGS_REQUIRE(bnorm > 0.0 && std::isfinite(bnorm), "b must be nonzero and finite");
+        const double stop_tol = (opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * sbnorm);
+        int cycles = 0, total = 0;
+        double rel = NAN;
+        for (;;) {
+            rgs_launch_residual(h, *A, x, b, sc.r, sc.part, sc.val);     // true FP64 residual
+            int ctlv[8];
+            RGS_CUDA(cudaMemcpyAsync(hv, sc.val, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaMemcpyAsync(ctlv, h->ctl.ptr, sizeof(ctlv), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaStreamSynchronize(h->stream));
+            if (ctlv[0] != 0) throw RgsError{(rgs_status)ctlv[0], "device status in cycle " + std::to_string(cycles)};
+            if (cycles > 0) total += ctlv[kStepsWord];
+            rel = hv[0] / bnorm;
+            if (info && info->history) info->history[cycles] = rel;
+            if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
+            if (rel <= opts->rtol) { converged = true; break; }
+            if (cycles >= opts->max_cycles) break;
+            reset_cycle(&obj);
+            // Arnoldi step 0: q'_0 from r, w'_1 = A q'_0, column 0 appended and p_1 solved
+            int sp = launch_update(&obj, 0, sc.r, 0);
+            int pp = launch_product(&obj, *A, 0);
+            launch_ls(&obj, 0, sp, m >= 1, pp, true, stop_tol);
+            for (int i = 1; i <= m; ++i) {
+                sp = launch_update(&obj, i, obj.wbuf.ptr, (sketch_is_df(&obj) && s->kind == RGS_SKETCH_SRHT) ? 1 : 0);
+                if (i < m) pp = launch_product(&obj, *A, i);
+                launch_ls(&obj, i, sp, i < m, pp, true, stop_tol);
+            }
+            rgs_launch_hess_solve(h, obj.ls.Hr, obj.mmax, obj.ls.g, obj.ls.sigma, m, y_buf(&obj), cy_buf(&obj),
+                                  h->ctl.as<int>());
+            rgs_launch_sol_update(h, s->n, obj.Q.ptr, obj.qtype, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>());
+            ++cycles;
+        }
+        if (info) {
+            info->cycles = cycles;
+            info->total_steps = total;
+            info->converged = converged ? 1 : 0;
+            info->rel_residual = rel;
+        }
+    });
+    if (info) info->status = st;
+    if (st == RGS_OK && !converged) return RGS_ERR_NOT_CONVERGED;
+    return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+// After the last CGS pass of step j: ||w||, sigma_{j+1}, the Givens rotation of H(:, j), stop test.
+__global__ void cgs_finish_kernel(const double* part, int np, int j, double* sigma, const double* hacc, double* cs,
+                                  double* sn, double* g, double* Hr, int ldh, double stop_tol, int* ctl) {
+    if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
+    const int lane = threadIdx.x;
+    double v = 0.0;
+    for (int b = lane; b < np; b += 32) v += part[b];
+    const double wn = sqrt(warp_sum(v));
+    const double sj = sigma[j];
+    double hmax = 0.0;
+    for (int t = lane; t <= j; t += 32) hmax = fmax(hmax, fabs(sigma[t] * hacc[t]));
+    for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    auto hcol = [&](int t) { return t <= j ? sj * sigma[t] * hacc[t] : sj * wn; };
+    const double res = givens_column_warp(j, hcol, cs, sn, g, Hr, ldh);
+    if (lane == 0) {
+        const bool breakdown = !(wn * sj > 16.0 * 0x1p-53 * sj * hmax);
+        sigma[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
+        if (breakdown || res <= stop_tol) atomicCAS(ctl + kStopWord, 0, j + 1);
+    }
+}
+
+__global__ void set_first_kernel(const double* r, const double* rnorm, int64_t n, double* v0, double* sigma,
+                                 double* g) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v0[i] = r[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sigma[0] = 1.0 / rnorm[0];
+        g[0] = rnorm[0];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, double* x, const rgmres_opts* opts,
+                            rgmres_info* info) {
+    if (!h || !A || !opts) return RGS_ERR_INVALID_ARG;
+    if (info) {
+        info->cycles = info->total_steps = info->converged = 0;
+        info->status = RGS_OK;
+        info->rel_residual = NAN;
+    }
+    bool converged = false;
+    rgs_status st = guarded(h, [&] {
+        check_csr(A, A->n);
+        RGS_REQUIRE(b && x, "null b or x");
+        RGS_REQUIRE(opts->restart >= 1 && opts->restart < 1024, "need 1 <= restart < 1024");
+        const int m = opts->restart;
+        const int64_t n = A->n, ldv = (n + 7) & ~(int64_t)7;
+        DevBuf V, wv, gv, work;
+        V.ensure(sizeof(double) * (size_t)ldv * (m + 1));
+        wv.ensure(sizeof(double) * (size_t)n);
+        const int mp = m + 1;
+        gv.ensure(sizeof(double) * (7 * (size_t)mp + 2 + (size_t)mp * mp));
+        double* sigma = gv.as<double>();
+        double* cs = sigma + mp;
+        double* sn = cs + mp;
+        double* g = sn + mp;                    // mp + 2
+        double* hacc = g + mp + 2;
+        double* coef = hacc + mp;
+        double* cyv = coef + mp;
+        double* yv = cyv + mp;
+        double* Hr = yv + mp;                   // mp x mp
+        const int mdg = rgs_multidot_grid(h, n);
+        work.ensure(sizeof(double) * ((size_t)n + (size_t)mdg * mp + 8 * (size_t)h->num_sms + 64));
+        double* r = work.as<double>();
+        double* part = r + n;                                  // multidot partials (mdg x mp)
+        double* npart = part + (size_t)mdg * mp;               // norm partials
+        double* val = npart + 8 * (size_t)h->num_sms;          // device scalars
+        int* ctl = h->ctl.as<int>();
+        h->launches = 0;
+        RGS_CUDA(cudaMemsetAsync(ctl, 0, kCtlWords * sizeof(int), h->stream));
+        rgs_launch_norm(h, n, b, npart, val + 1);
+        double bn;
+        RGS_CUDA(cudaMemcpyAsync(&bn, val + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+        RGS_REQUIRE(bn > 0.0 && std::isfinite(bn), "b must be nonzero and finite");
+        const double stop_tol = opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * bn;
+        const int ng = rgs_norm_grid(h, n);
+        int cycles = 0, total = 0;
+        double rel = NAN;
+        for (;;) {
+            rgs_launch_residual(h, *A, x, b, r, npart, val);
+            double rn;
+            int ctlv[8];
+            RGS_CUDA(cudaMemcpyAsync(&rn, val, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaMemcpyAsync(ctlv, ctl, sizeof(ctlv), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaStreamSynchronize(h->stream));
+            if (ctlv[0] != 0) throw RgsError{(rgs_status)ctlv[0], "device status"};
+            if (cycles > 0) total += ctlv[kStepsWord];
+            rel = rn / bn;
+            if (info && info->history) info->history[cycles] = rel;
+            if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
+            if (rel <= opts->rtol) { converged = true; break; }
+            if (cycles >= opts->max_cycles) break;
+            RGS_CUDA(cudaMemsetAsync(ctl + kStopWord, 0, 2 * sizeof(int), h->stream));
+            RGS_CUDA(cudaMemsetAsync(gv.ptr, 0, gv.bytes, h->stream));
+            set_first_kernel<<<ng, 256, 0, h->stream>>>(r, val, n, V.as<double>(), sigma, g);
+            RGS_CUDA(cudaGetLastError());
+            for (int j = 0; j < m; ++j) {
+                double* vj = V.as<double>() + (size_t)j * ldv;
+                double* vn = V.as<double>() + (size_t)(j + 1) * ldv;
+                rgs_launch_spmv(h, *A, nullptr, vj, RGS_F64, wv.ptr, 0, nullptr, nullptr, ctl);     // w = A v'_j
+                rgs_launch_cgs_pass(h, n, V.as<double>(), ldv, j + 1, sigma, wv.as<double>(), part, coef, hacc, 0, ctl);
+                rgs_launch_cgs_update(h, n, V.as<double>(), ldv, j + 1, coef, wv.as<double>(), nullptr, nullptr, ctl);
+                rgs_launch_cgs_pass(h, n, V.as<double>(), ldv, j + 1, sigma, wv.as<double>(), part, coef, hacc, 1, ctl);
+                rgs_launch_cgs_update(h, n, V.as<double>(), ldv, j + 1, coef, wv.as<double>(), vn, npart, ctl);
+                cgs_finish_kernel<<<1, 32, 0, h->stream>>>(npart, ng, j, sigma, hacc, cs, sn, g, Hr, mp, stop_tol, ctl);
+                RGS_CUDA(cudaGetLastError());
+            }
+            rgs_launch_hess_solve(h, Hr, mp, g, sigma, m, yv, cyv, ctl);
+            rgs_launch_sol_update(h, n, V.ptr, RGS_F64, ldv, cyv, x, ctl);
+            ++cycles;
+        }
+        if (info) {
+            info->cycles = cycles;
+            info->total_steps = total;
+            info->converged = converged ? 1 : 0;
+            info->rel_residual = rel;
+        }
+    });
+    if (info) info->status = st;
+    if (st == RGS_OK && !converged) return RGS_ERR_NOT_CONVERGED;
+    return st;
+}
+
+rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void*, int32_t) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    (void)kind;
     return RGS_ERR_NOT_IMPLEMENTED;
 }
-rgs_status rgs_arnoldi_destroy(rgs_arnoldi) { return RGS_ERR_NOT_IMPLEMENTED; }
-rgs_status rgs_arnoldi_start(rgs_handle, rgs_arnoldi, const double*) { return RGS_ERR_NOT_IMPLEMENTED; }
-rgs_status rgs_arnoldi_step(rgs_handle, rgs_arnoldi, const rgs_csr*, const double*) { return RGS_ERR_NOT_IMPLEMENTED; }
-rgs_status rgs_arnoldi_get(rgs_handle, rgs_arnoldi, int32_t*, double*, int64_t, double*) { return RGS_ERR_NOT_IMPLEMENTED; }
-rgs_status rgs_arnoldi_basis(rgs_arnoldi, void**, int64_t*) { return RGS_ERR_NOT_IMPLEMENTED; }
-rgs_status rgmres_solve(rgs_handle, rgs_sketch, const rgs_csr*, const double*, double*, const rgmres_opts*,
-                        rgmres_info*) {
-    return RGS_ERR_NOT_IMPLEMENTED;
-}
-rgs_status cgs2_gmres_solve(rgs_handle, const rgs_csr*, const double*, double*, const rgmres_opts*, rgmres_info*) {
-    return RGS_ERR_NOT_IMPLEMENTED;
-}
-rgs_status rgmres_set_preconditioner(rgs_handle, rgs_precond_kind, const void*, int32_t) {
-    return RGS_ERR_NOT_IMPLEMENTED;
-}
-rgs_status rgmres_solve_batched(rgs_handle, int32_t, const rgs_sketch*, const rgs_csr*, const double* const*,
+
+rgs_status rgmres_solve_batched(rgs_handle h, int32_t, const rgs_sketch*, const rgs_csr*, const double* const*,
                                 double* const*, const rgmres_opts*, rgmres_info*) {
+    if (!h) return RGS_ERR_INVALID_ARG;
     return RGS_ERR_NOT_IMPLEMENTED;
 }
 

@@ -10,6 +10,7 @@
 //   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta.
 // One cooperative launch per column; phases are separated by bounded grid barriers.
 #include "common.cuh"
+#include "givens.cuh"
 
 #include <algorithm>
 
@@ -202,8 +203,24 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_NONFINITE); ctl[kDetailWord] = i; }
             return;
         }
-        if (!(r > 16.0 * 0x1p-53 * pref)) {
-            if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
+        const bool breakdown = !(r > 16.0 * 0x1p-53 * pref);
+        if (a.givens) {
+            // GMRES: H(:, i-1) = sigma_{i-1} R(0:i+1, i) is complete now that r_ii is known
+            if (i == 0) {
+                if (gtid == 0) st.g[0] = r;
+            } else if (blockIdx.x == G - 1 && tid < 32) {
+                const double sg = st.sigma[i - 1];
+                const double* rc = st.R + (size_t)i * st.ldr;
+                auto hcol = [&](int t) { return sg * (t < i ? rc[t] : r); };
+                const double res = givens_column_warp(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, mm);
+                if (tid == 0 && (breakdown || res <= a.stop_tol)) atomicCAS(ctl + kStopWord, 0, i);
+            }
+        }
+        if (breakdown) {
+            if (!(a.arnoldi && i > 0) && gtid == 0) {
+                atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN);
+                ctl[kDetailWord] = i;
+            }
             return;
         }
         inv_r = 1.0 / r;

@@ -1,0 +1,418 @@
+// Sparse operator kernels of RGS-GMRES (Alg. 3 step 3, Sec. 4.2) and of the CGS2 comparator.
+//  - spmv_sketch_kernel: w = A x for a tile of 1024 rows (CSR), stored, and its SRHT sketch
+//    partials from the same registers (Alg. 2 step 1 for the next Arnoldi column).  With an
+//    FP32/BF16 basis the products and sums run in double-float arithmetic on A's values
+//    pre-split into float pairs (the paper allows a coarser matvec than u_fine as long as its
+//    error stays O(u_crs), Sec. 4.1); with an FP64 basis everything is FP64.
+//  - residual_kernel: r = b - A x in FP64 with per-CTA partial sums of r^2 (restart residual).
+//  - sol_update_kernel: x += Q' cy (the GMRES solution update at the end of a cycle).
+//  - hess_solve_kernel: y from the Givens-rotated Hessenberg system (one warp).
+//  - multidot / axpy-style kernels for the CGS2 passes h = V^T w, w -= V h.
+#include "fwht.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+using namespace rgsdev;
+
+namespace {
+
+__global__ void csr_split_df_kernel(const double* __restrict__ val, int64_t nnz, df* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = val[e];
+        const float h = __double2float_rn(v);
+        out[e] = {h, __double2float_rn(v - (double)h)};
+    }
+}
+
+template <typename TX> __device__ __forceinline__ float xf(const TX* x, int c) {
+    if constexpr (sizeof(TX) == 2) return __bfloat162float(x[c]);
+    else return (float)x[c];
+}
+
+// double-float product (ah + al) * b for an exact FP32 b (FMA gives the exact error of ah*b)
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = a.h * b;
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+
+struct SpmvParams {
+    int64_t n;
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const double* val;      // FP64 values (FP64 mode)
+    const df* vdf;          // double-float values (double-float mode)
+    const void* x;
+    void* w;                // FP64 or double-float output
+    const uint32_t* signbits;
+    const int32_t* rows;
+    int k;
+    int ntiles;
+    double* partials;
+    const int* ctl;
+};
+
+template <typename TX, bool DFM, bool SRHT>
+__global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams p) {
+    using V = typename std::conditional<DFM, df, double>::type;
+    using F = FW<V>;
+    extern __shared__ __align__(16) double smem[];
+    V* zt = reinterpret_cast<V*>(smem);
+    V* part = zt + TILE;
+    int32_t* srow = reinterpret_cast<int32_t*>(part + (SRHT ? p.k : 0));
+    if (p.ctl != nullptr && (p.ctl[kStatusWord] != 0 || p.ctl[kStopWord] != 0)) return;
+    const TX* x = reinterpret_cast<const TX*>(p.x);
+    if (SRHT) {
+        for (int j = threadIdx.x; j < p.k; j += TILE_THREADS) { srow[j] = p.rows[j]; part[j] = F::zero(); }
+        __syncthreads();
+    }
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const int64_t r0 = (int64_t)tile * TILE + threadIdx.x * 4;
+        V z[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t r = r0 + e;
+            V acc = F::zero();
+            if (r < p.n) {
+                const int b0 = __ldg(p.rowptr + r), b1 = __ldg(p.rowptr + r + 1);
+                if constexpr (DFM) {
+                    for (int q = b0; q < b1; ++q) acc = df_add(acc, df_mul_f(p.vdf[q], xf(x, __ldg(p.colind + q))));
+                    reinterpret_cast<df*>(p.w)[r] = acc;
+                } else {
+                    double a = 0.0;
+                    for (int q = b0; q < b1; ++q) a = fma(__ldg(p.val + q), (double)x[__ldg(p.colind + q)], a);
+                    acc = a;
+                    reinterpret_cast<double*>(p.w)[r] = a;
+                }
+            }
+            z[e] = acc;
+        }
+        if (SRHT) srht_tile<V>(z, r0, p.n, tile, p.signbits, srow, p.k, zt, part);
+    }
+    if (SRHT) {
+        __syncthreads();
+        V* out = reinterpret_cast<V*>(p.partials) + (int64_t)blockIdx.x * p.k;
+        for (int j = threadIdx.x; j < p.k; j += TILE_THREADS) out[j] = part[j];
+    }
+}
+
+// r = b - A x (FP64), per-CTA partial sums of r^2 in part[blockIdx.x]
+__global__ void __launch_bounds__(256) residual_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ colind,
+                                                       const double* __restrict__ val, const double* __restrict__ x,
+                                                       const double* __restrict__ b, double* __restrict__ r,
+                                                       double* __restrict__ part) {
+    __shared__ double sh[8];
+    double s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = b[i];
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) a = fma(-val[q], x[colind[q]], a);
+        if (r) r[i] = a;
+        s2 = fma(a, a, s2);
+    }
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// out[0] = sqrt(sum of part[0..np)) (one warp, fixed order)
+__global__ void norm_final_kernel(const double* part, int np, double* out) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < np; b += 32) v += part[b];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[0] = sqrt(v);
+}
+
+// sum of squares of a vector into per-CTA partials
+__global__ void __launch_bounds__(256) sumsq_kernel(int64_t n, const double* __restrict__ v, double* __restrict__ part) {
+    __shared__ double sh[8];
+    double s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s2 = fma(v[i], v[i], s2);
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// x += sum_{c < nsteps} Q'(:, c) cy[c]; nsteps from ctl[kStepsWord]
+template <typename TQ>
+__global__ void __launch_bounds__(256) sol_update_kernel(int64_t n, const TQ* __restrict__ Q, int64_t ldq,
+                                                         const double* __restrict__ cy, double* __restrict__ x,
+                                                         const int* ctl) {
+    __shared__ df cdf[1024];
+    __shared__ double cd[1024];
+    const int nsteps = ctl[kStepsWord];
+    if (ctl[kStatusWord] != 0 || nsteps <= 0) return;
+    for (int c = threadIdx.x; c < nsteps && c < 1024; c += blockDim.x) {
+        const double v = cy[c];
+        const float h = __double2float_rn(v);
+        cdf[c] = {h, __double2float_rn(v - (double)h)};
+        cd[c] = v;
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(TQ) == 8) {
+            double a = 0.0;
+            for (int c = 0; c < nsteps; ++c) a = fma(Q[(int64_t)c * ldq + i], cd[c], a);
+            x[i] += a;
+        } else {
+            df a = {0.f, 0.f};
+            for (int c = 0; c < nsteps; ++c) {
+                float q;
+                if constexpr (sizeof(TQ) == 2) q = __bfloat162float(Q[(int64_t)c * ldq + i]);
+                else q = Q[(int64_t)c * ldq + i];
+                a = df_add(a, df_mul_f(cdf[c], q));
+            }
+            x[i] += (double)a.h + (double)a.l;
+        }
+    }
+}
+
+// Back substitution on the rotated Hessenberg factor: Hr(0:j, 0:j) y = g(0:j), cy = sigma .* y.
+// One warp; j = ctl[kStopWord] if the cycle stopped early, else jmax.  Writes ctl[kStepsWord] = j.
+__global__ void hess_solve_kernel(const double* __restrict__ Hr, int ldh, const double* __restrict__ g,
+                                  const double* __restrict__ colscale, int jmax, double* __restrict__ y,
+                                  double* __restrict__ cy, int* ctl) {
+    __shared__ double gs[1024];
+    __shared__ double inv[1024];
+    const int lane = threadIdx.x;
+    if (ctl[kStatusWord] != 0) return;
+    const int stop = ctl[kStopWord];
+    const int j = stop > 0 ? stop : jmax;
+    for (int t = lane; t < j; t += 32) {
+        gs[t] = g[t];
+        inv[t] = 1.0 / Hr[(size_t)t * ldh + t];
+    }
+    __syncwarp();
+    for (int r = j - 1; r >= 0; --r) {
+        const double yr = gs[r] * inv[r];
+        for (int t = lane; t < r; t += 32) gs[t] = fma(-Hr[(size_t)r * ldh + t], yr, gs[t]);
+        if (lane == 0) y[r] = yr;
+        __syncwarp();
+    }
+    __syncwarp();
+    for (int t = lane; t < j; t += 32) cy[t] = y[t] * (colscale ? colscale[t] : 1.0);
+    if (lane == 0) ctl[kStepsWord] = j;
+}
+
+// CGS2 pass: partial dots part[blockIdx.x * ncols + c] = sum over the CTA's rows of V'(r, c) w(r).
+// Warp w of the CTA handles columns c = w, w + 8, ...; lanes walk the CTA's row range.
+__global__ void __launch_bounds__(256) multidot_kernel(int64_t n, const double* __restrict__ Vp, int64_t ldv,
+                                                       int ncols, const double* __restrict__ w,
+                                                       double* __restrict__ part, const int* ctl) {
+    if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int c = wp; c < ncols; c += 8) {
+        const double* v = Vp + (int64_t)c * ldv;
+        double a0 = 0.0, a1 = 0.0;
+        int64_t r = r0 + lane;
+        for (; r + 32 < r1; r += 64) {
+            a0 = fma(v[r], w[r], a0);
+            a1 = fma(v[r + 32], w[r + 32], a1);
+        }
+        if (r < r1) a0 = fma(v[r], w[r], a0);
+        const double t = warp_sum(a0 + a1);
+        if (lane == 0) part[(int64_t)blockIdx.x * ncols + c] = t;
+    }
+}
+
+// Sum the multidot partials over CTAs (warp per column): t[c]; coef[c] = sigma_c^2 t[c]; hacc[c] += t[c]
+__global__ void multidot_reduce_kernel(const double* __restrict__ part, int np, int ncols,
+                                       const double* __restrict__ sigma, double* __restrict__ coef,
+                                       double* __restrict__ hacc, int accumulate, const int* ctl) {
+    if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncols) return;
+    double v = 0.0;
+    for (int b = lane; b < np; b += 32) v += part[(int64_t)b * ncols + c];
+    v = warp_sum(v);
+    if (lane == 0) {
+        coef[c] = sigma[c] * sigma[c] * v;
+        hacc[c] = accumulate ? hacc[c] + v : v;
+    }
+}
+
+// w -= V' coef (FP64); optionally per-CTA partial sums of the updated w^2 and a copy into out
+__global__ void __launch_bounds__(256) cgs_update_kernel(int64_t n, const double* __restrict__ Vp, int64_t ldv,
+                                                         int ncols, const double* __restrict__ coef,
+                                                         double* __restrict__ w, double* __restrict__ out,
+                                                         double* __restrict__ part, const int* ctl) {
+    __shared__ double sc[1024];
+    __shared__ double sh[8];
+    if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) sc[c] = coef[c];
+    __syncthreads();
+    double s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a0 = w[i], a1 = 0.0;
+        int c = 0;
+        for (; c + 1 < ncols; c += 2) {
+            a0 = fma(-Vp[(int64_t)c * ldv + i], sc[c], a0);
+            a1 = fma(-Vp[(int64_t)(c + 1) * ldv + i], sc[c + 1], a1);
+        }
+        if (c < ncols) a0 = fma(-Vp[(int64_t)c * ldv + i], sc[c], a0);
+        const double a = a0 + a1;
+        w[i] = a;
+        if (out) out[i] = a;
+        s2 = fma(a, a, s2);
+    }
+    if (part) {
+        s2 = warp_sum(s2);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+            t = warp_sum(t);
+            if (threadIdx.x == 0) part[blockIdx.x] = t;
+        }
+    }
+}
+
+template <typename TX, bool DFM, bool SRHT>
+void launch_spmv_t(rgs_context* ctx, const SpmvParams& p, int grid, size_t smem) {
+    auto kern = spmv_sketch_kernel<TX, DFM, SRHT>;
+    if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, TILE_THREADS, smem, ctx->stream>>>(p);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+}  // namespace
+
+void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* out) {
+    const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 4 * ctx->num_sms);
+    csr_split_df_kernel<<<std::max(grid, 1), 256, 0, ctx->stream>>>(val, nnz, reinterpret_cast<df*>(out));
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+int rgs_spmv_nparts(const rgs_context* ctx, int64_t n) {
+    const int ntiles = (int)((n + TILE - 1) / TILE);
+    return std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+}
+
+// w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
+int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
+                    const rgs_sketch_obj* sk, double* partials, const int* ctl) {
+    SpmvParams p{};
+    p.n = A.n;
+    p.rowptr = A.rowptr;
+    p.colind = A.colind;
+    p.val = A.val;
+    p.vdf = reinterpret_cast<const df*>(vdf);
+    p.x = x;
+    p.w = w;
+    p.ctl = ctl;
+    p.ntiles = (int)((A.n + TILE - 1) / TILE);
+    const bool srht = sk != nullptr;
+    if (srht) {
+        p.signbits = sk->signbits.as<uint32_t>();
+        p.rows = sk->rows.as<int32_t>();
+        p.k = sk->k;
+        p.partials = partials;
+    }
+    const int grid = rgs_spmv_nparts(ctx, A.n);
+    const size_t smem = srht ? TILE * 8 + (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 + 16 : 16;
+    if (dfm) {
+        RGS_REQUIRE(xtype != RGS_F64, "double-float product needs an FP32 or BF16 vector");
+        if (xtype == RGS_F32) {
+            if (srht) launch_spmv_t<float, true, true>(ctx, p, grid, smem);
+            else launch_spmv_t<float, true, false>(ctx, p, grid, smem);
+        } else {
+            if (srht) launch_spmv_t<__nv_bfloat16, true, true>(ctx, p, grid, smem);
+            else launch_spmv_t<__nv_bfloat16, true, false>(ctx, p, grid, smem);
+        }
+    } else {
+        if (xtype == RGS_F64) {
+            if (srht) launch_spmv_t<double, false, true>(ctx, p, grid, smem);
+            else launch_spmv_t<double, false, false>(ctx, p, grid, smem);
+        } else if (xtype == RGS_F32) {
+            if (srht) launch_spmv_t<float, false, true>(ctx, p, grid, smem);
+            else launch_spmv_t<float, false, false>(ctx, p, grid, smem);
+        } else {
+            if (srht) launch_spmv_t<__nv_bfloat16, false, true>(ctx, p, grid, smem);
+            else launch_spmv_t<__nv_bfloat16, false, false>(ctx, p, grid, smem);
+        }
+    }
+    return grid;
+}
+
+int rgs_norm_grid(const rgs_context* ctx, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * ctx->num_sms));
+}
+
+// r = b - A x; *norm_out (device) = ||r||
+void rgs_launch_residual(rgs_context* ctx, const rgs_csr& A, const double* x, const double* b, double* r,
+                         double* part, double* norm_out) {
+    const int grid = rgs_norm_grid(ctx, A.n);
+    residual_kernel<<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, A.val, x, b, r, part);
+    RGS_CUDA(cudaGetLastError());
+    norm_final_kernel<<<1, 32, 0, ctx->stream>>>(part, grid, norm_out);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+}
+
+void rgs_launch_norm(rgs_context* ctx, int64_t n, const double* v, double* part, double* norm_out) {
+    const int grid = rgs_norm_grid(ctx, n);
+    sumsq_kernel<<<grid, 256, 0, ctx->stream>>>(n, v, part);
+    RGS_CUDA(cudaGetLastError());
+    norm_final_kernel<<<1, 32, 0, ctx->stream>>>(part, grid, norm_out);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+}
+
+void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype, int64_t ldq, const double* cy,
+                           double* x, const int* ctl) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms));
+    if (qtype == RGS_F64) sol_update_kernel<double><<<grid, 256, 0, ctx->stream>>>(n, (const double*)Q, ldq, cy, x, ctl);
+    else if (qtype == RGS_F32) sol_update_kernel<float><<<grid, 256, 0, ctx->stream>>>(n, (const float*)Q, ldq, cy, x, ctl);
+    else sol_update_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(n, (const __nv_bfloat16*)Q, ldq, cy, x, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+void rgs_launch_hess_solve(rgs_context* ctx, const double* Hr, int ldh, const double* g, const double* colscale,
+                           int jmax, double* y, double* cy, int* ctl) {
+    hess_solve_kernel<<<1, 32, 0, ctx->stream>>>(Hr, ldh, g, colscale, jmax, y, cy, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+int rgs_multidot_grid(const rgs_context* ctx, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 4 * ctx->num_sms));
+}
+
+void rgs_launch_cgs_pass(rgs_context* ctx, int64_t n, const double* Vp, int64_t ldv, int ncols, const double* sigma,
+                         double* w, double* part, double* coef, double* hacc, int accumulate, const int* ctl) {
+    const int grid = rgs_multidot_grid(ctx, n);
+    multidot_kernel<<<grid, 256, 0, ctx->stream>>>(n, Vp, ldv, ncols, w, part, ctl);
+    RGS_CUDA(cudaGetLastError());
+    multidot_reduce_kernel<<<(ncols + 7) / 8, 256, 0, ctx->stream>>>(part, grid, ncols, sigma, coef, hacc,
+                                                                       accumulate, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+}
+
+void rgs_launch_cgs_update(rgs_context* ctx, int64_t n, const double* Vp, int64_t ldv, int ncols, const double* coef,
+                           double* w, double* out, double* part, const int* ctl) {
+    const int grid = rgs_norm_grid(ctx, n);
+    cgs_update_kernel<<<grid, 256, 0, ctx->stream>>>(n, Vp, ldv, ncols, coef, w, out, part, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}

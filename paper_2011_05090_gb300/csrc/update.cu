@@ -6,7 +6,7 @@
 // (H_s = H_{s/1024} (x) H_1024, so output row a*1024+b gets
 // (-1)^popcount(a & t) * (H_1024 z_t)[b] from tile t).  Per-CTA partial
 // k-vectors are summed later in a fixed order (deterministic).
-#include "common.cuh"
+#include "fwht.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -15,9 +15,7 @@ using namespace rgsdev;
 
 namespace {
 
-constexpr int TILE = 1024;
-constexpr int LOG_TILE = 10;
-constexpr int UT = 256;      // threads per CTA, 4 consecutive rows each
+constexpr int UT = TILE_THREADS;   // threads per CTA, 4 consecutive rows each
 constexpr int UNROLL = 8;    // basis columns loaded ahead
 
 // Streaming loads of the basis and of w: they are read once per column step and would
@@ -112,6 +110,7 @@ struct UpdParams {
     const double* w;
     int64_t ldw;
     const double* wscale;
+    int w_df;                 // w holds double-float pairs (float2) instead of FP64
     const double* coef;
     void* qout;
     const uint32_t* signbits;
@@ -122,78 +121,6 @@ struct UpdParams {
     double* partials;
     const int* ctl;
 };
-
-// Arithmetic of the transform for the two value types.
-template <typename V> struct FW;
-template <> struct FW<double> {
-    __device__ static double add(double a, double b) { return a + b; }
-    __device__ static double sub(double a, double b) { return a - b; }
-    __device__ static double neg(double a) { return -a; }
-    __device__ static double shfl(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
-    __device__ static double from(double x) { return x; }
-    __device__ static double from_float(float x) { return (double)x; }
-    __device__ static double to_double(double a) { return a; }
-    __device__ static double zero() { return 0.0; }
-};
-template <> struct FW<df> {
-    __device__ static df add(df a, df b) { return df_add(a, b); }
-    __device__ static df sub(df a, df b) { return df_add(a, df_neg(b)); }
-    __device__ static df neg(df a) { return df_neg(a); }
-    __device__ static df shfl(df a, int m) {
-        return {__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
-    }
-    __device__ static df from(double x) {
-        const float h = __double2float_rn(x);
-        return {h, __double2float_rn(x - (double)h)};
-    }
-    __device__ static df from_float(float x) { return {x, 0.f}; }
-    __device__ static double to_double(df a) { return (double)a.h + (double)a.l; }
-    __device__ static df zero() { return {0.f, 0.f}; }
-};
-
-// Walsh-Hadamard transform of the CTA's 1024-element tile.  Element b = 4*tid + e:
-// bits 0-1 in registers, bits 2-6 across the warp, bits 7-9 through shared memory.
-// On return zt[b] holds (H_1024 z)[b] for every b.
-template <typename V>
-__device__ __forceinline__ void fwht_tile(V z[4], V* zt) {
-    using F = FW<V>;
-    V a0 = F::add(z[0], z[1]), a1 = F::sub(z[0], z[1]), a2 = F::add(z[2], z[3]), a3 = F::sub(z[2], z[3]);
-    z[0] = F::add(a0, a2); z[1] = F::add(a1, a3); z[2] = F::sub(a0, a2); z[3] = F::sub(a1, a3);
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int m = 1 << s;
-        const bool upper = (lane & m) != 0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const V o = F::shfl(z[e], m);
-            z[e] = upper ? F::sub(o, z[e]) : F::add(z[e], o);
-        }
-    }
-    __syncthreads();                               // previous readers of zt are done
-#pragma unroll
-    for (int e = 0; e < 4; ++e) zt[threadIdx.x * 4 + e] = z[e];
-    __syncthreads();
-    if (threadIdx.x < 128) {
-        const int g = threadIdx.x;
-        V v[8];
-#pragma unroll
-        for (int w = 0; w < 8; ++w) v[w] = zt[g + 128 * w];
-#pragma unroll
-        for (int h = 1; h < 8; h <<= 1)
-#pragma unroll
-            for (int a = 0; a < 8; a += 2 * h)
-#pragma unroll
-                for (int b = a; b < a + h; ++b) {
-                    const V u = v[b], t = v[b + h];
-                    v[b] = F::add(u, t);
-                    v[b + h] = F::sub(u, t);
-                }
-#pragma unroll
-        for (int w = 0; w < 8; ++w) zt[g + 128 * w] = v[w];
-    }
-    __syncthreads();
-}
 
 template <typename TQ, bool SRHT, bool DF>
 __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
@@ -226,10 +153,20 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
         const bool full = p.vec && (r0 + 4 <= n);
         Acc acc[4];
         if (full) {
-            double2 a = ld_stream_d2(w + r0, pol);
-            double2 b = ld_stream_d2(w + r0 + 2, pol);
-            if (p.wscale) { a.x *= wmul; a.y *= wmul; b.x *= wmul; b.y *= wmul; }
-            acc[0] = (Acc)a.x; acc[1] = (Acc)a.y; acc[2] = (Acc)b.x; acc[3] = (Acc)b.y;
+            if (p.w_df) {            // hi + lo rounded once to the accumulation type
+                const float4 a = ld_stream_f4(w + r0, pol), b = ld_stream_f4(w + r0 + 2, pol);
+                if constexpr (sizeof(Acc) == 4) {
+                    acc[0] = a.x + a.y; acc[1] = a.z + a.w; acc[2] = b.x + b.y; acc[3] = b.z + b.w;
+                } else {
+                    acc[0] = (double)a.x + (double)a.y; acc[1] = (double)a.z + (double)a.w;
+                    acc[2] = (double)b.x + (double)b.y; acc[3] = (double)b.z + (double)b.w;
+                }
+            } else {
+                double2 a = ld_stream_d2(w + r0, pol);
+                double2 b = ld_stream_d2(w + r0 + 2, pol);
+                if (p.wscale) { a.x *= wmul; a.y *= wmul; b.x *= wmul; b.y *= wmul; }
+                acc[0] = (Acc)a.x; acc[1] = (Acc)a.y; acc[2] = (Acc)b.x; acc[3] = (Acc)b.y;
+            }
             int j = 0;
             for (; j + UNROLL <= p.ncols; j += UNROLL) {
                 Acc q[UNROLL][4];
@@ -251,7 +188,16 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[e] = (r0 + e < n) ? (Acc)(w[r0 + e] * wmul) : (Acc)0;
+            for (int e = 0; e < 4; ++e) {
+                if (r0 + e >= n) { acc[e] = (Acc)0; continue; }
+                if (p.w_df) {
+                    const float2 d = reinterpret_cast<const float2*>(w)[r0 + e];
+                    if constexpr (sizeof(Acc) == 4) acc[e] = d.x + d.y;
+                    else acc[e] = (Acc)((double)d.x + (double)d.y);
+                } else {
+                    acc[e] = (Acc)(w[r0 + e] * wmul);
+                }
+            }
             for (int j = 0; j < p.ncols; ++j) {
                 const Acc c = sc[j];
 #pragma unroll
@@ -275,20 +221,7 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
                     if (r0 + e < n) IO::store1(qout + r0 + e, acc[e]);
             }
         }
-        if (SRHT) {
-            if (r0 < n) {
-                const uint32_t bits = __ldg(p.signbits + (r0 >> 5)) >> (r0 & 31);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if ((bits >> e) & 1u) z[e] = F::neg(z[e]);
-            }
-            fwht_tile<V>(z, zt);
-            for (int j = threadIdx.x; j < p.k; j += UT) {
-                const int r = srow[j];
-                const V v = zt[r & (TILE - 1)];
-                part[j] = (__popc((r >> LOG_TILE) & tile) & 1) ? F::sub(part[j], v) : F::add(part[j], v);
-            }
-        }
+        if (SRHT) srht_tile<V>(z, r0, n, tile, p.signbits, srow, p.k, zt, part);
     }
     if (SRHT) {
         __syncthreads();
@@ -422,6 +355,7 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     p.w = L.w;
     p.ldw = L.ldw;
     p.wscale = L.wscale;
+    p.w_df = L.w_df;
     p.coef = L.coef;
     p.qout = L.qout;
     p.ntiles = ntiles;

@@ -1,0 +1,163 @@
+"""GPU parity of RGS-Arnoldi (Alg. 3), randomized GMRES (Sec. 4.2) and CGS2-GMRES against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import paper_2011_05090_gb300 as rgs
+import synth
+from oracle import c_oracle
+from oracle import gmres as og
+from oracle.sketch import Sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2011_05090_gb300 import build
+    build.build()
+    return rgs.rgs_create()
+
+
+def system(nx, ny, pe=20.0, seed=0, angle=0.4):
+    csr = synth.convdiff_2d(nx, ny, pe, angle)
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    b = synth.rhs(nx * ny, seed)
+    return csr, A, b
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def dev(v):
+    return torch.tensor(np.asarray(v, dtype=np.float64), device="cuda")
+
+
+# ------------------------------------------------------------------ Arnoldi
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+@pytest.mark.parametrize("given_w", [False, True])
+def test_arnoldi_steps_match_oracle(h, kind, given_w):
+    csr, A, b = system(30, 27, 25.0, 1)
+    n, m, k = A.shape[0], 16, 60
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 4)
+    a = rgs.rgs_arnoldi_create(h, sk, n, m, torch.float64)
+    rgs.rgs_arnoldi_start(h, a, dev(b))
+    for i in range(1, m):
+        if given_w:
+            _, _, qs = rgs.rgs_arnoldi_get(h, a)
+            q_prev = rgs.rgs_arnoldi_basis(a, i)[:, i - 1].cpu().numpy() * qs[i - 1]
+            rgs.rgs_arnoldi_step(h, a, w=dev(A @ q_prev))
+        else:
+            rgs.rgs_arnoldi_step(h, a, csr=C)
+    nc, R, qs = rgs.rgs_arnoldi_get(h, a)
+    assert nc == m
+    ref = og.rgs_arnoldi(lambda v: A @ v, b, Sketch(kind, n, k, 4), m - 1)
+    assert rel(R, ref.R) <= 1e-12
+    Q = rgs.rgs_arnoldi_basis(a, m).cpu().numpy() * qs[None, :]
+    assert rel(Q, ref.Q) <= 1e-11
+    # Arnoldi identity A Q_{m-1} = Q_m H_m with H = R(1:m, 2:m) (Sec. 4.1)
+    H = R[:, 1:]
+    assert np.linalg.norm(A @ Q[:, :-1] - Q @ H) <= 1e-12 * np.linalg.norm(A @ Q[:, :-1])
+
+
+def test_arnoldi_rejects_overflow_and_missing_start(h):
+    n = 100
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, 10, 1)
+    a = rgs.rgs_arnoldi_create(h, sk, n, 3)
+    with pytest.raises(rgs.RgsError):
+        rgs.rgs_arnoldi_step(h, a, w=dev(np.ones(n)))
+    with pytest.raises(rgs.RgsError):
+        rgs.rgs_arnoldi_create(h, sk, n, 11)                      # mmax > k
+
+
+# ------------------------------------------------------------------ RGMRES
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_rgmres_fp64_one_cycle_matches_oracle(h, kind):
+    csr, A, b = system(24, 25, 30.0, 2)
+    n, m, k = A.shape[0], 20, 70
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 9)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=m, max_cycles=1, qdtype=torch.float64, fixed_steps=True)
+    ref = og.rgmres(A, b, Sketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True)
+    refc = c_oracle.rgmres(csr, b, c_oracle.CSketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True)
+    floor = max(1e-12, 10 * rel(refc.x, ref.x))
+    assert rel(x.cpu().numpy(), ref.x) <= floor
+    assert res["cycles"] == 1 and res["total_steps"] == m
+    assert abs(res["history"][1] - ref.true_residuals[1]) <= 1e-10 * ref.true_residuals[0]
+
+
+@pytest.mark.parametrize("qdtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_rgmres_converges_to_1e8(h, qdtype, kind):
+    csr, A, b = system(48, 40, 40.0, 3)
+    n, m, k = A.shape[0], 30, 90
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 1)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=m, rtol=1e-8, max_cycles=200, qdtype=qdtype)
+    xs = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - A @ xs) / np.linalg.norm(b)
+    ref = og.rgmres(A, b, Sketch(kind, n, k, 1), restart=m, tol=1e-8, max_cycles=200)
+    print(f"{kind}/{qdtype}: cycles {res['cycles']} steps {res['total_steps']} rel {true_rel:.2e}; "
+          f"oracle FP64 cycles {ref.cycles} steps {sum(ref.steps)}")
+    assert res["converged"] and true_rel <= 1e-8
+    assert abs(true_rel - res["rel_residual"]) <= 1e-3 * 1e-8
+    assert res["total_steps"] <= 1.3 * sum(ref.steps) + m
+    h_ = res["history"]
+    assert all(h_[i + 1] < h_[i] for i in range(len(h_) - 1))
+
+
+def test_rgmres_happy_breakdown(h):
+    # A = 2 I: the Krylov space of any b is one-dimensional; the first cycle is exact
+    n = 500
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    va = np.full(n, 2.0)
+    (r_, c_, v_), C = rgs.csr_to_device(rp, ci, va)
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, 40, 2)
+    b = synth.rhs(n, 5)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=10, rtol=1e-12, max_cycles=3, qdtype=torch.float64)
+    assert res["converged"] and res["cycles"] == 1 and res["total_steps"] == 1
+    assert rel(x.cpu().numpy(), b / 2.0) <= 1e-14
+
+
+def test_rgmres_nonzero_initial_guess_and_zero_steps(h):
+    csr, A, b = system(20, 20, 10.0, 4)
+    n = A.shape[0]
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, "srht", n, 60, 3)
+    xs = sp.linalg.spsolve(A.tocsc(), b)
+    x = dev(xs)
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=20, rtol=1e-8, max_cycles=5)
+    assert res["converged"] and res["cycles"] == 0
+    with pytest.raises(rgs.RgsError) as e:
+        rgs.rgmres_solve(h, sk, C, dev(np.zeros(n)), torch.zeros(n, dtype=torch.float64, device="cuda"), restart=20)
+    assert e.value.status == rgs.RGS_ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------------ CGS2-GMRES (FP64 comparator)
+def test_cgs2_one_cycle_matches_oracle(h):
+    csr, A, b = system(24, 25, 30.0, 2)
+    n, m = A.shape[0], 20
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rgs.cgs2_gmres_solve(h, C, dev(b), x, restart=m, max_cycles=1, fixed_steps=True)
+    ref = og.cgs2_gmres(A, b, restart=m, max_cycles=1, fixed_steps=True)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-11
+
+
+def test_cgs2_converges_like_oracle(h):
+    csr, A, b = system(48, 40, 40.0, 3)
+    n, m = A.shape[0], 30
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.cgs2_gmres_solve(h, C, dev(b), x, restart=m, rtol=1e-8, max_cycles=200)
+    ref = c_oracle.cgs2_gmres(csr, b, restart=m, tol=1e-8, max_cycles=200)
+    xs = x.cpu().numpy()
+    assert res["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
+    assert abs(res["total_steps"] - ref.steps) <= max(3, 0.05 * ref.steps)
