@@ -1,12 +1,14 @@
 // RGS-Arnoldi (Alg. 3), restarted randomized GMRES (Sec. 4.2, Eq. hls) and the FP64
 // CGS2-GMRES comparator (projector (I - Q Q^T)^2, Sec. 1.2).
 //
-// The RGS runs on the unnormalised Krylov columns w'_1 = r, w'_{i+1} = A q'_i (q'_i the stored
-// basis vector, q_i = q'_i sigma_i with sigma_i = 1 / r_ii), so the Arnoldi relation reads
-// A Q_m = Q_{m+1} H with H(:, j) = sigma_j R'(0:j+2, j+1); nothing ever rescales a stream.
+// The basis is stored as q'_i with q_i = q'_i sigma_i, sigma_i = 1 / r_ii.  The product
+// w'_{i+1} = A q'_i and its sketch are formed before r_ii is known; w_{i+1} = sigma_i w'_{i+1}
+// follows from the one-synchronisation "lag" of Sec. 2.4: the least-squares kernel scales the
+// sketch p'_{i+1} by 1 / r_ii when it appends column i, and the update of column i + 1 scales
+// its input.  (Unnormalised Krylov columns would grow like ||A||^i and overflow FP32 storage.)
 // One Arnoldi step is three launches: the fused update + sketch of column i (Alg. 2 steps 3-4),
-// the product w'_{i+1} = A q'_i with the sketch of w'_{i+1} fused in (Alg. 3 step 3, Alg. 2
-// step 1), and the least-squares kernel (steps 2, 5, 6 plus the Givens rotation of H(:, i-1)).
+// the product with the sketch fused in (Alg. 3 step 3, Alg. 2 step 1), and the least-squares
+// kernel (steps 2, 5, 6 plus the Givens rotation of H(:, i-1) = R(0:i+1, i), Sec. 4.1).
 // A converged or broken-down cycle raises a stop word that turns the remaining launches of
 // the cycle into no-ops; the host reads it once per cycle with the true residual.
 #include "common.cuh"
@@ -104,8 +106,8 @@ bool sketch_is_df(const rgs_arnoldi_obj* a) { return a->sk->kind == RGS_SKETCH_S
 
 double s_scale(const rgs_sketch_obj* sk) { return sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)sk->k) : 1.0; }
 
-// Steps 3-4 for column i from the input column w (FP64 or double-float), into spart.
-int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df) {
+// Steps 3-4 for column i from the input column w (FP64 or double-float) scaled by *wscale, into spart.
+int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const double* wscale = nullptr) {
     UpdateLaunch L{};
     L.n = a->n;
     L.ncols = i;
@@ -116,6 +118,7 @@ int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df) {
     L.ldw = a->n;
     L.wcols = 1;
     L.w_df = w_df;
+    L.wscale = wscale;
     L.coef = a->ls.coef;
     L.qout = a->Q.as<char>() + dsize(a->qtype) * (size_t)i * a->ldq;
     L.df_sketch = sketch_is_df(a) ? 1 : 0;
@@ -160,6 +163,7 @@ void launch_ls(rgs_arnoldi_obj* a, int i, int sparts, bool solve, int pparts, bo
     s.p_scale = s_scale(a->sk);
     s.p_df = sketch_is_df(a) ? 1 : 0;
     s.pnorm_idx = i + 1;
+    s.p_lag = 1;                    // p_{i+1} = Theta (A q'_i) / r_ii
     s.givens = gmres ? 1 : 0;
     s.arnoldi = 1;
     s.stop_tol = stop_tol;
@@ -411,7 +415,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             int pp = launch_product(&obj, *A, 0);
             launch_ls(&obj, 0, sp, m >= 1, pp, true, stop_tol);
             for (int i = 1; i <= m; ++i) {
-                sp = launch_update(&obj, i, obj.wbuf.ptr, (sketch_is_df(&obj) && s->kind == RGS_SKETCH_SRHT) ? 1 : 0);
+                sp = launch_update(&obj, i, obj.wbuf.ptr, sketch_is_df(&obj) ? 1 : 0, obj.ls.sigma + (i - 1));
                 if (i < m) pp = launch_product(&obj, *A, i);
                 launch_ls(&obj, i, sp, i < m, pp, true, stop_tol);
             }

@@ -205,13 +205,12 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
         const bool breakdown = !(r > 16.0 * 0x1p-53 * pref);
         if (a.givens) {
-            // GMRES: H(:, i-1) = sigma_{i-1} R(0:i+1, i) is complete now that r_ii is known
+            // GMRES: H(:, i-1) = R(0:i+1, i) (Sec. 4.1) is complete now that r_ii is known
             if (i == 0) {
                 if (gtid == 0) st.g[0] = r;
             } else if (blockIdx.x == G - 1 && tid < 32) {
-                const double sg = st.sigma[i - 1];
                 const double* rc = st.R + (size_t)i * st.ldr;
-                auto hcol = [&](int t) { return sg * (t < i ? rc[t] : r); };
+                auto hcol = [&](int t) { return t < i ? rc[t] : r; };
                 const double res = givens_column_warp(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, mm);
                 if (tid == 0 && (breakdown || res <= a.stop_tol)) atomicCAS(ctl + kStopWord, 0, i);
             }

@@ -157,9 +157,17 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
                 const float4 a = ld_stream_f4(w + r0, pol), b = ld_stream_f4(w + r0 + 2, pol);
                 if constexpr (sizeof(Acc) == 4) {
                     acc[0] = a.x + a.y; acc[1] = a.z + a.w; acc[2] = b.x + b.y; acc[3] = b.z + b.w;
+                    if (p.wscale) {
+                        const float fm = (float)wmul;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] *= fm;
+                    }
                 } else {
                     acc[0] = (double)a.x + (double)a.y; acc[1] = (double)a.z + (double)a.w;
                     acc[2] = (double)b.x + (double)b.y; acc[3] = (double)b.z + (double)b.w;
+                    if (p.wscale)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] *= wmul;
                 }
             } else {
                 double2 a = ld_stream_d2(w + r0, pol);
@@ -192,8 +200,8 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
                 if (r0 + e >= n) { acc[e] = (Acc)0; continue; }
                 if (p.w_df) {
                     const float2 d = reinterpret_cast<const float2*>(w)[r0 + e];
-                    if constexpr (sizeof(Acc) == 4) acc[e] = d.x + d.y;
-                    else acc[e] = (Acc)((double)d.x + (double)d.y);
+                    if constexpr (sizeof(Acc) == 4) acc[e] = (d.x + d.y) * (float)wmul;
+                    else acc[e] = (Acc)(((double)d.x + (double)d.y) * wmul);
                 } else {
                     acc[e] = (Acc)(w[r0 + e] * wmul);
                 }
