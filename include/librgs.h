@@ -75,7 +75,8 @@ RGS_API const char* rgs_last_error(rgs_handle h);
  * two n <= s < 2n, D random signs, H_s the +-1 Walsh-Hadamard matrix and P a
  * uniform sample of k rows.  Both are fully determined by (kind, n, k, seed).
  * Requires 1 <= k; SRHT requires k <= s; Gaussian stores Theta in device memory
- * (8 k n bytes).  The object holds device tables until rgs_sketch_destroy. */
+ * (8 k n bytes).  The object holds device tables until rgs_sketch_destroy, which
+ * does not use the handle (objects may be destroyed in any order). */
 RGS_API rgs_status rgs_sketch_create(rgs_handle h, rgs_sketch_kind kind, int64_t n, int32_t k,
                              uint64_t seed, rgs_sketch* out);
 RGS_API rgs_status rgs_sketch_destroy(rgs_sketch s);

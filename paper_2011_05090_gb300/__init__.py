@@ -10,10 +10,23 @@ keep the names of the C entry points in ``include/librgs.h``.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 
 import torch
+
+_exiting = False
+
+
+def _at_exit():
+    # the CUDA runtime may already be torn down when finalizers run at interpreter exit:
+    # leave the process's device memory to the driver instead of calling into the library
+    global _exiting
+    _exiting = True
+
+
+atexit.register(_at_exit)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "librgs.so")
@@ -150,7 +163,7 @@ class Handle:
         self.ptr = ptr
 
     def __del__(self):
-        if getattr(self, "ptr", None) and _lib is not None:
+        if getattr(self, "ptr", None) and _lib is not None and not _exiting:
             _lib.rgs_destroy(self.ptr)
             self.ptr = None
 
@@ -160,7 +173,7 @@ class Sketch:
         self.ptr, self.handle, self.kind, self.n, self.k, self.seed = ptr, handle, kind, n, k, seed
 
     def __del__(self):
-        if getattr(self, "ptr", None) and _lib is not None:
+        if getattr(self, "ptr", None) and _lib is not None and not _exiting:
             _lib.rgs_sketch_destroy(self.ptr)
             self.ptr = None
 
@@ -232,7 +245,7 @@ class Arnoldi:
         self.ptr, self.handle, self.sketch, self.n, self.mmax, self.qdtype = ptr, handle, sketch, n, mmax, qdtype
 
     def __del__(self):
-        if getattr(self, "ptr", None) and _lib is not None:
+        if getattr(self, "ptr", None) and _lib is not None and not _exiting:
             _lib.rgs_arnoldi_destroy(self.ptr)
             self.ptr = None
 

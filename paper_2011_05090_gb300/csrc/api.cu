@@ -215,9 +215,11 @@ rgs_status rgs_sketch_create(rgs_handle h, rgs_sketch_kind kind, int64_t n, int3
     return RGS_OK;
 }
 
+// The sketch outlives nothing it points to: its device tables are released with cudaFree
+// (which waits for work in flight) and the handle it was created on is not touched, so it
+// may be destroyed before or after that handle.
 rgs_status rgs_sketch_destroy(rgs_sketch s) {
     if (!s) return RGS_ERR_INVALID_ARG;
-    if (s->h) cudaStreamSynchronize(s->h->stream);
     delete s;
     return RGS_OK;
 }

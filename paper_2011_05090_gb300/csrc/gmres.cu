@@ -218,9 +218,9 @@ rgs_status rgs_arnoldi_create(rgs_handle h, rgs_sketch s, int64_t n, int32_t mma
     return RGS_OK;
 }
 
+// Like rgs_sketch_destroy: releases device memory only and never touches the handle.
 rgs_status rgs_arnoldi_destroy(rgs_arnoldi a) {
     if (!a) return RGS_ERR_INVALID_ARG;
-    if (a->h) cudaStreamSynchronize(a->h->stream);
     delete a;
     return RGS_OK;
 }

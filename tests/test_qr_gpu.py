@@ -212,3 +212,22 @@ def test_fp64_sketch_flag_close_to_double_float(h):
     d = rel(R1.cpu().numpy(), R2.cpu().numpy())
     print(f"FP32 storage, double-float vs FP64 transform: ||dR||/||R|| = {d:.3e}")
     assert d <= 1e-9
+
+
+def test_objects_may_outlive_their_handle():
+    """Destroying the handle first, then the sketch, then exiting must not crash (separate process)."""
+    import subprocess
+    import sys
+    code = (
+        "import torch, paper_2011_05090_gb300 as rgs\n"
+        "h = rgs.rgs_create()\n"
+        "sk = rgs.rgs_sketch_create(h, 'srht', 4096, 64, 1)\n"
+        "a = rgs.rgs_arnoldi_create(h, sk, 4096, 8)\n"
+        "rgs.load().rgs_destroy(h.ptr); h.ptr = None\n"
+        "del a, sk\n"
+        "h2 = rgs.rgs_create(); sk2 = rgs.rgs_sketch_create(h2, 'gaussian', 100, 8, 2)\n"
+        "print('ok')\n")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
