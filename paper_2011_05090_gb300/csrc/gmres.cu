@@ -441,6 +441,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
 namespace {
 
 // After the last CGS pass of step j: ||w||, sigma_{j+1}, the Givens rotation of H(:, j), stop test.
+// w = A v_j was formed from the normalised v_j = sigma_j v'_j, so H(:, j) = [sigma_t (t1 + t2)_t; ||w||].
 __global__ void cgs_finish_kernel(const double* part, int np, int j, double* sigma, const double* hacc, double* cs,
                                   double* sn, double* g, double* Hr, int ldh, double stop_tol, int* ctl) {
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
@@ -448,14 +449,13 @@ __global__ void cgs_finish_kernel(const double* part, int np, int j, double* sig
     double v = 0.0;
     for (int b = lane; b < np; b += 32) v += part[b];
     const double wn = sqrt(warp_sum(v));
-    const double sj = sigma[j];
     double hmax = 0.0;
     for (int t = lane; t <= j; t += 32) hmax = fmax(hmax, fabs(sigma[t] * hacc[t]));
     for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-    auto hcol = [&](int t) { return t <= j ? sj * sigma[t] * hacc[t] : sj * wn; };
+    auto hcol = [&](int t) { return t <= j ? sigma[t] * hacc[t] : wn; };
     const double res = givens_column_warp(j, hcol, cs, sn, g, Hr, ldh);
     if (lane == 0) {
-        const bool breakdown = !(wn * sj > 16.0 * 0x1p-53 * sj * hmax);
+        const bool breakdown = !(wn > 16.0 * 0x1p-53 * hmax);
         sigma[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
         if (breakdown || res <= stop_tol) atomicCAS(ctl + kStopWord, 0, j + 1);
     }
@@ -543,7 +543,8 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
             for (int j = 0; j < m; ++j) {
                 double* vj = V.as<double>() + (size_t)j * ldv;
                 double* vn = V.as<double>() + (size_t)(j + 1) * ldv;
-                rgs_launch_spmv(h, *A, nullptr, vj, RGS_F64, wv.ptr, 0, nullptr, nullptr, ctl);     // w = A v'_j
+                // w = A v_j = sigma_j A v'_j
+                rgs_launch_spmv(h, *A, nullptr, vj, RGS_F64, wv.ptr, 0, nullptr, nullptr, ctl, sigma + j);
                 rgs_launch_cgs_pass(h, n, V.as<double>(), ldv, j + 1, sigma, wv.as<double>(), part, coef, hacc, 0, ctl);
                 rgs_launch_cgs_update(h, n, V.as<double>(), ldv, j + 1, coef, wv.as<double>(), nullptr, nullptr, ctl);
                 rgs_launch_cgs_pass(h, n, V.as<double>(), ldv, j + 1, sigma, wv.as<double>(), part, coef, hacc, 1, ctl);

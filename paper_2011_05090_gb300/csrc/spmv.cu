@@ -46,6 +46,7 @@ struct SpmvParams {
     const double* val;      // FP64 values (FP64 mode)
     const df* vdf;          // double-float values (double-float mode)
     const void* x;
+    const double* yscale;   // optional device scalar multiplying the FP64 product
     void* w;                // FP64 or double-float output
     const uint32_t* signbits;
     const int32_t* rows;
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams
                 } else {
                     double a = 0.0;
                     for (int q = b0; q < b1; ++q) a = fma(__ldg(p.val + q), (double)x[__ldg(p.colind + q)], a);
+                    if (p.yscale) a *= *p.yscale;
                     acc = a;
                     reinterpret_cast<double*>(p.w)[r] = a;
                 }
@@ -309,8 +311,10 @@ int rgs_spmv_nparts(const rgs_context* ctx, int64_t n) {
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
 int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
-                    const rgs_sketch_obj* sk, double* partials, const int* ctl) {
+                    const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale) {
     SpmvParams p{};
+    RGS_REQUIRE(!(dfm && yscale), "scaled products are FP64 only");
+    p.yscale = yscale;
     p.n = A.n;
     p.rowptr = A.rowptr;
     p.colind = A.colind;

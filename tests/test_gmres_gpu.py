@@ -161,3 +161,23 @@ def test_cgs2_converges_like_oracle(h):
     xs = x.cpu().numpy()
     assert res["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
     assert abs(res["total_steps"] - ref.steps) <= max(3, 0.05 * ref.steps)
+
+
+@pytest.mark.parametrize("solver", ["rgmres_f32", "rgmres_f64", "cgs2"])
+def test_large_norm_operator_no_overflow(h, solver):
+    # ||A|| ~ 1e12: unnormalised Krylov vectors would grow like ||A||^j and overflow
+    csr, A, b = system(40, 40, 30.0, 6)
+    scale = 1e8
+    csr = (csr[0], csr[1], csr[2] * scale)
+    A = A * scale
+    n = A.shape[0]
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    if solver == "cgs2":
+        res = rgs.cgs2_gmres_solve(h, C, dev(b), x, restart=60, rtol=1e-8, max_cycles=100)
+    else:
+        sk = rgs.rgs_sketch_create(h, "srht", n, 150, 2)
+        q = torch.float32 if solver == "rgmres_f32" else torch.float64
+        res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=60, rtol=1e-8, max_cycles=100, qdtype=q)
+    xs = x.cpu().numpy()
+    assert res["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
