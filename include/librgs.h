@@ -29,6 +29,7 @@
 #ifndef LIBRGS_H
 #define LIBRGS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -85,6 +86,24 @@ RGS_API rgs_status rgs_sketch_destroy(rgs_sketch s);
  * The sketch of Alg. 2 step 1 / step 4 applied to a block of vectors. */
 RGS_API rgs_status rgs_sketch_apply(rgs_handle h, rgs_sketch s, int32_t ncols, const double* X, int64_t ldx,
                             double* Y, int64_t ldy);
+
+/* Y = Theta X exactly like rgs_sketch_apply, but without allocating device memory during the
+ * call, for callers that cannot allow an allocation there: cudaMalloc synchronises the device
+ * (a stall inside a latency-critical loop), and an application whose framework allocator holds
+ * nearly all free device memory would see it fail.  (The paper has no counterpart: this is an
+ * interface variant of the sketch of Sec. 2.1.)
+ *  - The partial sketches live in a fixed device array of RGS_NOALLOC_SCRATCH_BYTES (8 MiB),
+ *    reserved on every device that loads the library until the process exits.
+ *  - Requires k * ncols <= RGS_NOALLOC_SCRATCH_BYTES / 8; larger calls return
+ *    RGS_ERR_INVALID_ARG (split the columns).  The handle's device must be current.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture.
+ *  - Every call shares the array: calls whose work overlaps on the GPU (other streams or
+ *    host threads) race and must be serialised by the caller.
+ *  - Calls no cudaMalloc / cudaFree; work is queued on the handle's stream. */
+#define RGS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t ncols, const double* X,
+                                            int64_t ldx, double* Y, int64_t ldy);
 
 /* ---------------------------------------------------------------- RGS QR
  * Alg. 2: given W (n x m, FP64) and Theta with m <= k, computes Q (n x m) and

@@ -52,7 +52,7 @@ _DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF
 _KIND = {"gaussian": RGS_SKETCH_GAUSSIAN, "srht": RGS_SKETCH_SRHT}
 
 EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", "rgs_last_error",
-            "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_qr",
+            "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_sketch_apply_noalloc", "rgs_qr",
             "rgs_arnoldi_create", "rgs_arnoldi_destroy", "rgs_arnoldi_start", "rgs_arnoldi_step",
             "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgmres_solve", "cgs2_gmres_solve",
             "rgmres_set_preconditioner", "rgmres_solve_batched"]
@@ -108,6 +108,7 @@ def load():
         "rgs_sketch_create": [P, ctypes.c_int, I64, I32, ctypes.c_uint64, ctypes.POINTER(P)],
         "rgs_sketch_destroy": [P],
         "rgs_sketch_apply": [P, P, I32, P, I64, P, I64],
+        "rgs_sketch_apply_noalloc": [P, P, I32, P, I64, P, I64],
         "rgs_qr": [P, P, I64, I32, P, I64, P, ctypes.c_int, I64, P, P, I64, P, I64, I32, ctypes.POINTER(QRInfo)],
         "rgs_arnoldi_create": [P, P, I64, I32, ctypes.c_int, ctypes.POINTER(P)],
         "rgs_arnoldi_destroy": [P],
@@ -209,6 +210,21 @@ def rgs_sketch_apply(h, sk, X, Y=None):
     py, ldy = _colmajor(Y, sk.k, ncols)
     _check(load().rgs_sketch_apply(h.ptr, sk.ptr, ncols, px, ldx, py, ldy), h)
     return Y
+
+
+def rgs_sketch_apply_noalloc(h, sk, X, Y):
+    """Y (k x ncols) = Theta X like rgs_sketch_apply, with no device allocation during the call
+    (the partial sketches use the library's fixed scratch array; see include/librgs.h)."""
+    if X.dim() == 1:
+        X = X[:, None]
+    ncols = X.shape[1]
+    px, ldx = _colmajor(X, sk.n, ncols)
+    py, ldy = _colmajor(Y, sk.k, ncols)
+    _check(load().rgs_sketch_apply_noalloc(h.ptr, sk.ptr, ncols, px, ldx, py, ldy), h)
+    return Y
+
+
+RGS_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 def rgs_qr(h, sk, W, Q, R, qscale=None, S=None, flags=0):

@@ -277,6 +277,7 @@ struct UpdateLaunch {
     const double* coef;     // ncols FP64 coefficients (device)
     void* qout;             // optional stored result column (qtype)
     int df_sketch;          // SRHT transform in double-float (FP32 pairs) instead of FP64
+    int max_parts;          // 0, or an upper bound on the partial sketches per column
 };
 // Number of partial sketches (per input column) the next update/sketch launch will write.
 int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols);

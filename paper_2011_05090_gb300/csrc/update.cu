@@ -375,8 +375,9 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     if (L.qout) vec = vec && ((uintptr_t)L.qout % (4 * esz) == 0 || aligned16(L.qout)) && (L.ldq % 4 == 0);
     p.vec = vec ? 1 : 0;
     const bool srht = sk->kind == RGS_SKETCH_SRHT;
-    const int gx = srht ? rgs_update_nparts(ctx, sk, n, L.wcols)
-                        : std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+    int gx = srht ? rgs_update_nparts(ctx, sk, n, L.wcols)
+                  : std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+    if (srht && L.max_parts > 0) gx = std::min(gx, L.max_parts);
     if (srht) {
         p.signbits = sk->signbits.as<uint32_t>();
         p.rows = sk->rows.as<int32_t>();
@@ -411,7 +412,8 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
         return gx;
     }
     // Gaussian: sketch the stored column (or the input columns when nothing is stored)
-    const int gg = rgs_update_nparts(ctx, sk, n, L.wcols);
+    int gg = rgs_update_nparts(ctx, sk, n, L.wcols);
+    if (L.max_parts > 0) gg = std::min(gg, L.max_parts);
     if (L.qout) {
         switch (L.qtype) {
             case RGS_F64: launch_gauss_t<double>(ctx, sk->theta.as<double>(), sk->k, n, L.qout, L.ldq, 1, partials, gg, ctl); break;
