@@ -179,7 +179,7 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_gmres_c3(rgs, h, N=128):
+def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "cgs2")):
     """Time-to-1e-8 of RGMRES (FP32 basis) and FP64 CGS2-GMRES on the 3D convection-diffusion system."""
     import torch
     import synth
@@ -193,10 +193,13 @@ def run_gmres_c3(rgs, h, N=128):
     rgs.rgmres_solve(h, sk, C, b, xw, restart=100, max_cycles=1)
     rgs.cgs2_gmres_solve(h, C, b, xw.zero_(), restart=100, max_cycles=1)
     out = {"config": "convdiff3d 128^3 n=2097152 nnz=%d Pe=50 sigma=1 corr=8 restart=100 rtol=1e-8" % len(csr[1])}
-    for name, fn in (("rgmres_f32_srht400", lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8,
-                                                                     max_cycles=400, qdtype=torch.float32)),
-                     ("cgs2_gmres_f64", lambda x: rgs.cgs2_gmres_solve(h, C, b, x, restart=100, rtol=1e-8,
-                                                                      max_cycles=400))):
+    runs = (("rgmres_f32_srht400", "rgmres", lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8,
+                                                                    max_cycles=max_cycles, qdtype=torch.float32)),
+            ("cgs2_gmres_f64", "cgs2", lambda x: rgs.cgs2_gmres_solve(h, C, b, x, restart=100, rtol=1e-8,
+                                                                     max_cycles=max_cycles)))
+    for name, key, fn in runs:
+        if key not in solvers:
+            continue
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -206,9 +209,20 @@ def run_gmres_c3(rgs, h, N=128):
         out[name] = {"seconds": dt, "converged": res["converged"], "rel_residual": res["rel_residual"],
                      "cycles": res["cycles"], "arnoldi_steps": res["total_steps"],
                      "us_per_step": 1e6 * dt / max(1, res["total_steps"])}
-    a, c = out["rgmres_f32_srht400"], out["cgs2_gmres_f64"]
-    out["speedup_vs_cgs2_fp64"] = c["seconds"] / a["seconds"]
+    if "rgmres_f32_srht400" in out and "cgs2_gmres_f64" in out:
+        a, c = out["rgmres_f32_srht400"], out["cgs2_gmres_f64"]
+        out["speedup_vs_cgs2_fp64"] = c["seconds"] / a["seconds"]
     return out
+
+
+def run_gmres_profile(args):
+    """Profiling case: the 128^3 RGMRES and/or CGS2 solve for a few cycles only (no bench line)."""
+    import paper_2011_05090_gb300 as rgs
+    from paper_2011_05090_gb300 import build as libbuild
+    libbuild.build()
+    h = rgs.rgs_create()
+    print(json.dumps(run_gmres_c3(rgs, h, max_cycles=args.gmres_cycles, solvers=tuple(args.gmres_only.split(",")))),
+          flush=True)
 
 
 def run_ours(args):
@@ -335,10 +349,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--gmres-only", default="", help="profiling cases only: 'rgmres', 'cgs2' or both")
+    ap.add_argument("--gmres-cycles", type=int, default=400)
     ap.add_argument("--cols", type=int, default=0, help="profiling cases only: override m (the bench line is m=500)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.gmres_only:
+        run_gmres_profile(args)
     else:
         run_ours(args)
 
