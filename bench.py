@@ -61,7 +61,8 @@ def peaks():
 
 
 def profile_traffic():
-    """Per-launch DRAM traffic of the fused update kernel from the committed ncu summary, if any."""
+    """Mean per-launch DRAM traffic (bytes) of the fused update kernel over the m = 500 step, from the
+    committed ncu summary (measured on one launch, scaled by the launch's algorithmic bytes)."""
     path = os.path.join(ROOT, "profiles", "rgs_update_sketch_c2.txt")
     try:
         with open(path) as f:
@@ -284,7 +285,7 @@ def run_ours(args):
     achieved = upd / (upd_ms * 1e-3) / 1e9
     traffic_full = profile_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (traffic_full / m) if traffic_full else None,
+                "traffic": traffic_full if (traffic_full and m == M_COLS) else None,
                 "kernel": "update_sketch_kernel<float,SRHT>",
                 "bytes_per_launch": upd / m, "launches_per_step": m,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
