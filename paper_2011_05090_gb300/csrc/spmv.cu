@@ -56,8 +56,64 @@ struct SpmvParams {
     const int* ctl;
 };
 
+// (A x)_r for one row, stored to w and returned.  The column indices and values of up to
+// RB nonzeros are loaded together, then the gathers of x, then the products (two independent
+// accumulation chains), so a row costs three memory round trips instead of one per nonzero.
+constexpr int RB = 8;
+
+template <typename TX, bool DFM>
+__device__ __forceinline__ typename std::conditional<DFM, df, double>::type row_product(const SpmvParams& p,
+                                                                                       const TX* x, int64_t r) {
+    using V = typename std::conditional<DFM, df, double>::type;
+    if (r >= p.n) return FW<V>::zero();
+    const int b0 = __ldg(p.rowptr + r), b1 = __ldg(p.rowptr + r + 1);
+    V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
+    for (int q0 = b0; q0 < b1; q0 += RB) {
+        int c[RB];
+        V v[RB];
+        float xs[RB];
+        double xd[RB];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            if (q0 + t < b1) {
+                c[t] = __ldg(p.colind + q0 + t);
+                if constexpr (DFM) v[t] = p.vdf[q0 + t];
+                else v[t] = __ldg(p.val + q0 + t);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            if (q0 + t < b1) {
+                if constexpr (DFM) xs[t] = xf(x, c[t]);
+                else xd[t] = (double)x[c[t]];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+            if (q0 + t < b1) {
+                if constexpr (DFM) {
+                    const df pr = df_mul_f(v[t], xs[t]);
+                    if (t & 1) acc1 = df_add(acc1, pr); else acc0 = df_add(acc0, pr);
+                } else {
+                    if (t & 1) acc1 = fma(v[t], xd[t], acc1); else acc0 = fma(v[t], xd[t], acc0);
+                }
+            }
+        }
+    }
+    if constexpr (DFM) {
+        const df a = df_add(acc0, acc1);
+        reinterpret_cast<df*>(p.w)[r] = a;
+        return a;
+    } else {
+        double a = acc0 + acc1;
+        if (p.yscale) a *= *p.yscale;
+        reinterpret_cast<double*>(p.w)[r] = a;
+        return a;
+    }
+}
+
 template <typename TX, bool DFM, bool SRHT>
-__global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams p) {
+__global__ void __launch_bounds__(TILE_THREADS, 3) spmv_sketch_kernel(SpmvParams p) {
     using V = typename std::conditional<DFM, df, double>::type;
     using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
@@ -74,24 +130,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams
         const int64_t r0 = (int64_t)tile * TILE + threadIdx.x * 4;
         V z[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int64_t r = r0 + e;
-            V acc = F::zero();
-            if (r < p.n) {
-                const int b0 = __ldg(p.rowptr + r), b1 = __ldg(p.rowptr + r + 1);
-                if constexpr (DFM) {
-                    for (int q = b0; q < b1; ++q) acc = df_add(acc, df_mul_f(p.vdf[q], xf(x, __ldg(p.colind + q))));
-                    reinterpret_cast<df*>(p.w)[r] = acc;
-                } else {
-                    double a = 0.0;
-                    for (int q = b0; q < b1; ++q) a = fma(__ldg(p.val + q), (double)x[__ldg(p.colind + q)], a);
-                    if (p.yscale) a *= *p.yscale;
-                    acc = a;
-                    reinterpret_cast<double*>(p.w)[r] = a;
-                }
-            }
-            z[e] = acc;
-        }
+        for (int e = 0; e < 4; ++e) z[e] = row_product<TX, DFM>(p, x, r0 + e);
         if (SRHT) srht_tile<V>(z, r0, p.n, tile, p.signbits, srow, p.k, zt, part);
     }
     if (SRHT) {
@@ -306,7 +345,7 @@ void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* ou
 
 int rgs_spmv_nparts(const rgs_context* ctx, int64_t n) {
     const int ntiles = (int)((n + TILE - 1) / TILE);
-    return std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+    return std::max(1, std::min(ntiles, ctx->num_sms * 3));     // 3 resident CTAs per SM (80 registers)
 }
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
