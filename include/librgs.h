@@ -199,6 +199,8 @@ typedef struct {
     int32_t status;
     double rel_residual;    /* final ||b - A x|| / ||b|| in FP64 */
     double* history;        /* optional host array (max_cycles + 1): residual after each cycle */
+    int32_t fallback_cycle; /* cycle at which the preconditioner was switched off, or -1 */
+    int32_t reserved;
 } rgmres_info;
 
 RGS_API rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const double* b, double* x,
@@ -206,16 +208,57 @@ RGS_API rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, co
 RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, double* x,
                             const rgmres_opts* opts, rgmres_info* info);
 
-/* Batched solves (one persistent launch) and the learned preconditioner are
- * declared for interface stability; they return RGS_ERR_NOT_IMPLEMENTED until
- * built.  Right preconditioning follows Sec. 5.3 (A M, x = M y); kind 1 is the
- * Jacobi preconditioner diag(A)^-1. */
+/* ---------------------------------------------------------------- preconditioning
+ * Right preconditioning follows Sec. 5.3: GMRES runs on A M and returns x = x0 + M (Q y).
+ * rgmres_set_preconditioner selects it for the following rgmres_solve calls on the handle:
+ *   RGS_PRECOND_NONE         -- none (the default);
+ *   RGS_PRECOND_JACOBI       -- M = diag(A)^{-1} (linear; A D^{-1} is formed once per solve);
+ *   RGS_PRECOND_LEARNED_CONV -- M(r) = ||r|| net(r / ||r||, log kappa), a trained rgs_convnet on
+ *                               the H x W grid of the unknowns; nonlinear, so flexible = 1 is
+ *                               required and the solver keeps z_j = M(q_j) (flexible GMRES,
+ *                               x = x0 + Z y).  params points to an rgs_learned_precond.
+ * With a preconditioner set, a restart whose true residual is not below (1 - 2^-10) times the
+ * previous one switches the rest of the solve to the unpreconditioned method
+ * (rgmres_info.fallback_cycle).
+ * The handle keeps the pointers in params (not copies): keep them valid while solving. */
 typedef enum { RGS_PRECOND_NONE = 0, RGS_PRECOND_JACOBI = 1, RGS_PRECOND_LEARNED_CONV = 2 } rgs_precond_kind;
+typedef struct rgs_convnet_obj* rgs_convnet;
+typedef struct {
+    rgs_convnet net;
+    const double* logkappa;   /* device, H x W (row-major, x fastest): second input channel */
+} rgs_learned_precond;
 RGS_API rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void* params,
-                                     int32_t flexible);
+                                             int32_t flexible);
+
+/* ---------------------------------------------------------------- learned preconditioner network
+ * Six 3x3 convolutions (zero padding) with channels 2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 and
+ * ReLU between layers, on a batch of H x W grids (H a multiple of 8, W of 16).  Weights are
+ * BF16 copies of FP32 master parameters; products run on the tensor cores with FP32
+ * accumulation; activations are BF16.  Parameters are flat FP32: for each layer l the weights
+ * W_l[c_out][c_in][3][3] then the biases b_l[c_out] (rgs_convnet_num_params() in all).
+ *   in:     batch x 2 x H x W FP32 (device): channel 0 the normalised residual, 1 log kappa.
+ *   out:    batch x H x W FP32 (device).
+ *   target: batch x H x W FP32 (device), for the loss mean_b ||out_b - t_b||^2 / ||t_b||^2.
+ * rgs_convnet_train_step: forward, loss, backward and one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on the batch; rgs_convnet_loss_grad: loss and the FP32 gradient (host) without
+ * updating.  max_batch bounds the batch of every call (it sizes the saved activations). */
+RGS_API int64_t rgs_convnet_num_params(void);
+RGS_API rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32_t max_batch, uint64_t seed,
+                                      rgs_convnet* out);
+RGS_API rgs_status rgs_convnet_destroy(rgs_convnet net);
+RGS_API rgs_status rgs_convnet_get_params(rgs_handle h, rgs_convnet net, float* host, int64_t count);
+RGS_API rgs_status rgs_convnet_set_params(rgs_handle h, rgs_convnet net, const float* host, int64_t count);
+RGS_API rgs_status rgs_convnet_forward(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, float* out);
+RGS_API rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, const float* in,
+                                         const float* target, double* loss, float* grad_host);
+RGS_API rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, const float* in,
+                                          const float* target, float lr, double* loss);
+
+/* Batched solves in one persistent launch are declared for interface stability; they return
+ * RGS_ERR_NOT_IMPLEMENTED until built. */
 RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_sketch* sketches,
-                                const rgs_csr* A, const double* const* b, double* const* x,
-                                const rgmres_opts* opts, rgmres_info* info);
+                                        const rgs_csr* A, const double* const* b, double* const* x,
+                                        const rgmres_opts* opts, rgmres_info* info);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,9 @@ EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", 
             "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_sketch_apply_noalloc", "rgs_qr",
             "rgs_arnoldi_create", "rgs_arnoldi_destroy", "rgs_arnoldi_start", "rgs_arnoldi_step",
             "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgmres_solve", "cgs2_gmres_solve",
-            "rgmres_set_preconditioner", "rgmres_solve_batched"]
+            "rgmres_set_preconditioner", "rgs_convnet_num_params", "rgs_convnet_create", "rgs_convnet_destroy",
+            "rgs_convnet_get_params", "rgs_convnet_set_params", "rgs_convnet_forward", "rgs_convnet_loss_grad",
+            "rgs_convnet_train_step", "rgmres_solve_batched"]
 
 
 class RgsError(RuntimeError):
@@ -84,7 +86,12 @@ class GmresOpts(ctypes.Structure):
 class GmresInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("total_steps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double))]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("fallback_cycle", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class LearnedPrecond(ctypes.Structure):
+    _fields_ = [("net", ctypes.c_void_p), ("logkappa", ctypes.c_void_p)]
 
 
 _lib = None
@@ -120,11 +127,20 @@ def load():
         "cgs2_gmres_solve": [P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
         "rgmres_set_preconditioner": [P, ctypes.c_int, P, I32],
         "rgmres_solve_batched": [P, I32, P, P, P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+        "rgs_convnet_num_params": [],
+        "rgs_convnet_create": [P, I32, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)],
+        "rgs_convnet_destroy": [P],
+        "rgs_convnet_get_params": [P, P, P, I64],
+        "rgs_convnet_set_params": [P, P, P, I64],
+        "rgs_convnet_forward": [P, P, I32, P, P],
+        "rgs_convnet_loss_grad": [P, P, I32, P, P, ctypes.POINTER(D), P],
+        "rgs_convnet_train_step": [P, P, I32, P, P, ctypes.c_float, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_char_p if name in ("rgs_status_string", "rgs_last_error") else ctypes.c_int
+    L.rgs_convnet_num_params.restype = I64
     _lib = L
     return L
 
@@ -326,7 +342,7 @@ def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps):
 def _gmres_result(st, info, hist, h):
     res = {"cycles": info.cycles, "total_steps": info.total_steps, "converged": bool(info.converged),
            "status": info.status, "rel_residual": info.rel_residual,
-           "history": [hist[i] for i in range(info.cycles + 1)]}
+           "history": [hist[i] for i in range(info.cycles + 1)], "fallback_cycle": info.fallback_cycle}
     if st not in (RGS_OK, RGS_ERR_NOT_CONVERGED):
         try:
             _check(st, h)
@@ -364,3 +380,92 @@ def csr_to_device(rowptr, colind, val, device="cuda"):
     t = (torch.as_tensor(rowptr, dtype=torch.int32).to(device), torch.as_tensor(colind, dtype=torch.int32).to(device),
          torch.as_tensor(val, dtype=torch.float64).to(device))
     return t, csr_struct(*t)
+
+
+# ------------------------------------------------------------------ preconditioning
+def rgmres_set_preconditioner(h, kind, net=None, logkappa=None, flexible=False):
+    """Select the right preconditioner of the following rgmres_solve calls on ``h``:
+    "none", "jacobi" or "learned" (a ConvNet and its log-kappa grid, FP64 on the device; flexible)."""
+    k = {"none": RGS_PRECOND_NONE, "jacobi": RGS_PRECOND_JACOBI, "learned": RGS_PRECOND_LEARNED_CONV}[kind]
+    params = None
+    if k == RGS_PRECOND_LEARNED_CONV:
+        if logkappa.dtype != torch.float64 or not logkappa.is_cuda or not logkappa.is_contiguous():
+            raise ValueError("logkappa must be a contiguous FP64 CUDA tensor")
+        h._precond = LearnedPrecond(net.ptr, logkappa.data_ptr())
+        h._precond_refs = (net, logkappa)          # the library keeps the pointers
+        params = ctypes.byref(h._precond)
+    else:
+        h._precond_refs = None
+    _check(load().rgmres_set_preconditioner(h.ptr, k, params, 1 if flexible else 0), h)
+
+
+class ConvNet:
+    def __init__(self, ptr, handle, height, width, max_batch):
+        self.ptr, self.handle, self.height, self.width, self.max_batch = ptr, handle, height, width, max_batch
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None and not _exiting:
+            _lib.rgs_convnet_destroy(self.ptr)
+            self.ptr = None
+
+
+def rgs_convnet_num_params():
+    return int(load().rgs_convnet_num_params())
+
+
+def rgs_convnet_create(h, height, width, max_batch=1, seed=0):
+    out = ctypes.c_void_p()
+    _check(load().rgs_convnet_create(h.ptr, int(height), int(width), int(max_batch), int(seed), ctypes.byref(out)), h)
+    return ConvNet(out.value, h, int(height), int(width), int(max_batch))
+
+
+def rgs_convnet_get_params(h, net):
+    """The flat FP32 parameters as a NumPy array."""
+    import numpy as np
+    p = np.empty(rgs_convnet_num_params(), dtype=np.float32)
+    _check(load().rgs_convnet_get_params(h.ptr, net.ptr, p.ctypes.data_as(ctypes.c_void_p), p.size), h)
+    return p
+
+
+def rgs_convnet_set_params(h, net, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().rgs_convnet_set_params(h.ptr, net.ptr, p.ctypes.data_as(ctypes.c_void_p), p.size), h)
+
+
+def _net_io(net, x, name, channels):
+    shape = (x.shape[0], channels, net.height, net.width) if channels > 1 else (x.shape[0], net.height, net.width)
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or tuple(x.shape) != shape:
+        raise ValueError(f"{name} must be a contiguous FP32 CUDA tensor of shape {shape}")
+
+
+def rgs_convnet_forward(h, net, x, out=None):
+    """out (B x H x W) = net(x) for x of shape (B, 2, H, W) FP32 on the device."""
+    _net_io(net, x, "x", 2)
+    if out is None:
+        out = torch.empty(x.shape[0], net.height, net.width, dtype=torch.float32, device=x.device)
+    _net_io(net, out, "out", 1)
+    _check(load().rgs_convnet_forward(h.ptr, net.ptr, x.shape[0], x.data_ptr(), out.data_ptr()), h)
+    return out
+
+
+def rgs_convnet_loss_grad(h, net, x, target):
+    """(loss, flat FP32 gradient as NumPy) of mean_b ||net(x_b) - t_b||^2 / ||t_b||^2."""
+    import numpy as np
+    _net_io(net, x, "x", 2)
+    _net_io(net, target, "target", 1)
+    loss = ctypes.c_double()
+    g = np.empty(rgs_convnet_num_params(), dtype=np.float32)
+    _check(load().rgs_convnet_loss_grad(h.ptr, net.ptr, x.shape[0], x.data_ptr(), target.data_ptr(),
+                                        ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)), h)
+    return loss.value, g
+
+
+def rgs_convnet_train_step(h, net, x, target, lr=1e-3):
+    """One Adam step on the batch; returns the loss before the step."""
+    _net_io(net, x, "x", 2)
+    _net_io(net, target, "target", 1)
+    loss = ctypes.c_double()
+    _check(load().rgs_convnet_train_step(h.ptr, net.ptr, x.shape[0], x.data_ptr(), target.data_ptr(), float(lr),
+                                         ctypes.byref(loss)), h)
+    return loss.value

@@ -65,7 +65,10 @@ struct rgs_context {
     DevBuf work;           // P = Theta W, certificates
     int upd_blocks_per_sm = 4;
     int ls_blocks = 0;     // cooperative grid of the least-squares kernel
-    int precond_kind = 0;
+    int precond_kind = 0;  // rgmres_set_preconditioner: RGS_PRECOND_*
+    int precond_flexible = 0;
+    void* precond_net = nullptr;           // RGS_PRECOND_LEARNED_CONV: the network
+    const double* precond_field = nullptr; // and its second input channel (log kappa, H x W)
     int launches = 0;      // kernels launched by the current call
     std::vector<cudaEvent_t> events;   // pool for per-phase timings
     ~rgs_context() { for (auto e : events) cudaEventDestroy(e); }
@@ -128,6 +131,7 @@ constexpr int kStatusWord = 0;
 constexpr int kDetailWord = 1;
 constexpr int kStopWord = 5;     // an Arnoldi cycle ended early (convergence or happy breakdown)
 constexpr int kStepsWord = 6;    // Arnoldi steps of the cycle just solved
+constexpr int kFlagWord = 7;     // set-up checks (e.g. a zero diagonal for Jacobi)
 // the grid barrier's words sit on separate 128-byte lines so that polling one
 // does not queue behind atomics on another
 constexpr int kBarCount = 32;     // the barrier word
@@ -297,7 +301,11 @@ void rgs_launch_residual(rgs_context* ctx, const rgs_csr& A, const double* x, co
                          double* part, double* norm_out);
 void rgs_launch_norm(rgs_context* ctx, int64_t n, const double* v, double* part, double* norm_out);
 void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype, int64_t ldq, const double* cy,
-                           double* x, const int* ctl);
+                           double* x, const int* ctl, const double* rowscale = nullptr);
+void rgs_launch_jacobi_setup(rgs_context* ctx, const rgs_csr& A, double* dinv, double* scaled_val);
+// convnet.cu: z = M(x) = ||x|| net(x / ||x||, log kappa) for one grid vector x (xtype), z FP32
+void rgs_convnet_apply_precond(rgs_context* ctx, void* net, const double* logkappa, const void* x, int xtype, float* z);
+int64_t rgs_convnet_grid_points(const void* net);     // H x W of the network's grid
 void rgs_launch_hess_solve(rgs_context* ctx, const double* Hr, int ldh, const double* g, const double* colscale,
                            int jmax, double* y, double* cy, int* ctl);
 int rgs_multidot_grid(const rgs_context* ctx, int64_t n);

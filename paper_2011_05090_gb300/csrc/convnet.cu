@@ -1,0 +1,703 @@
+// The learned preconditioner: six 3x3 convolutions (2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
+// between layers, zero padding) on H x W grids, with hand-written forward and backward kernels.
+//
+//  - conv3x3_mma_kernel: the convolution as an implicit GEMM (pixels x (tap, c_in) times
+//    (tap, c_in) x c_out) on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation).  A CTA
+//    stages an 8 x 16 pixel tile with its one-pixel halo and the layer's weights in shared memory
+//    (channel strides padded so fragment loads are bank-conflict free).  The same kernel computes
+//    the backward pass for the activations: the gradient of a layer's input is the convolution of
+//    the output gradient with the taps flipped and c_in / c_out swapped, masked by ReLU'.
+//  - dweight_kernel: weight and bias gradients (sums over all pixels of the batch) in FP32.
+//  - loss / Adam / packing kernels.
+// Activations are BF16 in NHWC layout; FP32 master parameters are repacked into BF16 after
+// every update.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+using bf16 = __nv_bfloat16;
+using namespace rgsdev;
+
+namespace {
+
+constexpr int NL = 6;
+constexpr int C_IN[NL] = {2, 32, 32, 32, 32, 32};
+constexpr int C_OUT[NL] = {32, 32, 32, 32, 32, 1};
+constexpr int CS_IN[NL] = {16, 32, 32, 32, 32, 32};   // stored channels of each layer's input
+constexpr int CO_P[NL] = {32, 32, 32, 32, 32, 8};     // output channels padded to n8 tiles
+constexpr int TH = 8, TW = 16;                        // pixel tile of a CTA
+
+constexpr int64_t layer_w_count(int l) { return (int64_t)C_OUT[l] * C_IN[l] * 9; }
+constexpr int64_t layer_count(int l) { return layer_w_count(l) + C_OUT[l]; }
+int64_t param_offset(int l) {
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += layer_count(i);
+    return o;
+}
+int64_t total_params() { return param_offset(NL); }
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct ConvArgs {
+    const bf16* x;        // input, NHWC with CS channels
+    const bf16* w;        // [9][CO][CS] (tap, output channel, input channel)
+    const float* bias;    // [CO] (MODE 0, 1)
+    void* out;            // MODE 0, 2: NHWC bf16 with CO channels; MODE 1: FP32 [b][y][x] (channel 0)
+    const bf16* mask;     // MODE 2: NHWC bf16 with CO channels; output zeroed where mask <= 0
+    const float* scale;   // MODE 1: optional per-sample factor
+    int H, W;
+};
+
+// MODE 0: bias + ReLU, BF16 out.  MODE 1: bias, FP32 channel 0 out (times scale).  MODE 2: ReLU'
+// mask (backward for the activations), BF16 out.
+template <int CS, int NT, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_mma_kernel(ConvArgs a) {
+    constexpr int HS = CS + 8;          // padded stride: fragment loads hit 32 distinct banks
+    constexpr int CO = NT * 8;
+    __shared__ __align__(16) bf16 sx[(TH + 2) * (TW + 2) * HS];
+    __shared__ __align__(16) bf16 sw[9 * CO * HS];
+    const int b = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bf16* X = a.x + (size_t)b * a.H * a.W * CS;
+    for (int c = tid; c < (TH + 2) * (TW + 2) * (CS / 8); c += 128) {
+        const int pix = c / (CS / 8), ch = (c % (CS / 8)) * 8;
+        const int hy = pix / (TW + 2), hx = pix % (TW + 2);
+        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+            v = *reinterpret_cast<const uint4*>(X + ((size_t)gy * a.W + gx) * CS + ch);
+        *reinterpret_cast<uint4*>(sx + pix * HS + ch) = v;
+    }
+    for (int c = tid; c < 9 * CO * (CS / 8); c += 128) {
+        const int row = c / (CS / 8), ch = (c % (CS / 8)) * 8;
+        *reinterpret_cast<uint4*>(sw + row * HS + ch) = *reinterpret_cast<const uint4*>(a.w + (size_t)row * CS + ch);
+    }
+    __syncthreads();
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+        for (int kc = 0; kc < CS; kc += 16) {
+            uint32_t afr[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const bf16* base = sx + ((warp * 2 + mt + dy) * (TW + 2) + dx) * HS + kc + 2 * t;
+                afr[mt][0] = ld32(base + g * HS);
+                afr[mt][1] = ld32(base + (g + 8) * HS);
+                afr[mt][2] = ld32(base + g * HS + 8);
+                afr[mt][3] = ld32(base + (g + 8) * HS + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const bf16* wb = sw + (tap * CO + nt * 8 + g) * HS + kc + 2 * t;
+                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], afr[mt], b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int y = y0 + warp * 2 + mt;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int co = nt * 8 + 2 * t;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + g + 8 * half;
+                const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (MODE == 0) {
+                    v0 = fmaxf(v0 + a.bias[co], 0.f);
+                    v1 = fmaxf(v1 + a.bias[co + 1], 0.f);
+                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(a.out) + pix * CO + co) =
+                        __floats2bfloat162_rn(v0, v1);
+                } else if (MODE == 1) {
+                    if (co == 0) {
+                        const float s = a.scale ? a.scale[b] : 1.f;
+                        reinterpret_cast<float*>(a.out)[pix] = (v0 + a.bias[0]) * s;
+                    }
+                } else {
+                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * CO + co);
+                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(a.out) + pix * CO + co) =
+                        __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// Weight and bias gradients of one layer: dW[co][ci][tap] = sum over pixels of
+// dA[p][co] h[p + off(tap)][ci], db[co] = sum dA[p][co].  Per-CTA partial sums (fixed order)
+// over a grid-stride range of pixel tiles; part has NOUT = COUT*CIN*9 + COUT floats per CTA.
+template <int CSH, int CIN, int CSD, int COUT>
+__global__ void __launch_bounds__(256) dweight_kernel(const bf16* __restrict__ h, const bf16* __restrict__ dA,
+                                                      int B, int H, int W, float* __restrict__ part) {
+    constexpr int NW_ = COUT * CIN * 9;
+    constexpr int NOUT = NW_ + COUT;
+    constexpr int PER = (NOUT + 255) / 256;
+    __shared__ float sh[(TH + 2) * (TW + 2) * CIN];
+    __shared__ float sd[TH * TW * COUT];
+    float acc[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) acc[j] = 0.f;
+    const int tilesx = W / TW, tilesy = H / TH;
+    const int ntiles = B * tilesx * tilesy;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = tile / (tilesx * tilesy), r = tile % (tilesx * tilesy);
+        const int y0 = (r / tilesx) * TH, x0 = (r % tilesx) * TW;
+        __syncthreads();
+        for (int c = threadIdx.x; c < (TH + 2) * (TW + 2) * CIN; c += 256) {
+            const int pix = c / CIN, ci = c % CIN;
+            const int gy = y0 - 1 + pix / (TW + 2), gx = x0 - 1 + pix % (TW + 2);
+            float v = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = __bfloat162float(h[(((size_t)b * H + gy) * W + gx) * CSH + ci]);
+            sh[c] = v;
+        }
+        for (int c = threadIdx.x; c < TH * TW * COUT; c += 256) {
+            const int pix = c / COUT, co = c % COUT;
+            const int gy = y0 + pix / TW, gx = x0 + pix % TW;
+            sd[c] = __bfloat162float(dA[(((size_t)b * H + gy) * W + gx) * CSD + co]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int o = threadIdx.x + 256 * j;
+            if (o < NW_) {
+                const int co = o / (CIN * 9), rem = o % (CIN * 9), ci = rem / 9, tap = rem % 9;
+                const int dy = tap / 3, dx = tap % 3;
+                float s = 0.f;
+                for (int py = 0; py < TH; ++py)
+#pragma unroll 4
+                    for (int px = 0; px < TW; ++px)
+                        s = fmaf(sd[(py * TW + px) * COUT + co], sh[((py + dy) * (TW + 2) + px + dx) * CIN + ci], s);
+                acc[j] += s;
+            } else if (o < NOUT) {
+                const int co = o - NW_;
+                float s = 0.f;
+                for (int p = 0; p < TH * TW; ++p) s += sd[p * COUT + co];
+                acc[j] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int o = threadIdx.x + 256 * j;
+        if (o < NOUT) part[(size_t)blockIdx.x * NOUT + o] = acc[j];
+    }
+}
+
+// grad[off + o] = sum over CTAs of part[cta][o] (fixed order)
+__global__ void reduce_grad_kernel(const float* __restrict__ part, int nparts, int nout, float* __restrict__ grad) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += part[(size_t)c * nout + o];
+    grad[o] = (float)s;
+}
+
+// in: batch x 2 x H x W FP32 (NCHW) -> NHWC BF16 with 16 channels (2 used)
+__global__ void pack_input_kernel(const float* __restrict__ in, int B, int HW, bf16* __restrict__ x0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * HW) return;
+    const int64_t b = i / HW, p = i % HW;
+    alignas(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+    v[0] = __float2bfloat16_rn(in[(b * 2) * HW + p]);
+    v[1] = __float2bfloat16_rn(in[(b * 2 + 1) * HW + p]);
+    uint4* dst = reinterpret_cast<uint4*>(x0 + i * 16);
+    dst[0] = reinterpret_cast<uint4*>(v)[0];
+    dst[1] = reinterpret_cast<uint4*>(v)[1];
+}
+
+// Preconditioner input: channel 0 = x / ||x||, channel 1 = log kappa (single grid)
+template <typename TX>
+__global__ void pack_precond_kernel(const TX* __restrict__ x, const float* __restrict__ nrm, const double* __restrict__ lk,
+                                    int HW, bf16* __restrict__ x0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= HW) return;
+    float xv;
+    if constexpr (sizeof(TX) == 2) xv = __bfloat162float(x[i]);
+    else xv = (float)x[i];
+    const float inv = nrm[0] > 0.f ? 1.f / nrm[0] : 0.f;
+    alignas(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+    v[0] = __float2bfloat16_rn(xv * inv);
+    v[1] = __float2bfloat16_rn((float)lk[i]);
+    uint4* dst = reinterpret_cast<uint4*>(x0 + (size_t)i * 16);
+    dst[0] = reinterpret_cast<uint4*>(v)[0];
+    dst[1] = reinterpret_cast<uint4*>(v)[1];
+}
+
+template <typename TX>
+__global__ void norm_kernel(const TX* __restrict__ x, int n, float* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v;
+        if constexpr (sizeof(TX) == 2) v = __bfloat162float(x[i]);
+        else v = (double)x[i];
+        s = fma(v, v, s);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) out[0] = (float)sqrt(t);
+    }
+}
+
+// Loss terms per sample: stats[b] = (sum (out - t)^2, sum t^2), one CTA per (sample, chunk)
+__global__ void loss_stats_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int HW, int chunks,
+                                  double* __restrict__ part) {
+    __shared__ double sh[2][8];
+    const int b = blockIdx.y;
+    const int per = (HW + chunks - 1) / chunks;
+    const int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
+    double e2 = 0.0, t2 = 0.0;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const double o = out[(size_t)b * HW + p], t = tgt[(size_t)b * HW + p];
+        e2 += (o - t) * (o - t);
+        t2 += t * t;
+    }
+    e2 = warp_sum(e2);
+    t2 = warp_sum(t2);
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = e2; sh[1][threadIdx.x >> 5] = t2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; c += sh[1][w]; }
+        part[((size_t)b * chunks + blockIdx.x) * 2] = a;
+        part[((size_t)b * chunks + blockIdx.x) * 2 + 1] = c;
+    }
+}
+
+// loss = mean_b e2_b / t2_b ; per-sample gradient scale 2 / (t2_b B)
+__global__ void loss_final_kernel(const double* __restrict__ part, int B, int chunks, double* __restrict__ loss,
+                                  float* __restrict__ gscale) {
+    if (threadIdx.x != 0) return;
+    double L = 0.0;
+    for (int b = 0; b < B; ++b) {
+        double e2 = 0.0, t2 = 0.0;
+        for (int c = 0; c < chunks; ++c) { e2 += part[((size_t)b * chunks + c) * 2]; t2 += part[((size_t)b * chunks + c) * 2 + 1]; }
+        L += t2 > 0.0 ? e2 / t2 : 0.0;
+        gscale[b] = t2 > 0.0 ? (float)(2.0 / (t2 * B)) : 0.f;
+    }
+    loss[0] = L / B;
+}
+
+// dA6 = (out - t) * gscale_b, NHWC BF16 with 16 channels (channel 0 used)
+__global__ void dout_kernel(const float* __restrict__ out, const float* __restrict__ tgt, const float* __restrict__ gs,
+                            int B, int HW, bf16* __restrict__ d6) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * HW) return;
+    const int b = (int)(i / HW);
+    alignas(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+    v[0] = __float2bfloat16_rn((out[i] - tgt[i]) * gs[b]);
+    uint4* dst = reinterpret_cast<uint4*>(d6 + i * 16);
+    dst[0] = reinterpret_cast<uint4*>(v)[0];
+    dst[1] = reinterpret_cast<uint4*>(v)[1];
+}
+
+// Adam on the FP32 master parameters
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// FP32 master parameters -> BF16 forward ([tap][co][ci], padded) and backward ([8 - tap][ci][co])
+// weights and padded FP32 biases, for one layer.
+__global__ void repack_kernel(const float* __restrict__ p, int cin, int cout, int cs_in, int co_p, int cs_d,
+                              bf16* __restrict__ wf, bf16* __restrict__ wb, float* __restrict__ bias) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = cout * cin * 9;
+    if (o < nw) {
+        const int co = o / (cin * 9), rem = o % (cin * 9), ci = rem / 9, tap = rem % 9;
+        const bf16 v = __float2bfloat16_rn(p[o]);
+        wf[((size_t)tap * co_p + co) * cs_in + ci] = v;
+        if (wb) wb[((size_t)(8 - tap) * 32 + ci) * cs_d + co] = v;
+    } else if (o < nw + cout) {
+        bias[o - nw] = p[o];
+    }
+}
+
+// Kaiming-uniform initialisation from Philox (stream 8): U(-b, b), b = sqrt(6 / (9 c_in)); biases 0.
+__global__ void init_kernel(float* __restrict__ p, int64_t off, int64_t nw, int64_t nb, int cin, uint32_t k0, uint32_t k1) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw + nb) return;
+    if (i >= nw) { p[off + i] = 0.f; return; }
+    uint32_t c[4] = {(uint32_t)(off + i), 0u, 0u, 8u};
+    philox4x32_10(c, k0, k1);
+    const double u = u53(c[0], c[1]);
+    const double bound = sqrt(6.0 / (9.0 * cin));
+    p[off + i] = (float)((2.0 * u - 1.0) * bound);
+}
+
+template <int CS, int NT, int MODE>
+void launch_conv(rgs_context* ctx, const ConvArgs& a, int B) {
+    dim3 grid(a.W / TW, a.H / TH, B);
+    conv3x3_mma_kernel<CS, NT, MODE><<<grid, 128, 0, ctx->stream>>>(a);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+}  // namespace
+
+struct rgs_convnet_obj {
+    rgs_handle h = nullptr;
+    int H = 0, W = 0, max_batch = 0;
+    int64_t step = 0;
+    DevBuf params, grad, adam_m, adam_v;     // FP32, total_params()
+    DevBuf wf[NL], wb[NL], bias[NL];         // BF16 packed weights, FP32 padded biases
+    DevBuf act[NL];                          // act[0]: packed input (16 ch); act[l]: output of layer l (32 ch)
+    DevBuf out;                              // FP32 network output (max_batch x H x W)
+    DevBuf dA[2], d6;                        // backward activation gradients (ping-pong) and dA_6
+    DevBuf part;                             // per-CTA partial gradients
+    DevBuf lpart, scal;                      // loss partials; scalars (loss, scales, norm)
+};
+
+namespace {
+
+void repack_all(rgs_convnet_obj* net) {
+    rgs_context* h = net->h;
+    for (int l = 0; l < NL; ++l) {
+        const int n = (int)layer_count(l);
+        const int cs_d = (l == NL - 1) ? 16 : 32;     // channels of dA_l as stored
+        repack_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(
+            net->params.as<float>() + param_offset(l), C_IN[l], C_OUT[l], CS_IN[l], CO_P[l], cs_d,
+            net->wf[l].as<bf16>(), l > 0 ? net->wb[l].as<bf16>() : nullptr, net->bias[l].as<float>());
+        RGS_CUDA(cudaGetLastError());
+    }
+    h->launches += NL;
+}
+
+// Forward pass of `batch` grids whose packed input is act[0]; output FP32 into out (times scale).
+void forward(rgs_convnet_obj* net, int batch, float* out, const float* scale) {
+    rgs_context* h = net->h;
+    for (int l = 0; l < NL; ++l) {
+        ConvArgs a{};
+        a.x = net->act[l].as<bf16>();
+        a.w = net->wf[l].as<bf16>();
+        a.bias = net->bias[l].as<float>();
+        a.H = net->H;
+        a.W = net->W;
+        if (l == 0) {
+            a.out = net->act[1].ptr;
+            launch_conv<16, 4, 0>(h, a, batch);
+        } else if (l < NL - 1) {
+            a.out = net->act[l + 1].ptr;
+            launch_conv<32, 4, 0>(h, a, batch);
+        } else {
+            a.out = out;
+            a.scale = scale;
+            launch_conv<32, 1, 1>(h, a, batch);
+        }
+    }
+}
+
+int dweight_grid(const rgs_context* h) { return 2 * h->num_sms; }
+
+template <int CSH, int CIN, int CSD, int COUT>
+void launch_dweight(rgs_convnet_obj* net, int l, const bf16* hprev, const bf16* dA, int B) {
+    rgs_context* h = net->h;
+    const int grid = dweight_grid(h);
+    const int nout = COUT * CIN * 9 + COUT;
+    dweight_kernel<CSH, CIN, CSD, COUT><<<grid, 256, 0, h->stream>>>(hprev, dA, B, net->H, net->W, net->part.as<float>());
+    RGS_CUDA(cudaGetLastError());
+    reduce_grad_kernel<<<(nout + 255) / 256, 256, 0, h->stream>>>(net->part.as<float>(), grid, nout,
+                                                                  net->grad.as<float>() + param_offset(l));
+    RGS_CUDA(cudaGetLastError());
+    h->launches += 2;
+}
+
+// loss, gradient into net->grad; returns device pointer to the loss
+double* loss_and_backward(rgs_convnet_obj* net, int B, const float* target) {
+    rgs_context* h = net->h;
+    const int HW = net->H * net->W;
+    const int chunks = 16;
+    double* loss = net->scal.as<double>();                  // scal: [0] loss, [1] norm, [2..] scales
+    float* gscale = reinterpret_cast<float*>(loss + 2);
+    loss_stats_kernel<<<dim3(chunks, B), 256, 0, h->stream>>>(net->out.as<float>(), target, HW, chunks,
+                                                              net->lpart.as<double>());
+    RGS_CUDA(cudaGetLastError());
+    loss_final_kernel<<<1, 32, 0, h->stream>>>(net->lpart.as<double>(), B, chunks, loss, gscale);
+    RGS_CUDA(cudaGetLastError());
+    const int64_t tot = (int64_t)B * HW;
+    dout_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(net->out.as<float>(), target, gscale, B, HW,
+                                                                     net->d6.as<bf16>());
+    RGS_CUDA(cudaGetLastError());
+    h->launches += 3;
+    // layer 6: dW from (h_5, dA_6); dA_5 = (conv^T dA_6) masked by h_5 > 0
+    launch_dweight<32, 32, 16, 1>(net, 5, net->act[5].as<bf16>(), net->d6.as<bf16>(), B);
+    {
+        ConvArgs a{};
+        a.x = net->d6.as<bf16>();
+        a.w = net->wb[5].as<bf16>();
+        a.out = net->dA[0].ptr;
+        a.mask = net->act[5].as<bf16>();
+        a.H = net->H;
+        a.W = net->W;
+        launch_conv<16, 4, 2>(h, a, B);
+    }
+    int cur = 0;
+    for (int l = NL - 2; l >= 0; --l) {       // layers 5 .. 1 (0-based 4 .. 0)
+        const bf16* dAl = net->dA[cur].as<bf16>();
+        if (l == 0) {
+            launch_dweight<16, 2, 32, 32>(net, 0, net->act[0].as<bf16>(), dAl, B);
+        } else {
+            launch_dweight<32, 32, 32, 32>(net, l, net->act[l].as<bf16>(), dAl, B);
+            ConvArgs a{};
+            a.x = dAl;
+            a.w = net->wb[l].as<bf16>();
+            a.out = net->dA[cur ^ 1].ptr;
+            a.mask = net->act[l].as<bf16>();
+            a.H = net->H;
+            a.W = net->W;
+            launch_conv<32, 4, 2>(h, a, B);
+            cur ^= 1;
+        }
+    }
+    return loss;
+}
+
+void pack_training_input(rgs_convnet_obj* net, int B, const float* in) {
+    const int64_t tot = (int64_t)B * net->H * net->W;
+    pack_input_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, net->h->stream>>>(in, B, net->H * net->W,
+                                                                               net->act[0].as<bf16>());
+    RGS_CUDA(cudaGetLastError());
+    net->h->launches++;
+}
+
+template <class F>
+rgs_status guarded(rgs_handle h, F&& f) {
+    try {
+        f();
+        if (h) h->last_error.clear();
+        return RGS_OK;
+    } catch (const RgsError& e) {
+        if (h) h->last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (h) h->last_error = "host allocation failed";
+        return RGS_ERR_ALLOC;
+    } catch (...) {
+        if (h) h->last_error = "unexpected exception";
+        return RGS_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace
+
+int64_t rgs_convnet_grid_points(const void* netp) {
+    const rgs_convnet_obj* net = static_cast<const rgs_convnet_obj*>(netp);
+    return (int64_t)net->H * net->W;
+}
+
+// z = ||x|| net(x / ||x||, log kappa) on one grid (the flexible-GMRES preconditioner)
+void rgs_convnet_apply_precond(rgs_context* ctx, void* netp, const double* logkappa, const void* x, int xtype,
+                               float* z) {
+    rgs_convnet_obj* net = static_cast<rgs_convnet_obj*>(netp);
+    RGS_REQUIRE(net->h != nullptr, "network without handle");
+    const int HW = net->H * net->W;
+    float* nrm = reinterpret_cast<float*>(net->scal.as<double>() + 1);
+    if (xtype == RGS_F64) {
+        norm_kernel<double><<<1, 1024, 0, ctx->stream>>>((const double*)x, HW, nrm);
+        pack_precond_kernel<double><<<(HW + 255) / 256, 256, 0, ctx->stream>>>((const double*)x, nrm, logkappa, HW,
+                                                                                net->act[0].as<bf16>());
+    } else if (xtype == RGS_F32) {
+        norm_kernel<float><<<1, 1024, 0, ctx->stream>>>((const float*)x, HW, nrm);
+        pack_precond_kernel<float><<<(HW + 255) / 256, 256, 0, ctx->stream>>>((const float*)x, nrm, logkappa, HW,
+                                                                               net->act[0].as<bf16>());
+    } else {
+        norm_kernel<bf16><<<1, 1024, 0, ctx->stream>>>((const bf16*)x, HW, nrm);
+        pack_precond_kernel<bf16><<<(HW + 255) / 256, 256, 0, ctx->stream>>>((const bf16*)x, nrm, logkappa, HW,
+                                                                              net->act[0].as<bf16>());
+    }
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+    cudaStream_t keep = net->h->stream;
+    net->h->stream = ctx->stream;
+    forward(net, 1, z, nrm);
+    net->h->stream = keep;
+}
+
+extern "C" {
+
+int64_t rgs_convnet_num_params(void) { return total_params(); }
+
+rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32_t max_batch, uint64_t seed,
+                              rgs_convnet* out) {
+    if (!h || !out) return RGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    rgs_convnet_obj* net = new (std::nothrow) rgs_convnet_obj();
+    if (!net) return RGS_ERR_ALLOC;
+    rgs_status st = guarded(h, [&] {
+        RGS_REQUIRE(height >= TH && width >= TW && height % TH == 0 && width % TW == 0,
+                    "grid must be a multiple of 8 x 16");
+        RGS_REQUIRE(max_batch >= 1, "max_batch must be >= 1");
+        net->h = h;
+        net->H = height;
+        net->W = width;
+        net->max_batch = max_batch;
+        const int64_t P = total_params();
+        const size_t HW = (size_t)height * width;
+        net->params.ensure(P * 4);
+        net->grad.ensure(P * 4);
+        net->adam_m.ensure(P * 4);
+        net->adam_v.ensure(P * 4);
+        RGS_CUDA(cudaMemsetAsync(net->adam_m.ptr, 0, P * 4, h->stream));
+        RGS_CUDA(cudaMemsetAsync(net->adam_v.ptr, 0, P * 4, h->stream));
+        for (int l = 0; l < NL; ++l) {
+            net->wf[l].ensure(sizeof(bf16) * 9 * CO_P[l] * CS_IN[l]);
+            RGS_CUDA(cudaMemsetAsync(net->wf[l].ptr, 0, net->wf[l].bytes, h->stream));
+            if (l > 0) {
+                const int cs_d = (l == NL - 1) ? 16 : 32;
+                net->wb[l].ensure(sizeof(bf16) * 9 * 32 * cs_d);
+                RGS_CUDA(cudaMemsetAsync(net->wb[l].ptr, 0, net->wb[l].bytes, h->stream));
+            }
+            net->bias[l].ensure(sizeof(float) * CO_P[l]);
+            RGS_CUDA(cudaMemsetAsync(net->bias[l].ptr, 0, net->bias[l].bytes, h->stream));
+            const int64_t nw = layer_w_count(l), nb = C_OUT[l];
+            init_kernel<<<(unsigned)((nw + nb + 255) / 256), 256, 0, h->stream>>>(
+                net->params.as<float>(), param_offset(l), nw, nb, C_IN[l], (uint32_t)seed, (uint32_t)(seed >> 32));
+            RGS_CUDA(cudaGetLastError());
+        }
+        net->act[0].ensure(sizeof(bf16) * HW * 16 * max_batch);
+        for (int l = 1; l < NL; ++l) net->act[l].ensure(sizeof(bf16) * HW * 32 * max_batch);
+        net->out.ensure(sizeof(float) * HW * max_batch);
+        net->dA[0].ensure(sizeof(bf16) * HW * 32 * max_batch);
+        net->dA[1].ensure(sizeof(bf16) * HW * 32 * max_batch);
+        net->d6.ensure(sizeof(bf16) * HW * 16 * max_batch);
+        net->part.ensure(sizeof(float) * (size_t)dweight_grid(h) * (32 * 32 * 9 + 32));
+        net->lpart.ensure(sizeof(double) * 2 * 16 * (size_t)max_batch);
+        net->scal.ensure(sizeof(double) * (4 + (size_t)max_batch));
+        repack_all(net);
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
+    if (st != RGS_OK) {
+        delete net;
+        return st;
+    }
+    *out = net;
+    return RGS_OK;
+}
+
+rgs_status rgs_convnet_destroy(rgs_convnet net) {
+    if (!net) return RGS_ERR_INVALID_ARG;
+    delete net;
+    return RGS_OK;
+}
+
+rgs_status rgs_convnet_get_params(rgs_handle h, rgs_convnet net, float* host, int64_t count) {
+    if (!h || !net || !host) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(count == total_params(), "count must equal rgs_convnet_num_params()");
+        RGS_CUDA(cudaMemcpyAsync(host, net->params.ptr, count * 4, cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+rgs_status rgs_convnet_set_params(rgs_handle h, rgs_convnet net, const float* host, int64_t count) {
+    if (!h || !net || !host) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(count == total_params(), "count must equal rgs_convnet_num_params()");
+        RGS_CUDA(cudaMemcpyAsync(net->params.ptr, host, count * 4, cudaMemcpyHostToDevice, h->stream));
+        repack_all(net);
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+rgs_status rgs_convnet_forward(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, float* out) {
+    if (!h || !net || !in || !out) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(batch >= 1 && batch <= net->max_batch, "batch must be in [1, max_batch]");
+        cudaStream_t keep = net->h->stream;
+        net->h->stream = h->stream;
+        pack_training_input(net, batch, in);
+        forward(net, batch, out, nullptr);
+        net->h->stream = keep;
+    });
+}
+
+rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, const float* target,
+                                 double* loss, float* grad_host) {
+    if (!h || !net || !in || !target) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(batch >= 1 && batch <= net->max_batch, "batch must be in [1, max_batch]");
+        cudaStream_t keep = net->h->stream;
+        net->h->stream = h->stream;
+        pack_training_input(net, batch, in);
+        forward(net, batch, net->out.as<float>(), nullptr);
+        double* dl = loss_and_backward(net, batch, target);
+        net->h->stream = keep;
+        if (loss) RGS_CUDA(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (grad_host)
+            RGS_CUDA(cudaMemcpyAsync(grad_host, net->grad.ptr, total_params() * 4, cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, const float* target,
+                                  float lr, double* loss) {
+    if (!h || !net || !in || !target) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(batch >= 1 && batch <= net->max_batch, "batch must be in [1, max_batch]");
+        cudaStream_t keep = net->h->stream;
+        net->h->stream = h->stream;
+        pack_training_input(net, batch, in);
+        forward(net, batch, net->out.as<float>(), nullptr);
+        double* dl = loss_and_backward(net, batch, target);
+        net->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+        const int64_t P = total_params();
+        adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, h->stream>>>(net->params.as<float>(), net->grad.as<float>(),
+                                                                         net->adam_m.as<float>(), net->adam_v.as<float>(),
+                                                                         P, lr, b1, b2, 1e-8f, c1, c2);
+        RGS_CUDA(cudaGetLastError());
+        h->launches++;
+        repack_all(net);
+        net->h->stream = keep;
+        if (loss) {
+            RGS_CUDA(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaStreamSynchronize(h->stream));
+        }
+    });
+}
+
+}  // extern "C"

@@ -38,6 +38,8 @@ struct rgs_arnoldi_obj {
     DevBuf spart, ppart;     // partial sketches of q'_i and of w'_{i+1}
     DevBuf vdf;              // A's values split into double-float pairs
     DevBuf work;             // r (n), norm partials, scalars
+    DevBuf jac;              // Jacobi: diag(A)^{-1} (n) and the values of A D^{-1} (nnz)
+    DevBuf Z;                // flexible preconditioning: z'_i = M(q'_i), n x mmax FP32
 };
 
 namespace {
@@ -127,16 +129,18 @@ int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const doub
     return np;
 }
 
-// w' = A q'_col (+ sketch of w' into ppart); returns the number of partial sketches.
-int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col) {
+// w' = A v (+ sketch of w' into ppart) for v = q'_col (or the vector v of type vtype when
+// given); returns the number of partial sketches.
+int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v = nullptr, int vtype = -1) {
     rgs_context* h = a->h;
-    const void* x = a->Q.as<char>() + dsize(a->qtype) * (size_t)col * a->ldq;
+    const void* x = v ? v : a->Q.as<char>() + dsize(a->qtype) * (size_t)col * a->ldq;
+    const int xtype = v ? vtype : a->qtype;
     if (a->sk->kind == RGS_SKETCH_SRHT) {
         const int dfm = sketch_is_df(a) ? 1 : 0;
-        return rgs_launch_spmv(h, A, a->vdf.ptr, x, a->qtype, a->wbuf.ptr, dfm, a->sk, a->ppart.as<double>(),
+        return rgs_launch_spmv(h, A, a->vdf.ptr, x, xtype, a->wbuf.ptr, dfm, a->sk, a->ppart.as<double>(),
                                h->ctl.as<int>());
     }
-    rgs_launch_spmv(h, A, nullptr, x, a->qtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
+    rgs_launch_spmv(h, A, nullptr, x, xtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
     UpdateLaunch L{};
     L.n = a->n;
     L.qtype = RGS_F64;
@@ -367,10 +371,58 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         obj.mmax = m + 1;
         obj.qtype = opts->qtype;
         arnoldi_alloc(&obj);
+        // Right preconditioning A M, x = x0 + M (Q y) (Sec. 5.3 preconditions A_f P_f from the right).
+        // Jacobi, M = D^{-1}: the Arnoldi operator is A D^{-1} (column-scaled values), and the
+        // solution update applies D^{-1}.  Learned network (nonlinear): flexible GMRES, z'_i = M(q'_i)
+        // kept in Z, w' = A z'_i and x = x0 + Z y.
+        const int pk = h->precond_kind;
+        RGS_REQUIRE(pk == RGS_PRECOND_NONE || pk == RGS_PRECOND_JACOBI || pk == RGS_PRECOND_LEARNED_CONV,
+                    "unknown preconditioner");
+        const bool learned = pk == RGS_PRECOND_LEARNED_CONV;
+        rgs_csr Apc = *A;
+        const double* dinv = nullptr;
+        if (pk == RGS_PRECOND_JACOBI) {
+            obj.jac.ensure(sizeof(double) * ((size_t)s->n + (size_t)std::max<int64_t>(A->nnz, 1)));
+            double* jd = obj.jac.as<double>();
+            rgs_launch_jacobi_setup(h, *A, jd, jd + s->n);
+            dinv = jd;
+            Apc.val = jd + s->n;
+        }
+        if (learned) {
+            RGS_REQUIRE(h->precond_net != nullptr && h->precond_field != nullptr, "learned preconditioner not set");
+            RGS_REQUIRE(rgs_convnet_grid_points(h->precond_net) == s->n,
+                        "the network's H x W grid must have n points");
+            obj.Z.ensure(sizeof(float) * (size_t)obj.ldq * obj.mmax);
+        }
+        DevBuf vdf_pc;                       // double-float values of A D^{-1}
         if (sketch_is_df(&obj)) {
             obj.vdf.ensure(8 * (size_t)std::max<int64_t>(A->nnz, 1));
             rgs_csr_split_df(h, A->val, A->nnz, obj.vdf.ptr);
+            if (pk == RGS_PRECOND_JACOBI) {
+                vdf_pc.ensure(8 * (size_t)std::max<int64_t>(A->nnz, 1));
+                rgs_csr_split_df(h, Apc.val, A->nnz, vdf_pc.ptr);
+            }
         }
+        bool use_pc = pk != RGS_PRECOND_NONE;
+        double prev_rel = INFINITY;
+        int fallback_cycle = -1;
+        // w' = A M q'_i (or A q'_i once the preconditioner is off), with its sketch
+        auto product = [&](int i) -> int {
+            if (use_pc && learned) {
+                float* z = obj.Z.as<float>() + (size_t)i * obj.ldq;
+                rgs_convnet_apply_precond(h, h->precond_net, h->precond_field,
+                                          obj.Q.as<char>() + dsize(obj.qtype) * (size_t)i * obj.ldq, obj.qtype, z);
+                return launch_product(&obj, *A, i, z, RGS_F32);
+            }
+            if (use_pc) {
+                void* keep = obj.vdf.ptr;
+                if (vdf_pc.ptr) obj.vdf.ptr = vdf_pc.ptr;
+                const int np = launch_product(&obj, Apc, i);
+                obj.vdf.ptr = keep;
+                return np;
+            }
+            return launch_product(&obj, *A, i);
+        };
         Scalars sc = scalars(&obj);
         h->launches = 0;
         RGS_CUDA(cudaMemsetAsync(h->ctl.ptr, 0, kCtlWords * sizeof(int), h->stream));
@@ -409,19 +461,31 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
             if (rel <= opts->rtol) { converged = true; break; }
             if (cycles >= opts->max_cycles) break;
+            // fallback: a preconditioned cycle that did not reduce the true residual (by at least a
+            // relative 2^-10, so that rounding noise does not count as progress) turns the
+            // preconditioner off; the unpreconditioned method finishes the solve
+            if (use_pc && cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10))) {
+                use_pc = false;
+                fallback_cycle = cycles;
+            }
+            prev_rel = rel;
             reset_cycle(&obj);
-            // Arnoldi step 0: q'_0 from r, w'_1 = A q'_0, column 0 appended and p_1 solved
+            // Arnoldi step 0: q'_0 from r, w'_1 = A M q'_0, column 0 appended and p_1 solved
             int sp = launch_update(&obj, 0, sc.r, 0);
-            int pp = launch_product(&obj, *A, 0);
+            int pp = product(0);
             launch_ls(&obj, 0, sp, m >= 1, pp, true, stop_tol);
             for (int i = 1; i <= m; ++i) {
                 sp = launch_update(&obj, i, obj.wbuf.ptr, sketch_is_df(&obj) ? 1 : 0, obj.ls.sigma + (i - 1));
-                if (i < m) pp = launch_product(&obj, *A, i);
+                if (i < m) pp = product(i);
                 launch_ls(&obj, i, sp, i < m, pp, true, stop_tol);
             }
             rgs_launch_hess_solve(h, obj.ls.Hr, obj.mmax, obj.ls.g, obj.ls.sigma, m, y_buf(&obj), cy_buf(&obj),
                                   h->ctl.as<int>());
-            rgs_launch_sol_update(h, s->n, obj.Q.ptr, obj.qtype, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>());
+            if (use_pc && learned)
+                rgs_launch_sol_update(h, s->n, obj.Z.ptr, RGS_F32, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>());
+            else
+                rgs_launch_sol_update(h, s->n, obj.Q.ptr, obj.qtype, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>(),
+                                      use_pc ? dinv : nullptr);
             ++cycles;
         }
         if (info) {
@@ -429,6 +493,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             info->total_steps = total;
             info->converged = converged ? 1 : 0;
             info->rel_residual = rel;
+            info->fallback_cycle = fallback_cycle;
         }
     });
     if (info) info->status = st;
@@ -568,10 +633,25 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
     return st;
 }
 
-rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void*, int32_t) {
+rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void* params, int32_t flexible) {
     if (!h) return RGS_ERR_INVALID_ARG;
-    (void)kind;
-    return RGS_ERR_NOT_IMPLEMENTED;
+    return guarded(h, [&] {
+        RGS_REQUIRE(kind == RGS_PRECOND_NONE || kind == RGS_PRECOND_JACOBI || kind == RGS_PRECOND_LEARNED_CONV,
+                    "unknown preconditioner kind");
+        if (kind == RGS_PRECOND_LEARNED_CONV) {
+            RGS_REQUIRE(params != nullptr, "the learned preconditioner needs rgs_learned_precond parameters");
+            RGS_REQUIRE(flexible, "a nonlinear preconditioner needs flexible GMRES (flexible = 1)");
+            const rgs_learned_precond* lp = static_cast<const rgs_learned_precond*>(params);
+            RGS_REQUIRE(lp->net != nullptr && lp->logkappa != nullptr, "null network or field");
+            h->precond_net = lp->net;
+            h->precond_field = lp->logkappa;
+        } else {
+            h->precond_net = nullptr;
+            h->precond_field = nullptr;
+        }
+        h->precond_kind = kind;
+        h->precond_flexible = flexible;
+    });
 }
 
 rgs_status rgmres_solve_batched(rgs_handle h, int32_t, const rgs_sketch*, const rgs_csr*, const double* const*,

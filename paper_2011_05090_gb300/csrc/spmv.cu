@@ -188,11 +188,11 @@ __global__ void __launch_bounds__(256) sumsq_kernel(int64_t n, const double* __r
     }
 }
 
-// x += sum_{c < nsteps} Q'(:, c) cy[c]; nsteps from ctl[kStepsWord]
+// x += rowscale .* sum_{c < nsteps} Q'(:, c) cy[c]; nsteps from ctl[kStepsWord]
 template <typename TQ>
 __global__ void __launch_bounds__(256) sol_update_kernel(int64_t n, const TQ* __restrict__ Q, int64_t ldq,
                                                          const double* __restrict__ cy, double* __restrict__ x,
-                                                         const int* ctl) {
+                                                         const int* ctl, const double* __restrict__ rowscale) {
     __shared__ df cdf[1024];
     __shared__ double cd[1024];
     const int nsteps = ctl[kStepsWord];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) sol_update_kernel(int64_t n, const TQ* __
         if constexpr (sizeof(TQ) == 8) {
             double a = 0.0;
             for (int c = 0; c < nsteps; ++c) a = fma(Q[(int64_t)c * ldq + i], cd[c], a);
-            x[i] += a;
+            x[i] += rowscale ? rowscale[i] * a : a;
         } else {
             df a = {0.f, 0.f};
             for (int c = 0; c < nsteps; ++c) {
@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(256) sol_update_kernel(int64_t n, const TQ* __
                 else q = Q[(int64_t)c * ldq + i];
                 a = df_add(a, df_mul_f(cdf[c], q));
             }
-            x[i] += (double)a.h + (double)a.l;
+            const double d = (double)a.h + (double)a.l;
+            x[i] += rowscale ? rowscale[i] * d : d;
         }
     }
 }
@@ -325,6 +326,25 @@ __global__ void __launch_bounds__(256) cgs_update_kernel(int64_t n, const double
     }
 }
 
+// dinv[r] = 1 / A(r, r) (0 flags a missing or zero diagonal in dinv_bad)
+__global__ void jacobi_diag_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                   const double* __restrict__ val, double* __restrict__ dinv, int* bad) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int q = rowptr[r]; q < rowptr[r + 1]; ++q)
+            if (colind[q] == r) d += val[q];
+        if (d == 0.0 || !isfinite(d)) { atomicExch(bad, 1); dinv[r] = 0.0; }
+        else dinv[r] = 1.0 / d;
+    }
+}
+
+// values of the column-scaled operator A D^{-1}
+__global__ void jacobi_scale_kernel(int64_t nnz, const int32_t* __restrict__ colind, const double* __restrict__ val,
+                                    const double* __restrict__ dinv, double* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = val[e] * dinv[colind[e]];
+}
+
 template <typename TX, bool DFM, bool SRHT>
 void launch_spmv_t(rgs_context* ctx, const SpmvParams& p, int grid, size_t smem) {
     auto kern = spmv_sketch_kernel<TX, DFM, SRHT>;
@@ -421,11 +441,15 @@ void rgs_launch_norm(rgs_context* ctx, int64_t n, const double* v, double* part,
 }
 
 void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype, int64_t ldq, const double* cy,
-                           double* x, const int* ctl) {
+                           double* x, const int* ctl, const double* rowscale) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms));
-    if (qtype == RGS_F64) sol_update_kernel<double><<<grid, 256, 0, ctx->stream>>>(n, (const double*)Q, ldq, cy, x, ctl);
-    else if (qtype == RGS_F32) sol_update_kernel<float><<<grid, 256, 0, ctx->stream>>>(n, (const float*)Q, ldq, cy, x, ctl);
-    else sol_update_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(n, (const __nv_bfloat16*)Q, ldq, cy, x, ctl);
+    if (qtype == RGS_F64)
+        sol_update_kernel<double><<<grid, 256, 0, ctx->stream>>>(n, (const double*)Q, ldq, cy, x, ctl, rowscale);
+    else if (qtype == RGS_F32)
+        sol_update_kernel<float><<<grid, 256, 0, ctx->stream>>>(n, (const float*)Q, ldq, cy, x, ctl, rowscale);
+    else
+        sol_update_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(n, (const __nv_bfloat16*)Q, ldq, cy, x, ctl,
+                                                                         rowscale);
     RGS_CUDA(cudaGetLastError());
     ctx->launches++;
 }
@@ -458,4 +482,20 @@ void rgs_launch_cgs_update(rgs_context* ctx, int64_t n, const double* Vp, int64_
     cgs_update_kernel<<<grid, 256, 0, ctx->stream>>>(n, Vp, ldv, ncols, coef, w, out, part, ctl);
     RGS_CUDA(cudaGetLastError());
     ctx->launches++;
+}
+
+// Right Jacobi preconditioning: dinv = diag(A)^{-1} and the values of A D^{-1}.
+void rgs_launch_jacobi_setup(rgs_context* ctx, const rgs_csr& A, double* dinv, double* scaled_val) {
+    int* bad = ctx->ctl.as<int>() + kFlagWord;
+    RGS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 255) / 256, 4 * ctx->num_sms));
+    jacobi_diag_kernel<<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, A.val, dinv, bad);
+    RGS_CUDA(cudaGetLastError());
+    jacobi_scale_kernel<<<grid, 256, 0, ctx->stream>>>(A.nnz, A.colind, A.val, dinv, scaled_val);
+    RGS_CUDA(cudaGetLastError());
+    int hbad = 0;
+    RGS_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RGS_CUDA(cudaStreamSynchronize(ctx->stream));
+    RGS_REQUIRE(hbad == 0, "Jacobi preconditioner: zero or missing diagonal entry");
+    ctx->launches += 2;
 }

@@ -151,3 +151,13 @@ def csr_dense(csr, n=None):
     for r in range(n):
         A[r, colind[rowptr[r]:rowptr[r + 1]]] += val[rowptr[r]:rowptr[r + 1]]
     return A
+
+
+def diffusion_2d(N, sigma, corr_len, seed):
+    """-div(kappa grad u) = f on an N x N grid, kappa = exp(sigma g), g a unit-variance Gaussian
+    field of correlation length ``corr_len`` cells (seed).  The finite-volume matrix is scaled
+    by h^2 so that its entries are O(kappa).  Returns ((rowptr, colind, val), log kappa (N x N))."""
+    g = gaussian_field((N, N), corr_len, seed)
+    rowptr, colind, val = convdiff_csr((N, N), np.exp(sigma * g), np.zeros(2))
+    h = 1.0 / (N + 1)
+    return (rowptr, colind, val * h * h), sigma * g
