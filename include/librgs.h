@@ -186,7 +186,10 @@ typedef struct {
     int32_t restart;        /* Arnoldi steps (products with A) per cycle */
     int32_t max_cycles;
     double rtol;            /* stop when ||b - A x|| <= rtol ||b|| */
-    double inner_factor;    /* cycle ends when the Givens residual <= inner_factor * rtol * ||Theta b|| */
+    double inner_factor;    /* cycle ends when the Givens residual <= inner_factor * rtol * ||Theta b||;
+                               a cycle that ended so but left ||b - A x|| > rtol ||b|| multiplies
+                               this threshold by inner_factor * rtol ||b|| / ||b - A x|| for the
+                               cycles after it */
     rgs_dtype qtype;        /* basis storage (RGS only) */
     int32_t fixed_steps;    /* 1: always run `restart` steps per cycle */
     int32_t reserved;
@@ -203,6 +206,11 @@ typedef struct {
     int32_t reserved;
 } rgmres_info;
 
+/* y = A x in FP64 (device arrays of A->n entries, no aliasing), stream-ordered.  The product
+ * that Alg. 3 applies to each basis vector, exported for callers that form right-hand sides
+ * b = A y or residuals themselves. */
+RGS_API rgs_status rgs_csr_matvec(rgs_handle h, const rgs_csr* A, const double* x, double* y);
+
 RGS_API rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const double* b, double* x,
                         const rgmres_opts* opts, rgmres_info* info);
 RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, double* x,
@@ -213,7 +221,8 @@ RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double
  * rgmres_set_preconditioner selects it for the following rgmres_solve calls on the handle:
  *   RGS_PRECOND_NONE         -- none (the default);
  *   RGS_PRECOND_JACOBI       -- M = diag(A)^{-1} (linear; A D^{-1} is formed once per solve);
- *   RGS_PRECOND_LEARNED_CONV -- M(r) = ||r|| net(r / ||r||, log kappa), a trained rgs_convnet on
+ *   RGS_PRECOND_LEARNED_CONV -- M(r) = rms(r) net(r / rms(r), log kappa) with rms(r) = ||r|| / sqrt(n),
+ *                               a trained rgs_convnet on
  *                               the H x W grid of the unknowns; nonlinear, so flexible = 1 is
  *                               required and the solver keeps z_j = M(q_j) (flexible GMRES,
  *                               x = x0 + Z y).  params points to an rgs_learned_precond.
@@ -236,13 +245,22 @@ RGS_API rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind
  * BF16 copies of FP32 master parameters; products run on the tensor cores with FP32
  * accumulation; activations are BF16.  Parameters are flat FP32: for each layer l the weights
  * W_l[c_out][c_in][3][3] then the biases b_l[c_out] (rgs_convnet_num_params() in all).
- *   in:     batch x 2 x H x W FP32 (device): channel 0 the normalised residual, 1 log kappa.
+ *   in:     batch x 2 x H x W FP32 (device): channel 0 the residual scaled to unit root mean
+ *           square, channel 1 log kappa.
  *   out:    batch x H x W FP32 (device).
- *   target: batch x H x W FP32 (device), for the loss mean_b ||out_b - t_b||^2 / ||t_b||^2.
+ *   target: batch x H x W FP32 (device).
+ *   stencil: NULL, or batch x 5 x H x W FP32 (device): the 5-point operator A_b of each sample,
+ *           coefficients of row (y, x) for (y, x) itself, (y, x-1), (y, x+1), (y-1, x), (y+1, x)
+ *           (entries that reach outside the grid are ignored).
+ * Loss: mean_b ||F_b - t_b||^2 / ||t_b||^2 with F_b = out_b, or F_b = A_b out_b when stencil is
+ * given (the residual-norm loss: with t_b = r_b it measures ||A_b (out_b - A_b^{-1} r_b)||, the
+ * quantity a right preconditioner has to make small).
  * rgs_convnet_train_step: forward, loss, backward and one Adam step (beta1 0.9, beta2 0.999,
  * eps 1e-8) on the batch; rgs_convnet_loss_grad: loss and the FP32 gradient (host) without
  * updating.  max_batch bounds the batch of every call (it sizes the saved activations). */
 RGS_API int64_t rgs_convnet_num_params(void);
+/* rgs_convnet_create: weights drawn U(-1/sqrt(9 c_in), 1/sqrt(9 c_in)) from Philox (key = seed,
+ * counter (parameter index, 0, 0, 8)), biases 0. */
 RGS_API rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32_t max_batch, uint64_t seed,
                                       rgs_convnet* out);
 RGS_API rgs_status rgs_convnet_destroy(rgs_convnet net);
@@ -250,9 +268,10 @@ RGS_API rgs_status rgs_convnet_get_params(rgs_handle h, rgs_convnet net, float* 
 RGS_API rgs_status rgs_convnet_set_params(rgs_handle h, rgs_convnet net, const float* host, int64_t count);
 RGS_API rgs_status rgs_convnet_forward(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, float* out);
 RGS_API rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, const float* in,
-                                         const float* target, double* loss, float* grad_host);
+                                         const float* target, const float* stencil, double* loss,
+                                         float* grad_host);
 RGS_API rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, const float* in,
-                                          const float* target, float lr, double* loss);
+                                          const float* target, const float* stencil, float lr, double* loss);
 
 /* Batched solves in one persistent launch are declared for interface stability; they return
  * RGS_ERR_NOT_IMPLEMENTED until built. */

@@ -9,9 +9,13 @@ with flexible GMRES (z_j = M(q_j), x = x0 + Z y), defined here by plain formulas
 * six 3x3 convolutions with zero padding (cross-correlation, as in every deep-learning
   library): out[co, y, x] = b[co] + sum_{ci, dy, dx} W[co, ci, dy, dx] in[ci, y + dy - 1, x + dx - 1],
   channels 2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the first five;
-* input channels (r / ||r||, log kappa) on the H x W grid, output scaled by ||r|| (the map
-  r -> A^{-1} r it imitates is linear, so M(c r) = c M(r) for c > 0 by construction);
-* loss over a batch: mean_b ||out_b - t_b||^2 / ||t_b||^2;
+* input channels (r / rms(r), log kappa) on the H x W grid with rms(r) = ||r|| / sqrt(H W),
+  output scaled by rms(r) (the map r -> A^{-1} r it imitates is linear, so M(c r) = c M(r)
+  for c > 0 by construction);
+* loss over a batch: mean_b ||F_b - t_b||^2 / ||t_b||^2 with F_b = out_b, or, for the
+  residual-norm loss, F_b = A_b out_b with A_b the sample's 5-point operator (its rows as
+  coefficients of the centre, west, east, north and south neighbours); with t_b = r_b this is
+  ||A_b (out_b - A_b^{-1} r_b)||^2 / ||r_b||^2;
 * Adam (Kingma & Ba, ICLR 2015, Alg. 1): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
   p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
@@ -107,6 +111,38 @@ def forward(p, x, bf16=False):
     return out, acts, layers
 
 
+def stencil_from_csr(csr, H, W):
+    """(5, H, W) coefficients of a 5-point operator on an H x W grid (x fastest) from its CSR rows:
+    centre, west (x - 1), east (x + 1), north (y - 1), south (y + 1)."""
+    rowptr, colind, val = csr
+    S = np.zeros((5, H * W))
+    for p in range(H * W):
+        for q in range(rowptr[p], rowptr[p + 1]):
+            d = int(colind[q]) - p
+            c = {0: 0, -1: 1, 1: 2, -W: 3, W: 4}[d]
+            S[c, p] += val[q]
+    return S.reshape(5, H, W)
+
+
+def stencil_apply(S, v):
+    """(A v)[y, x] for stencils S (B, 5, H, W) and fields v (B, H, W), zero outside the grid."""
+    vp = np.zeros((v.shape[0], v.shape[1] + 2, v.shape[2] + 2))
+    vp[:, 1:-1, 1:-1] = v
+    return (S[:, 0] * v + S[:, 1] * vp[:, 1:-1, :-2] + S[:, 2] * vp[:, 1:-1, 2:]
+            + S[:, 3] * vp[:, :-2, 1:-1] + S[:, 4] * vp[:, 2:, 1:-1])
+
+
+def stencil_adjoint(S, g):
+    """(A^T g): every row's coefficient sent back to the column it reads."""
+    B, H, W = g.shape
+    out = S[:, 0] * g
+    out[:, :, 1:] += (S[:, 2] * g)[:, :, :-1]      # row (y, x-1) reads (y, x) through its east coefficient
+    out[:, :, :-1] += (S[:, 1] * g)[:, :, 1:]      # row (y, x+1) through its west coefficient
+    out[:, 1:, :] += (S[:, 4] * g)[:, :-1, :]      # row (y-1, x) through its south coefficient
+    out[:, :-1, :] += (S[:, 3] * g)[:, 1:, :]      # row (y+1, x) through its north coefficient
+    return out
+
+
 def loss(out, t):
     """mean_b ||out_b - t_b||^2 / ||t_b||^2."""
     B = out.shape[0]
@@ -115,16 +151,19 @@ def loss(out, t):
     return float(np.mean(e2 / t2))
 
 
-def loss_grad(p, x, t, bf16=False):
+def loss_grad(p, x, t, bf16=False, stencil=None):
     """(loss, flat gradient) by the chain rule through the layers, last to first."""
     out, acts, layers = forward(p, x, bf16)
     B = out.shape[0]
+    F = out if stencil is None else stencil_apply(stencil, out)
     t2 = (t ** 2).reshape(B, -1).sum(axis=1)
-    L = loss(out, t)
+    L = loss(F, t)
     scale = 2.0 / (t2 * B)
     if bf16:
         scale = scale.astype(np.float32).astype(np.float64)
-    d = _r((out - t) * scale[:, None, None], bf16)[:, None]          # dL / d out, (B, 1, H, W)
+    dF = (F - t) * scale[:, None, None]
+    dout = dF if stencil is None else stencil_adjoint(stencil, dF)
+    d = _r(dout, bf16)[:, None]                                      # dL / d out, (B, 1, H, W)
     grads = [None] * NUM_LAYERS
     for l in range(NUM_LAYERS - 1, -1, -1):
         W, _ = layers[l]
@@ -144,14 +183,16 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def precondition(p, r, logkappa, bf16=False):
-    """z = ||r|| net(r / ||r||, log kappa) for one residual r on the H x W grid (flattened)."""
+    """z = rms(r) net(r / rms(r), log kappa) for one residual r on the H x W grid (flattened)."""
     H, Wd = logkappa.shape
-    nr = np.linalg.norm(r)
-    if nr == 0:
+    rms = np.linalg.norm(r) / np.sqrt(H * Wd)
+    if rms == 0:
         return np.zeros_like(r)
-    x = np.stack([np.asarray(r).reshape(H, Wd) / nr, logkappa])[None]
+    if bf16:
+        rms = float(np.float32(rms))
+    x = np.stack([np.asarray(r).reshape(H, Wd) / rms, logkappa])[None]
     out, _, _ = forward(p, x, bf16)
-    return nr * out[0].ravel()
+    return rms * out[0].ravel()
 
 
 def init_params(seed):

@@ -54,7 +54,7 @@ _KIND = {"gaussian": RGS_SKETCH_GAUSSIAN, "srht": RGS_SKETCH_SRHT}
 EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", "rgs_last_error",
             "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_sketch_apply_noalloc", "rgs_qr",
             "rgs_arnoldi_create", "rgs_arnoldi_destroy", "rgs_arnoldi_start", "rgs_arnoldi_step",
-            "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgmres_solve", "cgs2_gmres_solve",
+            "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgs_csr_matvec", "rgmres_solve", "cgs2_gmres_solve",
             "rgmres_set_preconditioner", "rgs_convnet_num_params", "rgs_convnet_create", "rgs_convnet_destroy",
             "rgs_convnet_get_params", "rgs_convnet_set_params", "rgs_convnet_forward", "rgs_convnet_loss_grad",
             "rgs_convnet_train_step", "rgmres_solve_batched"]
@@ -123,6 +123,7 @@ def load():
         "rgs_arnoldi_step": [P, P, ctypes.POINTER(CSR), P],
         "rgs_arnoldi_get": [P, P, ctypes.POINTER(I32), P, I64, P],
         "rgs_arnoldi_basis": [P, ctypes.POINTER(P), ctypes.POINTER(I64)],
+        "rgs_csr_matvec": [P, ctypes.POINTER(CSR), P, P],
         "rgmres_solve": [P, P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
         "cgs2_gmres_solve": [P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
         "rgmres_set_preconditioner": [P, ctypes.c_int, P, I32],
@@ -133,8 +134,8 @@ def load():
         "rgs_convnet_get_params": [P, P, P, I64],
         "rgs_convnet_set_params": [P, P, P, I64],
         "rgs_convnet_forward": [P, P, I32, P, P],
-        "rgs_convnet_loss_grad": [P, P, I32, P, P, ctypes.POINTER(D), P],
-        "rgs_convnet_train_step": [P, P, I32, P, P, ctypes.c_float, ctypes.POINTER(D)],
+        "rgs_convnet_loss_grad": [P, P, I32, P, P, P, ctypes.POINTER(D), P],
+        "rgs_convnet_train_step": [P, P, I32, P, P, P, ctypes.c_float, ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -375,6 +376,14 @@ def cgs2_gmres_solve(h, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_fac
     return _gmres_result(st, info, hist, h)
 
 
+def rgs_csr_matvec(h, csr, x, y=None):
+    """y = A x (FP64 CUDA vectors)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check(load().rgs_csr_matvec(h.ptr, ctypes.byref(csr), x.data_ptr(), y.data_ptr()), h)
+    return y
+
+
 def csr_to_device(rowptr, colind, val, device="cuda"):
     """Device copies of CSR arrays (int32, int32, FP64) and the C struct pointing at them."""
     t = (torch.as_tensor(rowptr, dtype=torch.int32).to(device), torch.as_tensor(colind, dtype=torch.int32).to(device),
@@ -449,23 +458,35 @@ def rgs_convnet_forward(h, net, x, out=None):
     return out
 
 
-def rgs_convnet_loss_grad(h, net, x, target):
-    """(loss, flat FP32 gradient as NumPy) of mean_b ||net(x_b) - t_b||^2 / ||t_b||^2."""
+def _stencil_ptr(net, stencil, B):
+    if stencil is None:
+        return None
+    shape = (B, 5, net.height, net.width)
+    if stencil.dtype != torch.float32 or not stencil.is_cuda or not stencil.is_contiguous() or \
+            tuple(stencil.shape) != shape:
+        raise ValueError(f"stencil must be a contiguous FP32 CUDA tensor of shape {shape}")
+    return stencil.data_ptr()
+
+
+def rgs_convnet_loss_grad(h, net, x, target, stencil=None):
+    """(loss, flat FP32 gradient as NumPy) of mean_b ||F_b - t_b||^2 / ||t_b||^2, F_b = net(x_b)
+    or, with a 5-point ``stencil`` (B x 5 x H x W), F_b = A_b net(x_b)."""
     import numpy as np
     _net_io(net, x, "x", 2)
     _net_io(net, target, "target", 1)
     loss = ctypes.c_double()
     g = np.empty(rgs_convnet_num_params(), dtype=np.float32)
     _check(load().rgs_convnet_loss_grad(h.ptr, net.ptr, x.shape[0], x.data_ptr(), target.data_ptr(),
-                                        ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)), h)
+                                        _stencil_ptr(net, stencil, x.shape[0]), ctypes.byref(loss),
+                                        g.ctypes.data_as(ctypes.c_void_p)), h)
     return loss.value, g
 
 
-def rgs_convnet_train_step(h, net, x, target, lr=1e-3):
+def rgs_convnet_train_step(h, net, x, target, lr=1e-3, stencil=None):
     """One Adam step on the batch; returns the loss before the step."""
     _net_io(net, x, "x", 2)
     _net_io(net, target, "target", 1)
     loss = ctypes.c_double()
-    _check(load().rgs_convnet_train_step(h.ptr, net.ptr, x.shape[0], x.data_ptr(), target.data_ptr(), float(lr),
-                                         ctypes.byref(loss)), h)
+    _check(load().rgs_convnet_train_step(h.ptr, net.ptr, x.shape[0], x.data_ptr(), target.data_ptr(),
+                                         _stencil_ptr(net, stencil, x.shape[0]), float(lr), ctypes.byref(loss)), h)
     return loss.value

@@ -232,7 +232,7 @@ __global__ void pack_input_kernel(const float* __restrict__ in, int B, int HW, b
     dst[1] = reinterpret_cast<uint4*>(v)[1];
 }
 
-// Preconditioner input: channel 0 = x / ||x||, channel 1 = log kappa (single grid)
+// Preconditioner input: channel 0 = x / rms(x), channel 1 = log kappa (single grid)
 template <typename TX>
 __global__ void pack_precond_kernel(const TX* __restrict__ x, const float* __restrict__ nrm, const double* __restrict__ lk,
                                     int HW, bf16* __restrict__ x0) {
@@ -268,7 +268,7 @@ __global__ void norm_kernel(const TX* __restrict__ x, int n, float* __restrict__
     if (threadIdx.x < 32) {
         double t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
         t = warp_sum(t);
-        if (threadIdx.x == 0) out[0] = (float)sqrt(t);
+        if (threadIdx.x == 0) out[0] = (float)sqrt(t / n);       // root mean square
     }
 }
 
@@ -326,6 +326,55 @@ __global__ void dout_kernel(const float* __restrict__ out, const float* __restri
     dst[1] = reinterpret_cast<uint4*>(v)[1];
 }
 
+// Residual-norm loss: aout_b = A_b out_b for the 5-point operator of each sample, given as
+// S[b][c][y][x] with c = 0 centre, 1 west (x - 1), 2 east (x + 1), 3 north (y - 1), 4 south (y + 1)
+__global__ void stencil_apply_kernel(const float* __restrict__ out, const float* __restrict__ S, int B, int H, int W,
+                                     float* __restrict__ aout) {
+    const int HW = H * W;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * HW) return;
+    const int64_t b = i / HW;
+    const int p = (int)(i % HW), y = p / W, x = p % W;
+    const float* s = S + b * 5 * HW;
+    const float* o = out + b * HW;
+    float v = s[p] * o[p];
+    if (x > 0) v = fmaf(s[HW + p], o[p - 1], v);
+    if (x < W - 1) v = fmaf(s[2 * HW + p], o[p + 1], v);
+    if (y > 0) v = fmaf(s[3 * HW + p], o[p - W], v);
+    if (y < H - 1) v = fmaf(s[4 * HW + p], o[p + W], v);
+    aout[i] = v;
+}
+
+// dL/d out = A_b^T g_b with g_b = (aout_b - t_b) gscale_b; NHWC BF16 with 16 channels (channel 0).
+// Row q of A reaches p through its east (q = p - 1), west (q = p + 1), south (q = p - W) and
+// north (q = p + W) coefficient.
+__global__ void stencil_dout_kernel(const float* __restrict__ aout, const float* __restrict__ tgt,
+                                    const float* __restrict__ gs, const float* __restrict__ S, int B, int H, int W,
+                                    bf16* __restrict__ d6) {
+    const int HW = H * W;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * HW) return;
+    const int64_t b = i / HW;
+    const int p = (int)(i % HW), y = p / W, x = p % W;
+    const float* s = S + b * 5 * HW;
+    const float* a = aout + b * HW;
+    const float* t = tgt + b * HW;
+    const float sc = gs[b];
+    auto g = [&](int q) { return (a[q] - t[q]) * sc; };
+    float v = s[p] * g(p);
+    if (x > 0) v = fmaf(s[2 * HW + p - 1], g(p - 1), v);
+    if (x < W - 1) v = fmaf(s[HW + p + 1], g(p + 1), v);
+    if (y > 0) v = fmaf(s[4 * HW + p - W], g(p - W), v);
+    if (y < H - 1) v = fmaf(s[3 * HW + p + W], g(p + W), v);
+    alignas(16) bf16 o16[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o16[c] = __float2bfloat16_rn(0.f);
+    o16[0] = __float2bfloat16_rn(v);
+    uint4* dst = reinterpret_cast<uint4*>(d6 + i * 16);
+    dst[0] = reinterpret_cast<uint4*>(o16)[0];
+    dst[1] = reinterpret_cast<uint4*>(o16)[1];
+}
+
 // Adam on the FP32 master parameters
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
@@ -356,7 +405,9 @@ __global__ void repack_kernel(const float* __restrict__ p, int cin, int cout, in
     }
 }
 
-// Kaiming-uniform initialisation from Philox (stream 8): U(-b, b), b = sqrt(6 / (9 c_in)); biases 0.
+// Fan-in uniform initialisation from Philox (stream 8): U(-b, b), b = 1 / sqrt(9 c_in); biases 0.
+// Each layer shrinks the activations' variance (by about 6 with the ReLU), so the initial
+// output is small and the residual-norm loss starts near 1 instead of at ||A out||^2 >> 1.
 __global__ void init_kernel(float* __restrict__ p, int64_t off, int64_t nw, int64_t nb, int cin, uint32_t k0, uint32_t k1) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nw + nb) return;
@@ -364,7 +415,7 @@ __global__ void init_kernel(float* __restrict__ p, int64_t off, int64_t nw, int6
     uint32_t c[4] = {(uint32_t)(off + i), 0u, 0u, 8u};
     philox4x32_10(c, k0, k1);
     const double u = u53(c[0], c[1]);
-    const double bound = sqrt(6.0 / (9.0 * cin));
+    const double bound = 1.0 / sqrt(9.0 * cin);
     p[off + i] = (float)((2.0 * u - 1.0) * bound);
 }
 
@@ -386,6 +437,7 @@ struct rgs_convnet_obj {
     DevBuf wf[NL], wb[NL], bias[NL];         // BF16 packed weights, FP32 padded biases
     DevBuf act[NL];                          // act[0]: packed input (16 ch); act[l]: output of layer l (32 ch)
     DevBuf out;                              // FP32 network output (max_batch x H x W)
+    DevBuf aout;                             // FP32 A out (residual-norm loss)
     DevBuf dA[2], d6;                        // backward activation gradients (ping-pong) and dA_6
     DevBuf part;                             // per-CTA partial gradients
     DevBuf lpart, scal;                      // loss partials; scalars (loss, scales, norm)
@@ -446,20 +498,31 @@ void launch_dweight(rgs_convnet_obj* net, int l, const bf16* hprev, const bf16* 
 }
 
 // loss, gradient into net->grad; returns device pointer to the loss
-double* loss_and_backward(rgs_convnet_obj* net, int B, const float* target) {
+double* loss_and_backward(rgs_convnet_obj* net, int B, const float* target, const float* stencil) {
     rgs_context* h = net->h;
     const int HW = net->H * net->W;
     const int chunks = 16;
     double* loss = net->scal.as<double>();                  // scal: [0] loss, [1] norm, [2..] scales
     float* gscale = reinterpret_cast<float*>(loss + 2);
-    loss_stats_kernel<<<dim3(chunks, B), 256, 0, h->stream>>>(net->out.as<float>(), target, HW, chunks,
-                                                              net->lpart.as<double>());
+    const int64_t tot = (int64_t)B * HW;
+    const unsigned eg = (unsigned)((tot + 255) / 256);
+    const float* fit = net->out.as<float>();                // what is compared with the target
+    if (stencil) {
+        stencil_apply_kernel<<<eg, 256, 0, h->stream>>>(net->out.as<float>(), stencil, B, net->H, net->W,
+                                                        net->aout.as<float>());
+        RGS_CUDA(cudaGetLastError());
+        fit = net->aout.as<float>();
+        h->launches++;
+    }
+    loss_stats_kernel<<<dim3(chunks, B), 256, 0, h->stream>>>(fit, target, HW, chunks, net->lpart.as<double>());
     RGS_CUDA(cudaGetLastError());
     loss_final_kernel<<<1, 32, 0, h->stream>>>(net->lpart.as<double>(), B, chunks, loss, gscale);
     RGS_CUDA(cudaGetLastError());
-    const int64_t tot = (int64_t)B * HW;
-    dout_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(net->out.as<float>(), target, gscale, B, HW,
-                                                                     net->d6.as<bf16>());
+    if (stencil)
+        stencil_dout_kernel<<<eg, 256, 0, h->stream>>>(fit, target, gscale, stencil, B, net->H, net->W,
+                                                       net->d6.as<bf16>());
+    else
+        dout_kernel<<<eg, 256, 0, h->stream>>>(fit, target, gscale, B, HW, net->d6.as<bf16>());
     RGS_CUDA(cudaGetLastError());
     h->launches += 3;
     // layer 6: dW from (h_5, dA_6); dA_5 = (conv^T dA_6) masked by h_5 > 0
@@ -528,7 +591,8 @@ int64_t rgs_convnet_grid_points(const void* netp) {
     return (int64_t)net->H * net->W;
 }
 
-// z = ||x|| net(x / ||x||, log kappa) on one grid (the flexible-GMRES preconditioner)
+// z = rms(x) net(x / rms(x), log kappa) on one grid (the flexible-GMRES preconditioner),
+// rms(x) = ||x|| / sqrt(H W)
 void rgs_convnet_apply_precond(rgs_context* ctx, void* netp, const double* logkappa, const void* x, int xtype,
                                float* z) {
     rgs_convnet_obj* net = static_cast<rgs_convnet_obj*>(netp);
@@ -600,6 +664,7 @@ rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32
         net->act[0].ensure(sizeof(bf16) * HW * 16 * max_batch);
         for (int l = 1; l < NL; ++l) net->act[l].ensure(sizeof(bf16) * HW * 32 * max_batch);
         net->out.ensure(sizeof(float) * HW * max_batch);
+        net->aout.ensure(sizeof(float) * HW * max_batch);
         net->dA[0].ensure(sizeof(bf16) * HW * 32 * max_batch);
         net->dA[1].ensure(sizeof(bf16) * HW * 32 * max_batch);
         net->d6.ensure(sizeof(bf16) * HW * 16 * max_batch);
@@ -655,7 +720,7 @@ rgs_status rgs_convnet_forward(rgs_handle h, rgs_convnet net, int32_t batch, con
 }
 
 rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, const float* target,
-                                 double* loss, float* grad_host) {
+                                 const float* stencil, double* loss, float* grad_host) {
     if (!h || !net || !in || !target) return RGS_ERR_INVALID_ARG;
     return guarded(h, [&] {
         RGS_REQUIRE(batch >= 1 && batch <= net->max_batch, "batch must be in [1, max_batch]");
@@ -663,7 +728,7 @@ rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, c
         net->h->stream = h->stream;
         pack_training_input(net, batch, in);
         forward(net, batch, net->out.as<float>(), nullptr);
-        double* dl = loss_and_backward(net, batch, target);
+        double* dl = loss_and_backward(net, batch, target, stencil);
         net->h->stream = keep;
         if (loss) RGS_CUDA(cudaMemcpyAsync(loss, dl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         if (grad_host)
@@ -673,7 +738,7 @@ rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t batch, c
 }
 
 rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, const float* in, const float* target,
-                                  float lr, double* loss) {
+                                  const float* stencil, float lr, double* loss) {
     if (!h || !net || !in || !target) return RGS_ERR_INVALID_ARG;
     return guarded(h, [&] {
         RGS_REQUIRE(batch >= 1 && batch <= net->max_batch, "batch must be in [1, max_batch]");
@@ -681,7 +746,7 @@ rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, 
         net->h->stream = h->stream;
         pack_training_input(net, batch, in);
         forward(net, batch, net->out.as<float>(), nullptr);
-        double* dl = loss_and_backward(net, batch, target);
+        double* dl = loss_and_backward(net, batch, target, stencil);
         net->step += 1;
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);

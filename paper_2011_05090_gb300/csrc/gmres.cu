@@ -152,6 +152,16 @@ int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v 
     return np;
 }
 
+// The inner test ends a cycle once the Givens residual estimate falls below
+// inner_factor * rtol * ||b|| (sketched norm for RGMRES).  With a reduced-precision basis the
+// true residual of the updated x can stay above that estimate; a cycle that stopped on the
+// test but left the true residual above rtol tightens the test of the following cycles by
+// the ratio (target / true residual), so that restarts keep making progress.
+void tighten_inner(double& stop_tol, int cycles, int last_steps, int m, double rel, const rgmres_opts& o) {
+    if (cycles == 0 || stop_tol <= 0.0 || last_steps >= m || rel <= o.rtol || !(rel > 0.0)) return;
+    stop_tol *= std::min(1.0, o.inner_factor * o.rtol / rel);
+}
+
 void launch_ls(rgs_arnoldi_obj* a, int i, int sparts, bool solve, int pparts, bool gmres, double stop_tol) {
     LSStep s{};
     s.i = i;
@@ -445,7 +455,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         RGS_CUDA(cudaStreamSynchronize(h->stream));
         const double bnorm = hv[1], sbnorm = hv[2];
         RGS_REQUIRE(bnorm > 0.0 && std::isfinite(bnorm), "b must be nonzero and finite");
-        const double stop_tol = (opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * sbnorm);
+        double stop_tol = (opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * sbnorm);
         int cycles = 0, total = 0;
         double rel = NAN;
         for (;;) {
@@ -457,6 +467,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             if (ctlv[0] != 0) throw RgsError{(rgs_status)ctlv[0], "device status in cycle " + std::to_string(cycles)};
             if (cycles > 0) total += ctlv[kStepsWord];
             rel = hv[0] / bnorm;
+            tighten_inner(stop_tol, cycles, ctlv[kStepsWord], m, rel, *opts);
             if (info && info->history) info->history[cycles] = rel;
             if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
             if (rel <= opts->rtol) { converged = true; break; }
@@ -583,7 +594,7 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
         RGS_CUDA(cudaMemcpyAsync(&bn, val + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         RGS_CUDA(cudaStreamSynchronize(h->stream));
         RGS_REQUIRE(bn > 0.0 && std::isfinite(bn), "b must be nonzero and finite");
-        const double stop_tol = opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * bn;
+        double stop_tol = opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * bn;
         const int ng = rgs_norm_grid(h, n);
         int cycles = 0, total = 0;
         double rel = NAN;
@@ -597,6 +608,7 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
             if (ctlv[0] != 0) throw RgsError{(rgs_status)ctlv[0], "device status"};
             if (cycles > 0) total += ctlv[kStepsWord];
             rel = rn / bn;
+            tighten_inner(stop_tol, cycles, ctlv[kStepsWord], m, rel, *opts);
             if (info && info->history) info->history[cycles] = rel;
             if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
             if (rel <= opts->rtol) { converged = true; break; }
@@ -651,6 +663,18 @@ rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const 
         }
         h->precond_kind = kind;
         h->precond_flexible = flexible;
+    });
+}
+
+rgs_status rgs_csr_matvec(rgs_handle h, const rgs_csr* A, const double* x, double* y) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(A != nullptr, "null CSR");
+        check_csr(A, A->n);
+        RGS_REQUIRE(A->n == 0 || (x && y), "null x or y");
+        RGS_REQUIRE(x != y, "x and y must not alias");
+        if (A->n == 0) return;
+        rgs_launch_spmv(h, *A, nullptr, x, RGS_F64, y, 0, nullptr, nullptr, nullptr);
     });
 }
 

@@ -1,0 +1,129 @@
+"""Training data, training and use of the learned right preconditioner (flexible RGMRES).
+
+The network is trained on residuals that plain restarted RGMRES produces itself.  After restart
+cycle j of a solve of A x = b, the residual r_j = b - A x_j and the error e_j = A^{-1} r_j form
+the pair (r_j, e_j) that shows the map r -> A^{-1} r a right preconditioner M approximates.
+The loss measures the error of M(r_j) in the residual norm,
+||A (M(r_j) - e_j)|| = ||A M(r_j) - r_j||, so it needs r_j and A but never e_j itself; it is
+what a right preconditioner must make small (an error that is small in the plain norm but
+rough is amplified by A and makes a useless preconditioner).  A solve started from a
+white-noise right-hand side yields residuals from white noise (r_0 = b) to smooth (late
+cycles), the range of vectors a flexible solver later applies M to.  Arnoldi basis vectors
+of the cycles can be added as further inputs.
+
+Inputs are scaled to unit root mean square, rms(v) = ||v|| / sqrt(n), like the network's
+input inside the solver; the operators travel as 5-point stencils (centre, west, east,
+north, south coefficients of each row).
+
+Everything numerical runs in librgs (the solver, the products with A, the network's forward,
+backward and Adam kernels); this module only moves tensors between those calls.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import (rgmres_set_preconditioner, rgmres_solve, rgs_arnoldi_basis, rgs_arnoldi_create, rgs_arnoldi_start,
+               rgs_arnoldi_step, rgs_convnet_train_step, rgs_csr_matvec)
+
+
+def _rms(v):
+    return torch.linalg.vector_norm(v.double()) / math.sqrt(v.numel())
+
+
+def stencil_from_csr(rowptr, colind, val, H, W):
+    """(5, H, W) FP32 coefficients of a 5-point operator on an H x W grid (x fastest) from its
+    CSR arrays (torch tensors on one device); raises if a row reaches another neighbour."""
+    n = H * W
+    counts = rowptr[1:].long() - rowptr[:-1].long()
+    rows = torch.repeat_interleave(torch.arange(n, device=rowptr.device), counts)
+    d = colind.long() - rows
+    chan = torch.full_like(d, -1)
+    for c, off in enumerate((0, -1, 1, -W, W)):
+        chan[d == off] = c
+    if bool((chan < 0).any()):
+        raise ValueError("not a 5-point operator on this grid")
+    S = torch.zeros(5, n, dtype=torch.float64, device=rowptr.device)
+    S.index_put_((chan, rows), val.double(), accumulate=True)
+    return S.view(5, H, W).float()
+
+
+def harvest(h, sk, csr, logkappa, b, inputs, start=0, cycles=100, restart=50, qdtype=torch.float32,
+            basis_cols=()):
+    """Run plain RGMRES(restart) on A x = b from x = 0 and write, for j = 0, 1, ..., the input
+    (r_j / rms(r_j), log kappa) of every restart residual into inputs[start:] (N x 2 x H x W
+    FP32), followed, for each column index c in ``basis_cols``, by the c-th Arnoldi basis vector
+    of an RGS-Arnoldi process started from r_j.  Stops after ``cycles`` residuals, when the
+    solve reaches 1e-10, or when ``inputs`` is full.  Returns the number of rows written."""
+    H, W = logkappa.shape
+    lk = logkappa.float()
+    x = torch.zeros_like(b)
+    N = inputs.shape[0]
+    w = start
+    arn = None
+    if basis_cols:
+        arn = rgs_arnoldi_create(h, sk, H * W, max(basis_cols) + 1, qdtype)
+
+    def put(v):
+        nonlocal w
+        rr = _rms(v)
+        if w >= N or not rr > 0:
+            return False
+        inputs[w, 0] = (v.double() / rr).view(H, W).float()
+        inputs[w, 1] = lk
+        w += 1
+        return True
+
+    for j in range(cycles):
+        r = b - rgs_csr_matvec(h, csr, x)
+        if not put(r):
+            break
+        if arn is not None:
+            rgs_arnoldi_start(h, arn, r)
+            for _ in range(max(basis_cols)):
+                rgs_arnoldi_step(h, arn, csr=csr)
+            Q = rgs_arnoldi_basis(arn, max(basis_cols) + 1)
+            for c in basis_cols:
+                if not put(Q[:, c].contiguous()):
+                    break
+        res = rgmres_solve(h, sk, csr, b, x, restart=restart, rtol=1e-10, max_cycles=1, qdtype=qdtype)
+        if res["converged"] or w >= N:
+            break
+    return w - start
+
+
+def train(h, net, inputs, steps, stencils, field_of, batch=16, lr=1e-3, lr_final=1e-5, seed=0, log_every=0):
+    """Adam on random minibatches of ``inputs`` for ``steps`` steps with the residual-norm loss
+    mean_b ||A_b net(x_b) - r_b||^2 / ||r_b||^2 (r_b = channel 0 of x_b, A_b =
+    stencils[field_of[b]]), the learning rate decaying along a cosine from ``lr`` to
+    ``lr_final``.  Returns the per-step losses."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed))
+    N = inputs.shape[0]
+    losses = []
+    for t in range(steps):
+        idx = torch.randint(0, N, (batch,), generator=g).to(inputs.device)
+        xb = inputs.index_select(0, idx).contiguous()
+        rb = xb[:, 0].contiguous()
+        sb = stencils.index_select(0, field_of.index_select(0, idx)).contiguous()
+        a = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * t / max(steps - 1, 1)))
+        losses.append(rgs_convnet_train_step(h, net, xb, rb, lr=a, stencil=sb))
+        if log_every and (t % log_every == 0 or t == steps - 1):
+            print(f"step {t}: loss {losses[-1]:.4f} (lr {a:.2e})", flush=True)
+    return losses
+
+
+def solve(h, sk, csr, b, x, restart=50, rtol=1e-8, max_cycles=1000, qdtype=torch.float32, precond="none",
+          net=None, logkappa=None):
+    """rgmres_solve with the right preconditioner ``precond`` ("none", "jacobi" or "learned";
+    the learned one runs flexible), restoring "none" afterwards."""
+    if precond == "learned":
+        lk = logkappa.reshape(-1).to(torch.float64).contiguous()
+        rgmres_set_preconditioner(h, "learned", net, lk, flexible=True)
+    else:
+        rgmres_set_preconditioner(h, precond)
+    try:
+        return rgmres_solve(h, sk, csr, b, x, restart=restart, rtol=rtol, max_cycles=max_cycles, qdtype=qdtype)
+    finally:
+        rgmres_set_preconditioner(h, "none")

@@ -8,6 +8,9 @@ import numpy as np
 import pytest
 from scipy import signal
 
+import scipy.sparse as sp
+
+import synth
 from oracle import convnet as oc
 
 
@@ -118,3 +121,35 @@ def test_bf16_emulation_is_close_to_fp64():
     a, _, _ = oc.forward(p, x)
     b, _, _ = oc.forward(p, x, bf16=True)
     assert 1e-5 < np.linalg.norm(a - b) / np.linalg.norm(a) < 3e-2
+
+
+def test_stencil_apply_and_adjoint_match_the_sparse_matrix():
+    # a nonsymmetric operator (convection) so that the adjoint differs from the operator
+    H, W = 6, 9
+    csr = synth.convdiff_csr((H, W), np.exp(rng(11).standard_normal((H, W))), np.array([3.0, -5.0]))
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    S = oc.stencil_from_csr(csr, H, W)[None]
+    v = rng(12).standard_normal((1, H, W))
+    assert np.allclose(oc.stencil_apply(S, v).ravel(), A @ v.ravel(), rtol=1e-14, atol=1e-12)
+    assert np.allclose(oc.stencil_adjoint(S, v).ravel(), A.T @ v.ravel(), rtol=1e-14, atol=1e-12)
+
+
+def test_residual_loss_grad_matches_finite_differences():
+    g = rng(13)
+    H, W = 8, 16
+    p = oc.init_params(3)
+    p[-289:] += 0.01 * g.standard_normal(289)
+    csr = synth.convdiff_csr((H, W), np.exp(g.standard_normal((H, W))), np.array([2.0, 1.0]))
+    S = np.stack([oc.stencil_from_csr(csr, H, W)] * 2) * (1.0 / (H + 1) ** 2)
+    x = g.standard_normal((2, 2, H, W))
+    t = g.standard_normal((2, H, W))
+    L, grad = oc.loss_grad(p, x, t, stencil=S)
+    assert L == pytest.approx(oc.loss(oc.stencil_apply(S, oc.forward(p, x)[0]), t), rel=1e-14)
+    for i in g.choice(len(p), 30, replace=False):
+        eps = 1e-6 * max(1.0, abs(p[i]))
+        pp, pm = p.copy(), p.copy()
+        pp[i] += eps
+        pm[i] -= eps
+        f = lambda q: oc.loss(oc.stencil_apply(S, oc.forward(q, x)[0]), t)
+        fd = (f(pp) - f(pm)) / (2 * eps)
+        assert abs(fd - grad[i]) <= 1e-6 * max(abs(grad[i]), 1e-3 * np.abs(grad).max()), i
