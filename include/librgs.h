@@ -273,11 +273,37 @@ RGS_API rgs_status rgs_convnet_loss_grad(rgs_handle h, rgs_convnet net, int32_t 
 RGS_API rgs_status rgs_convnet_train_step(rgs_handle h, rgs_convnet net, int32_t batch, const float* in,
                                           const float* target, const float* stencil, float lr, double* loss);
 
-/* Batched solves in one persistent launch are declared for interface stability; they return
- * RGS_ERR_NOT_IMPLEMENTED until built. */
-RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_sketch* sketches,
-                                        const rgs_csr* A, const double* const* b, double* const* x,
-                                        const rgmres_opts* opts, rgmres_info* info);
+/* ---------------------------------------------------------------- batched solves
+ * rgmres_solve_batched solves nbatch independent systems A_b x_b = b_b with restarted RGMRES in
+ * one persistent cooperative kernel (issued through a CUDA graph): the grid is split into
+ * teams of CTAs, each team runs the whole solve of its instance(s) with team-local barriers
+ * (bounded waits; RGS_ERR_TIMEOUT), so no host round trip happens between cycles.
+ * Sketch: Gaussian, Theta_b = G[0:k_b, 0:n_b] / sqrt(k_b) with G the N(0,1) draws of the
+ * Gaussian sketch layout above for sketch_seed, rounded to bfloat16 (one shared matrix for the
+ * whole batch); products with it accumulate in double-float.  The sketched least-squares
+ * problem (step 2 of Alg. 2) is solved in FP64 through a CGS2 QR factorisation of S; Givens
+ * rotations and the restart residual b - A x are FP64.
+ *   A, b, x, opts, info: host arrays of nbatch entries; A[i] holds device CSR arrays, b[i] and
+ *   x[i] device FP64 vectors (x[i]: initial guess in, solution out).  info may be NULL;
+ *   info[i].history, if set, is a host array of max_cycles + 1 entries.
+ *   opts[i]: restart in [1, 127], restart + 1 <= k <= 192, one qtype (RGS_F64 or RGS_F32) for
+ *   the whole batch.
+ * Returns RGS_OK when the launch completed; per-instance results (RGS_OK,
+ * RGS_ERR_NOT_CONVERGED, RGS_ERR_NONFINITE, ...) are in info[i].status. */
+typedef struct {
+    int32_t restart;
+    int32_t k;
+    int32_t max_cycles;
+    int32_t qtype;
+    double rtol;
+    double inner_factor;
+    int32_t fixed_steps;
+    int32_t reserved;
+} rgmres_batch_opts;
+
+RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, const double* const* b,
+                                        double* const* x, const rgmres_batch_opts* opts, uint64_t sketch_seed,
+                                        rgmres_info* info);
 
 #ifdef __cplusplus
 }

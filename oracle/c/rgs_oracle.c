@@ -435,6 +435,7 @@ int orc_rgmres(orc_sketch* sk, int64_t n, const int32_t* rowptr, const int32_t* 
     double rel = nrm2(n, w) / bn;
     res_hist[0] = rel;
     int cycles = 0, total = 0;
+    double thr = inner_factor * tol * sb;   /* inner threshold, tightened after a short cycle */
     while (!(rel <= tol) && cycles < max_cycles) {
         rgs_state st;
         rgs_init(&st, n, k, mcols, ls, sweeps, storage, Qp, sigma, S);
@@ -457,7 +458,7 @@ int orc_rgmres(orc_sketch* sk, int64_t n, const int32_t* rowptr, const int32_t* 
             double rho = hess_column(h, i - 1, cs, sn, g);
             j = i;
             if (bd) break;                                     /* invariant subspace */
-            if (!fixed_steps && rho <= inner_factor * tol * sb) break;
+            if (!fixed_steps && rho <= thr) break;
         }
         rgs_free(&st);
         if (j == 0) break;
@@ -473,6 +474,7 @@ int orc_rgmres(orc_sketch* sk, int64_t n, const int32_t* rowptr, const int32_t* 
         cycles++;
         total += j;
         res_hist[cycles] = rel;
+        if (!(rel <= tol) && j < restart) thr *= fmin(1.0, inner_factor * tol / rel);
     }
     info[0] = cycles;
     info[1] = total;
@@ -500,6 +502,7 @@ int orc_cgs2_gmres(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
     double rel = nrm2(n, w) / bn;
     res_hist[0] = rel;
     int cycles = 0, total = 0;
+    double thr = inner_factor * tol * bn;   /* inner threshold, tightened after a short cycle */
     while (!(rel <= tol) && cycles < max_cycles) {
         double beta = nrm2(n, w);
         for (int64_t r = 0; r < n; ++r) V[r] = w[r] / beta;
@@ -529,7 +532,7 @@ int orc_cgs2_gmres(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
             j = i + 1;
             if (!(hn > 16.0 * 0x1p-53 * hmax)) break;
             for (int64_t r = 0; r < n; ++r) V[(size_t)(i + 1) * n + r] = w[r] / hn;
-            if (!fixed_steps && rho <= inner_factor * tol * bn) break;
+            if (!fixed_steps && rho <= thr) break;
         }
         hess_solve(H, mcols + 1, j, g, y);
         for (int64_t r = 0; r < n; ++r) {
@@ -543,6 +546,7 @@ int orc_cgs2_gmres(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
         cycles++;
         total += j;
         res_hist[cycles] = rel;
+        if (!(rel <= tol) && j < restart) thr *= fmin(1.0, inner_factor * tol / rel);
     }
     info[0] = cycles;
     info[1] = total;

@@ -124,7 +124,9 @@ def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="househol
     """Restarted randomized GMRES with RGS-Arnoldi; ``A`` is anything with ``A @ v``.
 
     Inner stop (unless ``fixed_steps``): sketched residual estimate
-    <= inner_factor * tol * ||Theta b||.  Outer stop: ||b - A x|| <= tol ||b||.
+    <= threshold, initially inner_factor * tol * ||Theta b||; a cycle that stopped on it
+    but left the true residual above tol multiplies the threshold of the following cycles by
+    inner_factor * tol / (true relative residual).  Outer stop: ||b - A x|| <= tol ||b||.
     """
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
@@ -139,8 +141,9 @@ def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="househol
     res.true_residuals.append(float(np.linalg.norm(r) / bnorm))
     converged = res.true_residuals[-1] <= tol
     cycles = 0
+    thr = inner_factor * tol * sb
     while not converged and cycles < max_cycles:
-        stop = None if fixed_steps else (lambda rho, j: rho <= inner_factor * tol * sb)
+        stop = None if fixed_steps else (lambda rho, j, thr=thr: rho <= thr)
         cyc = rgs_arnoldi(matvec, r, sketch, restart, ls, sweeps, storage,
                           precond=precond, stop=stop)
         j = cyc.steps
@@ -157,6 +160,8 @@ def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="househol
         res.rho.append(cyc.rho)
         cycles += 1
         converged = res.true_residuals[-1] <= tol
+        if not converged and j < restart:
+            thr *= min(1.0, inner_factor * tol / res.true_residuals[-1])
     res.x = x
     res.cycles = cycles
     res.converged = converged
@@ -211,8 +216,9 @@ def cgs2_gmres(A, b, restart, tol=1e-8, max_cycles=50, x0=None, inner_factor=0.5
     res.true_residuals.append(float(np.linalg.norm(r) / bnorm))
     converged = res.true_residuals[-1] <= tol
     cycles = 0
+    thr = inner_factor * tol * bnorm
     while not converged and cycles < max_cycles:
-        stop = None if fixed_steps else (lambda rho, j: rho <= inner_factor * tol * bnorm)
+        stop = None if fixed_steps else (lambda rho, j, thr=thr: rho <= thr)
         V, H, y, rho = cgs2_arnoldi(lambda v: A @ v, r, restart, stop)
         x = x + V[:, : len(y)] @ y
         r = b - A @ x
@@ -220,6 +226,8 @@ def cgs2_gmres(A, b, restart, tol=1e-8, max_cycles=50, x0=None, inner_factor=0.5
         res.steps.append(len(y))
         cycles += 1
         converged = res.true_residuals[-1] <= tol
+        if not converged and len(y) < restart:
+            thr *= min(1.0, inner_factor * tol / res.true_residuals[-1])
     res.x = x
     res.cycles = cycles
     res.converged = converged

@@ -81,6 +81,12 @@ def _u53(hi, lo):
 
 def gaussian_theta(k, n, seed, col0=0, ncols=None):
     """Columns [col0, col0+ncols) of the k x n Gaussian sketch with N(0, 1/k) entries (FP64)."""
+    return gaussian_normals(k, n, seed, col0, ncols) / np.sqrt(k)
+
+
+def gaussian_normals(k, n, seed, col0=0, ncols=None):
+    """The N(0, 1) draws behind the Gaussian sketch: entry (l, c) from counter (c, l >> 1, 0, 0),
+    Box-Muller (cosine for even l, sine for odd l)."""
     if ncols is None:
         ncols = n - col0
     cols = np.arange(col0, col0 + ncols, dtype=np.uint64)
@@ -97,7 +103,7 @@ def gaussian_theta(k, n, seed, col0=0, ncols=None):
     out = np.empty((2 * len(pairs), len(cols)))
     out[0::2] = rad * np.cos(ang)
     out[1::2] = rad * np.sin(ang)
-    return out[:k] / np.sqrt(k)
+    return out[:k]
 
 
 def srht_signs(n, seed):

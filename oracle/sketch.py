@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Sec. 2.1 defines the two families used here:
 
 * Gaussian (the paper's experiments note no difference from Rademacher, Sec. 5):
-  i.i.d. N(0, 1/k) entries;
+  i.i.d. N(0, 1/k) entries; "gaussian_bf16" is the same draws rounded to bfloat16 before
+  the 1/sqrt(k) scale (the sketch of the batched solver);
 * (P-)SRHT: for s the power of two with n <= s < 2n, Theta is the first n
   columns of (1/sqrt(k)) * P * H_s * D, with D a diagonal of random signs, H_s
   the (unnormalised, +-1) Walsh-Hadamard matrix of order s and P a uniform
@@ -51,11 +52,14 @@ class Sketch:
     """A seeded sketching matrix Theta; ``apply(X)`` returns Theta @ X in FP64."""
 
     def __init__(self, kind, n, k, seed):
-        if kind not in ("gaussian", "srht"):
+        if kind not in ("gaussian", "gaussian_bf16", "srht"):
             raise ValueError(kind)
         self.kind, self.n, self.k, self.seed = kind, int(n), int(k), int(seed)
         if kind == "gaussian":
             self._theta = philox.gaussian_theta(self.k, self.n, self.seed)
+        elif kind == "gaussian_bf16":
+            from .rgs import round_bf16
+            self._theta = round_bf16(philox.gaussian_normals(self.k, self.n, self.seed)) / np.sqrt(self.k)
         else:
             self.s = next_pow2(self.n)
             if self.k > self.s:
@@ -70,7 +74,7 @@ class Sketch:
             X = X[:, None]
         if X.shape[0] != self.n:
             raise ValueError("row count mismatch")
-        if self.kind == "gaussian":
+        if self.kind in ("gaussian", "gaussian_bf16"):
             Y = self._theta @ X
         else:
             Z = np.zeros((self.s, X.shape[1]))

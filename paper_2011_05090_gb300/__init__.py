@@ -90,6 +90,12 @@ class GmresInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("k", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
+                ("qtype", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_factor", ctypes.c_double),
+                ("fixed_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class LearnedPrecond(ctypes.Structure):
     _fields_ = [("net", ctypes.c_void_p), ("logkappa", ctypes.c_void_p)]
 
@@ -127,7 +133,8 @@ def load():
         "rgmres_solve": [P, P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
         "cgs2_gmres_solve": [P, ctypes.POINTER(CSR), P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
         "rgmres_set_preconditioner": [P, ctypes.c_int, P, I32],
-        "rgmres_solve_batched": [P, I32, P, P, P, P, ctypes.POINTER(GmresOpts), ctypes.POINTER(GmresInfo)],
+        "rgmres_solve_batched": [P, I32, ctypes.POINTER(CSR), ctypes.POINTER(P), ctypes.POINTER(P),
+                                 ctypes.POINTER(BatchOpts), ctypes.c_uint64, ctypes.POINTER(GmresInfo)],
         "rgs_convnet_num_params": [],
         "rgs_convnet_create": [P, I32, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)],
         "rgs_convnet_destroy": [P],
@@ -382,6 +389,31 @@ def rgs_csr_matvec(h, csr, x, y=None):
         y = torch.empty_like(x)
     _check(load().rgs_csr_matvec(h.ptr, ctypes.byref(csr), x.data_ptr(), y.data_ptr()), h)
     return y
+
+
+def rgmres_solve_batched(h, csrs, bs, xs, restarts, ks, rtol=1e-8, max_cycles=100, inner_factor=0.5,
+                         qdtype=torch.float32, fixed_steps=False, sketch_seed=0):
+    """Independent restarted RGMRES solves in one persistent launch.  csrs: CSR structs,
+    bs / xs: FP64 CUDA vectors (xs: initial guesses, overwritten), restarts / ks: per instance.
+    Returns one result dict per instance (as rgmres_solve)."""
+    nb = len(csrs)
+    if not (len(bs) == len(xs) == len(restarts) == len(ks) == nb):
+        raise ValueError("one b, x, restart and k per system")
+    A = (CSR * nb)(*csrs)
+    bp = (ctypes.c_void_p * nb)(*[v.data_ptr() for v in bs])
+    xp = (ctypes.c_void_p * nb)(*[v.data_ptr() for v in xs])
+    rt = [rtol] * nb if not hasattr(rtol, "__len__") else list(rtol)
+    mc = [max_cycles] * nb if not hasattr(max_cycles, "__len__") else list(max_cycles)
+    opts = (BatchOpts * nb)(*[BatchOpts(int(restarts[i]), int(ks[i]), int(mc[i]), _DTYPE[qdtype], float(rt[i]),
+                                        float(inner_factor), 1 if fixed_steps else 0, 0) for i in range(nb)])
+    hists = [(ctypes.c_double * (mc[i] + 1))() for i in range(nb)]
+    info = (GmresInfo * nb)()
+    for i in range(nb):
+        info[i].history = ctypes.cast(hists[i], ctypes.POINTER(ctypes.c_double))
+    _check(load().rgmres_solve_batched(h.ptr, nb, A, bp, xp, opts, int(sketch_seed), info), h)
+    return [{"cycles": info[i].cycles, "total_steps": info[i].total_steps, "converged": bool(info[i].converged),
+             "status": info[i].status, "rel_residual": info[i].rel_residual,
+             "history": [hists[i][c] for c in range(info[i].cycles + 1)]} for i in range(nb)]
 
 
 def csr_to_device(rowptr, colind, val, device="cuda"):

@@ -69,9 +69,20 @@ struct rgs_context {
     int precond_flexible = 0;
     void* precond_net = nullptr;           // RGS_PRECOND_LEARNED_CONV: the network
     const double* precond_field = nullptr; // and its second input channel (log kappa, H x W)
+    DevBuf batch_theta;    // rgmres_solve_batched: shared BF16 Gaussian G (k x n)
+    uint64_t batch_theta_seed = ~0ull;
+    int batch_theta_k = 0;
+    int64_t batch_theta_n = 0;
+    int batch_blocks_per_sm = 0;           // 0: the occupancy limit, at most 4
+    DevBuf batch_ws;       // per-instance workspaces of the batched solve
+    DevBuf batch_desc;     // instance descriptors and team tables
+    cudaStream_t capture_stream = nullptr; // private stream on which launches are captured into graphs
     int launches = 0;      // kernels launched by the current call
     std::vector<cudaEvent_t> events;   // pool for per-phase timings
-    ~rgs_context() { for (auto e : events) cudaEventDestroy(e); }
+    ~rgs_context() {
+        for (auto e : events) cudaEventDestroy(e);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+    }
 };
 
 // Accumulates the device time of repeated phases from pairs of events.

@@ -678,10 +678,6 @@ rgs_status rgs_csr_matvec(rgs_handle h, const rgs_csr* A, const double* x, doubl
     });
 }
 
-rgs_status rgmres_solve_batched(rgs_handle h, int32_t, const rgs_sketch*, const rgs_csr*, const double* const*,
-                                double* const*, const rgmres_opts*, rgmres_info*) {
-    if (!h) return RGS_ERR_INVALID_ARG;
-    return RGS_ERR_NOT_IMPLEMENTED;
-}
+
 
 }  // extern "C"

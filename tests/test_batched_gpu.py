@@ -1,0 +1,129 @@
+"""GPU parity of the batched persistent RGMRES (one launch, many instances) against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import paper_2011_05090_gb300 as rgs
+import synth
+from oracle import gmres as og
+from oracle.sketch import Sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2011_05090_gb300 import build
+    build.build()
+    return rgs.rgs_create()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def dev(v):
+    return torch.tensor(np.asarray(v, dtype=np.float64), device="cuda")
+
+
+def instance(nx, ny, pe, angle, seed):
+    csr = synth.convdiff_2d(nx, ny, pe, angle)
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    return {"csr": csr, "A": A, "C": C, "keep": (rp, ci, va), "b": synth.rhs(nx * ny, seed)}
+
+
+def run(h, insts, restarts, ks, qdtype=torch.float64, x0=None, **kw):
+    xs = [dev(np.zeros(I["A"].shape[0])) if x0 is None else dev(x0[i]) for i, I in enumerate(insts)]
+    bs = [dev(I["b"]) for I in insts]
+    res = rgs.rgmres_solve_batched(h, [I["C"] for I in insts], bs, xs, restarts, ks, qdtype=qdtype, **kw)
+    return res, [x.cpu().numpy() for x in xs]
+
+
+def test_one_cycle_matches_oracle(h):
+    # uneven sizes, restarts and sketch sizes in one launch; FP64 basis, fixed steps
+    shapes = [(20, 30, 10.0, 0.3, 1), (33, 17, 40.0, 2.0, 2), (48, 48, 5.0, 4.0, 3), (16, 64, 80.0, 1.0, 4)]
+    insts = [instance(*s) for s in shapes]
+    restarts, ks = [12, 25, 30, 7], [24, 60, 61, 20]
+    res, xs = run(h, insts, restarts, ks, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
+        n = I["A"].shape[0]
+        ref = og.rgmres(I["A"], I["b"], Sketch("gaussian_bf16", n, k, 5), restart=m, max_cycles=1, fixed_steps=True)
+        assert r["cycles"] == 1 and r["total_steps"] == m
+        assert rel(x, ref.x) <= 1e-11
+        assert abs(r["history"][1] - ref.true_residuals[1] / ref.true_residuals[0]) <= 1e-10
+
+
+@pytest.mark.parametrize("qdtype", [torch.float64, torch.float32])
+def test_batch_converges_like_the_oracle(h, qdtype):
+    g = np.random.default_rng(0)
+    insts, restarts, ks = [], [], []
+    for i in range(10):
+        nx, ny = int(g.integers(16, 60)), int(g.integers(16, 60))
+        insts.append(instance(nx, ny, float(g.uniform(1, 100)), float(g.uniform(0, 2 * np.pi)), 10 + i))
+        m = int(g.integers(20, 41))
+        restarts.append(m)
+        ks.append(2 * m)
+    res, xs = run(h, insts, restarts, ks, qdtype=qdtype, rtol=1e-8, max_cycles=300, sketch_seed=1)
+    for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
+        n = I["A"].shape[0]
+        true_rel = np.linalg.norm(I["b"] - I["A"] @ x) / np.linalg.norm(I["b"])
+        assert r["converged"] and r["status"] == rgs.RGS_OK and true_rel <= 1e-8
+        assert abs(true_rel - r["rel_residual"]) <= 1e-3 * 1e-8
+        ref = og.rgmres(I["A"], I["b"], Sketch("gaussian_bf16", n, k, 1), restart=m, tol=1e-8, max_cycles=300)
+        assert ref.converged and r["total_steps"] <= 1.3 * sum(ref.steps) + m
+        # the minimised residual is the sketched one (k = 2m: a coarse embedding), so the true
+        # residual may rise a little at a restart, never by more than the embedding allows
+        hist = r["history"]
+        assert all(hist[j + 1] < 3.0 * hist[j] for j in range(len(hist) - 1))
+
+
+def test_large_instance_spans_a_team_of_ctas(h):
+    # a 160 x 160 system beside two tiny ones: its team has several CTAs (barriers across CTAs)
+    insts = [instance(160, 160, 30.0, 0.7, 21), instance(12, 16, 3.0, 0.1, 22), instance(16, 12, 9.0, 1.1, 23)]
+    restarts, ks = [20, 8, 8], [40, 16, 16]
+    res, xs = run(h, insts, restarts, ks, max_cycles=1, fixed_steps=True, sketch_seed=9)
+    for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
+        n = I["A"].shape[0]
+        ref = og.rgmres(I["A"], I["b"], Sketch("gaussian_bf16", n, k, 9), restart=m, max_cycles=1, fixed_steps=True)
+        assert rel(x, ref.x) <= 1e-11
+
+
+def test_more_instances_than_ctas(h):
+    # instances beyond the grid are queued on single-CTA teams
+    n_inst = 700
+    g = np.random.default_rng(1)
+    insts = [instance(8, 16, float(g.uniform(1, 50)), float(g.uniform(0, 6)), 100 + i) for i in range(n_inst)]
+    res, xs = run(h, insts, [10] * n_inst, [20] * n_inst, qdtype=torch.float32, rtol=1e-8, max_cycles=100)
+    for I, r, x in zip(insts, res, xs):
+        assert r["converged"]
+        assert np.linalg.norm(I["b"] - I["A"] @ x) <= 1e-8 * np.linalg.norm(I["b"])
+
+
+def test_deterministic_and_initial_guess(h):
+    insts = [instance(30, 20, 20.0, 0.5, 31), instance(25, 25, 60.0, 2.5, 32)]
+    r1, x1 = run(h, insts, [15, 20], [30, 40], qdtype=torch.float32, rtol=1e-8, max_cycles=200)
+    r2, x2 = run(h, insts, [15, 20], [30, 40], qdtype=torch.float32, rtol=1e-8, max_cycles=200)
+    for a, b in zip(x1, x2):
+        assert np.array_equal(a, b)
+    exact = [sp.linalg.spsolve(I["A"].tocsc(), I["b"]) for I in insts]
+    r3, _ = run(h, insts, [15, 20], [30, 40], x0=exact, rtol=1e-8, max_cycles=5)
+    assert all(r["converged"] and r["cycles"] == 0 for r in r3)
+
+
+def test_not_converged_is_reported_per_instance(h):
+    insts = [instance(40, 40, 10.0, 0.2, 41), instance(10, 10, 1.0, 0.0, 42)]
+    res, _ = run(h, insts, [5, 30], [10, 60], rtol=1e-8, max_cycles=[2, 50])
+    assert not res[0]["converged"] and res[0]["status"] == rgs.RGS_ERR_NOT_CONVERGED and res[0]["cycles"] == 2
+    assert res[1]["converged"] and res[1]["status"] == rgs.RGS_OK
+
+
+def test_invalid_arguments(h):
+    I = instance(10, 10, 1.0, 0.0, 1)
+    with pytest.raises(rgs.RgsError):
+        run(h, [I], [0], [10])                     # restart 0
+    with pytest.raises(rgs.RgsError):
+        run(h, [I], [10], [200])                   # k beyond 192
+    with pytest.raises(rgs.RgsError):
+        run(h, [I], [10], [10])                    # k < restart + 1

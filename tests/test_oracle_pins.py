@@ -334,3 +334,18 @@ def test_right_preconditioned_rgmres_solves_original_system():
                            precond=lambda v: dinv * v, flexible=flexible)
         assert res.converged
         assert np.linalg.norm(b - A @ res.x) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_gaussian_bf16_sketch_is_the_rounded_gaussian():
+    from oracle.rgs import round_bf16
+    k, n = 40, 300
+    g = Sketch("gaussian", n, k, 7).dense()
+    b = Sketch("gaussian_bf16", n, k, 7).dense()
+    scaled = b * np.sqrt(k)
+    assert np.allclose(round_bf16(scaled), scaled, rtol=1e-15, atol=0)   # bf16 values before the scale
+    assert np.all(np.abs(b - g) <= 2.0 ** -8 * np.abs(g) + 1e-300)  # within half a bf16 ulp of N(0,1/k)
+    assert np.abs(b - g).max() > 0
+    # still an embedding in expectation: mean of ||Theta x||^2 over seeds
+    x = np.random.default_rng(3).standard_normal(n)
+    vals = [np.linalg.norm(Sketch("gaussian_bf16", n, k, s).apply(x)) ** 2 for s in range(60)]
+    assert abs(np.mean(vals) / np.dot(x, x) - 1.0) < 0.08
