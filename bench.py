@@ -21,6 +21,15 @@ residual of 1e-8 on a 3D convection-diffusion operator: 128^3 grid (n = 2,097,15
 7-point CSR, FP64 values), log-normal diffusion (sigma = 1, correlation length 8
 cells), Peclet number 50, iid N(0,1) right-hand side.
 
+"batched" in the same line: 256 independent 2D convection-diffusion RGMRES solves in one
+persistent launch (rgmres_solve_batched, FP32 basis, Gaussian k = 2 restart) against the
+same 256 systems solved one after another with FP64 CGS2-GMRES, at the full sizes (sides
+64..512) for two fixed cycles each, and to 1e-8 on sides 16..64.
+
+--c5 N prints a separate line for the learned preconditioner on N x N diffusion grids:
+training-data harvest from plain RGMRES, training with the library's kernels, and held-out
+solves with the learned (flexible), Jacobi and no preconditioner.
+
 --impl reference times the CPU oracle (oracle/c/rgs_oracle.c) on a bounded
 sample of the same workload on the host cores.
 """
@@ -216,6 +225,139 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "cgs2")):
     return out
 
 
+def c4_instances(rgs, NB, lo, hi, seed0):
+    """The batched workload: 2D upwind convection-diffusion, sides uniform in [lo, hi], Peclet
+    U[1, 100] at an angle U[0, 2 pi), restart U{30..80}, Gaussian k = 2 restart, b iid N(0,1)."""
+    import torch
+    import synth
+    insts = []
+    for i in range(NB):
+        g = np.random.default_rng(seed0 + i)
+        nx, ny = int(g.integers(lo, hi + 1)), int(g.integers(lo, hi + 1))
+        ang, pe, m = float(g.uniform(0, 2 * np.pi)), float(g.uniform(1, 100)), int(g.integers(30, 81))
+        csr = synth.convdiff_2d(nx, ny, pe, ang)
+        arrays, C = rgs.csr_to_device(*csr)
+        insts.append({"n": nx * ny, "m": m, "C": C, "arrays": arrays,
+                      "b": torch.tensor(synth.rhs(nx * ny, seed0 + i), device="cuda")})
+    return insts
+
+
+def run_batched_c4(rgs, h):
+    """256 instances in one persistent launch (FP32 basis) against 256 sequential FP64 CGS2-GMRES
+    solves: (a) at the full sizes (sides 64..512) for two fixed cycles per instance (most of these
+    unpreconditioned solves need tens of thousands of steps to reach 1e-8), (b) time to 1e-8 on
+    sides 16..64, where every instance converges."""
+    import torch
+
+    def batched(insts, **kw):
+        xs = [torch.zeros(I["n"], dtype=torch.float64, device="cuda") for I in insts]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = rgs.rgmres_solve_batched(h, [I["C"] for I in insts], [I["b"] for I in insts], xs,
+                                       [I["m"] for I in insts], [2 * I["m"] for I in insts], sketch_seed=1,
+                                       qdtype=torch.float32, **kw)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    def sequential_cgs2(insts, **kw):
+        dt, steps, conv = 0.0, 0, 0
+        for I in insts:
+            x = torch.zeros(I["n"], dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = rgs.cgs2_gmres_solve(h, I["C"], I["b"], x, restart=I["m"], **kw)
+            torch.cuda.synchronize()
+            dt += time.perf_counter() - t0
+            steps += r["total_steps"]
+            conv += r["converged"]
+        return dt, steps, conv
+
+    out = {}
+    full = c4_instances(rgs, 256, 64, 512, 0)
+    batched(full[:8], max_cycles=1, fixed_steps=True)                      # warm-up
+    dt, res = batched(full, max_cycles=2, fixed_steps=True)
+    steps = sum(r["total_steps"] for r in res)
+    ct, cs, _ = sequential_cgs2(full, max_cycles=2, fixed_steps=True)
+    out["full_fixed_2_cycles"] = {
+        "config": "256 x convdiff2d sides U[64,512] Pe U[1,100] restart U{30..80} gaussian k=2m, 2 fixed cycles",
+        "sum_n": sum(I["n"] for I in full), "arnoldi_steps": steps, "batched_f32_s": dt,
+        "batched_steps_per_s": steps / dt, "sequential_cgs2_f64_s": ct, "speedup": ct / dt}
+    del full
+    small = c4_instances(rgs, 256, 16, 64, 1000)
+    dt, res = batched(small, max_cycles=400, rtol=1e-8)
+    ct, cs, cconv = sequential_cgs2(small, max_cycles=400, rtol=1e-8)
+    out["small_to_1e-8"] = {
+        "config": "256 x convdiff2d sides U[16,64], same draws otherwise, rtol 1e-8",
+        "batched_f32_s": dt, "converged": sum(r["converged"] for r in res),
+        "arnoldi_steps": sum(r["total_steps"] for r in res), "sequential_cgs2_f64_s": ct,
+        "cgs2_converged": cconv, "cgs2_steps": cs, "speedup": ct / dt, "launches": 1}
+    return out
+
+
+def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=3, steps=1500, ntest=3,
+                   max_cycles=400, batch=16):
+    """Learned preconditioner: harvest restart residuals of plain RGMRES(50) solves on nfields
+    diffusion problems (kappa = exp(1.5 g), correlation ell; right-hand sides from white noise to
+    smooth), train the conv net with the residual-norm loss, then solve held-out fields with
+    flexible RGMRES(50) + the net, Jacobi RGMRES(50) and plain RGMRES(50) (FP32 basis,
+    Gaussian k = 100)."""
+    import torch
+    import synth
+    from paper_2011_05090_gb300 import learned
+    n = N * N
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, 100, 1)
+    cap = nfields * rhs_per_field * cycles
+    inputs = torch.zeros(cap, 2, N, N, device="cuda")
+    stencils = torch.zeros(nfields, 5, N, N, device="cuda")
+    field_of = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    w = 0
+    for f in range(nfields):
+        csr, lk = synth.diffusion_2d(N, 1.5, ell, 1000 + f)
+        arrays, C = rgs.csr_to_device(*csr)
+        stencils[f] = learned.stencil_from_csr(*arrays, N, N)
+        g = np.random.default_rng(f)
+        for j in range(rhs_per_field):
+            corr = float(g.choice([0.0, 1.0, 2.0, 4.0, 8.0])) * N / 32
+            b = synth.gaussian_field((N, N), corr, g.integers(1 << 30)).ravel() if corr else g.standard_normal(n)
+            got = learned.harvest(h, sk, C, torch.tensor(lk, device="cuda"), torch.tensor(b, device="cuda"),
+                                  inputs, start=w, cycles=cycles, restart=50)
+            field_of[w:w + got] = f
+            w += got
+    torch.cuda.synchronize()
+    harvest_s = time.perf_counter() - t0
+    net = rgs.rgs_convnet_create(h, N, N, batch, seed=7)
+    t0 = time.perf_counter()
+    losses = learned.train(h, net, inputs[:w], steps, stencils, field_of[:w], batch=batch, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del inputs
+    res = {"none": [], "jacobi": [], "learned": []}
+    for f in range(ntest):
+        csr, lk = synth.diffusion_2d(N, 1.5, ell, 900000 + f)
+        arrays, C = rgs.csr_to_device(*csr)
+        b = torch.tensor(synth.rhs(n, 77 + f), device="cuda")
+        lkd = torch.tensor(lk, device="cuda")
+        for pc in res:
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            r = learned.solve(h, sk, C, b, x, restart=50, rtol=1e-8, max_cycles=max_cycles, precond=pc, net=net,
+                              logkappa=lkd)
+            torch.cuda.synchronize()
+            res[pc].append({"seconds": time.perf_counter() - t1, "steps": r["total_steps"],
+                            "converged": r["converged"], "rel_residual": r["rel_residual"],
+                            "fallback_cycle": r["fallback_cycle"]})
+    summary = {k: {"converged": sum(e["converged"] for e in v), "mean_steps": float(np.mean([e["steps"] for e in v])),
+                   "mean_seconds": float(np.mean([e["seconds"] for e in v])),
+                   "median_rel_residual": float(np.median([e["rel_residual"] for e in v]))} for k, v in res.items()}
+    return {"config": f"diffusion2d {N}^2 sigma=1.5 corr={ell} RGMRES(50) gaussian k=100 f32, cap {max_cycles} cycles",
+            "training": {"fields": nfields, "inputs": w, "harvest_s": harvest_s, "steps": steps, "batch": batch,
+                         "train_s": train_s, "ms_per_step": 1e3 * train_s / steps,
+                         "loss_first_50": float(np.mean(losses[:50])), "loss_last_50": float(np.mean(losses[-50:]))},
+            "held_out_fields": ntest, "summary": summary, "per_field": res}
+
+
 def run_gmres_profile(args):
     """Profiling case: the 128^3 RGMRES and/or CGS2 solve for a few cycles only (no bench line)."""
     import paper_2011_05090_gb300 as rgs
@@ -317,6 +459,9 @@ def run_ours(args):
     gm = None
     if rank == 0 and not args.no_gmres:
         gm = run_gmres_c3(rgs, h)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched_c4(rgs, h)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -334,7 +479,7 @@ def run_ours(args):
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "phases_ms": phases,
                "certificates": {"delta": last["delta"], "delta_tilde": last["delta_tilde"]},
-               "rgmres": gm,
+               "rgmres": gm, "batched": batched,
                "hbm_frac_whole_job": value / world / peak}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -353,9 +498,24 @@ def main():
     ap.add_argument("--gmres-only", default="", help="profiling cases only: 'rgmres', 'cgs2' or both")
     ap.add_argument("--gmres-cycles", type=int, default=400)
     ap.add_argument("--cols", type=int, default=0, help="profiling cases only: override m (the bench line is m=500)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--c5", type=int, default=0, metavar="N",
+                    help="only the learned-preconditioner workload on N x N grids (one JSON line)")
+    ap.add_argument("--c5-steps", type=int, default=1500)
+    ap.add_argument("--c5-fields", type=int, default=40)
+    ap.add_argument("--c5-test", type=int, default=3)
+    ap.add_argument("--c5-cycles", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.c5:
+        import paper_2011_05090_gb300 as rgs
+        from paper_2011_05090_gb300 import build as libbuild
+        libbuild.build()
+        h = rgs.rgs_create()
+        out = run_learned_c5(rgs, h, N=args.c5, ell=args.c5 / 16.0, nfields=args.c5_fields, steps=args.c5_steps,
+                             ntest=args.c5_test, max_cycles=args.c5_cycles)
+        print(json.dumps({"metric": "learned preconditioner: iterations and time to 1e-8", **out}), flush=True)
     elif args.gmres_only:
         run_gmres_profile(args)
     else:

@@ -179,16 +179,28 @@ __device__ void sketch_phase(const BatchParams& P, const BInst& I, int i, int64_
         __syncthreads();
         const int nt = (int)(r1 - c0 < (int64_t)BT ? r1 - c0 : (int64_t)BT);
         const int e = min(nt, grp * GL + GL);
-        for (int rr = grp * GL; rr < e; ++rr) {
-            const bf16* th = P.theta + (size_t)(c0 + rr) * P.ldt;
-            const float2 a0 = sv0[rr], a1 = sv1[rr];
+        // the entries of G come from L2 or HBM: load those of RU rows before using any of them
+        constexpr int RU = 8;
+        for (int rb = grp * GL; rb < e; rb += RU) {
+            float tv[RU][LPT];
 #pragma unroll
-            for (int j = 0; j < LPT; ++j) {
-                const int l = tl + j * GL;
-                if (l < k) {
-                    const float tv = __bfloat162float(th[l]);
-                    acc0[j] = df_fma(tv, a0, acc0[j]);
-                    if (MODE == 1) acc1[j] = df_fma(tv, a1, acc1[j]);
+            for (int u = 0; u < RU; ++u) {
+                const bf16* th = P.theta + (size_t)(c0 + rb + u) * P.ldt;
+#pragma unroll
+                for (int j = 0; j < LPT; ++j) {
+                    const int l = tl + j * GL;
+                    tv[u][j] = (rb + u < e && l < k) ? __bfloat162float(th[l]) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                if (rb + u < e) {
+                    const float2 a0 = sv0[rb + u], a1 = sv1[rb + u];
+#pragma unroll
+                    for (int j = 0; j < LPT; ++j) {
+                        acc0[j] = df_fma(tv[u][j], a0, acc0[j]);
+                        if (MODE == 1) acc1[j] = df_fma(tv[u][j], a1, acc1[j]);
+                    }
                 }
             }
         }
@@ -606,16 +618,15 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
         std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
         std::vector<int> team_size, team_begin, team_list;
         if (nbatch <= G) {
-            // one instance per team, team sizes proportional to the work (at least 1 CTA)
-            const double W = std::accumulate(work.begin(), work.end(), 0.0);
+            // one instance per team: every team starts with one CTA and each spare CTA goes to
+            // the team with the most work per CTA (balances the longest team's time)
             std::vector<int> ts(nbatch, 1);
-            int left = G - nbatch;
-            for (int i = 0; i < nbatch && left > 0; ++i) {
-                const int extra = std::min(left, (int)std::floor((double)G * work[i] / W) - 1);
-                if (extra > 0) {
-                    ts[i] += extra;
-                    left -= extra;
-                }
+            for (int left = G - nbatch; left > 0; --left) {
+                int best = 0;
+                for (int i = 1; i < nbatch; ++i)
+                    if (work[i] / ts[i] > work[best] / ts[best]) best = i;
+                if (work[best] / ts[best] < 8192.0 * 64.0) break;    // not worth a barrier
+                ts[best] += 1;
             }
             for (int i = 0; i < nbatch; ++i) {
                 team_begin.push_back(i);
