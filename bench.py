@@ -368,6 +368,21 @@ def run_gmres_profile(args):
           flush=True)
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's timed region (the whole job ends when it does)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -413,13 +428,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms = start.elapsed_time(stop)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(start.elapsed_time(stop), world, "cuda")
     total, upd = qr_bytes(n, m)
-    value = world * total * args.steps / (ms_max * 1e-3) / 1e9
+    value = job_rate(total * args.steps, world, ms_max) / 1e9
 
     # dominant kernel: the fused update + sketch, timed per launch on the library's stream
     upd_ms = sum(i["update_ms"] for i in infos) / len(infos)
