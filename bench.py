@@ -358,6 +358,38 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
             "held_out_fields": ntest, "summary": summary, "per_field": res}
 
 
+def run_profile_case(args):
+    """Small cases for ncu captures (no bench line): 'convnet' runs three training steps and one
+    forward pass of the network on a batch of four 256 x 256 grids; 'batched' runs 16 instances
+    (sides 32..64) of the batched solver for two fixed cycles."""
+    import torch
+    import synth
+    import paper_2011_05090_gb300 as rgs
+    from paper_2011_05090_gb300 import build as libbuild
+    from paper_2011_05090_gb300 import learned
+    libbuild.build()
+    h = rgs.rgs_create()
+    if args.profile_case == "convnet":
+        N, B = 256, 4
+        net = rgs.rgs_convnet_create(h, N, N, B, seed=1)
+        g = torch.Generator(device="cpu")
+        g.manual_seed(0)
+        x = torch.randn(B, 2, N, N, generator=g).cuda()
+        csr, _ = synth.diffusion_2d(N, 1.5, 16, 0)
+        arrays, _ = rgs.csr_to_device(*csr)
+        S = learned.stencil_from_csr(*arrays, N, N).expand(B, 5, N, N).contiguous()
+        for _ in range(3):
+            rgs.rgs_convnet_train_step(h, net, x, x[:, 0].contiguous(), lr=1e-3, stencil=S)
+        rgs.rgs_convnet_forward(h, net, x)
+    else:
+        insts = c4_instances(rgs, 16, 32, 64, 0)
+        xs = [torch.zeros(I["n"], dtype=torch.float64, device="cuda") for I in insts]
+        rgs.rgmres_solve_batched(h, [I["C"] for I in insts], [I["b"] for I in insts], xs, [I["m"] for I in insts],
+                                 [2 * I["m"] for I in insts], max_cycles=2, fixed_steps=True, qdtype=torch.float32)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case}), flush=True)
+
+
 def run_gmres_profile(args):
     """Profiling case: the 128^3 RGMRES and/or CGS2 solve for a few cycles only (no bench line)."""
     import paper_2011_05090_gb300 as rgs
@@ -510,6 +542,8 @@ def main():
     ap.add_argument("--gmres-cycles", type=int, default=400)
     ap.add_argument("--cols", type=int, default=0, help="profiling cases only: override m (the bench line is m=500)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--profile-case", choices=["convnet", "batched"], default="",
+                    help="small case for an ncu capture only (no bench line)")
     ap.add_argument("--c5", type=int, default=0, metavar="N",
                     help="only the learned-preconditioner workload on N x N grids (one JSON line)")
     ap.add_argument("--c5-steps", type=int, default=1500)
@@ -519,6 +553,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     elif args.c5:
         import paper_2011_05090_gb300 as rgs
         from paper_2011_05090_gb300 import build as libbuild

@@ -141,6 +141,27 @@ def test_qr_reduced_precision_within_emulated_oracle(h, qdtype, storage, kind):
     assert np.linalg.cond(Qg) <= 10 * np.linalg.cond(emu.Q)
 
 
+def test_c2_shaped_precision_errors_vs_fp64_oracle(h):
+    """The reduced-precision bases on a smaller copy of the 2^20 x 500 workload (same D range,
+    SRHT, k / m = 4): errors of the FP32 and BF16 storage against the FP64 oracle, as numbers."""
+    n, m, k = 1 << 16, 200, 800
+    A = synth.gdw_matrix(n, m, 1e10, 0).numpy().T.copy()
+    ref = c_oracle.rgs_qr(A, c_oracle.CSketch("srht", n, k, 0))
+    Qref = ref.Qp * ref.sigma[None, :]
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 0)
+    out = {}
+    for name, qd in (("f64", torch.float64), ("f32", torch.float32), ("bf16", torch.bfloat16)):
+        g = run_qr(h, sk, to_gpu(A), qdtype=qd, qscale=True)
+        Qg = g["Q"] * g["qscale"][None, :]
+        out[name] = (rel(g["R"], ref.R), rel(A, Qg @ g["R"]), np.linalg.cond(Qg), g["info"]["delta"])
+        print(f"{name}: ||R-R_or||/||R_or|| {out[name][0]:.3e}  ||A-QR||/||A|| {out[name][1]:.3e}  "
+              f"cond(Q) {out[name][2]:.3f}  Delta_m {out[name][3]:.3e}")
+    print(f"oracle FP64: ||A-QR||/||A|| {rel(A, Qref @ ref.R):.3e}  cond(Q) {np.linalg.cond(Qref):.3f}")
+    assert out["f64"][0] <= 1e-11 and out["f64"][1] <= 1e-13
+    assert out["f32"][1] <= 1e-6 and out["f32"][2] <= 10
+    assert out["bf16"][1] <= 1e-2 and out["bf16"][2] <= 100
+
+
 # ------------------------------------------------------------------ status, modes, edge cases
 def test_breakdown_reported_with_column(h):
     n, m, k = 2000, 6, 30
