@@ -7,7 +7,8 @@
 //    (channel strides padded so fragment loads are bank-conflict free).  The same kernel computes
 //    the backward pass for the activations: the gradient of a layer's input is the convolution of
 //    the output gradient with the taps flipped and c_in / c_out swapped, masked by ReLU'.
-//  - dweight_kernel: weight and bias gradients (sums over all pixels of the batch) in FP32.
+//  - dweight_mma_kernel: weight and bias gradients (sums over all pixels of the batch) as
+//    GEMMs over the pixels on the tensor cores, FP32 accumulation.
 //  - loss / Adam / packing kernels.
 // Activations are BF16 in NHWC layout; FP32 master parameters are repacked into BF16 after
 // every update.
@@ -148,74 +149,120 @@ __global__ void __launch_bounds__(128) conv3x3_mma_kernel(ConvArgs a) {
     }
 }
 
-// Weight and bias gradients of one layer: dW[co][ci][tap] = sum over pixels of
-// dA[p][co] h[p + off(tap)][ci], db[co] = sum dA[p][co].  Per-CTA partial sums (fixed order)
-// over a grid-stride range of pixel tiles; part has NOUT = COUT*CIN*9 + COUT floats per CTA.
-template <int CSH, int CIN, int CSD, int COUT>
-__global__ void __launch_bounds__(256) dweight_kernel(const bf16* __restrict__ h, const bf16* __restrict__ dA,
-                                                      int B, int H, int W, float* __restrict__ part) {
-    constexpr int NW_ = COUT * CIN * 9;
-    constexpr int NOUT = NW_ + COUT;
-    constexpr int PER = (NOUT + 255) / 256;
-    __shared__ float sh[(TH + 2) * (TW + 2) * CIN];
-    __shared__ float sd[TH * TW * COUT];
-    float acc[PER];
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const bf16* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// Weight and bias gradients on the tensor cores: for tap t,
+// dW_t[co][ci] = sum_p dA[p][co] h[p + off(t)][ci] is a GEMM with the pixels as the reduction
+// dimension.  One warp per tap (9 warps); a CTA stages an 8 x 16 pixel tile of dA and the
+// halo of h (channel strides padded by 8 elements: conflict-free 8 x 8 ldmatrix rows), reads
+// both transposed with ldmatrix.trans (pixels become the k index of the fragments) and
+// accumulates (CO_S / 16) x (CI_S / 8) m16n8 tiles per warp in FP32 over its grid-stride
+// tiles.  CI_S / CO_S are the stored channel counts (16 or 32); only the layer's CIN x COUT
+// entries are written.  Each CTA writes its partial sums; reduce_grad_kernel adds them.
+constexpr int DWM_THREADS = 288;
+template <int CI_S, int CO_S, int CIN, int COUT>
+__global__ void __launch_bounds__(DWM_THREADS) dweight_mma_kernel(const bf16* __restrict__ h,
+                                                                  const bf16* __restrict__ dA, int B, int H, int W,
+                                                                  float* __restrict__ part) {
+    constexpr int HSI = CI_S + 8, HSO = CO_S + 8, MT = CO_S / 16, NT = CI_S / 8;
+    constexpr int NOUT = COUT * CIN * 9 + COUT;
+    __shared__ __align__(16) bf16 sh[(TH + 2) * (TW + 2) * HSI];
+    __shared__ __align__(16) bf16 sd[TH * TW * HSO];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tap = warp, dy = tap / 3, dx = tap % 3;
+    const int i8 = lane & 7, mat = lane >> 3;
+    float acc[MT][NT][4];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) acc[j] = 0.f;
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[a][b][e] = 0.f;
+    float bacc = 0.f;
     const int tilesx = W / TW, tilesy = H / TH;
     const int ntiles = B * tilesx * tilesy;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int b = tile / (tilesx * tilesy), r = tile % (tilesx * tilesy);
         const int y0 = (r / tilesx) * TH, x0 = (r % tilesx) * TW;
         __syncthreads();
-        for (int c = threadIdx.x; c < (TH + 2) * (TW + 2) * CIN; c += 256) {
-            const int pix = c / CIN, ci = c % CIN;
+        for (int c = tid; c < (TH + 2) * (TW + 2) * (CI_S / 8); c += DWM_THREADS) {
+            const int pix = c / (CI_S / 8), ch = (c % (CI_S / 8)) * 8;
             const int gy = y0 - 1 + pix / (TW + 2), gx = x0 - 1 + pix % (TW + 2);
-            float v = 0.f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = __bfloat162float(h[(((size_t)b * H + gy) * W + gx) * CSH + ci]);
-            sh[c] = v;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                v = *reinterpret_cast<const uint4*>(h + (((size_t)b * H + gy) * W + gx) * CI_S + ch);
+            *reinterpret_cast<uint4*>(sh + pix * HSI + ch) = v;
         }
-        for (int c = threadIdx.x; c < TH * TW * COUT; c += 256) {
-            const int pix = c / COUT, co = c % COUT;
+        for (int c = tid; c < TH * TW * (CO_S / 8); c += DWM_THREADS) {
+            const int pix = c / (CO_S / 8), ch = (c % (CO_S / 8)) * 8;
             const int gy = y0 + pix / TW, gx = x0 + pix % TW;
-            sd[c] = __bfloat162float(dA[(((size_t)b * H + gy) * W + gx) * CSD + co]);
+            *reinterpret_cast<uint4*>(sd + pix * HSO + ch) =
+                *reinterpret_cast<const uint4*>(dA + (((size_t)b * H + gy) * W + gx) * CO_S + ch);
         }
         __syncthreads();
+        if (tid < COUT)
+            for (int p = 0; p < TH * TW; ++p) bacc += __bfloat162float(sd[p * HSO + tid]);
+#pragma unroll 2
+        for (int ks = 0; ks < TH; ++ks) {               // k step = one pixel row of the tile (16 pixels)
+            uint32_t a[MT][4];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int o = threadIdx.x + 256 * j;
-            if (o < NW_) {
-                const int co = o / (CIN * 9), rem = o % (CIN * 9), ci = rem / 9, tap = rem % 9;
-                const int dy = tap / 3, dx = tap % 3;
-                float s = 0.f;
-                for (int py = 0; py < TH; ++py)
-#pragma unroll 4
-                    for (int px = 0; px < TW; ++px)
-                        s = fmaf(sd[(py * TW + px) * COUT + co], sh[((py + dy) * (TW + 2) + px + dx) * CIN + ci], s);
-                acc[j] += s;
-            } else if (o < NOUT) {
-                const int co = o - NW_;
-                float s = 0.f;
-                for (int p = 0; p < TH * TW; ++p) s += sd[p * COUT + co];
-                acc[j] += s;
+            for (int mt = 0; mt < MT; ++mt)
+                ldsm_x4_trans(a[mt], sd + (ks * TW + i8 + ((mat >> 1) ? 8 : 0)) * HSO + mt * 16 + ((mat & 1) ? 8 : 0));
+            uint32_t bf[NT][2];
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                uint32_t q[4];
+                const int hpos = (ks + dy) * (TW + 2) + i8 + ((mat & 1) ? 8 : 0) + dx;
+                ldsm_x4_trans(q, sh + hpos * HSI + np * 16 + ((mat >> 1) ? 8 : 0));
+                bf[2 * np][0] = q[0];
+                bf[2 * np][1] = q[1];
+                bf[2 * np + 1][0] = q[2];
+                bf[2 * np + 1][1] = q[3];
             }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a[mt], bf[nt][0], bf[nt][1]);
         }
     }
+    float* out = part + (size_t)blockIdx.x * NOUT;
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int o = threadIdx.x + 256 * j;
-        if (o < NOUT) part[(size_t)blockIdx.x * NOUT + o] = acc[j];
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = mt * 16 + g + (e >= 2 ? 8 : 0), ci = nt * 8 + 2 * t + (e & 1);
+                if (co < COUT && ci < CIN) out[co * (CIN * 9) + ci * 9 + tap] = acc[mt][nt][e];
+            }
+    if (tid < COUT) out[COUT * CIN * 9 + tid] = bacc;
+}
+
+// grad[o] = sum over CTAs of part[cta][o], summed in a fixed order: a CTA takes 32 consecutive
+// outputs (one per lane); warp w adds the partials w, w + 8, ... and the 8 warp sums are added
+// in warp order.
+__global__ void reduce_grad_kernel(const float* __restrict__ part, int nparts, int nout, float* __restrict__ grad) {
+    __shared__ double ws[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (o < nout)
+        for (int c = warp; c < nparts; c += 8) s += part[(size_t)c * nout + o];
+    ws[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && o < nout) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += ws[w][lane];
+        grad[o] = (float)t;
     }
 }
 
-// grad[off + o] = sum over CTAs of part[cta][o] (fixed order)
-__global__ void reduce_grad_kernel(const float* __restrict__ part, int nparts, int nout, float* __restrict__ grad) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= nout) return;
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(size_t)c * nout + o];
-    grad[o] = (float)s;
-}
 
 // in: batch x 2 x H x W FP32 (NCHW) -> NHWC BF16 with 16 channels (2 used)
 __global__ void pack_input_kernel(const float* __restrict__ in, int B, int HW, bf16* __restrict__ x0) {
@@ -489,10 +536,11 @@ void launch_dweight(rgs_convnet_obj* net, int l, const bf16* hprev, const bf16* 
     rgs_context* h = net->h;
     const int grid = dweight_grid(h);
     const int nout = COUT * CIN * 9 + COUT;
-    dweight_kernel<CSH, CIN, CSD, COUT><<<grid, 256, 0, h->stream>>>(hprev, dA, B, net->H, net->W, net->part.as<float>());
+    dweight_mma_kernel<CSH, CSD, CIN, COUT><<<grid, DWM_THREADS, 0, h->stream>>>(hprev, dA, B, net->H, net->W,
+                                                                                  net->part.as<float>());
     RGS_CUDA(cudaGetLastError());
-    reduce_grad_kernel<<<(nout + 255) / 256, 256, 0, h->stream>>>(net->part.as<float>(), grid, nout,
-                                                                  net->grad.as<float>() + param_offset(l));
+    reduce_grad_kernel<<<(nout + 31) / 32, 256, 0, h->stream>>>(net->part.as<float>(), grid, nout,
+                                                                net->grad.as<float>() + param_offset(l));
     RGS_CUDA(cudaGetLastError());
     h->launches += 2;
 }
