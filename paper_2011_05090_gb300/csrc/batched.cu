@@ -44,6 +44,7 @@ constexpr int MB_MAX = 127;              // restart length of one instance
 constexpr int GROUPS = 4;                // row groups of the sketch accumulation
 constexpr int GL = BT / GROUPS;          // threads per group; a thread owns sketch rows tl + GL j
 constexpr int LPT = KB_MAX / GL;         // sketch rows per thread
+constexpr int RR = 4;                    // rows per thread in the streaming phases
 
 // Device-side description of one instance and its workspace.
 struct BInst {
@@ -84,8 +85,9 @@ struct BatchParams {
     const int* team_size;
     const int* team_begin;   // team t solves team_list[team_begin[t] .. team_begin[t+1])
     const int* team_list;
-    const bf16* theta;       // shared G, column-major, ld ldt
-    int ldt;
+    const bf16* theta;       // shared G, column pairs interleaved: (l, c) at (c >> 1) * 2 ldt + 2 l + (c & 1)
+    int ldt;                 // rows of G (k_max)
+    int64_t nt;              // columns of G (n_max rounded up to even)
     int* ctl;                // [kStatusWord] first error, [kAbortWord] abort
 };
 
@@ -144,6 +146,7 @@ __device__ __forceinline__ double cta_sum(double v, double* red) { return block_
 struct SketchSmem {
     float2 sv0[BT], sv1[BT];                 // double-float split of the tile's vectors
     df red0[GROUPS][KB_MAX], red1[GROUPS][KB_MAX];
+    __align__(16) bf16 pc[8][RR * BT + 8];   // tensor-core path: bf16 pieces of the two vectors
 };
 
 template <typename TQ, int MODE>
@@ -185,11 +188,12 @@ __device__ void sketch_phase(const BatchParams& P, const BInst& I, int i, int64_
             float tv[RU][LPT];
 #pragma unroll
             for (int u = 0; u < RU; ++u) {
-                const bf16* th = P.theta + (size_t)(c0 + rb + u) * P.ldt;
+                const int64_t cc = c0 + rb + u;
+                const bf16* th = P.theta + (size_t)(cc >> 1) * 2 * P.ldt + (cc & 1);
 #pragma unroll
                 for (int j = 0; j < LPT; ++j) {
                     const int l = tl + j * GL;
-                    tv[u][j] = (rb + u < e && l < k) ? __bfloat162float(th[l]) : 0.f;
+                    tv[u][j] = (rb + u < e && l < k) ? __bfloat162float(th[2 * l]) : 0.f;
                 }
             }
 #pragma unroll
@@ -225,6 +229,148 @@ __device__ void sketch_phase(const BatchParams& P, const BInst& I, int i, int64_
         out[l] = (double)s0.h + (double)s0.l;
         if (MODE == 1) out[k + l] = (double)s1.h + (double)s1.l;
     }
+}
+
+__device__ __forceinline__ void mma_a02(float (&d)[4], uint32_t a0, uint32_t a2, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(0u), "r"(a2), "r"(0u), "r"(b0), "r"(b1));
+}
+
+// v = p0 + p1 + p2 with bfloat16 pieces (exact for an FP32 value, 24 significant bits otherwise)
+__device__ __forceinline__ void split3(double v, bf16& p0, bf16& p1, bf16& p2) {
+    p0 = __float2bfloat16_rn((float)v);
+    const double r1 = v - (double)__bfloat162float(p0);
+    p1 = __float2bfloat16_rn((float)r1);
+    const double r2 = r1 - (double)__bfloat162float(p1);
+    p2 = __float2bfloat16_rn((float)r2);
+}
+
+// The same partial sketches as sketch_phase, for FP32 bases on the tensor cores.  Each vector
+// is split into three bfloat16 pieces (exact for FP32 values), so the 16 x 16 A operand of
+// mma.m16n8k16 holds 6 piece rows (vector 0: rows 0-2, vector 1: rows 3-5) over 16 grid rows,
+// and the B operand is a 16 x 8 block of G (grid rows x sketch rows), one 32-bit word per
+// column pair of the interleaved layout.  Products are exact; the FP32 accumulator is flushed
+// into double-float sums every 64 grid rows; the pieces are added at the end.
+template <int MODE>
+__device__ void sketch_phase_tc(const BatchParams& P, const BInst& I, int i, int64_t r0, int64_t r1, int rank,
+                                SketchSmem& S) {
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
+    const int k = I.k, ntiles = (k + 7) / 8;
+    const float* qcol = static_cast<const float*>(I.Q) + (size_t)i * I.ldq;
+    const uint32_t* G = reinterpret_cast<const uint32_t*>(P.theta);
+    const int64_t npairs = P.nt / 2;
+    constexpr int NJ = KB_MAX / 8 / (BT / 32);          // n-tiles per warp
+    df sums[NJ][2];
+    float acc[NJ][4];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        sums[j][0] = sums[j][1] = {0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    }
+    for (int64_t c0 = r0; c0 < r1; c0 += RR * BT) {
+        double v0[RR], v1[RR];
+        int64_t cr[RR];
+        int p0[RR], p1[RR];
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            cr[q] = c0 + q * BT + t;
+            v0[q] = v1[q] = 0.0;
+            p0[q] = p1[q] = 0;
+            if (cr[q] < r1) {
+                if (MODE == 0) {
+                    v0[q] = I.b[cr[q]];
+                } else {
+                    v0[q] = (double)__ldcg(qcol + cr[q]);
+                    if (MODE == 1) {
+                        p0[q] = I.rowptr[cr[q]];
+                        p1[q] = I.rowptr[cr[q] + 1];
+                    }
+                }
+            }
+        }
+        if (MODE == 1) {
+            // w = A q'_i for the RR rows at once (independent loads), entries in CSR order
+            int len = 0;
+#pragma unroll
+            for (int q = 0; q < RR; ++q) len = max(len, p1[q] - p0[q]);
+            for (int e = 0; e < len; ++e)
+#pragma unroll
+                for (int q = 0; q < RR; ++q)
+                    if (p0[q] + e < p1[q])
+                        v1[q] = fma(I.val[p0[q] + e], (double)__ldcg(qcol + I.colind[p0[q] + e]), v1[q]);
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+                if (cr[q] < r1) I.w[cr[q]] = v1[q];
+        }
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            split3(v0[q], S.pc[0][q * BT + t], S.pc[1][q * BT + t], S.pc[2][q * BT + t]);
+            split3(v1[q], S.pc[3][q * BT + t], S.pc[4][q * BT + t], S.pc[5][q * BT + t]);
+        }
+        __syncthreads();
+        const int nvalid = (int)(r1 - c0 < (int64_t)(RR * BT) ? r1 - c0 : (int64_t)(RR * BT));
+        const int nks = (nvalid + 15) / 16;
+        for (int k4 = 0; k4 < nks; k4 += 4) {
+            uint32_t bw[4][NJ][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t cp = (c0 + (int64_t)(k4 + u) * 16) / 2 + tq;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    const int l = (warp + 8 * j) * 8 + g;
+                    const bool ok = k4 + u < nks && warp + 8 * j < ntiles && l < P.ldt;
+                    bw[u][j][0] = (ok && cp < npairs) ? __ldg(G + (size_t)cp * P.ldt + l) : 0u;
+                    bw[u][j][1] = (ok && cp + 4 < npairs) ? __ldg(G + (size_t)(cp + 4) * P.ldt + l) : 0u;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k4 + u < nks) {
+                    const int kk = (k4 + u) * 16 + 2 * tq;
+                    const uint32_t a0 = g < 6 ? *reinterpret_cast<const uint32_t*>(&S.pc[g][kk]) : 0u;
+                    const uint32_t a2 = g < 6 ? *reinterpret_cast<const uint32_t*>(&S.pc[g][kk + 8]) : 0u;
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j)
+                        if (warp + 8 * j < ntiles) mma_a02(acc[j], a0, a2, bw[u][j][0], bw[u][j][1]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                sums[j][0] = df_add(sums[j][0], {acc[j][0], 0.f});
+                sums[j][1] = df_add(sums[j][1], {acc[j][1], 0.f});
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+    // add the three pieces of each vector: lanes 4g + tq with g = 0, 1, 2 (vector 0) and 3, 4, 5 (vector 1)
+    double* out = I.part + (size_t)rank * 2 * k;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            df v = sums[j][e];
+            const df v1 = {__shfl_down_sync(0xffffffffu, v.h, 4), __shfl_down_sync(0xffffffffu, v.l, 4)};
+            const df v2 = {__shfl_down_sync(0xffffffffu, v.h, 8), __shfl_down_sync(0xffffffffu, v.l, 8)};
+            v = df_add(df_add(v, v1), v2);
+            const int l = (warp + 8 * j) * 8 + 2 * tq + e;
+            if (warp + 8 * j < ntiles && l < k) {
+                if (g == 0) out[l] = (double)v.h + (double)v.l;
+                if (MODE == 1 && g == 3) out[k + l] = (double)v.h + (double)v.l;
+            }
+        }
+}
+
+template <typename TQ, int MODE>
+__device__ __forceinline__ void sketch_any(const BatchParams& P, const BInst& I, int i, int64_t r0, int64_t r1,
+                                           int rank, SketchSmem& S) {
+    if constexpr (sizeof(TQ) == 4) sketch_phase_tc<MODE>(P, I, i, r0, r1, rank, S);
+    else sketch_phase<TQ, MODE>(P, I, i, r0, r1, rank, S);
 }
 
 // The first CTA: sum of the team's partial vectors into dst (length len, offset off).
@@ -325,10 +471,14 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
         for (int q = t; q < i; q += BT) RSc[q] = h1[q] + h2[q];
         if (t == 0) RSc[i] = rho;
         __syncthreads();
-        for (int q = t; q < i; q += BT) {
-            double s = 0.0;
-            for (int j = q; j < i; ++j) s = fma(I.RSi[(size_t)j * ld + q], RSc[j], s);
-            RIc[q] = -s / rho;
+        {   // one warp per entry, lanes along the row
+            const int warp = t >> 5, lane = t & 31;
+            for (int q = warp; q < i; q += BT / 32) {
+                double s = 0.0;
+                for (int j = q + lane; j < i; j += 32) s = fma(I.RSi[(size_t)j * ld + q], RSc[j], s);
+                s = warp_sum(s);
+                if (lane == 0) RIc[q] = -s / rho;
+            }
         }
         if (t == 0) RIc[i] = 1.0 / rho;
         __syncthreads();
@@ -340,11 +490,17 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
         const double pnn = sqrt(cta_sum(a, red));
         cta_dots(I.U, k, i + 1, pp, h1);
         double* Rn = I.R + (size_t)(i + 1) * (m + 2);
-        for (int q = t; q <= i; q += BT) {
-            double s = 0.0;
-            for (int j = q; j <= i; ++j) s = fma(I.RSi[(size_t)j * ld + q], h1[j], s);
-            Rn[q] = s;
-            I.coef[q] = s * I.sigma[q];
+        {
+            const int warp = t >> 5, lane = t & 31;
+            for (int q = warp; q <= i; q += BT / 32) {
+                double s = 0.0;
+                for (int j = q + lane; j <= i; j += 32) s = fma(I.RSi[(size_t)j * ld + q], h1[j], s);
+                s = warp_sum(s);
+                if (lane == 0) {
+                    Rn[q] = s;
+                    I.coef[q] = s * I.sigma[q];
+                }
+            }
         }
         if (t == 0) I.scal[3] = pnn;
     }
@@ -371,6 +527,117 @@ __device__ void hess_solve_warp(const BInst& I, int j, double* gs) {
     }
 }
 
+// q'_i = sg w - Q'_{0:i} cy over rows [r0, r1): RR rows per thread, the loads of 8 columns
+// issued before their products; each row's FMA chain runs over j = 0 .. i-1 in order.
+template <typename TQ>
+__device__ void update_rows(TQ* Q, int64_t ldq, const double* w, double sg, const double* cy, int i, int64_t r0,
+                            int64_t r1) {
+    using A = TQ;
+    for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)BT * RR) {
+        A acc[RR];
+        int64_t c[RR];
+        bool ok[RR];
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            c[q] = base + (int64_t)q * BT;
+            ok[q] = c[q] < r1;
+            if constexpr (sizeof(TQ) == 4) acc[q] = ok[q] ? __double2float_rn(sg * w[c[q]]) : 0.f;
+            else acc[q] = ok[q] ? sg * w[c[q]] : 0.0;
+        }
+        int j = 0;
+        for (; j + 8 <= i; j += 8) {
+            A v[RR][8];
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[q][u] = ok[q] ? Q[c[q] + (size_t)(j + u) * ldq] : (A)0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < RR; ++q) acc[q] = fma(-(A)cy[j + u], v[q][u], acc[q]);
+        }
+        for (; j < i; ++j)
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+                if (ok[q]) acc[q] = fma(-(A)cy[j], Q[c[q] + (size_t)j * ldq], acc[q]);
+#pragma unroll
+        for (int q = 0; q < RR; ++q)
+            if (ok[q]) Q[c[q] + (size_t)i * ldq] = acc[q];
+    }
+}
+
+// x += Q'_{0:steps} cy (FP64 sums, columns in order), RR rows per thread
+template <typename TQ>
+__device__ void solution_rows(const TQ* Q, int64_t ld, const double* cy, int steps, double* x, int64_t r0,
+                              int64_t r1) {
+    for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)BT * RR) {
+        double acc[RR];
+        int64_t c[RR];
+        bool ok[RR];
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            c[q] = base + (int64_t)q * BT;
+            ok[q] = c[q] < r1;
+            acc[q] = 0.0;
+        }
+        int j = 0;
+        for (; j + 8 <= steps; j += 8) {
+            double v[RR][8];
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[q][u] = ok[q] ? ldq(Q + c[q] + (size_t)(j + u) * ld) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int q = 0; q < RR; ++q) acc[q] = fma(v[q][u], cy[j + u], acc[q]);
+        }
+        for (; j < steps; ++j)
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+                if (ok[q]) acc[q] = fma(ldq(Q + c[q] + (size_t)j * ld), cy[j], acc[q]);
+#pragma unroll
+        for (int q = 0; q < RR; ++q)
+            if (ok[q]) x[c[q]] += acc[q];
+    }
+}
+
+// r = b - A x over rows [r0, r1), stored as q'_0 (TQ); returns the thread's sum of r^2
+template <typename TQ>
+__device__ double residual_rows(const BInst& I, TQ* Q, int64_t r0, int64_t r1) {
+    double a = 0.0;
+    for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)BT * RR) {
+        double s[RR];
+        int64_t c[RR];
+        int p0[RR], p1[RR];
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            c[q] = base + (int64_t)q * BT;
+            s[q] = 0.0;
+            p0[q] = p1[q] = 0;
+            if (c[q] < r1) {
+                s[q] = I.b[c[q]];
+                p0[q] = I.rowptr[c[q]];
+                p1[q] = I.rowptr[c[q] + 1];
+            }
+        }
+        int len = 0;
+#pragma unroll
+        for (int q = 0; q < RR; ++q) len = max(len, p1[q] - p0[q]);
+        for (int e = 0; e < len; ++e)
+#pragma unroll
+            for (int q = 0; q < RR; ++q)
+                if (p0[q] + e < p1[q]) s[q] = fma(-I.val[p0[q] + e], __ldcg(I.x + I.colind[p0[q] + e]), s[q]);
+#pragma unroll
+        for (int q = 0; q < RR; ++q)
+            if (c[q] < r1) {
+                Q[c[q]] = to_q<TQ>(s[q]);
+                a = fma(s[q], s[q], a);
+            }
+    }
+    return a;
+}
+
 template <typename TQ>
 __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T) {
     __shared__ double red[BT / 32 + 1];
@@ -389,7 +656,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
         double a = 0.0;
         for (int64_t c = r0 + t; c < r1; c += BT) a = fma(I.b[c], I.b[c], a);
         a = cta_sum(a, red);
-        sketch_phase<TQ, 0>(P, I, 0, r0, r1, rank, sks);
+        sketch_any<TQ, 0>(P, I, 0, r0, r1, rank, sks);
         if (t == 0) I.part[(size_t)rank * 2 * k + k] = a;
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
         if (leader) {
@@ -413,13 +680,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
     }
     for (int cycle = 0;; ++cycle) {
         // R: r = b - A x, q'_0 = r, ||r||^2
-        double a = 0.0;
-        for (int64_t c = r0 + t; c < r1; c += BT) {
-            double s = I.b[c];
-            for (int q = I.rowptr[c]; q < I.rowptr[c + 1]; ++q) s = fma(-I.val[q], __ldcg(I.x + I.colind[q]), s);
-            Q[c] = to_q<TQ>(s);
-            a = fma(s, s, a);
-        }
+        double a = residual_rows<TQ>(I, Q, r0, r1);
         a = cta_sum(a, red);
         if (t == 0) I.part[(size_t)rank * 2 * k + k] = a;
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
@@ -459,22 +720,12 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
                 const double sg = __ldcg(I.sigma + i - 1);
                 for (int j = t; j < i; j += BT) cy[j] = __ldcg(I.coef + j);
                 __syncthreads();
-                for (int64_t c = r0 + t; c < r1; c += BT) {
-                    if constexpr (sizeof(TQ) == 4) {
-                        float acc = __double2float_rn(sg * I.w[c]);
-                        for (int j = 0; j < i; ++j) acc = fmaf(-(float)cy[j], Q[c + (size_t)j * I.ldq], acc);
-                        Q[c + (size_t)i * I.ldq] = acc;
-                    } else {
-                        double acc = sg * I.w[c];
-                        for (int j = 0; j < i; ++j) acc = fma(-cy[j], Q[c + (size_t)j * I.ldq], acc);
-                        Q[c + (size_t)i * I.ldq] = acc;
-                    }
-                }
+                update_rows<TQ>(Q, I.ldq, I.w, sg, cy, i, r0, r1);
                 if (!team_barrier(I.bar, T, rank, ctl)) return false;
             }
             // S: w = A q'_i with the sketches of q'_i and w
-            if (i < m) sketch_phase<TQ, 1>(P, I, i, r0, r1, rank, sks);
-            else sketch_phase<TQ, 2>(P, I, i, r0, r1, rank, sks);
+            if (i < m) sketch_any<TQ, 1>(P, I, i, r0, r1, rank, sks);
+            else sketch_any<TQ, 2>(P, I, i, r0, r1, rank, sks);
             if (!team_barrier(I.bar, T, rank, ctl)) return false;
             if (leader) {
                 reduce_parts(I, T, 0, k, ss);
@@ -508,11 +759,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
         for (int j = t; j < steps; j += BT) cy[j] = __ldcg(I.y + j);
         __syncthreads();
-        for (int64_t c = r0 + t; c < r1; c += BT) {
-            double s = 0.0;
-            for (int j = 0; j < steps; ++j) s = fma(ldq(Q + c + (size_t)j * I.ldq), cy[j], s);
-            I.x[c] += s;
-        }
+        solution_rows<TQ>(Q, I.ldq, cy, steps, I.x, r0, r1);
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
     }
     return true;
@@ -528,8 +775,10 @@ __global__ void __launch_bounds__(BT) rgmres_batched_kernel(BatchParams P) {
     }
 }
 
-// Shared Gaussian G (k x n, ld k): entry (l, c) from counter (c, l >> 1, 0, 0), Box-Muller,
-// rounded to bfloat16 (the single-instance Gaussian sketch before its 1/sqrt(k) scale).
+// Shared Gaussian G (k x n): entry (l, c) from counter (c, l >> 1, 0, 0), Box-Muller, rounded to
+// bfloat16 (the single-instance Gaussian sketch before its 1/sqrt(k) scale).  Columns are stored
+// in interleaved pairs, (l, c) at (c >> 1) * 2k + 2l + (c & 1), so that (l, c) and (l, c + 1)
+// form one 32-bit word: the k-pair of a tensor-core fragment.
 __global__ void batched_theta_kernel(bf16* G, int k, int64_t n, uint32_t key0, uint32_t key1) {
     const int pairs = (k + 1) / 2;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -542,8 +791,9 @@ __global__ void batched_theta_kernel(bf16* G, int k, int64_t n, uint32_t key0, u
     const double rad = sqrt(-2.0 * log(u1));
     double sn, cs;
     sincos(2.0 * M_PI * u2, &sn, &cs);
-    G[c * k + 2 * pr] = __float2bfloat16_rn(__double2float_rn(rad * cs));
-    if (2 * pr + 1 < k) G[c * k + 2 * pr + 1] = __float2bfloat16_rn(__double2float_rn(rad * sn));
+    bf16* col = G + (size_t)(c >> 1) * 2 * k + (c & 1);
+    col[2 * (2 * pr)] = __float2bfloat16_rn(__double2float_rn(rad * cs));
+    if (2 * pr + 1 < k) col[2 * (2 * pr + 1)] = __float2bfloat16_rn(__double2float_rn(rad * sn));
 }
 
 template <class F>
@@ -593,16 +843,18 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
         }
         // shared G (cached on the handle)
         rgs_context* ctx = h;
-        const size_t gbytes = sizeof(bf16) * (size_t)kmax * nmax;
-        if (ctx->batch_theta_seed != sketch_seed || ctx->batch_theta_k != kmax || ctx->batch_theta_n < nmax) {
+        const int64_t ncols = (nmax + 1) & ~(int64_t)1;
+        const size_t gbytes = sizeof(bf16) * (size_t)kmax * ncols;
+        if (ctx->batch_theta_seed != sketch_seed || ctx->batch_theta_k != kmax || ctx->batch_theta_n < ncols) {
             ctx->batch_theta.ensure(gbytes);
+            RGS_CUDA(cudaMemsetAsync(ctx->batch_theta.ptr, 0, gbytes, ctx->stream));
             const int64_t tot = (int64_t)((kmax + 1) / 2) * nmax;
             batched_theta_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
                 ctx->batch_theta.as<bf16>(), kmax, nmax, (uint32_t)sketch_seed, (uint32_t)(sketch_seed >> 32));
             RGS_CUDA(cudaGetLastError());
             ctx->batch_theta_seed = sketch_seed;
             ctx->batch_theta_k = kmax;
-            ctx->batch_theta_n = nmax;
+            ctx->batch_theta_n = ncols;
         }
         // grid and teams: every CTA resident (cooperative launch)
         auto kern = qtype == RGS_F64 ? rgmres_batched_kernel<double> : rgmres_batched_kernel<float>;
@@ -761,6 +1013,7 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
         P.team_list = d_tab + o_list;
         P.theta = ctx->batch_theta.as<bf16>();
         P.ldt = kmax;
+        P.nt = ctx->batch_theta_n;
         P.ctl = ctx->ctl.as<int>();
         void* args[] = {&P};
         // one persistent launch, issued through a CUDA graph: captured on the handle's private
