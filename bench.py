@@ -55,8 +55,12 @@ WORKLOAD = "rgs_qr n=1048576 m=500 cond=1e10 srht k=2000 q=f32"
 
 
 def qr_bytes(n, m, esz=4, wbytes=8):
-    upd = sum(esz * n * i + wbytes * n + esz * n for i in range(m))
-    return wbytes * n * m + upd, upd
+    """(total, update-pass) algorithmic bytes of one factorization.  Total: 8 n m (step 1 reads W)
+    + sum_i 4 n (i + 3) (steps 3-4 read Q'_{i-1} and w_i, write q'_i).  With the SRHT the update
+    pass of column i also reads w_{i+1} for its step-1 sketch, so the update launches carry
+    8 n (m - 1) of the step-1 bytes and one separate sketch reads w_1."""
+    steps34 = sum(esz * n * i + wbytes * n + esz * n for i in range(m))
+    return wbytes * n * m + steps34, steps34 + wbytes * n * (m - 1)
 
 
 def peaks():

@@ -294,7 +294,9 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         double* certw = P + (size_t)k * m;
         double* certo = certw + 3 * (size_t)m;
         const int np1 = rgs_update_nparts(h, s, n, 1);
-        h->partials.ensure(sizeof(double) * (size_t)np1 * k);
+        // SRHT: step 1 of column i + 1 is sketched in the same pass as steps 3-4 of column i
+        const bool fused_p = s->kind == RGS_SKETCH_SRHT;
+        h->partials.ensure(sizeof(double) * (size_t)np1 * k * (fused_p ? 2 : 1));
 
         PhaseTimer timer(h, (flags & RGS_QR_TIMINGS) != 0);
         // RGS_TRACE=1 in the environment: per-phase device timestamps of the least-squares kernel
@@ -305,12 +307,13 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         rgs_ls_reset(h, ls);
         RGS_CUDA(cudaMemset2DAsync(dR, sizeof(double) * dldr, 0, sizeof(double) * m, m, st));
 
-        // step 1 for all columns at once: P = Theta W (one pass over W)
+        // step 1: P = Theta W in one pass over W (Gaussian), or only p_1 (SRHT; the other
+        // columns are sketched inside the update passes)
         timer.start(0);
         const bool df = qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH);
-        sketch_block(h, s, m, dW, dldw, P, k, df);
+        sketch_block(h, s, fused_p ? 1 : m, dW, dldw, P, k, df);
         timer.stop(0);
-        h->partials.ensure(sizeof(double) * (size_t)np1 * k);
+        h->partials.ensure(sizeof(double) * (size_t)np1 * k * (fused_p ? 2 : 1));
 
         const double s_scale = s->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)k) : 1.0;
         for (int i = 0; i < m; ++i) {
@@ -326,6 +329,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             L.coef = ls.coef;
             L.qout = static_cast<char*>(dQ) + esz * (size_t)i * dldq;
             L.df_sketch = df ? 1 : 0;
+            L.w_next = (fused_p && i + 1 < m) ? dW + (int64_t)(i + 1) * dldw : nullptr;
             int nparts = 0;
             timer.start(1);
             rgs_launch_update_sketch(h, s, L, h->partials.as<double>(), &nparts, ls.ctl);   // steps 3, 4
@@ -339,8 +343,16 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             a.s_df = (df && s->kind == RGS_SKETCH_SRHT) ? 1 : 0;
             a.solve = (i + 1 < m) ? 1 : 0;                     // step 2 of the next column
             a.xcol = i + 1;
-            a.p_vec = P + (size_t)(i + 1) * k;
-            a.p_scale = 1.0;
+            if (fused_p) {
+                a.p_part = h->partials.as<double>() + (size_t)nparts * k;
+                a.p_nparts = nparts;
+                a.p_df = a.s_df;
+                a.p_scale = s_scale;
+                a.p_store = P + (size_t)(i + 1) * k;
+            } else {
+                a.p_vec = P + (size_t)(i + 1) * k;
+                a.p_scale = 1.0;
+            }
             a.pnorm_idx = i + 1;
             a.trace = trace ? h->trace.as<unsigned long long>() + 10 * (size_t)i : nullptr;
             timer.start(2);

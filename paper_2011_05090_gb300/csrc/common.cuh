@@ -293,6 +293,8 @@ struct UpdateLaunch {
     void* qout;             // optional stored result column (qtype)
     int df_sketch;          // SRHT transform in double-float (FP32 pairs) instead of FP64
     int max_parts;          // 0, or an upper bound on the partial sketches per column
+    const double* w_next;   // SRHT, wcols == 1: also sketch this FP64 column (no update) into the
+                            // second block of partials (step 1 of the next column in the same pass)
 };
 // Number of partial sketches (per input column) the next update/sketch launch will write.
 int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols);
@@ -351,6 +353,7 @@ struct LSStep {
     double s_scale;
     const double* p_vec;    // p given directly (scaled by p_scale), or
     const double* p_part;   // reduced from partials
+    double* p_store;        // optional: the reduced p is also written here (FP64, k entries)
     int p_nparts;
     double p_scale;
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)

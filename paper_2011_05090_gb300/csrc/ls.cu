@@ -183,7 +183,11 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                                : a.p_part[(size_t)lane * k + l];
                 }
                 v = warp_sum(v) * a.p_scale;
-                if (lane == 0) { st.pbuf[l] = v; nrm[1] = fma(v, v, nrm[1]); }
+                if (lane == 0) {
+                    st.pbuf[l] = v;
+                    if (a.p_store) a.p_store[l] = v;
+                    nrm[1] = fma(v, v, nrm[1]);
+                }
             }
         }
         block_sum_lane0<2>(nrm, sh);

@@ -113,6 +113,7 @@ struct UpdParams {
     int w_df;                 // w holds double-float pairs (float2) instead of FP64
     const double* coef;
     void* qout;
+    const double* w_next;     // blockIdx.y == 1 sketches this FP64 column (no update, no store)
     const uint32_t* signbits;
     const int32_t* rows;
     int k;
@@ -136,7 +137,10 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
 
     if (p.ctl != nullptr && p.ctl[kStatusWord] != 0) return;   // an earlier step failed or broke down
     const int col = blockIdx.y;
-    const double* w = p.w + (int64_t)col * p.ldw;
+    // the second row of blocks of a launch with w_next sketches the next input column as it is
+    // (Alg. 2 step 1 of column i + 1, in FP64 / double-float) while the first updates column i
+    const bool next_role = p.w_next != nullptr && col == 1;
+    const double* w = next_role ? p.w_next : p.w + (int64_t)col * p.ldw;
     const double wmul = p.wscale ? *p.wscale : 1.0;
     const TQ* Q = reinterpret_cast<const TQ*>(p.Q);
     TQ* qout = reinterpret_cast<TQ*>(p.qout);
@@ -151,6 +155,18 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         const int64_t r0 = (int64_t)tile * TILE + threadIdx.x * 4;
         const bool full = p.vec && (r0 + 4 <= n);
+        if (SRHT && next_role) {
+            V z[4];
+            if (full) {
+                const double2 a = ld_stream_d2(w + r0, pol), b = ld_stream_d2(w + r0 + 2, pol);
+                z[0] = F::from(a.x); z[1] = F::from(a.y); z[2] = F::from(b.x); z[3] = F::from(b.y);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) z[e] = F::from(r0 + e < n ? w[r0 + e] : 0.0);
+            }
+            srht_tile<V>(z, r0, n, tile, p.signbits, srow, p.k, zt, part);
+            continue;
+        }
         Acc acc[4];
         if (full) {
             if (p.w_df) {            // hi + lo rounded once to the accumulation type
@@ -366,11 +382,15 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     p.w_df = L.w_df;
     p.coef = L.coef;
     p.qout = L.qout;
+    p.w_next = L.w_next;
     p.ntiles = ntiles;
     p.ctl = ctl;
     p.k = sk->k;
     // vector path: every 4-row group of w, Q and q_out starts on a 16-byte (bf16: 8-byte) boundary
+    RGS_REQUIRE(L.w_next == nullptr || (L.wcols == 1 && sk->kind == RGS_SKETCH_SRHT),
+                "a fused next-column sketch needs one input column and an SRHT sketch");
     bool vec = aligned16(L.w) && (L.wcols == 1 || L.ldw % 2 == 0);
+    if (L.w_next) vec = vec && aligned16(L.w_next);
     if (L.ncols > 0) vec = vec && aligned16(L.Q) && (L.ldq % 4 == 0);
     if (L.qout) vec = vec && ((uintptr_t)L.qout % (4 * esz) == 0 || aligned16(L.qout)) && (L.ldq % 4 == 0);
     p.vec = vec ? 1 : 0;
@@ -386,7 +406,7 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     size_t accsz = (L.qtype == RGS_F64) ? 8 : 4;
     size_t smem = TILE * 8 + (srht ? (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 : 0) + (size_t)L.ncols * accsz + 16;
     if (L.ncols > 0 || L.qout || srht) {
-        const int gy = L.wcols;
+        const int gy = L.w_next ? 2 : L.wcols;
         if (srht && L.df_sketch) {
             switch (L.qtype) {
                 case RGS_F64: launch_update_t<double, true, true>(ctx, p, gx, gy, smem); break;
