@@ -226,9 +226,9 @@ RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double
  *                               the H x W grid of the unknowns; nonlinear, so flexible = 1 is
  *                               required and the solver keeps z_j = M(q_j) (flexible GMRES,
  *                               x = x0 + Z y).  params points to an rgs_learned_precond.
- * With a preconditioner set, a restart whose true residual is not below (1 - 2^-10) times the
- * previous one switches the rest of the solve to the unpreconditioned method
- * (rgmres_info.fallback_cycle).
+ * With the learned preconditioner set, a restart whose true residual is not below (1 - 2^-10)
+ * times the previous one switches the rest of the solve to the unpreconditioned method
+ * (rgmres_info.fallback_cycle); Jacobi is never switched off.
  * The handle keeps the pointers in params (not copies): keep them valid while solving. */
 typedef enum { RGS_PRECOND_NONE = 0, RGS_PRECOND_JACOBI = 1, RGS_PRECOND_LEARNED_CONV = 2 } rgs_precond_kind;
 typedef struct rgs_convnet_obj* rgs_convnet;

@@ -472,10 +472,11 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             if (!std::isfinite(rel)) throw RgsError{RGS_ERR_NONFINITE, "non-finite residual"};
             if (rel <= opts->rtol) { converged = true; break; }
             if (cycles >= opts->max_cycles) break;
-            // fallback: a preconditioned cycle that did not reduce the true residual (by at least a
-            // relative 2^-10, so that rounding noise does not count as progress) turns the
-            // preconditioner off; the unpreconditioned method finishes the solve
-            if (use_pc && cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10))) {
+            // fallback: a cycle with the learned (nonlinear) preconditioner that did not reduce the
+            // true residual (by at least a relative 2^-10, so that rounding noise does not count as
+            // progress) turns it off; the unpreconditioned method finishes the solve.  A fixed linear
+            // preconditioner (Jacobi) is kept: its slow cycles are the restarted method's, not its own.
+            if (use_pc && learned && cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10))) {
                 use_pc = false;
                 fallback_cycle = cycles;
             }
