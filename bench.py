@@ -279,6 +279,9 @@ def run_batched_c4(rgs, h):
     out = {}
     full = c4_instances(rgs, 256, 64, 512, 0)
     batched(full[:8], max_cycles=1, fixed_steps=True)                      # warm-up
+    out["tuning"] = rgs.rgs_autotune_batched(h, [I["C"] for I in full], [I["b"] for I in full],
+                                             [I["m"] for I in full], [2 * I["m"] for I in full], cycles=1,
+                                             sketch_seed=1)
     dt, res = batched(full, max_cycles=2, fixed_steps=True)
     steps = sum(r["total_steps"] for r in res)
     ct, cs, _ = sequential_cgs2(full, max_cycles=2, fixed_steps=True)
@@ -446,6 +449,7 @@ def run_ours(args):
     R = rgs.colmajor_empty(m, m)
     qs = torch.empty(m, dtype=torch.float64, device="cuda")
     flags = rgs.RGS_QR_TIMINGS
+    tuning = rgs.rgs_autotune_update(h, sk, m // 2, torch.float32)     # launch shape of the update pass
 
     for _ in range(args.warmup):
         rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=flags)
@@ -522,7 +526,8 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
                "config": {"workload": WORKLOAD if m == M_COLS else f"profiling case m={m}", "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
-                          "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}"},
+                          "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}",
+                          "tuning": tuning},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "phases_ms": phases,
                "certificates": {"delta": last["delta"], "delta_tilde": last["delta_tilde"]},

@@ -305,6 +305,33 @@ RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_
                                         double* const* x, const rgmres_batch_opts* opts, uint64_t sketch_seed,
                                         rgmres_info* info);
 
+/* ---------------------------------------------------------------- launch tuning
+ * Tunable launch shapes of the handle (no counterpart in the paper; every choice computes the
+ * same quantities, only the grouping of partial sums changes):
+ *   upd_blocks_per_sm    CTAs per SM of the fused update / sketch pass of steps 3-4 (1..4); it is
+ *                        also the number of partial sketches per SM that step 2 reduces.
+ *   batch_blocks_per_sm  CTAs per SM of the batched solver's persistent grid (0 = occupancy limit).
+ *   batch_min_team_work  rows x (k + restart) per CTA below which a batched instance gets no
+ *                        further CTA for its team.
+ * rgs_autotune_update times the update pass of an n-row basis of ncols columns (s->n rows, SRHT s)
+ * for upd_blocks_per_sm in 2..4 and keeps the fastest; ms (optional, 3 entries) receives the
+ * mean launch times.  rgs_autotune_batched times `cycles` fixed cycles of the given batch for
+ * batch_blocks_per_sm in {1, 2} x batch_min_team_work in {2^17, 2^19, 2^21} and keeps the
+ * fastest; ms (optional, 6 entries) receives the times.  Both leave the choice on the handle and
+ * copy it to out (optional). */
+typedef struct {
+    int32_t upd_blocks_per_sm;
+    int32_t batch_blocks_per_sm;
+    double batch_min_team_work;
+} rgs_tuning;
+RGS_API rgs_status rgs_get_tuning(rgs_handle h, rgs_tuning* out);
+RGS_API rgs_status rgs_set_tuning(rgs_handle h, const rgs_tuning* t);
+RGS_API rgs_status rgs_autotune_update(rgs_handle h, rgs_sketch s, int32_t ncols, rgs_dtype qtype, rgs_tuning* out,
+                                       float* ms);
+RGS_API rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, const double* const* b,
+                                        const rgmres_batch_opts* opts, uint64_t sketch_seed, int32_t cycles,
+                                        rgs_tuning* out, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

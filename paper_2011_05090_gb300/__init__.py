@@ -57,7 +57,8 @@ EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", 
             "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgs_csr_matvec", "rgmres_solve", "cgs2_gmres_solve",
             "rgmres_set_preconditioner", "rgs_convnet_num_params", "rgs_convnet_create", "rgs_convnet_destroy",
             "rgs_convnet_get_params", "rgs_convnet_set_params", "rgs_convnet_forward", "rgs_convnet_loss_grad",
-            "rgs_convnet_train_step", "rgmres_solve_batched"]
+            "rgs_convnet_train_step", "rgmres_solve_batched", "rgs_get_tuning", "rgs_set_tuning",
+            "rgs_autotune_update", "rgs_autotune_batched"]
 
 
 class RgsError(RuntimeError):
@@ -94,6 +95,11 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("k", ctypes.c_int32), ("max_cycles", ctypes.c_int32),
                 ("qtype", ctypes.c_int32), ("rtol", ctypes.c_double), ("inner_factor", ctypes.c_double),
                 ("fixed_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("upd_blocks_per_sm", ctypes.c_int32), ("batch_blocks_per_sm", ctypes.c_int32),
+                ("batch_min_team_work", ctypes.c_double)]
 
 
 class LearnedPrecond(ctypes.Structure):
@@ -135,6 +141,11 @@ def load():
         "rgmres_set_preconditioner": [P, ctypes.c_int, P, I32],
         "rgmres_solve_batched": [P, I32, ctypes.POINTER(CSR), ctypes.POINTER(P), ctypes.POINTER(P),
                                  ctypes.POINTER(BatchOpts), ctypes.c_uint64, ctypes.POINTER(GmresInfo)],
+        "rgs_get_tuning": [P, ctypes.POINTER(Tuning)],
+        "rgs_set_tuning": [P, ctypes.POINTER(Tuning)],
+        "rgs_autotune_update": [P, P, I32, ctypes.c_int, ctypes.POINTER(Tuning), P],
+        "rgs_autotune_batched": [P, I32, ctypes.POINTER(CSR), ctypes.POINTER(P), ctypes.POINTER(BatchOpts),
+                                 ctypes.c_uint64, I32, ctypes.POINTER(Tuning), P],
         "rgs_convnet_num_params": [],
         "rgs_convnet_create": [P, I32, I32, I32, ctypes.c_uint64, ctypes.POINTER(P)],
         "rgs_convnet_destroy": [P],
@@ -414,6 +425,43 @@ def rgmres_solve_batched(h, csrs, bs, xs, restarts, ks, rtol=1e-8, max_cycles=10
     return [{"cycles": info[i].cycles, "total_steps": info[i].total_steps, "converged": bool(info[i].converged),
              "status": info[i].status, "rel_residual": info[i].rel_residual,
              "history": [hists[i][c] for c in range(info[i].cycles + 1)]} for i in range(nb)]
+
+
+def _tuning_dict(t):
+    return {"upd_blocks_per_sm": t.upd_blocks_per_sm, "batch_blocks_per_sm": t.batch_blocks_per_sm,
+            "batch_min_team_work": t.batch_min_team_work}
+
+
+def rgs_get_tuning(h):
+    t = Tuning()
+    _check(load().rgs_get_tuning(h.ptr, ctypes.byref(t)), h)
+    return _tuning_dict(t)
+
+
+def rgs_set_tuning(h, upd_blocks_per_sm, batch_blocks_per_sm, batch_min_team_work):
+    t = Tuning(int(upd_blocks_per_sm), int(batch_blocks_per_sm), float(batch_min_team_work))
+    _check(load().rgs_set_tuning(h.ptr, ctypes.byref(t)), h)
+
+
+def rgs_autotune_update(h, sk, ncols, qdtype=torch.float32):
+    """Time the fused update pass for 2..4 CTAs per SM on this sketch's n; keep the fastest."""
+    t = Tuning()
+    ms = (ctypes.c_float * 3)()
+    _check(load().rgs_autotune_update(h.ptr, sk.ptr, int(ncols), _DTYPE[qdtype], ctypes.byref(t), ms), h)
+    return {**_tuning_dict(t), "ms": list(ms)}
+
+
+def rgs_autotune_batched(h, csrs, bs, restarts, ks, cycles=1, qdtype=torch.float32, sketch_seed=0):
+    """Time the batched solver's grid candidates on this batch (fixed cycles); keep the fastest."""
+    nb = len(csrs)
+    A = (CSR * nb)(*csrs)
+    bp = (ctypes.c_void_p * nb)(*[v.data_ptr() for v in bs])
+    opts = (BatchOpts * nb)(*[BatchOpts(int(restarts[i]), int(ks[i]), 1, _DTYPE[qdtype], 1e-8, 0.5, 1, 0)
+                              for i in range(nb)])
+    t = Tuning()
+    ms = (ctypes.c_float * 6)()
+    _check(load().rgs_autotune_batched(h.ptr, nb, A, bp, opts, int(sketch_seed), int(cycles), ctypes.byref(t), ms), h)
+    return {**_tuning_dict(t), "ms": list(ms)}
 
 
 def csr_to_device(rowptr, colind, val, device="cuda"):

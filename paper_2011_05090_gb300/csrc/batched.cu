@@ -877,7 +877,7 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
                 int best = 0;
                 for (int i = 1; i < nbatch; ++i)
                     if (work[i] / ts[i] > work[best] / ts[best]) best = i;
-                if (work[best] / ts[best] < 8192.0 * 64.0) break;    // not worth a barrier
+                if (work[best] / ts[best] < ctx->batch_min_team_work) break;    // not worth a barrier
                 ts[best] += 1;
             }
             for (int i = 0; i < nbatch; ++i) {

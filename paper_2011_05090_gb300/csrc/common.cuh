@@ -63,7 +63,7 @@ struct rgs_context {
     DevBuf scratch;        // staging for host-pointer calls
     DevBuf lsbuf;          // Householder factors and vectors of the least-squares engine
     DevBuf work;           // P = Theta W, certificates
-    int upd_blocks_per_sm = 4;
+    int upd_blocks_per_sm = 4;             // tuning: CTAs per SM of the update / sketch pass (<= kUpdMaxBlocksPerSm)
     int ls_blocks = 0;     // cooperative grid of the least-squares kernel
     int precond_kind = 0;  // rgmres_set_preconditioner: RGS_PRECOND_*
     int precond_flexible = 0;
@@ -73,7 +73,8 @@ struct rgs_context {
     uint64_t batch_theta_seed = ~0ull;
     int batch_theta_k = 0;
     int64_t batch_theta_n = 0;
-    int batch_blocks_per_sm = 0;           // 0: the occupancy limit, at most 4
+    int batch_blocks_per_sm = 0;           // tuning: 0 = the occupancy limit, at most 4
+    double batch_min_team_work = 8192.0 * 64.0;   // tuning: rows x (k + restart) per CTA worth an extra CTA
     DevBuf batch_ws;       // per-instance workspaces of the batched solve
     DevBuf batch_desc;     // instance descriptors and team tables
     cudaStream_t capture_stream = nullptr; // private stream on which launches are captured into graphs
@@ -134,6 +135,10 @@ struct rgs_sketch_obj {
     DevBuf signbits;       // SRHT: ceil(n/32) words, bit set => -1
     DevBuf rows;           // SRHT: k int32 sample rows (ascending)
 };
+
+// Workspaces for partial sketches are sized for this many update CTAs per SM, whatever the
+// tuning chooses at run time.
+constexpr int kUpdMaxBlocksPerSm = 4;
 
 // ---------------------------------------------------------------- device helpers
 namespace rgsdev {

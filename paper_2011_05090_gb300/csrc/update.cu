@@ -359,7 +359,7 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols) {
     const int ntiles = (int)((n + TILE - 1) / TILE);
     if (sk->kind != RGS_SKETCH_SRHT) return std::max(1, std::min((int)((n + 255) / 256), ctx->num_sms * 2));
-    const int slots = ctx->num_sms * ctx->upd_blocks_per_sm;
+    const int slots = ctx->num_sms * std::min(ctx->upd_blocks_per_sm, kUpdMaxBlocksPerSm);
     if (wcols <= 1) return std::max(1, std::min(ntiles, slots));
     return std::max(1, std::min(ntiles, std::max(4, 8 * slots / wcols)));
 }
@@ -396,7 +396,7 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     p.vec = vec ? 1 : 0;
     const bool srht = sk->kind == RGS_SKETCH_SRHT;
     int gx = srht ? rgs_update_nparts(ctx, sk, n, L.wcols)
-                  : std::max(1, std::min(ntiles, ctx->num_sms * ctx->upd_blocks_per_sm));
+                  : std::max(1, std::min(ntiles, ctx->num_sms * std::min(ctx->upd_blocks_per_sm, kUpdMaxBlocksPerSm)));
     if (srht && L.max_parts > 0) gx = std::min(gx, L.max_parts);
     if (srht) {
         p.signbits = sk->signbits.as<uint32_t>();
