@@ -282,13 +282,15 @@ def run_batched_c4(rgs, h):
     out["tuning"] = rgs.rgs_autotune_batched(h, [I["C"] for I in full], [I["b"] for I in full],
                                              [I["m"] for I in full], [2 * I["m"] for I in full], cycles=1,
                                              sketch_seed=1)
-    dt, res = batched(full, max_cycles=2, fixed_steps=True)
+    with Clocks(0) as clk:
+        dt, res = batched(full, max_cycles=2, fixed_steps=True)
     steps = sum(r["total_steps"] for r in res)
     ct, cs, _ = sequential_cgs2(full, max_cycles=2, fixed_steps=True)
     out["full_fixed_2_cycles"] = {
         "config": "256 x convdiff2d sides U[64,512] Pe U[1,100] restart U{30..80} gaussian k=2m, 2 fixed cycles",
         "sum_n": sum(I["n"] for I in full), "arnoldi_steps": steps, "batched_f32_s": dt,
-        "batched_steps_per_s": steps / dt, "sequential_cgs2_f64_s": ct, "speedup": ct / dt}
+        "batched_steps_per_s": steps / dt, "sequential_cgs2_f64_s": ct, "speedup": ct / dt,
+        "clocks": clk.summary()}
     del full
     small = c4_instances(rgs, 256, 16, 64, 1000)
     dt, res = batched(small, max_cycles=400, rtol=1e-8)

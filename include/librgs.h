@@ -316,8 +316,8 @@ RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_
  * rgs_autotune_update times the update pass of an n-row basis of ncols columns (s->n rows, SRHT s)
  * for upd_blocks_per_sm in 2..4 and keeps the fastest; ms (optional, 3 entries) receives the
  * mean launch times.  rgs_autotune_batched times `cycles` fixed cycles of the given batch for
- * batch_blocks_per_sm in {1, 2} x batch_min_team_work in {2^17, 2^19, 2^21} and keeps the
- * fastest; ms (optional, 6 entries) receives the times.  Both leave the choice on the handle and
+ * batch_blocks_per_sm in {occupancy limit, one less} x batch_min_team_work in {2^17, 2^19, 2^21}
+ * and keeps the fastest; ms (optional, 6 entries) receives the times (unused entries 0).  Both leave the choice on the handle and
  * copy it to out (optional). */
 typedef struct {
     int32_t upd_blocks_per_sm;

@@ -157,14 +157,15 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
         }
         const int saved_b = h->batch_blocks_per_sm;
         const double saved_w = h->batch_min_team_work;
-        const int bpm[2] = {1, 2};
+        const int occ = rgs_batched_max_blocks_per_sm(opts[0].qtype);
+        const int bpm[2] = {occ, std::max(1, occ - 1)};
         const double tw[3] = {131072.0, 524288.0, 2097152.0};
         Events ev;
         float best = INFINITY;
         int best_b = saved_b;
         double best_w = saved_w;
         int c = 0;
-        for (int bi = 0; bi < 2; ++bi)
+        for (int bi = 0; bi < (bpm[1] < bpm[0] ? 2 : 1); ++bi)
             for (int wi = 0; wi < 3; ++wi, ++c) {
                 h->batch_blocks_per_sm = bpm[bi];
                 h->batch_min_team_work = tw[wi];

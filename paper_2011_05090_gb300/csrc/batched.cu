@@ -818,6 +818,14 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+// Resident CTAs per SM of the batched kernel for a basis type (the cooperative grid's limit).
+int rgs_batched_max_blocks_per_sm(int qtype) {
+    auto kern = qtype == RGS_F64 ? rgmres_batched_kernel<double> : rgmres_batched_kernel<float>;
+    int per_sm = 0;
+    RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, 0));
+    return std::min(per_sm, 4);
+}
+
 extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, const double* const* b,
                                            double* const* x, const rgmres_batch_opts* opts, uint64_t sketch_seed,
                                            rgmres_info* info) {
