@@ -304,7 +304,7 @@ def run_batched_c4(rgs, h):
 
 
 def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=3, steps=1500, ntest=3,
-                   max_cycles=400, batch=16):
+                   max_cycles=400, batch=16, nval=0, eval_every=1000):
     """Learned preconditioner: harvest restart residuals of plain RGMRES(50) solves on nfields
     diffusion problems (kappa = exp(1.5 g), correlation ell; right-hand sides from white noise to
     smooth), train the conv net with the residual-norm loss, then solve held-out fields with
@@ -337,7 +337,20 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
     harvest_s = time.perf_counter() - t0
     net = rgs.rgs_convnet_create(h, N, N, batch, seed=7)
     t0 = time.perf_counter()
-    losses = learned.train(h, net, inputs[:w], steps, stencils, field_of[:w], batch=batch, lr=1e-3)
+    scores = None
+    if nval:
+        # model selection on validation fields (seeds 800000..), distinct from training and test fields
+        val = []
+        for f in range(nval):
+            csr, lk = synth.diffusion_2d(N, 1.5, ell, 800000 + f)
+            arrays, C = rgs.csr_to_device(*csr)
+            val.append((C, torch.tensor(synth.rhs(n, 55 + f), device="cuda"), torch.tensor(lk, device="cuda"),
+                        arrays))
+        losses, scores = learned.train_selected(h, net, inputs[:w], steps, stencils, field_of[:w], sk,
+                                                [(c, b_, l_) for c, b_, l_, _ in val], eval_every=eval_every,
+                                                batch=batch, lr=1e-3, max_cycles=max_cycles // 3)
+    else:
+        losses = learned.train(h, net, inputs[:w], steps, stencils, field_of[:w], batch=batch, lr=1e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del inputs
@@ -362,7 +375,8 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
                    "median_rel_residual": float(np.median([e["rel_residual"] for e in v]))} for k, v in res.items()}
     return {"config": f"diffusion2d {N}^2 sigma=1.5 corr={ell} RGMRES(50) gaussian k=100 f32, cap {max_cycles} cycles",
             "training": {"fields": nfields, "inputs": w, "harvest_s": harvest_s, "steps": steps, "batch": batch,
-                         "train_s": train_s, "ms_per_step": 1e3 * train_s / steps,
+                         "train_s": train_s, "ms_per_step": 1e3 * train_s / steps, "validation": scores,
+                         "validation_fields": nval,
                          "loss_first_50": float(np.mean(losses[:50])), "loss_last_50": float(np.mean(losses[-50:]))},
             "held_out_fields": ntest, "summary": summary, "per_field": res}
 
@@ -561,6 +575,8 @@ def main():
     ap.add_argument("--c5-fields", type=int, default=40)
     ap.add_argument("--c5-test", type=int, default=3)
     ap.add_argument("--c5-cycles", type=int, default=400)
+    ap.add_argument("--c5-val", type=int, default=0, help="validation fields for model selection (0: none)")
+    ap.add_argument("--c5-eval-every", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -572,7 +588,8 @@ def main():
         libbuild.build()
         h = rgs.rgs_create()
         out = run_learned_c5(rgs, h, N=args.c5, ell=args.c5 / 16.0, nfields=args.c5_fields, steps=args.c5_steps,
-                             ntest=args.c5_test, max_cycles=args.c5_cycles)
+                             ntest=args.c5_test, max_cycles=args.c5_cycles, nval=args.c5_val,
+                             eval_every=args.c5_eval_every)
         print(json.dumps({"metric": "learned preconditioner: iterations and time to 1e-8", **out}), flush=True)
     elif args.gmres_only:
         run_gmres_profile(args)

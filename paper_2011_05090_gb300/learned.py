@@ -114,6 +114,51 @@ def train(h, net, inputs, steps, stencils, field_of, batch=16, lr=1e-3, lr_final
     return losses
 
 
+def validation_score(h, sk, systems, net, restart=50, max_cycles=100):
+    """Cost of flexible RGMRES with the network on validation systems [(csr, b, log kappa)]: the
+    Arnoldi steps to 1e-8, or for a solve that stops short, the step budget times
+    (1 + log10(residual reached / 1e-8)).  Lower is better."""
+    score = 0.0
+    for csr, b, lk in systems:
+        x = torch.zeros_like(b)
+        r = solve(h, sk, csr, b, x, restart=restart, rtol=1e-8, max_cycles=max_cycles, precond="learned", net=net,
+                  logkappa=lk)
+        if r["converged"]:
+            score += r["total_steps"]
+        else:
+            rel = max(r["rel_residual"], 1e-8) if r["rel_residual"] == r["rel_residual"] else 1.0
+            score += restart * max_cycles * (1.0 + math.log10(rel / 1e-8))
+    return score
+
+
+def train_selected(h, net, inputs, steps, stencils, field_of, sk, val_systems, eval_every=1000, batch=16, lr=1e-3,
+                   lr_final=1e-5, seed=0, restart=50, max_cycles=100, log=False):
+    """train() in rounds of eval_every steps on one learning-rate schedule, scoring the network on
+    the validation systems after each round and keeping the parameters of the best round (the
+    training loss tracks the solver's behaviour only loosely).  Returns (losses, scores)."""
+    from . import rgs_convnet_get_params, rgs_convnet_set_params
+    losses, scores = [], []
+    best, best_p = float("inf"), None
+    done = 0
+    while done < steps:
+        n = min(eval_every, steps - done)
+        # the slice [done, done + n) of one cosine schedule over all steps
+        a0 = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * done / max(steps - 1, 1)))
+        a1 = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * (done + n - 1) / max(steps - 1, 1)))
+        losses += train(h, net, inputs, n, stencils, field_of, batch=batch, lr=a0, lr_final=a1, seed=seed + done)
+        done += n
+        sc = validation_score(h, sk, val_systems, net, restart=restart, max_cycles=max_cycles)
+        scores.append((done, sc))
+        if log:
+            print(f"step {done}: loss {sum(losses[-50:]) / min(50, len(losses)):.4f}, validation cost {sc:.0f}",
+                  flush=True)
+        if sc < best:
+            best, best_p = sc, rgs_convnet_get_params(h, net)
+    if best_p is not None:
+        rgs_convnet_set_params(h, net, best_p)
+    return losses, scores
+
+
 def solve(h, sk, csr, b, x, restart=50, rtol=1e-8, max_cycles=1000, qdtype=torch.float32, precond="none",
           net=None, logkappa=None):
     """rgmres_solve with the right preconditioner ``precond`` ("none", "jacobi" or "learned";
