@@ -313,6 +313,7 @@ RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_
  *   batch_blocks_per_sm  CTAs per SM of the batched solver's persistent grid (0 = occupancy limit).
  *   batch_min_team_work  rows x (k + restart) per CTA below which a batched instance gets no
  *                        further CTA for its team.
+ *   ls_blocks            CTAs of the cooperative least-squares kernel (0: one per SM).
  * rgs_autotune_update times the update pass of an n-row basis of ncols columns (s->n rows, SRHT s)
  * for upd_blocks_per_sm in 2..4 and keeps the fastest; ms (optional, 3 entries) receives the
  * mean launch times.  rgs_autotune_batched times `cycles` fixed cycles of the given batch for
@@ -323,6 +324,8 @@ typedef struct {
     int32_t upd_blocks_per_sm;
     int32_t batch_blocks_per_sm;
     double batch_min_team_work;
+    int32_t ls_blocks;            /* CTAs of the least-squares kernel of step 2 (0: one per SM) */
+    int32_t reserved;
 } rgs_tuning;
 RGS_API rgs_status rgs_get_tuning(rgs_handle h, rgs_tuning* out);
 RGS_API rgs_status rgs_set_tuning(rgs_handle h, const rgs_tuning* t);

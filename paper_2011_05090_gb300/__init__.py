@@ -99,7 +99,8 @@ class BatchOpts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("upd_blocks_per_sm", ctypes.c_int32), ("batch_blocks_per_sm", ctypes.c_int32),
-                ("batch_min_team_work", ctypes.c_double)]
+                ("batch_min_team_work", ctypes.c_double), ("ls_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class LearnedPrecond(ctypes.Structure):
@@ -429,7 +430,7 @@ def rgmres_solve_batched(h, csrs, bs, xs, restarts, ks, rtol=1e-8, max_cycles=10
 
 def _tuning_dict(t):
     return {"upd_blocks_per_sm": t.upd_blocks_per_sm, "batch_blocks_per_sm": t.batch_blocks_per_sm,
-            "batch_min_team_work": t.batch_min_team_work}
+            "batch_min_team_work": t.batch_min_team_work, "ls_blocks": t.ls_blocks}
 
 
 def rgs_get_tuning(h):
@@ -438,8 +439,8 @@ def rgs_get_tuning(h):
     return _tuning_dict(t)
 
 
-def rgs_set_tuning(h, upd_blocks_per_sm, batch_blocks_per_sm, batch_min_team_work):
-    t = Tuning(int(upd_blocks_per_sm), int(batch_blocks_per_sm), float(batch_min_team_work))
+def rgs_set_tuning(h, upd_blocks_per_sm, batch_blocks_per_sm, batch_min_team_work, ls_blocks=0):
+    t = Tuning(int(upd_blocks_per_sm), int(batch_blocks_per_sm), float(batch_min_team_work), int(ls_blocks), 0)
     _check(load().rgs_set_tuning(h.ptr, ctypes.byref(t)), h)
 
 

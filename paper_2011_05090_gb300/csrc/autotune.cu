@@ -44,6 +44,8 @@ void fill_tuning(const rgs_context* h, rgs_tuning* t) {
     t->upd_blocks_per_sm = h->upd_blocks_per_sm;
     t->batch_blocks_per_sm = h->batch_blocks_per_sm;
     t->batch_min_team_work = h->batch_min_team_work;
+    t->ls_blocks = h->ls_blocks_tuned;
+    t->reserved = 0;
 }
 
 __global__ void fill_kernel(double* q, int64_t n) {
@@ -68,6 +70,8 @@ rgs_status rgs_set_tuning(rgs_handle h, const rgs_tuning* t) {
                     "upd_blocks_per_sm must be in [1, 4]");
         RGS_REQUIRE(t->batch_blocks_per_sm >= 0 && t->batch_blocks_per_sm <= 4, "batch_blocks_per_sm must be in [0, 4]");
         RGS_REQUIRE(t->batch_min_team_work > 0.0, "batch_min_team_work must be positive");
+        RGS_REQUIRE(t->ls_blocks >= 0 && t->ls_blocks <= h->num_sms, "ls_blocks must be in [0, SMs]");
+        h->ls_blocks_tuned = t->ls_blocks;
         h->upd_blocks_per_sm = t->upd_blocks_per_sm;
         h->batch_blocks_per_sm = t->batch_blocks_per_sm;
         h->batch_min_team_work = t->batch_min_team_work;

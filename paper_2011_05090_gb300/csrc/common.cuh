@@ -64,7 +64,8 @@ struct rgs_context {
     DevBuf lsbuf;          // Householder factors and vectors of the least-squares engine
     DevBuf work;           // P = Theta W, certificates
     int upd_blocks_per_sm = 4;             // tuning: CTAs per SM of the update / sketch pass (<= kUpdMaxBlocksPerSm)
-    int ls_blocks = 0;     // cooperative grid of the least-squares kernel
+    int ls_blocks = 0;     // cooperative grid of the least-squares kernel (at most num_sms)
+    int ls_blocks_tuned = 0;   // tuning: 0 = one CTA per SM
     int precond_kind = 0;  // rgmres_set_preconditioner: RGS_PRECOND_*
     int precond_flexible = 0;
     void* precond_net = nullptr;           // RGS_PRECOND_LEARNED_CONV: the network

@@ -535,7 +535,8 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     LSState s = st;
     LSStep p = a;
     void* args[] = {&s, &p};
-    RGS_CUDA(cudaLaunchCooperativeKernel((const void*)ls_kernel, dim3(ctx->ls_blocks), dim3(LT), args, 0, ctx->stream));
+    const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
+    RGS_CUDA(cudaLaunchCooperativeKernel((const void*)ls_kernel, dim3(grid), dim3(LT), args, 0, ctx->stream));
     ctx->launches++;
 }
 

@@ -33,7 +33,8 @@ def qr_R(h, sk, A):
 def test_tuning_roundtrip_and_checks(h):
     t0 = rgs.rgs_get_tuning(h)
     rgs.rgs_set_tuning(h, 3, 1, 1e6)
-    assert rgs.rgs_get_tuning(h) == {"upd_blocks_per_sm": 3, "batch_blocks_per_sm": 1, "batch_min_team_work": 1e6}
+    assert rgs.rgs_get_tuning(h) == {"upd_blocks_per_sm": 3, "batch_blocks_per_sm": 1, "batch_min_team_work": 1e6,
+                                     "ls_blocks": 0}
     for bad in [(0, 1, 1e6), (5, 1, 1e6), (2, 5, 1e6), (2, 1, 0.0)]:
         with pytest.raises(rgs.RgsError):
             rgs.rgs_set_tuning(h, *bad)
