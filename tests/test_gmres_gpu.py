@@ -181,3 +181,25 @@ def test_large_norm_operator_no_overflow(h, solver):
         res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=60, rtol=1e-8, max_cycles=100, qdtype=q)
     xs = x.cpu().numpy()
     assert res["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
+
+
+@pytest.mark.parametrize("solver", ["rgmres", "cgs2"])
+def test_7_point_operator_full_tiles(h, solver):
+    # 3D 7-point operator: 1024-row tiles hold ~7,000 nonzeros (the SpMV stages a tile's column
+    # indices in shared memory); one fixed cycle in FP64 against the oracle
+    csr = synth.convdiff_3d(20, 30.0, 1.0, 3, 4)
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    n = A.shape[0]
+    b = synth.rhs(n, 9)
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    if solver == "cgs2":
+        rgs.cgs2_gmres_solve(h, C, dev(b), x, restart=15, max_cycles=1, fixed_steps=True)
+        ref = og.cgs2_gmres(A, b, restart=15, max_cycles=1, fixed_steps=True)
+    else:
+        sk = rgs.rgs_sketch_create(h, "srht", n, 60, 3)
+        rgs.rgmres_solve(h, sk, C, dev(b), x, restart=15, max_cycles=1, qdtype=torch.float64, fixed_steps=True)
+        ref = og.rgmres(A, b, Sketch("srht", n, 60, 3), restart=15, max_cycles=1, fixed_steps=True)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-10
+    y = rgs.rgs_csr_matvec(h, C, dev(b))
+    assert np.allclose(y.cpu().numpy(), A @ b, rtol=1e-13, atol=1e-12 * np.abs(A @ b).max())
