@@ -36,6 +36,8 @@ def stencil_from_csr(rowptr, colind, val, H, W):
     """(5, H, W) FP32 coefficients of a 5-point operator on an H x W grid (x fastest) from its
     CSR arrays (torch tensors on one device); raises if a row reaches another neighbour."""
     n = H * W
+    if rowptr.numel() != n + 1:
+        raise ValueError(f"the operator has {rowptr.numel() - 1} rows, the grid {n} points")
     counts = rowptr[1:].long() - rowptr[:-1].long()
     rows = torch.repeat_interleave(torch.arange(n, device=rowptr.device), counts)
     d = colind.long() - rows

@@ -44,3 +44,23 @@ def test_status_strings(lib):
     assert lib.rgs_status_string(rgs.RGS_OK) == b"ok"
     assert b"breakdown" in lib.rgs_status_string(rgs.RGS_ERR_BREAKDOWN)
     assert lib.rgs_status_string(99) == b"unknown status"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the binding has no CPU fallback: without librgs.so every entry point raises
+    import subprocess
+    import sys
+    code = (
+        "import paper_2011_05090_gb300 as rgs\n"
+        f"rgs.LIB_PATH = {str(tmp_path / 'absent.so')!r}\n"
+        "rgs._lib = None\n"
+        "try:\n"
+        "    rgs.rgs_create()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    raise SystemExit('no error without the library')\n"
+    )
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert "raised:" in out.stdout and "is missing" in out.stdout
