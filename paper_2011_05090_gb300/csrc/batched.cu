@@ -417,14 +417,12 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
                             double* h2, double* red) {
     const int k = I.k, m = I.m, ld = m + 1;
     const int t = threadIdx.x;
-    __shared__ double sh_r, sh_res;
     __shared__ int sh_stop, sh_bad;
     double a = 0.0;
     for (int l = t; l < k; l += BT) a = fma(ss[l], ss[l], a);
     const double rii = sqrt(cta_sum(a, red));
     const double pn = __ldcg(I.scal + 3);
     if (t == 0) {
-        sh_r = rii;
         sh_stop = 0;
         sh_bad = !isfinite(rii) ? 1 : 0;
         // r_ii at the rounding level of ||p_i||: the Krylov space is invariant (happy breakdown)
@@ -442,10 +440,7 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
         const double* Rc = I.R + (size_t)i * (m + 2);
         auto hcol = [&](int q) { return q < i ? Rc[q] : rii; };
         const double res = givens_column_warp(i - 1, hcol, I.cs, I.sn, I.g, I.Hr, ld);
-        if (t == 0) {
-            sh_res = res;
-            if (res <= stop_tol && sh_stop == 0) sh_stop = i;
-        }
+        if (t == 0 && res <= stop_tol && sh_stop == 0) sh_stop = i;
     }
     __syncthreads();
     const bool more = sh_stop == 0 && i < m;

@@ -158,7 +158,9 @@ constexpr int kCtlWords = 128;
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies.
 __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int r = 0; r < 10; ++r) {
         uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
         uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];

@@ -540,10 +540,12 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     ctx->launches++;
 }
 
+// One CTA of LT threads per SM (its registers fill the SM), so the cooperative grid is the SM count.
 int rgs_ls_max_blocks(int num_sms) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ls_kernel, LT, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    return num_sms;   // one CTA of LT threads per SM
+    RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ls_kernel, LT, 0));
+    RGS_REQUIRE(per_sm >= 1, "the least-squares kernel does not fit on an SM");
+    return num_sms;
 }
 
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
