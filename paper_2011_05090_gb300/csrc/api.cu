@@ -268,6 +268,20 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         void* dQ = Q;
         double* dR = R;
         int64_t dldw = ldw, dldq = ldq, dldr = ldr;
+        // With the SRHT, column i of W is needed only from the update pass of column i - 1, and
+        // (with qscale) q'_i is final after its own pass: host copies then run in column chunks on
+        // a copy stream, overlapped with the factorization, ordered by events.
+        const bool pipelined = host && s->kind == RGS_SKETCH_SRHT;
+        const int CB = 8;                                       // columns per copy chunk
+        const int nchunks = (m + CB - 1) / CB;
+        std::vector<cudaEvent_t> wready, qdone;
+        struct EventList {
+            std::vector<cudaEvent_t>* v[2];
+            ~EventList() {
+                for (auto* l : v)
+                    for (auto e : *l) cudaEventDestroy(e);
+            }
+        } event_guard{{&wready, &qdone}};
         if (host) {
             const size_t wb = sizeof(double) * (size_t)n * m, qb = esz * (size_t)n * m, rb = sizeof(double) * (size_t)m * m;
             h->scratch.ensure(wb + qb + rb + 256);
@@ -275,13 +289,43 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             double* sW = reinterpret_cast<double*>(base);
             dQ = base + wb;
             dR = reinterpret_cast<double*>(base + wb + qb);
-            RGS_CUDA(cudaMemcpy2DAsync(sW, sizeof(double) * n, W, sizeof(double) * ldw, sizeof(double) * n, m,
-                                       cudaMemcpyHostToDevice, st));
+            if (pipelined) {
+                if (!h->copy_stream) RGS_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+                cudaEvent_t start_ev;
+                RGS_CUDA(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+                wready.push_back(start_ev);                      // (destroyed with the others)
+                RGS_CUDA(cudaEventRecord(start_ev, st));         // earlier work on the staging is done
+                RGS_CUDA(cudaStreamWaitEvent(h->copy_stream, start_ev, 0));
+                for (int c = 0; c < nchunks; ++c) {
+                    const int c0 = c * CB, cols = std::min(CB, m - c0);
+                    RGS_CUDA(cudaMemcpy2DAsync(sW + (size_t)c0 * n, sizeof(double) * n, W + (size_t)c0 * ldw,
+                                               sizeof(double) * ldw, sizeof(double) * n, cols, cudaMemcpyHostToDevice,
+                                               h->copy_stream));
+                    cudaEvent_t e;
+                    RGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                    wready.push_back(e);
+                    RGS_CUDA(cudaEventRecord(e, h->copy_stream));
+                }
+            } else {
+                RGS_CUDA(cudaMemcpy2DAsync(sW, sizeof(double) * n, W, sizeof(double) * ldw, sizeof(double) * n, m,
+                                           cudaMemcpyHostToDevice, st));
+            }
             dW = sW;
             dldw = n;
             dldq = n;
             dldr = m;
         }
+        // chunk c of W is on the device once wready[1 + c] has completed
+        int w_waited = -1;
+        auto need_w = [&](int col) {
+            if (!pipelined) return;
+            const int c = std::min(col, m - 1) / CB;
+            while (w_waited < c) {
+                ++w_waited;
+                RGS_CUDA(cudaStreamWaitEvent(st, wready[1 + w_waited], 0));
+            }
+        };
+        const bool early_q = pipelined && qscale != nullptr;   // Q' columns final as they are written
 
         // workspaces: Householder engine, P = Theta W, partial sketches, certificates
         LSState ls{};
@@ -311,6 +355,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         // columns are sketched inside the update passes)
         timer.start(0);
         const bool df = qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH);
+        need_w(fused_p ? 0 : m - 1);
         sketch_block(h, s, fused_p ? 1 : m, dW, dldw, P, k, df);
         timer.stop(0);
         h->partials.ensure(sizeof(double) * (size_t)np1 * k * (fused_p ? 2 : 1));
@@ -331,9 +376,22 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             L.df_sketch = df ? 1 : 0;
             L.w_next = (fused_p && i + 1 < m) ? dW + (int64_t)(i + 1) * dldw : nullptr;
             int nparts = 0;
+            need_w(i + 1);
             timer.start(1);
             rgs_launch_update_sketch(h, s, L, h->partials.as<double>(), &nparts, ls.ctl);   // steps 3, 4
             timer.stop(1);
+            if (early_q && ((i + 1) % CB == 0 || i + 1 == m)) {
+                // chunk of q' columns complete: copy it back while the factorization continues
+                const int c0 = (i / CB) * CB, cols = i + 1 - c0;
+                cudaEvent_t e;
+                RGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                qdone.push_back(e);
+                RGS_CUDA(cudaEventRecord(e, st));
+                RGS_CUDA(cudaStreamWaitEvent(h->copy_stream, e, 0));
+                RGS_CUDA(cudaMemcpy2DAsync(static_cast<char*>(Q) + esz * (size_t)c0 * ldq, esz * ldq,
+                                           static_cast<char*>(dQ) + esz * (size_t)c0 * dldq, esz * dldq, esz * n, cols,
+                                           cudaMemcpyDeviceToHost, h->copy_stream));
+            }
             LSStep a{};
             a.i = i;
             a.append = 1;                                      // steps 5, 6 (+ append to the QR of S)
@@ -372,9 +430,19 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         const bool certs = !(flags & RGS_QR_NO_CERTIFICATES);
         if (certs) rgs_launch_certificates(h, ls.S, k, m, dR, dldr, P, certo, certw);
         if (host) {
-            RGS_CUDA(cudaMemcpy2DAsync(Q, esz * ldq, dQ, esz * dldq, esz * n, m, cudaMemcpyDeviceToHost, st));
+            if (!early_q)
+                RGS_CUDA(cudaMemcpy2DAsync(Q, esz * ldq, dQ, esz * dldq, esz * n, m, cudaMemcpyDeviceToHost, st));
             RGS_CUDA(cudaMemcpy2DAsync(R, sizeof(double) * ldr, dR, sizeof(double) * dldr, sizeof(double) * m, m,
                                        cudaMemcpyDeviceToHost, st));
+        }
+        if (pipelined) {
+            // every copy on the copy stream (the last Q' chunks) is done before the call returns,
+            // and later work on the bound stream waits for it
+            cudaEvent_t e;
+            RGS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            qdone.push_back(e);
+            RGS_CUDA(cudaEventRecord(e, h->copy_stream));
+            RGS_CUDA(cudaStreamWaitEvent(st, e, 0));
         }
         int ctl[2] = {0, 0};
         double cert[2] = {NAN, NAN};

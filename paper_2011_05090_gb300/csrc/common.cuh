@@ -79,11 +79,13 @@ struct rgs_context {
     DevBuf batch_ws;       // per-instance workspaces of the batched solve
     DevBuf batch_desc;     // instance descriptors and team tables
     cudaStream_t capture_stream = nullptr; // private stream on which launches are captured into graphs
+    cudaStream_t copy_stream = nullptr;    // host <-> device copies overlapped with rgs_qr
     int launches = 0;      // kernels launched by the current call
     std::vector<cudaEvent_t> events;   // pool for per-phase timings
     ~rgs_context() {
         for (auto e : events) cudaEventDestroy(e);
         if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
     }
 };
 

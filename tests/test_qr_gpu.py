@@ -177,16 +177,28 @@ def test_breakdown_reported_with_column(h):
     run_qr(h, sk, to_gpu(A))
 
 
-def test_host_pointers_match_device_path(h):
-    n, m, k = 5000, 16, 48
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+@pytest.mark.parametrize("qdtype,qscale,pin", [(torch.float64, False, True), (torch.float32, True, True),
+                                               (torch.float32, True, False), (torch.bfloat16, False, True)])
+def test_host_pointers_match_device_path(h, kind, qdtype, qscale, pin):
+    """Host buffers (copied in column chunks behind the factorization for the SRHT) give the
+    device path's result bit for bit; m = 21 leaves a ragged last chunk."""
+    n, m, k = 5000, 21, 64
     A = synth.gdw_matrix(n, m, 1e4, 6).numpy().T.copy()
-    sk = rgs.rgs_sketch_create(h, "srht", n, k, 4)
-    d = run_qr(h, sk, to_gpu(A))
-    Wh = torch.from_numpy(A.T.copy()).pin_memory().T
-    Qh = rgs.colmajor_empty(n, m, pin=True)
-    Rh = rgs.colmajor_empty(m, m, pin=True)
-    rgs.rgs_qr(h, sk, Wh, Qh, Rh)
-    assert np.array_equal(Rh.numpy(), d["R"]) and np.array_equal(Qh.numpy(), d["Q"])
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 4)
+    d = run_qr(h, sk, to_gpu(A), qdtype, qscale)
+    Wh = torch.from_numpy(A.T.copy()).T
+    if pin:
+        Wh = Wh.pin_memory()
+    Qh = rgs.colmajor_empty(n, m, dtype=qdtype, device="cpu", pin=pin)
+    Rh = rgs.colmajor_empty(m, m, device="cpu", pin=pin)
+    qs = torch.empty(m, dtype=torch.float64).pin_memory() if qscale else None
+    for _ in range(2):                               # the second call reuses the staging buffers
+        Qh.zero_()
+        rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qs)
+        assert np.array_equal(Rh.numpy(), d["R"]) and np.array_equal(Qh.double().numpy(), d["Q"])
+        if qscale:
+            assert np.array_equal(qs.numpy(), d["qscale"])
 
 
 def test_deterministic_reruns(h):
