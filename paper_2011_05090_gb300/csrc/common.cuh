@@ -224,11 +224,6 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
 
-// Grid-wide barrier for a cooperative launch on one word: every CTA arrives with one
-// acquire-release atomic add and polls the word with acquire loads until its top bit
-// flips.  Every wait is bounded: after
-// about two seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word
-// and returns false, and every other CTA then leaves at its next barrier.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -249,34 +244,52 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_barrier(int* ctl) {
-    __shared__ int ok_sh;
-    __syncthreads();                       // the CTA's writes are ordered before thread 0's release
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned* word = reinterpret_cast<unsigned*>(ctl + kBarCount);
-        // CTA 0 adds 2^31 - (G-1), the others 1: the sum over one barrier is exactly 2^31,
-        // so the top bit flips once per barrier and the low bits return to their value.
-        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        const unsigned old = atom_add_acq_rel(word, add);
-        const long long start = clock64();
-        unsigned spins = 0;
-        while (((old ^ ld_acquire(word)) & 0x80000000u) == 0u) {
-            if ((++spins & 63u) == 0) {
-                if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
-                if (clock64() - start > 4000000000LL) {
-                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
-                    atomicExch(ctl + kAbortWord, 1);
-                    ok = 0;
-                    break;
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch on one word (the control word kBarCount, zero in
+// its low 31 bits between barriers).  Every CTA arrives with a release reduction, whose reply
+// nobody waits for: CTA 0 adds 2^31 - (G-1), the others 1, so the sum over one barrier is
+// exactly 2^31 and the top bit flips when the last CTA arrives.  Thread 0 of each CTA reads the
+// top bit once, before its first arrival (the bit cannot change before that arrival), and then
+// polls with acquire loads for the alternating value.  Every wait is bounded: after about two
+// seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word and returns false,
+// and every other CTA then leaves at its next barrier.
+struct GridBarrier {
+    unsigned* word;
+    unsigned expect;                       // thread 0: the top bit that completes the next barrier
+    __device__ explicit GridBarrier(int* ctl) : word(reinterpret_cast<unsigned*>(ctl + kBarCount)), expect(0u) {
+        if (threadIdx.x == 0) expect = (ld_relaxed(word) & 0x80000000u) ^ 0x80000000u;
+    }
+    __device__ bool sync(int* ctl) {
+        __shared__ int ok_sh;
+        __syncthreads();                   // the CTA's writes are ordered before thread 0's release
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            red_add_release(word, blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u);
+            const long long start = clock64();
+            unsigned spins = 0;
+            while ((ld_acquire(word) & 0x80000000u) != expect) {
+                if ((++spins & 63u) == 0) {
+                    if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
+                    if (clock64() - start > 4000000000LL) {
+                        atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                        atomicExch(ctl + kAbortWord, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
+            expect ^= 0x80000000u;
+            ok_sh = ok;
         }
-        ok_sh = ok;
+        __syncthreads();
+        return ok_sh != 0;
     }
-    __syncthreads();
-    return ok_sh != 0;
-}
+};
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -344,7 +357,8 @@ struct LSState {
     int k, mmax;
     double *V, *VT, *T, *TT, *RinvT, *S;   // V column-major k x mmax; VT its row-major copy (ld mmax)
     double *sbuf, *pbuf, *ys, *yp;
-    double *us, *up, *u2s, *u2p;
+    double *M;              // M = V T (column-major k x mmax): Q_H^T x = x - V (M^T x)
+    double *u2s, *u2p;
     double *zp, *d1, *d2;   // per-column dots of phase 4
     double *red;            // first-level sums of partial sketches
     double *blk;            // 4 * grid

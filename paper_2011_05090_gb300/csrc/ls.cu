@@ -2,13 +2,16 @@
 // argmin_y ||S_{i-1} y - p_i|| solved through a Householder QR of S (the solver
 // of the paper's experiments, Sec. 5), kept incrementally in compact-WY form
 //     H_0 H_1 ... H_{i-1} = I - V T V^T,    S_i = (H_0 ... H_{i-1}) [R_S; 0],
-// together with R_S^{-1}.  With that form every phase is a parallel matrix-vector
+// together with M = V T and R_S^{-1}.  With that form every phase is a parallel matrix-vector
 // product spread over the whole GPU instead of i dependent reflector applications:
-//   y  = (I - V T^T V^T) [s, p]          (apply the i existing reflectors)
+//   y  = [s, p] - V (M^T [s, p])         (apply the i existing reflectors: I - V T^T V^T)
 //   new reflector H_i from y_s(i:k)      (appends s_i, column i of R_S = [y_s(0:i); beta])
 //   x  = R_S^{-1} (H_i y_p)(0:i+1)       (the least-squares solution)
-//   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta.
-// One cooperative launch per column; phases are separated by bounded grid barriers.
+//   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta,
+//   M(:, i) = V T(:, i) (formed at the start of the next launch).
+// One cooperative launch per column; phases are separated by bounded grid barriers.  GB300 runs
+// FP64 at 2 operations per clock per SM and an L2 round trip costs about a microsecond, so the
+// phases are arranged to keep dependent round trips and redundant FP64 scalar work short.
 #include "common.cuh"
 #include "givens.cuh"
 
@@ -72,16 +75,26 @@ __device__ __forceinline__ void block_sum_lane0(double (&v)[N], double* sm) {
     for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
 }
 
+constexpr int kTotMax = 8;     // grid_total2 reads up to 32 * kTotMax CTAs' values in one round trip
+
 // Deterministic totals of the per-CTA values blk[b*4 + off] and blk[b*4 + off + 1],
-// identical in every CTA; one warp does the FP64 adds and broadcasts through shared memory.
+// identical in every CTA; one warp issues all the loads at once, does the FP64 adds and
+// broadcasts through shared memory.
 __device__ double2 grid_total2(const double* blk, int off, double* sh) {
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v0 = 0.0, v1 = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-            v0 += ldcg(blk + (size_t)b * 4 + off);
-            v1 += ldcg(blk + (size_t)b * 4 + off + 1);
+        const int G = gridDim.x;
+        double a0[kTotMax], a1[kTotMax];
+#pragma unroll
+        for (int q = 0; q < kTotMax; ++q) {
+            const int b = threadIdx.x + 32 * q;
+            a0[q] = b < G ? ldcg(blk + (size_t)b * 4 + off) : 0.0;
+            a1[q] = b < G ? ldcg(blk + (size_t)b * 4 + off + 1) : 0.0;
         }
+        double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < kTotMax; ++q)
+            if (32 * q < G) { v0 += a0[q]; v1 += a1[q]; }
         v0 = warp_sum(v0);
         v1 = warp_sum(v1);
         if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
@@ -92,13 +105,15 @@ __device__ double2 grid_total2(const double* blk, int off, double* sh) {
     return t;
 }
 
-// Sum of the GS partial sketches of group g at row l (double-float or FP64 partials).
+// Sum over b in [b0, b1) of src[b * k + l]: partial sketches (double-float or FP64) written by an
+// earlier launch, or (CG) FP64 group sums written by this launch, read through L2.
+template <bool CG = false>
 __device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
     if (sdf) {
         const df* d = reinterpret_cast<const df*>(src);
         df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
         int b = b0;
-#pragma unroll 4
+#pragma unroll 16
         for (; b + 1 < b1; b += 2) {
             t0 = df_add(t0, d[(size_t)b * k + l]);
             t1 = df_add(t1, d[(size_t)(b + 1) * k + l]);
@@ -107,15 +122,17 @@ __device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0,
         t0 = df_add(t0, t1);
         return (double)t0.h + (double)t0.l;
     }
+    auto ld = [&](int b) { return CG ? ldcg(src + (size_t)b * k + l) : src[(size_t)b * k + l]; };
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     int b = b0;
+#pragma unroll 2
     for (; b + 3 < b1; b += 4) {
-        v0 += src[(size_t)b * k + l];
-        v1 += src[(size_t)(b + 1) * k + l];
-        v2 += src[(size_t)(b + 2) * k + l];
-        v3 += src[(size_t)(b + 3) * k + l];
+        v0 += ld(b);
+        v1 += ld(b + 1);
+        v2 += ld(b + 2);
+        v3 += ld(b + 3);
     }
-    for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
+    for (; b < b1; ++b) v0 += ld(b);
     return (v0 + v1) + (v2 + v3);
 }
 
@@ -134,6 +151,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const bool p_parts = sol && a.p_vec == nullptr;
     unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
     if (trace) trace[0] = globaltimer();
+    GridBarrier bar(ctl);
+    const double pref = (app && tid == 0) ? st.pnorm[i] : 0.0;   // ||p_i||, for the breakdown test
 
     // ---- phase 0a: with more than GS partial sketches, a first level sums groups of GS
     const int sgroups = app ? (a.s_nparts + GS - 1) / GS : 0;
@@ -151,63 +170,86 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 st.red[(size_t)g * k + l] = group_sum(is_s ? a.s_part : a.p_part, is_s ? a.s_df : a.p_df,
                                                       gg * GS, min(np, gg * GS + GS), k, l);
         }
-        if (!grid_barrier(ctl)) return;
+        if (!bar.sync(ctl)) return;
     }
     if (trace) trace[1] = globaltimer();
 
-    // ---- phase 0b: warp per row, lanes over groups (or partials): s', p and their squared norms
+    // ---- phase 0b: a warp per 32 rows (lane = row), each lane summing the groups (or partials)
+    //      of its row in order: s', p and their squared norms
     {
         double nrm[2] = {0.0, 0.0};
-        for (int l = gwarp; l < k; l += nwarps) {
+        const int nseg = (k + 31) / 32;
+        const bool busy = gwarp < nseg;
+        for (int seg = gwarp; seg < nseg; seg += nwarps) {
+            const int l = seg * 32 + lane;
+            if (l >= k) continue;
             if (app) {
-                double v = 0.0;
-                if (level1) {
-                    for (int g = lane; g < sgroups; g += 32) v += ldcg(st.red + (size_t)g * k + l);
-                } else if (lane < a.s_nparts) {
-                    v = a.s_df ? (double)reinterpret_cast<const df*>(a.s_part)[(size_t)lane * k + l].h +
-                                     (double)reinterpret_cast<const df*>(a.s_part)[(size_t)lane * k + l].l
-                               : a.s_part[(size_t)lane * k + l];
-                }
-                v = warp_sum(v) * a.s_scale;
-                if (lane == 0) { st.sbuf[l] = v; nrm[0] = fma(v, v, nrm[0]); }
+                const double v = (level1 ? group_sum<true>(st.red, false, 0, sgroups, k, l)
+                                         : group_sum(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l)) * a.s_scale;
+                st.sbuf[l] = v;
+                nrm[0] = fma(v, v, nrm[0]);
             }
             if (sol) {
-                double v = 0.0;
-                if (!p_parts) {
-                    v = lane == 0 ? a.p_vec[l] : 0.0;
-                } else if (level1) {
-                    for (int g = lane; g < pgroups; g += 32) v += ldcg(st.red + (size_t)(sgroups + g) * k + l);
-                } else if (lane < a.p_nparts) {
-                    v = a.p_df ? (double)reinterpret_cast<const df*>(a.p_part)[(size_t)lane * k + l].h +
-                                     (double)reinterpret_cast<const df*>(a.p_part)[(size_t)lane * k + l].l
-                               : a.p_part[(size_t)lane * k + l];
-                }
-                v = warp_sum(v) * a.p_scale;
-                if (lane == 0) {
-                    st.pbuf[l] = v;
-                    if (a.p_store) a.p_store[l] = v;
-                    nrm[1] = fma(v, v, nrm[1]);
-                }
+                const double v = (!p_parts ? a.p_vec[l]
+                                  : level1 ? group_sum<true>(st.red + (size_t)sgroups * k, false, 0, pgroups, k, l)
+                                           : group_sum(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l)) * a.p_scale;
+                st.pbuf[l] = v;
+                if (a.p_store) a.p_store[l] = v;
+                nrm[1] = fma(v, v, nrm[1]);
             }
+        }
+        if (i > 0) {
+            // M(:, i-1) = V(:, 0:i) T(0:i, i-1): T's column i-1 was completed by the previous
+            // launch; warp per row of the row-major copy VT, lanes over the columns
+            const double* tc = st.T + (size_t)(i - 1) * mm;
+            for (int l = gwarp; l < k; l += nwarps) {
+                const double* vr = st.VT + (size_t)l * mm;
+                const int jend = min(i, l + 1);
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                int j = lane;
+                for (; j + 96 < jend; j += 128)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fma(vr[j + 32 * q], tc[j + 32 * q], acc[q]);
+                for (; j < jend; j += 32) acc[0] = fma(vr[j], tc[j], acc[0]);
+                const double d = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+                if (lane == 0) st.M[(size_t)(i - 1) * k + l] = d;
+            }
+        }
+        if (busy) {                                    // idle warps skip the FP64 shuffles
+            nrm[0] = warp_sum(nrm[0]);
+            nrm[1] = warp_sum(nrm[1]);
         }
         block_sum_lane0<2>(nrm, sh);
         if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm[0]; st.blk[blockIdx.x * 4 + 1] = nrm[1]; }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!bar.sync(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
-    // ---- phase 1: r_ii, s_i = s'/r_ii; u = V(:, 0:i)^T [s, p]
+    // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
     const double2 tot01 = grid_total2(st.blk, 0, sh);
-    const double r = sqrt(tot01.x);
-    const double pn = sqrt(tot01.y);
+    // The phase's scalars come from one thread through shared memory: an FP64 square root or
+    // division is a long sequence on the FP64 pipe, which would otherwise run in every thread.
+    if (tid == 0) {
+        const double r0 = sqrt(tot01.x);
+        int code = 0;                                  // 1: non-finite r_ii, 2: breakdown
+        if (app) code = !isfinite(r0) ? 1 : (!(r0 > 16.0 * 0x1p-53 * pref) ? 2 : 0);
+        const double ir = code == 0 ? 1.0 / r0 : 1.0;
+        sc[0] = r0;
+        sc[1] = app ? ir : 1.0;
+        sc[2] = (app && a.p_lag) ? ir : 1.0;
+        sc[3] = sol ? sqrt(tot01.y) : 0.0;
+        sc[4] = (double)code;
+    }
+    __syncthreads();
+    const double r = sc[0], pn = sc[3];
+    const int code = (int)sc[4];
     double inv_r = 1.0, pmul = 1.0;
     if (app) {
-        const double pref = st.pnorm[i];
-        if (!isfinite(r)) {
+        if (code == 1) {
             if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_NONFINITE); ctl[kDetailWord] = i; }
             return;
         }
-        const bool breakdown = !(r > 16.0 * 0x1p-53 * pref);
+        const bool breakdown = code == 2;
         if (a.givens) {
             // GMRES: H(:, i-1) = R(0:i+1, i) (Sec. 4.1) is complete now that r_ii is known
             if (i == 0) {
@@ -226,31 +268,30 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             return;
         }
-        inv_r = 1.0 / r;
-        if (a.p_lag) pmul = inv_r;
+        inv_r = sc[1];
+        pmul = sc[2];
         if (gtid == 0) {
             st.R[(size_t)i * st.ldr + i] = r;
             st.sigma[i] = inv_r;
         }
-        for (int l = gtid; l < k; l += nthreads) st.S[(size_t)i * k + l] = ldcg(st.sbuf + l) * inv_r;
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
     {
         // a quad of warps (one per SM sub-partition) per column; each warp a quarter of the rows
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
         double* qs = sh + 3 * (NW + 1) + 2;                // [NW/4 quads][4 warps][2]
+        const int seg = (k + 3) / 4;
         for (int base = 0; base < i; base += G * (NW / 4)) {
             const int j = base + blockIdx.x + G * quad;
             double ds = 0.0, dp = 0.0;
             if (j < i) {
-                const double* v = st.V + (size_t)j * k;
-                const int len = k - j, seg = (len + 3) / 4;
-                const int l0 = j + qw * seg, l1 = min(k, l0 + seg);
-#pragma unroll 4
+                const double* mc = st.M + (size_t)j * k;      // column i-1 was written by phase 0b
+                const int l0 = qw * seg, l1 = min(k, l0 + seg);
+#pragma unroll 8
                 for (int l = l0 + lane; l < l1; l += 32) {
-                    const double vv = v[l];
-                    if (app) ds = fma(vv, ldcg(st.sbuf + l), ds);
-                    if (sol) dp = fma(vv, ldcg(st.pbuf + l), dp);
+                    const double mv = ldcg(mc + l);
+                    if (app) ds = fma(mv, ldcg(st.sbuf + l), ds);
+                    if (sol) dp = fma(mv, ldcg(st.pbuf + l), dp);
                 }
                 ds = warp_sum(ds);
                 dp = warp_sum(dp);
@@ -259,36 +300,16 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             __syncthreads();
             if (j < i && qw == 0 && lane == 0) {
                 const double* q4 = qs + quad * 8;
-                st.us[j] = ((q4[0] + q4[2]) + (q4[4] + q4[6])) * inv_r;
-                st.up[j] = ((q4[1] + q4[3]) + (q4[5] + q4[7])) * pmul;
+                st.u2s[j] = ((q4[0] + q4[2]) + (q4[4] + q4[6])) * inv_r;
+                st.u2p[j] = ((q4[1] + q4[3]) + (q4[5] + q4[7])) * pmul;
             }
             __syncthreads();
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!bar.sync(ctl)) return;
     if (trace) trace[3] = globaltimer();
 
-    // ---- phase 2: u2 = T(0:i, 0:i)^T u   (warp per column of T)
-    for (int j = gwarp; j < i; j += nwarps) {
-        const double* t = st.T + (size_t)j * mm;
-        double ds = 0.0, dp = 0.0, ds1 = 0.0, dp1 = 0.0;
-        int l = lane;
-        for (; l + 32 <= j; l += 64) {
-            const double t0 = t[l], t1 = t[l + 32];
-            if (app) { ds = fma(t0, ldcg(st.us + l), ds); ds1 = fma(t1, ldcg(st.us + l + 32), ds1); }
-            if (sol) { dp = fma(t0, ldcg(st.up + l), dp); dp1 = fma(t1, ldcg(st.up + l + 32), dp1); }
-        }
-        if (l <= j) {
-            const double tv = t[l];
-            if (app) ds = fma(tv, ldcg(st.us + l), ds);
-            if (sol) dp = fma(tv, ldcg(st.up + l), dp);
-        }
-        ds = warp_sum(ds + ds1);
-        dp = warp_sum(dp + dp1);
-        if (lane == 0) { st.u2s[j] = ds; st.u2p[j] = dp; }
-    }
-    if (!grid_barrier(ctl)) return;
-    if (trace) trace[4] = globaltimer();
+    if (trace) trace[4] = trace[3];                  // (no separate T^T u phase: M holds V T)
 
     // ---- phase 3: y = [s, p] - V u2 (the i reflectors applied), warp per row using the
     //      row-major copy VT of V; plus the sums the new reflector needs over rows > i
@@ -315,7 +336,9 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             const double ws = warp_sum((as[0] + as[1]) + (as[2] + as[3]));
             const double wp = warp_sum((ap[0] + ap[1]) + (ap[2] + ap[3]));
             if (lane == 0) {
-                const double ysl = app ? ldcg(st.sbuf + l) * inv_r - ws : 0.0;
+                const double sl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
+                if (app) st.S[(size_t)i * k + l] = sl;     // s_i (Alg. 2 step 6)
+                const double ysl = app ? sl - ws : 0.0;
                 const double ypl = sol ? ldcg(st.pbuf + l) * pmul - wp : 0.0;
                 st.ys[l] = ysl;
                 st.yp[l] = ypl;
@@ -325,7 +348,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         block_sum_lane0<2>(sums, sh);
         if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sums[0]; st.blk[blockIdx.x * 4 + 3] = sums[1]; }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!bar.sync(ctl)) return;
     if (trace) trace[5] = globaltimer();
 
     if (!app) {
@@ -390,14 +413,18 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             __syncthreads();
         }
     }
-    if (!grid_barrier(ctl)) return;
+    if (!bar.sync(ctl)) return;
     if (trace) trace[6] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
+    double alpha = 0.0, ypi0 = 0.0;
+    if (tid == 0) {                                    // issued before the totals' round trip
+        alpha = ldcg(st.ys + i);
+        ypi0 = sol ? ldcg(st.yp + i) : 0.0;
+    }
     const double2 tot23 = grid_total2(st.blk, 2, sh);
     const double SG = tot23.x, CR = tot23.y;
     if (tid == 0) {
-        const double alpha = ldcg(st.ys + i);
         double beta, tau, vs;
         if (SG == 0.0) {
             beta = alpha; tau = 0.0; vs = 0.0;
@@ -408,7 +435,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             vs = 1.0 / (alpha - beta);
         }
         sc[0] = beta; sc[1] = tau; sc[2] = vs;
-        sc[3] = sol ? ldcg(st.yp + i) - tau * (ldcg(st.yp + i) + CR * vs) : 0.0;
+        sc[3] = sol ? ypi0 - tau * (ypi0 + CR * vs) : 0.0;
     }
     __syncthreads();
     const double beta = sc[0], tau = sc[1], vs = sc[2], ypi = sc[3];
@@ -505,7 +532,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
     const size_t oV = take((size_t)k * mmax), oVT = take((size_t)k * mmax), oT = take((size_t)mmax * mmax),
                  oTT = take((size_t)mmax * mmax), oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax),
-                 osb = take(k), opb = take(k), oys = take(k), oyp = take(k), ous = take(mmax), oup = take(mmax),
+                 osb = take(k), opb = take(k), oys = take(k), oyp = take(k), oM = take((size_t)k * mmax),
                  ou2s = take(mmax), ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
                  ored = take((size_t)groups * k), oblk = take((size_t)4 * grid), osg = take(mmax + 1),
                  opn = take(mmax + 2), oco = take(mmax + 1);
@@ -514,7 +541,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState
     st->k = k; st->mmax = mmax; st->max_parts = max_parts;
     st->V = b + oV; st->VT = b + oVT; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
-    st->us = b + ous; st->up = b + oup; st->u2s = b + ou2s; st->u2p = b + ou2p;
+    st->M = b + oM; st->u2s = b + ou2s; st->u2p = b + ou2p;
     st->zp = b + ozp; st->d1 = b + od1; st->d2 = b + od2;
     st->red = b + ored; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
     st->coef = b + oco;
@@ -536,6 +563,7 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     LSStep p = a;
     void* args[] = {&s, &p};
     const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
+    RGS_REQUIRE(grid <= 32 * kTotMax, "least-squares grid larger than the per-CTA totals support");
     RGS_CUDA(cudaLaunchCooperativeKernel((const void*)ls_kernel, dim3(grid), dim3(LT), args, 0, ctx->stream));
     ctx->launches++;
 }
