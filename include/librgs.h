@@ -110,10 +110,13 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  * the upper-triangular R (m x m, FP64, positive diagonal) with W = Q R and
  * Theta Q orthonormal.  Step 2 uses a Householder QR of S_{i-1} (Sec. 5),
  * step 3 runs in the storage precision qtype (FP64, or FP32 accumulation for
- * RGS_F32 / RGS_BF16 storage: the working precision u_crs), steps 1, 4-8 run
- * in FP64 (u_fine).  With FP32 / BF16 storage the SRHT's Walsh-Hadamard sums
- * use double-float arithmetic (about 2^-48 relative error, against 2^-24 for
- * u_crs) unless RGS_QR_FP64_SKETCH is set; everything after them is FP64.
+ * RGS_F32 / RGS_BF16 storage: the working precision u_crs), steps 1, 2, 4-8 in
+ * a fine precision u_fine: FP64 for FP64 storage.  With FP32 / BF16 storage the
+ * SRHT's Walsh-Hadamard sums and the least-squares steps 2, 5, 6 use double-float
+ * arithmetic (a value is hi + lo in two FP32 words: about 2^-48 relative error
+ * per operation, against 2^-24 for u_crs; GB300's FP64 rate is 1/64 of its FP32
+ * rate), squared norms and every returned value stay FP64; RGS_QR_FP64_FINE makes
+ * all of it FP64 in every storage mode.
  *   Q      n x m in qtype, ldq >= n.  If qscale is non-NULL, Q receives the
  *          unnormalised q'_i and qscale[i] = 1/r_ii (FP64), so the basis is
  *          Q diag(qscale) exactly (the Step 7 division is never rounded to
@@ -121,13 +124,15 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  *   R      m x m, ldr >= m (strictly lower part set to 0).
  *   S      optional (NULL): k x m, lds >= k, receives S = Theta Q (FP64).
  *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings;
- *          RGS_QR_FP64_SKETCH: FP64 transform sums in every storage mode.
+ *          RGS_QR_FP64_FINE (= RGS_QR_FP64_SKETCH): FP64 transform sums and least
+ *          squares in every storage mode.
  *   info   optional host struct: step-8 certificates and breakdown column.
  * W, Q, R, S, qscale may be all device or all host pointers.  Returns
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
 #define RGS_QR_NO_CERTIFICATES 1
 #define RGS_QR_TIMINGS 2         /* bit 1: time each phase with CUDA events (fills the *_ms fields) */
-#define RGS_QR_FP64_SKETCH 4     /* bit 2: FP64 Walsh-Hadamard sums also for FP32/BF16 storage */
+#define RGS_QR_FP64_FINE 4       /* bit 2: FP64 transform sums and least squares for every storage */
+#define RGS_QR_FP64_SKETCH RGS_QR_FP64_FINE
 typedef struct {
     double delta;          /* Delta_m  = ||I - S^T S||_F            (Alg. 2 step 8) */
     double delta_tilde;    /* Delta~_m = ||P - S R||_F / ||P||_F    (Alg. 2 step 8) */
@@ -155,7 +160,8 @@ typedef struct {
  * Alg. 3: builds Q_j (Theta-orthonormal Krylov basis) and R_j one column at a
  * time; H_j = R_j(1:j, 2:j) (Sec. 4.1).  The object owns the basis (n x mmax in
  * qtype, stored as q'_i with scale 1/r_ii), S, R, the Householder factors of S
- * and a work vector.
+ * and a work vector.  The least-squares steps run in FP64 for an FP64 basis and
+ * in double-float arithmetic (about 2^-48) for FP32 / BF16 bases, as in rgs_qr.
  *   rgs_arnoldi_start: iteration 1 with w_1 (device FP64, n).
  *   rgs_arnoldi_step:  next iteration with w_i = A q_{i-1} (A given, FP64 SpMV),
  *                      or with the caller's w (device FP64) when A is NULL.

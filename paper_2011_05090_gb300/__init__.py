@@ -45,7 +45,8 @@ RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
 RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
 RGS_QR_NO_CERTIFICATES = 1
 RGS_QR_TIMINGS = 2
-RGS_QR_FP64_SKETCH = 4
+RGS_QR_FP64_FINE = 4            # FP64 transform sums and least squares for every storage
+RGS_QR_FP64_SKETCH = RGS_QR_FP64_FINE
 RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
 
 _DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF16}

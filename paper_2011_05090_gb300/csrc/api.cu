@@ -329,7 +329,8 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
 
         // workspaces: Householder engine, P = Theta W, partial sketches, certificates
         LSState ls{};
-        rgs_ls_alloc(h->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm, &ls);
+        rgs_ls_alloc(h->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm,
+                     qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH), &ls);
         ls.ctl = h->ctl.as<int>();
         ls.R = dR;
         ls.ldr = dldr;

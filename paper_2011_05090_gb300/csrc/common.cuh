@@ -367,6 +367,7 @@ struct LSState {
     int64_t ldr;
     double *cs, *sn, *g, *Hr;       // Givens state of the Hessenberg problem (GMRES); Hr ld mmax
     int max_parts;
+    int fine_df;            // internal arrays hold double-float values (FP32 / BF16 bases), else FP64
     int* ctl;
 };
 struct LSStep {
@@ -390,7 +391,7 @@ struct LSStep {
     int arnoldi;            // a vanishing r_ii ends the cycle (happy breakdown) instead of failing
     double stop_tol;        // GMRES: stop the cycle when the rotated residual falls to this value
 };
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st);
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fine_df, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a);
 int rgs_ls_max_blocks(int num_sms);

@@ -75,7 +75,7 @@ void arnoldi_alloc(rgs_arnoldi_obj* a) {
     const int k = a->sk->k, m = a->mmax;
     a->ldq = (a->n + 7) & ~(int64_t)7;
     a->Q.ensure(dsize(a->qtype) * (size_t)a->ldq * m);
-    rgs_ls_alloc(a->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm, &a->ls);
+    rgs_ls_alloc(a->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm, a->qtype != RGS_F64, &a->ls);
     a->R.ensure(sizeof(double) * (size_t)m * m);
     a->gv.ensure(sizeof(double) * (4 * (size_t)m + 2 + (size_t)m * m + 2 * (size_t)m));
     double* g = a->gv.as<double>();

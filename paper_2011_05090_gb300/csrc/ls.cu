@@ -1,4 +1,4 @@
-// Alg. 2 steps 2, 5, 6 on the GPU in FP64: the sketched least-squares problem
+// Alg. 2 steps 2, 5, 6 on the GPU: the sketched least-squares problem
 // argmin_y ||S_{i-1} y - p_i|| solved through a Householder QR of S (the solver
 // of the paper's experiments, Sec. 5), kept incrementally in compact-WY form
 //     H_0 H_1 ... H_{i-1} = I - V T V^T,    S_i = (H_0 ... H_{i-1}) [R_S; 0],
@@ -9,13 +9,24 @@
 //   x  = R_S^{-1} (H_i y_p)(0:i+1)       (the least-squares solution)
 //   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta,
 //   M(:, i) = V T(:, i) (formed at the start of the next launch).
-// One cooperative launch per column; phases are separated by bounded grid barriers.  GB300 runs
-// FP64 at 2 operations per clock per SM and an L2 round trip costs about a microsecond, so the
-// phases are arranged to keep dependent round trips and redundant FP64 scalar work short.
+// One cooperative launch per column; phases are separated by bounded grid barriers.
+//
+// Fine-precision arithmetic (u_fine).  GB300 runs FP64 at 2 operations per clock per SM, with
+// about 65 cycles between dependent FP64 operations, against 128 FP32 operations per clock and
+// about 5 cycles.  The kernel is therefore written once over an arithmetic type A:
+//   FineF64  FP64 storage and arithmetic (FP64 bases, or on request);
+//   FineDF   double-float storage and arithmetic (value hi + lo in two FP32 words, about 2^-48
+//            relative error per operation), for FP32 / BF16 bases, where u_crs = 2^-24 or
+//            2^-8: products by Dekker's TwoProduct through fmaf, sums by Knuth's TwoSum, dot
+//            products accumulated as in Ogita, Rump and Oishi's Dot2 (a TwoSum chain of the
+//            products' high parts plus one FP32 sum of all low-order terms).
+// Squared norms (r_ii and ||p||) are summed in FP64 in both, for the exponent range, and every
+// value leaving the kernel (R, x, sigma, S, ||p||) is FP64.
 #include "common.cuh"
 #include "givens.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 using namespace rgsdev;
 
@@ -24,38 +35,126 @@ namespace {
 constexpr int LT = 512;        // threads per CTA (one CTA per SM)
 constexpr int NW = LT / 32;    // warps per CTA
 constexpr int GS = 32;         // partial sketches summed per warp in the first reduction level
+constexpr int kTotMax = 8;     // per-CTA totals are read for up to 32 * kTotMax CTAs at once
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Block-wide sums of N values at once (trees: shuffles within warps, then one warp),
-// identical in every thread; sm holds at least N * (NW + 1) doubles.
-template <int N>
-__device__ __forceinline__ void block_sum_n(double (&v)[N], double* sm) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < N; ++q) v[q] = warp_sum(v[q]);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < N; ++q) sm[q * NW + w] = v[q];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-            double t = lane < NW ? sm[q * NW + lane] : 0.0;
-            t = warp_sum(t);
-            if (lane == 0) sm[N * NW + q] = t;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
+// ------------------------------------------------------------------ arithmetic types
+struct FineF64 {
+    using T = double;
+    struct Acc {
+        double v;
+    };
+    __device__ static T zero() { return 0.0; }
+    __device__ static T one() { return 1.0; }
+    __device__ static T from_d(double x) { return x; }
+    __device__ static double to_d(T x) { return x; }
+    __device__ static T add(T a, T b) { return a + b; }
+    __device__ static T sub(T a, T b) { return a - b; }
+    __device__ static T mul(T a, T b) { return a * b; }
+    __device__ static T neg(T a) { return -a; }
+    __device__ static T div(T a, T b) { return a / b; }
+    __device__ static T sqrt_(T a) { return sqrt(a); }
+    __device__ static bool is_zero(T a) { return a == 0.0; }
+    __device__ static bool nonneg(T a) { return a >= 0.0; }
+    __device__ static T wsum(T v) { return warp_sum(v); }
+    __device__ static T ld(const double* p) { return *p; }
+    __device__ static T ldg(const double* p) { return __ldcg(p); }     // written earlier in this launch
+    __device__ static void st(double* p, T v) { *p = v; }
+    __device__ static Acc acc0() { return {0.0}; }
+    __device__ static void acc(Acc& s, T a, T b) { s.v = fma(a, b, s.v); }
+    __device__ static T val(Acc s) { return s.v; }
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv))};
+}
+__device__ __forceinline__ df df_fast(float a, float b) {      // |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
+struct FineDF {
+    using T = df;
+    struct Acc {
+        float s, c;           // running sum of the products' high parts, FP32 sum of the rest
+    };
+    __device__ static T zero() { return {0.f, 0.f}; }
+    __device__ static T one() { return {1.f, 0.f}; }
+    __device__ static T from_d(double x) {
+        const float h = __double2float_rn(x);
+        return {h, __double2float_rn(x - (double)h)};
+    }
+    __device__ static double to_d(T x) { return (double)x.h + (double)x.l; }
+    __device__ static T add(T a, T b) {
+        const df s = df_two_sum(a.h, b.h);
+        return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+    }
+    __device__ static T neg(T a) { return {-a.h, -a.l}; }
+    __device__ static T sub(T a, T b) { return add(a, neg(b)); }
+    __device__ static T mul(T a, T b) {
+        const float p = __fmul_rn(a.h, b.h);
+        float e = __fmaf_rn(a.h, b.h, -p);
+        e = __fmaf_rn(a.h, b.l, e);
+        e = __fmaf_rn(a.l, b.h, e);
+        return df_fast(p, e);
+    }
+    // a / b: quotient of the high words, corrected once by the remainder a - q b
+    __device__ static T div(T a, T b) {
+        const float q1 = __fdiv_rn(a.h, b.h);
+        const T r = sub(a, mul(b, {q1, 0.f}));
+        const float q2 = __fdiv_rn(r.h, b.h);
+        return df_fast(q1, q2);
+    }
+    // sqrt(a): FP32 root of the high word and one Newton correction in double-float
+    __device__ static T sqrt_(T a) {
+        if (!(a.h > 0.f)) return {sqrtf(a.h), 0.f};
+        const float y = sqrtf(a.h);
+        const float p = __fmul_rn(y, y);
+        const float e = __fmaf_rn(y, y, -p);
+        const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), e), a.l);
+        return df_fast(y, __fdiv_rn(d, __fmul_rn(2.f, y)));
+    }
+    __device__ static bool is_zero(T a) { return a.h == 0.f && a.l == 0.f; }
+    __device__ static bool nonneg(T a) { return a.h > 0.f || (a.h == 0.f && a.l >= 0.f); }
+    __device__ static T wsum(T v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T t = {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+            v = add(v, t);    // TwoSum is exact, so both lanes of a pair get the same bits
+        }
+        return v;
+    }
+    __device__ static T ld(const double* p) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        return {v.x, v.y};
+    }
+    __device__ static T ldg(const double* p) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+        return {v.x, v.y};
+    }
+    __device__ static void st(double* p, T v) { *reinterpret_cast<float2*>(p) = make_float2(v.h, v.l); }
+    __device__ static Acc acc0() { return {0.f, 0.f}; }
+    __device__ static void acc(Acc& s, T a, T b) {
+        const float p = __fmul_rn(a.h, b.h);
+        float e = __fmaf_rn(a.h, b.h, -p);
+        e = __fmaf_rn(a.h, b.l, e);
+        e = __fmaf_rn(a.l, b.h, e);
+        const df t = df_two_sum(s.s, p);
+        s.s = t.h;
+        s.c = __fadd_rn(s.c, __fadd_rn(t.l, e));
+    }
+    __device__ static T val(Acc s) { return df_fast(s.s, s.c); }
+};
+
+// ------------------------------------------------------------------ reductions
 // Block-wide sums of N values held by lane 0 of each warp (other lanes ignored): one warp
-// adds the NW per-warp values, so only NW/32-wide FP64 work is spent on the reduction.
-template <int N>
-__device__ __forceinline__ void block_sum_lane0(double (&v)[N], double* sm) {
+// adds the NW per-warp values.  Identical in every thread; sm holds >= N * (NW + 1) values.
+template <class A, int N>
+__device__ __forceinline__ void block_sum_lane0(typename A::T (&v)[N], typename A::T* sm) {
+    using T = typename A::T;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0)
@@ -65,8 +164,8 @@ __device__ __forceinline__ void block_sum_lane0(double (&v)[N], double* sm) {
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            double t = lane < NW ? sm[q * NW + lane] : 0.0;
-            t = warp_sum(t);
+            T t = lane < NW ? sm[q * NW + lane] : A::zero();
+            t = A::wsum(t);
             if (lane == 0) sm[N * NW + q] = t;
         }
     }
@@ -75,40 +174,39 @@ __device__ __forceinline__ void block_sum_lane0(double (&v)[N], double* sm) {
     for (int q = 0; q < N; ++q) v[q] = sm[N * NW + q];
 }
 
-constexpr int kTotMax = 8;     // grid_total2 reads up to 32 * kTotMax CTAs' values in one round trip
-
-// Deterministic totals of the per-CTA values blk[b*4 + off] and blk[b*4 + off + 1],
-// identical in every CTA; one warp issues all the loads at once, does the FP64 adds and
-// broadcasts through shared memory.
-__device__ double2 grid_total2(const double* blk, int off, double* sh) {
+// Deterministic totals of the per-CTA values blk[b*4 + off], blk[b*4 + off + 1] (type A::T),
+// identical in every CTA; one warp issues all the loads at once, adds and broadcasts.
+template <class A>
+__device__ void grid_total2(const double* blk, int off, typename A::T* sh, typename A::T& t0, typename A::T& t1) {
+    using T = typename A::T;
     __syncthreads();
     if (threadIdx.x < 32) {
         const int G = gridDim.x;
-        double a0[kTotMax], a1[kTotMax];
+        T a0[kTotMax], a1[kTotMax];
 #pragma unroll
         for (int q = 0; q < kTotMax; ++q) {
             const int b = threadIdx.x + 32 * q;
-            a0[q] = b < G ? ldcg(blk + (size_t)b * 4 + off) : 0.0;
-            a1[q] = b < G ? ldcg(blk + (size_t)b * 4 + off + 1) : 0.0;
+            a0[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off) : A::zero();
+            a1[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off + 1) : A::zero();
         }
-        double v0 = 0.0, v1 = 0.0;
+        T v0 = A::zero(), v1 = A::zero();
 #pragma unroll
         for (int q = 0; q < kTotMax; ++q)
-            if (32 * q < G) { v0 += a0[q]; v1 += a1[q]; }
-        v0 = warp_sum(v0);
-        v1 = warp_sum(v1);
+            if (32 * q < G) { v0 = A::add(v0, a0[q]); v1 = A::add(v1, a1[q]); }
+        v0 = A::wsum(v0);
+        v1 = A::wsum(v1);
         if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
     }
     __syncthreads();
-    const double2 t = make_double2(sh[0], sh[1]);
+    t0 = sh[0];
+    t1 = sh[1];
     __syncthreads();
-    return t;
 }
 
-// Sum over b in [b0, b1) of src[b * k + l]: partial sketches (double-float or FP64) written by an
-// earlier launch, or (CG) FP64 group sums written by this launch, read through L2.
-template <bool CG = false>
-__device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
+// Sum over b in [b0, b1) of the partial sketch entries src[b * k + l] (double-float or FP64),
+// written by an earlier launch, in the arithmetic of A.
+template <class A>
+__device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
     if (sdf) {
         const df* d = reinterpret_cast<const df*>(src);
         df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
@@ -120,25 +218,89 @@ __device__ __forceinline__ double group_sum(const double* src, bool sdf, int b0,
         }
         if (b < b1) t0 = df_add(t0, d[(size_t)b * k + l]);
         t0 = df_add(t0, t1);
-        return (double)t0.h + (double)t0.l;
+        if constexpr (std::is_same<typename A::T, df>::value)
+            return t0;
+        else
+            return (double)t0.h + (double)t0.l;
     }
-    auto ld = [&](int b) { return CG ? ldcg(src + (size_t)b * k + l) : src[(size_t)b * k + l]; };
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     int b = b0;
 #pragma unroll 2
     for (; b + 3 < b1; b += 4) {
-        v0 += ld(b);
-        v1 += ld(b + 1);
-        v2 += ld(b + 2);
-        v3 += ld(b + 3);
+        v0 += src[(size_t)b * k + l];
+        v1 += src[(size_t)(b + 1) * k + l];
+        v2 += src[(size_t)(b + 2) * k + l];
+        v3 += src[(size_t)(b + 3) * k + l];
     }
-    for (; b < b1; ++b) v0 += ld(b);
-    return (v0 + v1) + (v2 + v3);
+    for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
+    return A::from_d((v0 + v1) + (v2 + v3));
 }
 
+// Sum over g in [0, ng) of first-level group sums red[g * k + l] (type A::T, this launch).
+template <class A>
+__device__ __forceinline__ typename A::T group_total(const double* red, int ng, int k, int l) {
+    using T = typename A::T;
+    T v0 = A::zero(), v1 = A::zero();
+    int g = 0;
+#pragma unroll 4
+    for (; g + 1 < ng; g += 2) {
+        v0 = A::add(v0, A::ldg(red + (size_t)g * k + l));
+        v1 = A::add(v1, A::ldg(red + (size_t)(g + 1) * k + l));
+    }
+    if (g < ng) v0 = A::add(v0, A::ldg(red + (size_t)g * k + l));
+    return A::add(v0, v1);
+}
+
+// Dot product of a row (stride 1, entries [0, jend)) with a vector y (stride 1), a warp with
+// lanes over the entries: the lane partials, summed over the warp (valid in every lane).
+template <class A, bool Y_CG>
+__device__ __forceinline__ typename A::T warp_row_dot(const double* row, const double* y, int jend) {
+    const int lane = threadIdx.x & 31;
+    typename A::Acc acc[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
+    int j = lane;
+    for (; j + 96 < jend; j += 128)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            A::acc(acc[q], A::ld(row + j + 32 * q), Y_CG ? A::ldg(y + j + 32 * q) : A::ld(y + j + 32 * q));
+    for (; j < jend; j += 32) A::acc(acc[0], A::ld(row + j), Y_CG ? A::ldg(y + j) : A::ld(y + j));
+    return A::wsum(A::add(A::add(A::val(acc[0]), A::val(acc[1])), A::add(A::val(acc[2]), A::val(acc[3]))));
+}
+
+// The same warp dot for two vectors y1, y2 sharing the row (one pass over the row).
+template <class A>
+__device__ __forceinline__ void warp_row_dot2(const double* row, const double* y1, const double* y2, int jend,
+                                              bool use1, bool use2, typename A::T& o1, typename A::T& o2) {
+    const int lane = threadIdx.x & 31;
+    typename A::Acc a1[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
+    typename A::Acc a2[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
+    int j = lane;
+    for (; j + 96 < jend; j += 128)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const typename A::T v = A::ld(row + j + 32 * q);
+            if (use1) A::acc(a1[q], v, A::ldg(y1 + j + 32 * q));
+            if (use2) A::acc(a2[q], v, A::ldg(y2 + j + 32 * q));
+        }
+    for (; j < jend; j += 32) {
+        const typename A::T v = A::ld(row + j);
+        if (use1) A::acc(a1[0], v, A::ldg(y1 + j));
+        if (use2) A::acc(a2[0], v, A::ldg(y2 + j));
+    }
+    o1 = use1 ? A::wsum(A::add(A::add(A::val(a1[0]), A::val(a1[1])), A::add(A::val(a1[2]), A::val(a1[3]))))
+              : A::zero();
+    o2 = use2 ? A::wsum(A::add(A::add(A::val(a2[0]), A::val(a2[1])), A::add(A::val(a2[2]), A::val(a2[3]))))
+              : A::zero();
+}
+
+template <class A>
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
-    __shared__ double sh[3 * (NW + 1) + 2 + 3 * NW];
-    __shared__ double sc[8];
+    using T = typename A::T;
+    using Acc = typename A::Acc;
+    __shared__ double shd[2 * (NW + 1) + 2];   // FP64 block sums and totals (squared norms)
+    __shared__ T shT[2 * (NW + 1) + 2];        // A::T block sums and totals
+    __shared__ T qs[3 * NW];                   // per-warp partial dots of the column phases
+    __shared__ T scT[8];                       // scalars of the current phase, in A::T
+    __shared__ double sc[8];                   // FP64 scalars of phase 1
     int* ctl = st.ctl;
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
     const int k = st.k, mm = st.mmax, i = a.i;
@@ -149,10 +311,15 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const int gwarp = blockIdx.x + G * (tid >> 5), nwarps = nthreads >> 5;
     const bool app = a.append != 0, sol = a.solve != 0;
     const bool p_parts = sol && a.p_vec == nullptr;
+    const T zero = A::zero();
     unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
     if (trace) trace[0] = globaltimer();
     GridBarrier bar(ctl);
     const double pref = (app && tid == 0) ? st.pnorm[i] : 0.0;   // ||p_i||, for the breakdown test
+    if (tid == 0) {                                              // the partial sketches' scales
+        scT[6] = A::from_d(a.s_scale);
+        scT[7] = A::from_d(a.p_scale);
+    }
 
     // ---- phase 0a: with more than GS partial sketches, a first level sums groups of GS
     const int sgroups = app ? (a.s_nparts + GS - 1) / GS : 0;
@@ -167,15 +334,17 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             const int np = is_s ? a.s_nparts : a.p_nparts;
             const int l = seg * 32 + lane;
             if (l < k)
-                st.red[(size_t)g * k + l] = group_sum(is_s ? a.s_part : a.p_part, is_s ? a.s_df : a.p_df,
-                                                      gg * GS, min(np, gg * GS + GS), k, l);
+                A::st(st.red + (size_t)g * k + l, part_sum<A>(is_s ? a.s_part : a.p_part, (is_s ? a.s_df : a.p_df) != 0,
+                                                             gg * GS, min(np, gg * GS + GS), k, l));
         }
         if (!bar.sync(ctl)) return;
     }
     if (trace) trace[1] = globaltimer();
+    __syncthreads();
+    const T s_scale = scT[6], p_scale = scT[7];
 
     // ---- phase 0b: a warp per 32 rows (lane = row), each lane summing the groups (or partials)
-    //      of its row in order: s', p and their squared norms
+    //      of its row in order: s', p and their squared norms (FP64); and M(:, i-1)
     {
         double nrm[2] = {0.0, 0.0};
         const int nseg = (k + 31) / 32;
@@ -184,18 +353,22 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             const int l = seg * 32 + lane;
             if (l >= k) continue;
             if (app) {
-                const double v = (level1 ? group_sum<true>(st.red, false, 0, sgroups, k, l)
-                                         : group_sum(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l)) * a.s_scale;
-                st.sbuf[l] = v;
-                nrm[0] = fma(v, v, nrm[0]);
+                const T v = A::mul(level1 ? group_total<A>(st.red, sgroups, k, l)
+                                          : part_sum<A>(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l),
+                                   s_scale);
+                A::st(st.sbuf + l, v);
+                const double vd = A::to_d(v);
+                nrm[0] = fma(vd, vd, nrm[0]);
             }
             if (sol) {
-                const double v = (!p_parts ? a.p_vec[l]
-                                  : level1 ? group_sum<true>(st.red + (size_t)sgroups * k, false, 0, pgroups, k, l)
-                                           : group_sum(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l)) * a.p_scale;
-                st.pbuf[l] = v;
-                if (a.p_store) a.p_store[l] = v;
-                nrm[1] = fma(v, v, nrm[1]);
+                const T v = A::mul(!p_parts ? A::from_d(a.p_vec[l])
+                                   : level1 ? group_total<A>(st.red + (size_t)sgroups * k, pgroups, k, l)
+                                            : part_sum<A>(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l),
+                                   p_scale);
+                A::st(st.pbuf + l, v);
+                const double vd = A::to_d(v);
+                if (a.p_store) a.p_store[l] = vd;
+                nrm[1] = fma(vd, vd, nrm[1]);
             }
         }
         if (i > 0) {
@@ -203,47 +376,44 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             // launch; warp per row of the row-major copy VT, lanes over the columns
             const double* tc = st.T + (size_t)(i - 1) * mm;
             for (int l = gwarp; l < k; l += nwarps) {
-                const double* vr = st.VT + (size_t)l * mm;
-                const int jend = min(i, l + 1);
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                int j = lane;
-                for (; j + 96 < jend; j += 128)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = fma(vr[j + 32 * q], tc[j + 32 * q], acc[q]);
-                for (; j < jend; j += 32) acc[0] = fma(vr[j], tc[j], acc[0]);
-                const double d = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
-                if (lane == 0) st.M[(size_t)(i - 1) * k + l] = d;
+                T d, unused;
+                warp_row_dot2<A>(st.VT + (size_t)l * mm, tc, tc, min(i, l + 1), true, false, d, unused);
+                if (lane == 0) A::st(st.M + (size_t)(i - 1) * k + l, d);
             }
         }
         if (busy) {                                    // idle warps skip the FP64 shuffles
             nrm[0] = warp_sum(nrm[0]);
             nrm[1] = warp_sum(nrm[1]);
         }
-        block_sum_lane0<2>(nrm, sh);
+        block_sum_lane0<FineF64, 2>(nrm, shd);
         if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm[0]; st.blk[blockIdx.x * 4 + 1] = nrm[1]; }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
-    const double2 tot01 = grid_total2(st.blk, 0, sh);
+    double tn0, tn1;
+    grid_total2<FineF64>(st.blk, 0, shd, tn0, tn1);
     // The phase's scalars come from one thread through shared memory: an FP64 square root or
     // division is a long sequence on the FP64 pipe, which would otherwise run in every thread.
     if (tid == 0) {
-        const double r0 = sqrt(tot01.x);
+        const double r0 = sqrt(tn0);
         int code = 0;                                  // 1: non-finite r_ii, 2: breakdown
         if (app) code = !isfinite(r0) ? 1 : (!(r0 > 16.0 * 0x1p-53 * pref) ? 2 : 0);
         const double ir = code == 0 ? 1.0 / r0 : 1.0;
         sc[0] = r0;
         sc[1] = app ? ir : 1.0;
         sc[2] = (app && a.p_lag) ? ir : 1.0;
-        sc[3] = sol ? sqrt(tot01.y) : 0.0;
+        sc[3] = sol ? sqrt(tn1) : 0.0;
         sc[4] = (double)code;
+        scT[0] = A::from_d(sc[1]);
+        scT[1] = A::from_d(sc[2]);
     }
     __syncthreads();
     const double r = sc[0], pn = sc[3];
     const int code = (int)sc[4];
-    double inv_r = 1.0, pmul = 1.0;
+    const double inv_r = sc[1], pmul = sc[2];
+    const T inv_rT = scT[0], pmulT = scT[1];
     if (app) {
         if (code == 1) {
             if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_NONFINITE); ctl[kDetailWord] = i; }
@@ -268,8 +438,6 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             return;
         }
-        inv_r = sc[1];
-        pmul = sc[2];
         if (gtid == 0) {
             st.R[(size_t)i * st.ldr + i] = r;
             st.sigma[i] = inv_r;
@@ -279,74 +447,59 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     {
         // a quad of warps (one per SM sub-partition) per column; each warp a quarter of the rows
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
-        double* qs = sh + 3 * (NW + 1) + 2;                // [NW/4 quads][4 warps][2]
         const int seg = (k + 3) / 4;
         for (int base = 0; base < i; base += G * (NW / 4)) {
             const int j = base + blockIdx.x + G * quad;
-            double ds = 0.0, dp = 0.0;
             if (j < i) {
                 const double* mc = st.M + (size_t)j * k;      // column i-1 was written by phase 0b
                 const int l0 = qw * seg, l1 = min(k, l0 + seg);
+                Acc as = A::acc0(), ap = A::acc0();
 #pragma unroll 8
                 for (int l = l0 + lane; l < l1; l += 32) {
-                    const double mv = ldcg(mc + l);
-                    if (app) ds = fma(mv, ldcg(st.sbuf + l), ds);
-                    if (sol) dp = fma(mv, ldcg(st.pbuf + l), dp);
+                    const T mv = A::ldg(mc + l);
+                    if (app) A::acc(as, mv, A::ldg(st.sbuf + l));
+                    if (sol) A::acc(ap, mv, A::ldg(st.pbuf + l));
                 }
-                ds = warp_sum(ds);
-                dp = warp_sum(dp);
+                const T ds = app ? A::wsum(A::val(as)) : zero;
+                const T dp = sol ? A::wsum(A::val(ap)) : zero;
                 if (lane == 0) { qs[(quad * 4 + qw) * 2] = ds; qs[(quad * 4 + qw) * 2 + 1] = dp; }
             }
             __syncthreads();
             if (j < i && qw == 0 && lane == 0) {
-                const double* q4 = qs + quad * 8;
-                st.u2s[j] = ((q4[0] + q4[2]) + (q4[4] + q4[6])) * inv_r;
-                st.u2p[j] = ((q4[1] + q4[3]) + (q4[5] + q4[7])) * pmul;
+                const T* q4 = qs + quad * 8;
+                A::st(st.u2s + j, A::mul(A::add(A::add(q4[0], q4[2]), A::add(q4[4], q4[6])), inv_rT));
+                A::st(st.u2p + j, A::mul(A::add(A::add(q4[1], q4[3]), A::add(q4[5], q4[7])), pmulT));
             }
             __syncthreads();
         }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[3] = globaltimer();
-
     if (trace) trace[4] = trace[3];                  // (no separate T^T u phase: M holds V T)
 
     // ---- phase 3: y = [s, p] - V u2 (the i reflectors applied), warp per row using the
-    //      row-major copy VT of V; plus the sums the new reflector needs over rows > i
+    //      row-major copy VT; s_i is stored (step 6); sums over rows > i for the new reflector
     const int krows = app ? k : i;                 // a pure solve needs rows 0..i-1 only
     {
-        double sums[2] = {0.0, 0.0};
+        Acc sg = A::acc0(), cr = A::acc0();
         for (int l = gwarp; l < krows; l += nwarps) {
-            const double* vr = st.VT + (size_t)l * mm;
-            const int jend = min(i, l + 1);
-            double as[4] = {0.0, 0.0, 0.0, 0.0}, ap[4] = {0.0, 0.0, 0.0, 0.0};
-            int j = lane;
-            for (; j + 96 < jend; j += 128)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const double vv = vr[j + 32 * q];
-                    if (app) as[q] = fma(vv, ldcg(st.u2s + j + 32 * q), as[q]);
-                    if (sol) ap[q] = fma(vv, ldcg(st.u2p + j + 32 * q), ap[q]);
-                }
-            for (; j < jend; j += 32) {
-                const double vv = vr[j];
-                if (app) as[0] = fma(vv, ldcg(st.u2s + j), as[0]);
-                if (sol) ap[0] = fma(vv, ldcg(st.u2p + j), ap[0]);
-            }
-            const double ws = warp_sum((as[0] + as[1]) + (as[2] + as[3]));
-            const double wp = warp_sum((ap[0] + ap[1]) + (ap[2] + ap[3]));
+            const T sl0 = app ? A::ldg(st.sbuf + l) : zero;     // issued before the row's dots
+            const T pl0 = sol ? A::ldg(st.pbuf + l) : zero;
+            T ws, wp;
+            warp_row_dot2<A>(st.VT + (size_t)l * mm, st.u2s, st.u2p, min(i, l + 1), app, sol, ws, wp);
             if (lane == 0) {
-                const double sl = app ? ldcg(st.sbuf + l) * inv_r : 0.0;
-                if (app) st.S[(size_t)i * k + l] = sl;     // s_i (Alg. 2 step 6)
-                const double ysl = app ? sl - ws : 0.0;
-                const double ypl = sol ? ldcg(st.pbuf + l) * pmul - wp : 0.0;
-                st.ys[l] = ysl;
-                st.yp[l] = ypl;
-                if (app && l > i) { sums[0] = fma(ysl, ysl, sums[0]); sums[1] = fma(ysl, ypl, sums[1]); }
+                const T sl = A::mul(sl0, inv_rT);
+                if (app) st.S[(size_t)i * k + l] = A::to_d(sl);      // s_i (Alg. 2 step 6)
+                const T ysl = app ? A::sub(sl, ws) : zero;
+                const T ypl = sol ? A::sub(A::mul(pl0, pmulT), wp) : zero;
+                A::st(st.ys + l, ysl);
+                A::st(st.yp + l, ypl);
+                if (app && l > i) { A::acc(sg, ysl, ysl); A::acc(cr, ysl, ypl); }
             }
         }
-        block_sum_lane0<2>(sums, sh);
-        if (tid == 0) { st.blk[blockIdx.x * 4 + 2] = sums[0]; st.blk[blockIdx.x * 4 + 3] = sums[1]; }
+        T sums[2] = {A::val(sg), A::val(cr)};
+        block_sum_lane0<A, 2>(sums, shT);
+        if (tid == 0) { A::st(st.blk + blockIdx.x * 4 + 2, sums[0]); A::st(st.blk + blockIdx.x * 4 + 3, sums[1]); }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[5] = globaltimer();
@@ -354,18 +507,12 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (!app) {
         // pure solve: x = R_S^{-1} y(0:i); row j of R_S^{-1} is column j of RinvT
         for (int j = gwarp; j < i; j += nwarps) {
-            const double* rr = st.RinvT + (size_t)j * mm;
-            double da = 0.0, db = 0.0;
-            int l = j + lane;
-            for (; l + 32 < i; l += 64) {
-                da = fma(rr[l], ldcg(st.yp + l), da);
-                db = fma(rr[l + 32], ldcg(st.yp + l + 32), db);
-            }
-            if (l < i) da = fma(rr[l], ldcg(st.yp + l), da);
-            const double d = warp_sum(da + db);
+            T d, unused;
+            warp_row_dot2<A>(st.RinvT + (size_t)j * mm + j, st.yp + j, st.yp + j, i - j, true, false, d, unused);
             if (lane == 0) {
-                st.R[(size_t)a.xcol * st.ldr + j] = d;
-                st.coef[j] = d * st.sigma[j];
+                const double dd = A::to_d(d);
+                st.R[(size_t)a.xcol * st.ldr + j] = dd;
+                st.coef[j] = dd * st.sigma[j];
             }
         }
         if (trace) { trace[6] = globaltimer(); trace[7] = trace[6]; }
@@ -376,27 +523,26 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
     {
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
-        double* qs = sh + 3 * (NW + 1) + 2;                // [NW/4 quads][4 warps][3]
         for (int base = 0; base < i; base += G * (NW / 4)) {
             const int j = base + blockIdx.x + G * quad;
-            double z = 0.0, d1 = 0.0, d2 = 0.0;
             if (j < i) {
                 const double* v = st.V + (size_t)j * k;
                 const int len = k - (i + 1), seg = (max(len, 0) + 3) / 4;
                 const int l0 = i + 1 + qw * seg, l1 = min(k, l0 + seg);
+                Acc az = A::acc0(), a1 = A::acc0(), a2 = A::acc0();
 #pragma unroll 4
-                for (int l = l0 + lane; l < l1; l += 32) z = fma(v[l], ldcg(st.ys + l), z);
+                for (int l = l0 + lane; l < l1; l += 32) A::acc(az, A::ld(v + l), A::ldg(st.ys + l));
                 const double* rr = st.RinvT + (size_t)j * mm;       // row j of R_S^{-1}
                 const int rlen = i - j, rseg = (rlen + 3) / 4;
                 const int r0 = j + qw * rseg, r1 = min(i, r0 + rseg);
                 for (int l = r0 + lane; l < r1; l += 32) {
-                    const double rv = rr[l];
-                    d1 = fma(rv, ldcg(st.ys + l), d1);
-                    if (sol) d2 = fma(rv, ldcg(st.yp + l), d2);
+                    const T rv = A::ld(rr + l);
+                    A::acc(a1, rv, A::ldg(st.ys + l));
+                    if (sol) A::acc(a2, rv, A::ldg(st.yp + l));
                 }
-                z = warp_sum(z);
-                d1 = warp_sum(d1);
-                if (sol) d2 = warp_sum(d2);
+                const T z = A::wsum(A::val(az));
+                const T d1 = A::wsum(A::val(a1));
+                const T d2 = sol ? A::wsum(A::val(a2)) : zero;
                 if (lane == 0) {
                     qs[(quad * 4 + qw) * 3] = z;
                     qs[(quad * 4 + qw) * 3 + 1] = d1;
@@ -405,10 +551,10 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             __syncthreads();
             if (j < i && qw == 0 && lane == 0) {
-                const double* q4 = qs + quad * 12;
-                st.zp[j] = (q4[0] + q4[3]) + (q4[6] + q4[9]);
-                st.d1[j] = (q4[1] + q4[4]) + (q4[7] + q4[10]);
-                st.d2[j] = (q4[2] + q4[5]) + (q4[8] + q4[11]);
+                const T* q4 = qs + quad * 12;
+                A::st(st.zp + j, A::add(A::add(q4[0], q4[3]), A::add(q4[6], q4[9])));
+                A::st(st.d1 + j, A::add(A::add(q4[1], q4[4]), A::add(q4[7], q4[10])));
+                A::st(st.d2 + j, A::add(A::add(q4[2], q4[5]), A::add(q4[8], q4[11])));
             }
             __syncthreads();
         }
@@ -417,43 +563,43 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (trace) trace[6] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    double alpha = 0.0, ypi0 = 0.0;
+    T alpha = zero, ypi0 = zero;
     if (tid == 0) {                                    // issued before the totals' round trip
-        alpha = ldcg(st.ys + i);
-        ypi0 = sol ? ldcg(st.yp + i) : 0.0;
+        alpha = A::ldg(st.ys + i);
+        ypi0 = sol ? A::ldg(st.yp + i) : zero;
     }
-    const double2 tot23 = grid_total2(st.blk, 2, sh);
-    const double SG = tot23.x, CR = tot23.y;
+    T SG, CR;
+    grid_total2<A>(st.blk, 2, shT, SG, CR);
     if (tid == 0) {
-        double beta, tau, vs;
-        if (SG == 0.0) {
-            beta = alpha; tau = 0.0; vs = 0.0;
+        T beta, tau, vs;
+        if (A::is_zero(SG)) {
+            beta = alpha; tau = zero; vs = zero;
         } else {
-            const double nrm = sqrt(alpha * alpha + SG);
-            beta = alpha >= 0.0 ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            vs = 1.0 / (alpha - beta);
+            const T nrm = A::sqrt_(A::add(A::mul(alpha, alpha), SG));
+            beta = A::nonneg(alpha) ? A::neg(nrm) : nrm;
+            tau = A::div(A::sub(beta, alpha), beta);
+            vs = A::div(A::one(), A::sub(alpha, beta));
         }
-        sc[0] = beta; sc[1] = tau; sc[2] = vs;
-        sc[3] = sol ? ypi0 - tau * (ypi0 + CR * vs) : 0.0;
+        scT[0] = beta; scT[1] = tau; scT[2] = vs;
+        scT[3] = sol ? A::sub(ypi0, A::mul(tau, A::add(ypi0, A::mul(CR, vs)))) : zero;
     }
     __syncthreads();
-    const double beta = sc[0], tau = sc[1], vs = sc[2], ypi = sc[3];
-    if (beta == 0.0) {
+    const T beta = scT[0], tau = scT[1], vs = scT[2], ypi = scT[3];
+    if (A::is_zero(beta)) {
         if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
         return;
     }
     for (int l = gtid; l < k; l += nthreads) {
-        const double vl = l < i ? 0.0 : (l == i ? 1.0 : ldcg(st.ys + l) * vs);
-        st.V[(size_t)i * k + l] = vl;
-        if (l >= i) st.VT[(size_t)l * mm + i] = vl;
+        const T vl = l < i ? zero : (l == i ? A::one() : A::mul(A::ldg(st.ys + l), vs));
+        A::st(st.V + (size_t)i * k + l, vl);
+        if (l >= i) A::st(st.VT + (size_t)l * mm + i, vl);
     }
     if (gtid == 0) {
-        st.T[(size_t)i * mm + i] = tau;
-        st.TT[(size_t)i * mm + i] = tau;
-        st.RinvT[(size_t)i * mm + i] = 1.0 / beta;
+        A::st(st.T + (size_t)i * mm + i, tau);
+        A::st(st.TT + (size_t)i * mm + i, tau);
+        A::st(st.RinvT + (size_t)i * mm + i, A::div(A::one(), beta));
         if (sol) {
-            const double xi = ypi / beta;
+            const double xi = A::to_d(A::div(ypi, beta));
             st.R[(size_t)a.xcol * st.ldr + i] = xi;
             st.coef[i] = xi * inv_r;
         }
@@ -462,22 +608,22 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     for (int j = gwarp; j < i; j += nwarps) {
         // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
         const double* tr = st.TT + (size_t)j * mm;
-        double da = 0.0, db = 0.0;
+        Acc c0 = A::acc0(), c1 = A::acc0();
         int l = j + lane;
         for (; l + 32 < i; l += 64) {
-            da = fma(tr[l], vrow_i[l] + vs * ldcg(st.zp + l), da);
-            db = fma(tr[l + 32], vrow_i[l + 32] + vs * ldcg(st.zp + l + 32), db);
+            A::acc(c0, A::ld(tr + l), A::add(A::ld(vrow_i + l), A::mul(vs, A::ldg(st.zp + l))));
+            A::acc(c1, A::ld(tr + l + 32), A::add(A::ld(vrow_i + l + 32), A::mul(vs, A::ldg(st.zp + l + 32))));
         }
-        if (l < i) da = fma(tr[l], vrow_i[l] + vs * ldcg(st.zp + l), da);
-        const double d = warp_sum(da + db);
+        if (l < i) A::acc(c0, A::ld(tr + l), A::add(A::ld(vrow_i + l), A::mul(vs, A::ldg(st.zp + l))));
+        const T d = A::wsum(A::add(A::val(c0), A::val(c1)));
         if (lane == 0) {
-            const double t = -tau * d;
-            st.T[(size_t)i * mm + j] = t;
-            st.TT[(size_t)j * mm + i] = t;
-            const double cnew = -ldcg(st.d1 + j) / beta;       // R_S^{-1}(j, i)
-            st.RinvT[(size_t)j * mm + i] = cnew;
+            const T t = A::neg(A::mul(tau, d));
+            A::st(st.T + (size_t)i * mm + j, t);
+            A::st(st.TT + (size_t)j * mm + i, t);
+            const T cnew = A::neg(A::div(A::ldg(st.d1 + j), beta));   // R_S^{-1}(j, i)
+            A::st(st.RinvT + (size_t)j * mm + i, cnew);
             if (sol) {
-                const double xj = ldcg(st.d2 + j) + cnew * ypi;
+                const double xj = A::to_d(A::add(A::ldg(st.d2 + j), A::mul(cnew, ypi)));
                 st.R[(size_t)a.xcol * st.ldr + j] = xj;
                 st.coef[j] = xj * st.sigma[j];
             }
@@ -526,7 +672,7 @@ __global__ void cert_final_kernel(const double* work, int m, double* out) {
 
 }  // namespace
 
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState* st) {
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fine_df, LSState* st) {
     const int groups = 2 * ((std::max(max_parts, 1) + GS - 1) / GS);
     size_t n = 0;
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
@@ -538,7 +684,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, LSState
                  opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
     double* b = buf.as<double>();
-    st->k = k; st->mmax = mmax; st->max_parts = max_parts;
+    st->k = k; st->mmax = mmax; st->max_parts = max_parts; st->fine_df = fine_df ? 1 : 0;
     st->V = b + oV; st->VT = b + oVT; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
     st->M = b + oM; st->u2s = b + ou2s; st->u2p = b + ou2p;
@@ -564,15 +710,18 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     void* args[] = {&s, &p};
     const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
     RGS_REQUIRE(grid <= 32 * kTotMax, "least-squares grid larger than the per-CTA totals support");
-    RGS_CUDA(cudaLaunchCooperativeKernel((const void*)ls_kernel, dim3(grid), dim3(LT), args, 0, ctx->stream));
+    const void* fn = st.fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
+    RGS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(LT), args, 0, ctx->stream));
     ctx->launches++;
 }
 
 // One CTA of LT threads per SM (its registers fill the SM), so the cooperative grid is the SM count.
 int rgs_ls_max_blocks(int num_sms) {
-    int per_sm = 0;
-    RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ls_kernel, LT, 0));
-    RGS_REQUIRE(per_sm >= 1, "the least-squares kernel does not fit on an SM");
+    for (const void* fn : {(const void*)ls_kernel<FineF64>, (const void*)ls_kernel<FineDF>}) {
+        int per_sm = 0;
+        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LT, 0));
+        RGS_REQUIRE(per_sm >= 1, "the least-squares kernel does not fit on an SM");
+    }
     return num_sms;
 }
 

@@ -235,15 +235,17 @@ def test_double_float_sketch_accuracy(h, qdtype):
     assert err <= 1e-13
 
 
-def test_fp64_sketch_flag_close_to_double_float(h):
+def test_fp64_fine_flag_close_to_double_float(h):
+    """FP32 storage: the double-float transform and least squares against all-FP64 fine
+    arithmetic (RGS_QR_FP64_FINE) on the same input."""
     n, m, k = 30000, 20, 80
     A = to_gpu(synth.gdw_matrix(n, m, 1e3, 13).numpy().T.copy())
     sk = rgs.rgs_sketch_create(h, "srht", n, k, 2)
     R1, R2 = rgs.colmajor_empty(m, m), rgs.colmajor_empty(m, m)
     rgs.rgs_qr(h, sk, A, rgs.colmajor_empty(n, m, dtype=torch.float32), R1)
-    rgs.rgs_qr(h, sk, A, rgs.colmajor_empty(n, m, dtype=torch.float32), R2, flags=rgs.RGS_QR_FP64_SKETCH)
+    rgs.rgs_qr(h, sk, A, rgs.colmajor_empty(n, m, dtype=torch.float32), R2, flags=rgs.RGS_QR_FP64_FINE)
     d = rel(R1.cpu().numpy(), R2.cpu().numpy())
-    print(f"FP32 storage, double-float vs FP64 transform: ||dR||/||R|| = {d:.3e}")
+    print(f"FP32 storage, double-float vs FP64 fine arithmetic: ||dR||/||R|| = {d:.3e}")
     assert d <= 1e-9
 
 
