@@ -175,32 +175,24 @@ __device__ __forceinline__ void block_sum_lane0(typename A::T (&v)[N], typename 
 }
 
 // Deterministic totals of the per-CTA values blk[b*4 + off], blk[b*4 + off + 1] (type A::T),
-// identical in every CTA; one warp issues all the loads at once, adds and broadcasts.
+// computed by one whole warp (all its loads issued at once) and valid in all its lanes.
 template <class A>
-__device__ void grid_total2(const double* blk, int off, typename A::T* sh, typename A::T& t0, typename A::T& t1) {
+__device__ void warp_total2(const double* blk, int off, typename A::T& t0, typename A::T& t1) {
     using T = typename A::T;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int G = gridDim.x;
-        T a0[kTotMax], a1[kTotMax];
+    const int lane = threadIdx.x & 31, G = gridDim.x;
+    T a0[kTotMax], a1[kTotMax];
 #pragma unroll
-        for (int q = 0; q < kTotMax; ++q) {
-            const int b = threadIdx.x + 32 * q;
-            a0[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off) : A::zero();
-            a1[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off + 1) : A::zero();
-        }
-        T v0 = A::zero(), v1 = A::zero();
-#pragma unroll
-        for (int q = 0; q < kTotMax; ++q)
-            if (32 * q < G) { v0 = A::add(v0, a0[q]); v1 = A::add(v1, a1[q]); }
-        v0 = A::wsum(v0);
-        v1 = A::wsum(v1);
-        if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
+    for (int q = 0; q < kTotMax; ++q) {
+        const int b = lane + 32 * q;
+        a0[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off) : A::zero();
+        a1[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off + 1) : A::zero();
     }
-    __syncthreads();
-    t0 = sh[0];
-    t1 = sh[1];
-    __syncthreads();
+    T v0 = A::zero(), v1 = A::zero();
+#pragma unroll
+    for (int q = 0; q < kTotMax; ++q)
+        if (32 * q < G) { v0 = A::add(v0, a0[q]); v1 = A::add(v1, a1[q]); }
+    t0 = A::wsum(v0);
+    t1 = A::wsum(v1);
 }
 
 // Sum over b in [b0, b1) of the partial sketch entries src[b * k + l] (double-float or FP64),
@@ -210,13 +202,16 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     if (sdf) {
         const df* d = reinterpret_cast<const df*>(src);
         df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
-        int b = b0;
-#pragma unroll 16
-        for (; b + 1 < b1; b += 2) {
-            t0 = df_add(t0, d[(size_t)b * k + l]);
-            t1 = df_add(t1, d[(size_t)(b + 1) * k + l]);
+        for (int bb = b0; bb < b1; bb += 16) {         // 16 loads in flight, then the sums
+            df v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = bb + q < b1 ? d[(size_t)(bb + q) * k + l] : df{0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) {
+                t0 = df_add(t0, v[q]);
+                t1 = df_add(t1, v[q + 1]);
+            }
         }
-        if (b < b1) t0 = df_add(t0, d[(size_t)b * k + l]);
         t0 = df_add(t0, t1);
         if constexpr (std::is_same<typename A::T, df>::value)
             return t0;
@@ -251,40 +246,31 @@ __device__ __forceinline__ typename A::T group_total(const double* red, int ng, 
     return A::add(v0, v1);
 }
 
-// Dot product of a row (stride 1, entries [0, jend)) with a vector y (stride 1), a warp with
-// lanes over the entries: the lane partials, summed over the warp (valid in every lane).
-template <class A, bool Y_CG>
-__device__ __forceinline__ typename A::T warp_row_dot(const double* row, const double* y, int jend) {
-    const int lane = threadIdx.x & 31;
-    typename A::Acc acc[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
-    int j = lane;
-    for (; j + 96 < jend; j += 128)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            A::acc(acc[q], A::ld(row + j + 32 * q), Y_CG ? A::ldg(y + j + 32 * q) : A::ld(y + j + 32 * q));
-    for (; j < jend; j += 32) A::acc(acc[0], A::ld(row + j), Y_CG ? A::ldg(y + j) : A::ld(y + j));
-    return A::wsum(A::add(A::add(A::val(acc[0]), A::val(acc[1])), A::add(A::val(acc[2]), A::val(acc[3]))));
-}
-
-// The same warp dot for two vectors y1, y2 sharing the row (one pass over the row).
+// Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2 (written earlier
+// in this launch), a warp with lanes over the entries: the lane partials summed over the warp,
+// valid in every lane; use1 / use2 select the vectors needed.
 template <class A>
 __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y1, const double* y2, int jend,
                                               bool use1, bool use2, typename A::T& o1, typename A::T& o2) {
     const int lane = threadIdx.x & 31;
     typename A::Acc a1[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
     typename A::Acc a2[4] = {A::acc0(), A::acc0(), A::acc0(), A::acc0()};
-    int j = lane;
-    for (; j + 96 < jend; j += 128)
+    // blocks of 4 x 32 entries: every load of a block is issued before its arithmetic
+    for (int j0 = 0; j0 < jend; j0 += 128) {
+        typename A::T v[4], w1[4], w2[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const typename A::T v = A::ld(row + j + 32 * q);
-            if (use1) A::acc(a1[q], v, A::ldg(y1 + j + 32 * q));
-            if (use2) A::acc(a2[q], v, A::ldg(y2 + j + 32 * q));
+            const int j = j0 + 32 * q + lane;
+            const bool ok = j < jend;
+            v[q] = ok ? A::ld(row + j) : A::zero();
+            w1[q] = (ok && use1) ? A::ldg(y1 + j) : A::zero();
+            w2[q] = (ok && use2) ? A::ldg(y2 + j) : A::zero();
         }
-    for (; j < jend; j += 32) {
-        const typename A::T v = A::ld(row + j);
-        if (use1) A::acc(a1[0], v, A::ldg(y1 + j));
-        if (use2) A::acc(a2[0], v, A::ldg(y2 + j));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (use1) A::acc(a1[q], v[q], w1[q]);
+            if (use2) A::acc(a2[q], v[q], w2[q]);
+        }
     }
     o1 = use1 ? A::wsum(A::add(A::add(A::val(a1[0]), A::val(a1[1])), A::add(A::val(a1[2]), A::val(a1[3]))))
               : A::zero();
@@ -392,24 +378,67 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (trace) trace[2] = globaltimer();
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
-    double tn0, tn1;
-    grid_total2<FineF64>(st.blk, 0, shd, tn0, tn1);
-    // The phase's scalars come from one thread through shared memory: an FP64 square root or
-    // division is a long sequence on the FP64 pipe, which would otherwise run in every thread.
-    if (tid == 0) {
-        const double r0 = sqrt(tn0);
-        int code = 0;                                  // 1: non-finite r_ii, 2: breakdown
-        if (app) code = !isfinite(r0) ? 1 : (!(r0 > 16.0 * 0x1p-53 * pref) ? 2 : 0);
-        const double ir = code == 0 ? 1.0 / r0 : 1.0;
-        sc[0] = r0;
-        sc[1] = app ? ir : 1.0;
-        sc[2] = (app && a.p_lag) ? ir : 1.0;
-        sc[3] = sol ? sqrt(tn1) : 0.0;
-        sc[4] = (double)code;
-        scT[0] = A::from_d(sc[1]);
-        scT[1] = A::from_d(sc[2]);
+    // Warp 0 reads the squared norms' totals and thread 0 forms the phase's scalars (one thread:
+    // an FP64 square root or division is a long sequence on the FP64 pipe) while warps 4..15,
+    // three quads of one warp per SM sub-partition, compute the column dots; the quads' sums are
+    // scaled once both are done.
+    const int warp = tid >> 5;
+    if (warp == 0) {
+        double tn0, tn1;
+        warp_total2<FineF64>(st.blk, 0, tn0, tn1);
+        if (lane == 0) {
+            const double r0 = sqrt(tn0);
+            int code = 0;                              // 1: non-finite r_ii, 2: breakdown
+            if (app) code = !isfinite(r0) ? 1 : (!(r0 > 16.0 * 0x1p-53 * pref) ? 2 : 0);
+            const double ir = code == 0 ? 1.0 / r0 : 1.0;
+            sc[0] = r0;
+            sc[1] = app ? ir : 1.0;
+            sc[2] = (app && a.p_lag) ? ir : 1.0;
+            sc[3] = sol ? sqrt(tn1) : 0.0;
+            sc[4] = (double)code;
+            scT[0] = A::from_d(sc[1]);
+            scT[1] = A::from_d(sc[2]);
+        }
     }
-    __syncthreads();
+    {
+        const int quad = warp / 4 - 1, qw = warp & 3;  // quads 0..2; warps 0..3 take no column
+        const int seg = (k + 3) / 4;
+        for (int base = 0; base < i; base += G * 3) {
+            const int j = quad >= 0 ? base + blockIdx.x + G * quad : i;
+            if (j < i) {
+                const double* mc = st.M + (size_t)j * k;      // column i-1 was written by phase 0b
+                const int l0 = qw * seg, l1 = min(k, l0 + seg);
+                Acc as = A::acc0(), ap = A::acc0();
+                for (int lb = l0; lb < l1; lb += 32 * 8) {   // 8 rows per lane: loads first
+                    T mv[8], sv[8], pv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int l = lb + 32 * q + lane;
+                        const bool ok = l < l1;
+                        mv[q] = ok ? A::ldg(mc + l) : zero;
+                        sv[q] = (ok && app) ? A::ldg(st.sbuf + l) : zero;
+                        pv[q] = (ok && sol) ? A::ldg(st.pbuf + l) : zero;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (app) A::acc(as, mv[q], sv[q]);
+                        if (sol) A::acc(ap, mv[q], pv[q]);
+                    }
+                }
+                const T ds = app ? A::wsum(A::val(as)) : zero;
+                const T dp = sol ? A::wsum(A::val(ap)) : zero;
+                if (lane == 0) { qs[(quad * 4 + qw) * 2] = ds; qs[(quad * 4 + qw) * 2 + 1] = dp; }
+            }
+            __syncthreads();
+            if (j < i && qw == 0 && lane == 0) {
+                const T* q4 = qs + quad * 8;
+                A::st(st.u2s + j, A::mul(A::add(A::add(q4[0], q4[2]), A::add(q4[4], q4[6])), scT[0]));
+                A::st(st.u2p + j, A::mul(A::add(A::add(q4[1], q4[3]), A::add(q4[5], q4[7])), scT[1]));
+            }
+            __syncthreads();
+        }
+        __syncthreads();                               // the scalars, also when no column was dotted
+    }
     const double r = sc[0], pn = sc[3];
     const int code = (int)sc[4];
     const double inv_r = sc[1], pmul = sc[2];
@@ -444,35 +473,6 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
-    {
-        // a quad of warps (one per SM sub-partition) per column; each warp a quarter of the rows
-        const int quad = tid >> 7, qw = (tid >> 5) & 3;
-        const int seg = (k + 3) / 4;
-        for (int base = 0; base < i; base += G * (NW / 4)) {
-            const int j = base + blockIdx.x + G * quad;
-            if (j < i) {
-                const double* mc = st.M + (size_t)j * k;      // column i-1 was written by phase 0b
-                const int l0 = qw * seg, l1 = min(k, l0 + seg);
-                Acc as = A::acc0(), ap = A::acc0();
-#pragma unroll 8
-                for (int l = l0 + lane; l < l1; l += 32) {
-                    const T mv = A::ldg(mc + l);
-                    if (app) A::acc(as, mv, A::ldg(st.sbuf + l));
-                    if (sol) A::acc(ap, mv, A::ldg(st.pbuf + l));
-                }
-                const T ds = app ? A::wsum(A::val(as)) : zero;
-                const T dp = sol ? A::wsum(A::val(ap)) : zero;
-                if (lane == 0) { qs[(quad * 4 + qw) * 2] = ds; qs[(quad * 4 + qw) * 2 + 1] = dp; }
-            }
-            __syncthreads();
-            if (j < i && qw == 0 && lane == 0) {
-                const T* q4 = qs + quad * 8;
-                A::st(st.u2s + j, A::mul(A::add(A::add(q4[0], q4[2]), A::add(q4[4], q4[6])), inv_rT));
-                A::st(st.u2p + j, A::mul(A::add(A::add(q4[1], q4[3]), A::add(q4[5], q4[7])), pmulT));
-            }
-            __syncthreads();
-        }
-    }
     if (!bar.sync(ctl)) return;
     if (trace) trace[3] = globaltimer();
     if (trace) trace[4] = trace[3];                  // (no separate T^T u phase: M holds V T)
@@ -530,15 +530,35 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 const int len = k - (i + 1), seg = (max(len, 0) + 3) / 4;
                 const int l0 = i + 1 + qw * seg, l1 = min(k, l0 + seg);
                 Acc az = A::acc0(), a1 = A::acc0(), a2 = A::acc0();
-#pragma unroll 4
-                for (int l = l0 + lane; l < l1; l += 32) A::acc(az, A::ld(v + l), A::ldg(st.ys + l));
+                for (int lb = l0; lb < l1; lb += 32 * 8) {   // loads of 8 rows per lane first
+                    T vv[8], yv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int l = lb + 32 * q + lane;
+                        vv[q] = l < l1 ? A::ld(v + l) : zero;
+                        yv[q] = l < l1 ? A::ldg(st.ys + l) : zero;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) A::acc(az, vv[q], yv[q]);
+                }
                 const double* rr = st.RinvT + (size_t)j * mm;       // row j of R_S^{-1}
                 const int rlen = i - j, rseg = (rlen + 3) / 4;
                 const int r0 = j + qw * rseg, r1 = min(i, r0 + rseg);
-                for (int l = r0 + lane; l < r1; l += 32) {
-                    const T rv = A::ld(rr + l);
-                    A::acc(a1, rv, A::ldg(st.ys + l));
-                    if (sol) A::acc(a2, rv, A::ldg(st.yp + l));
+                for (int lb = r0; lb < r1; lb += 32 * 4) {
+                    T rv[4], y1[4], y2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int l = lb + 32 * q + lane;
+                        const bool ok = l < r1;
+                        rv[q] = ok ? A::ld(rr + l) : zero;
+                        y1[q] = ok ? A::ldg(st.ys + l) : zero;
+                        y2[q] = (ok && sol) ? A::ldg(st.yp + l) : zero;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        A::acc(a1, rv[q], y1[q]);
+                        if (sol) A::acc(a2, rv[q], y2[q]);
+                    }
                 }
                 const T z = A::wsum(A::val(az));
                 const T d1 = A::wsum(A::val(a1));
@@ -563,32 +583,83 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (trace) trace[6] = globaltimer();
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    T alpha = zero, ypi0 = zero;
-    if (tid == 0) {                                    // issued before the totals' round trip
-        alpha = A::ldg(st.ys + i);
-        ypi0 = sol ? A::ldg(st.yp + i) : zero;
-    }
-    T SG, CR;
-    grid_total2<A>(st.blk, 2, shT, SG, CR);
-    if (tid == 0) {
-        T beta, tau, vs;
-        if (A::is_zero(SG)) {
-            beta = alpha; tau = zero; vs = zero;
-        } else {
-            const T nrm = A::sqrt_(A::add(A::mul(alpha, alpha), SG));
-            beta = A::nonneg(alpha) ? A::neg(nrm) : nrm;
-            tau = A::div(A::sub(beta, alpha), beta);
-            vs = A::div(A::one(), A::sub(alpha, beta));
+    // Warp 0 forms the reflector's scalars (totals SG, CR; alpha, beta, tau, vs) while warps
+    // 1..15 compute, per column j < i, the two dots of T(j, i) = -tau (a_j + vs b_j) with
+    // a_j = sum_l T(j,l) V(i,l) and b_j = sum_l T(j,l) zp_l (l in [j, i)), which need neither.
+    if (warp == 0) {
+        T alpha = zero, ypi0 = zero;
+        if (lane == 0) {                               // issued before the totals' round trip
+            alpha = A::ldg(st.ys + i);
+            ypi0 = sol ? A::ldg(st.yp + i) : zero;
         }
-        scT[0] = beta; scT[1] = tau; scT[2] = vs;
-        scT[3] = sol ? A::sub(ypi0, A::mul(tau, A::add(ypi0, A::mul(CR, vs)))) : zero;
+        T SG, CR;
+        warp_total2<A>(st.blk, 2, SG, CR);
+        if (lane == 0) {
+            T beta, tau, vs;
+            if (A::is_zero(SG)) {
+                beta = alpha; tau = zero; vs = zero;
+            } else {
+                const T nrm = A::sqrt_(A::add(A::mul(alpha, alpha), SG));
+                beta = A::nonneg(alpha) ? A::neg(nrm) : nrm;
+                tau = A::div(A::sub(beta, alpha), beta);
+                vs = A::div(A::one(), A::sub(alpha, beta));
+            }
+            scT[0] = beta; scT[1] = tau; scT[2] = vs;
+            scT[3] = sol ? A::sub(ypi0, A::mul(tau, A::add(ypi0, A::mul(CR, vs)))) : zero;
+        }
     }
+    const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
+    auto tdots = [&](int j, T& da, T& db) {
+        const double* tr = st.TT + (size_t)j * mm;
+        Acc ca[2] = {A::acc0(), A::acc0()}, cb[2] = {A::acc0(), A::acc0()};
+        for (int lb = j; lb < i; lb += 32 * 4) {       // loads of 4 entries per lane first
+            T tv[4], vv[4], zv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int l = lb + 32 * q + lane;
+                const bool ok = l < i;
+                tv[q] = ok ? A::ld(tr + l) : zero;
+                vv[q] = ok ? A::ld(vrow_i + l) : zero;
+                zv[q] = ok ? A::ldg(st.zp + l) : zero;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                A::acc(ca[q & 1], tv[q], vv[q]);
+                A::acc(cb[q & 1], tv[q], zv[q]);
+            }
+        }
+        da = A::wsum(A::add(A::val(ca[0]), A::val(ca[1])));
+        db = A::wsum(A::add(A::val(cb[0]), A::val(cb[1])));
+    };
+    const int gw1 = blockIdx.x + G * (warp - 1), nw1 = G * (NW - 1);
+    const bool first = warp >= 1 && gw1 < i;
+    T da0 = zero, db0 = zero;
+    if (first) tdots(gw1, da0, db0);
     __syncthreads();
     const T beta = scT[0], tau = scT[1], vs = scT[2], ypi = scT[3];
     if (A::is_zero(beta)) {
         if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
         return;
     }
+    auto finish = [&](int j, T da, T db) {           // lane 0: column j's entries of T, R_S^{-1}, x
+        const T t = A::neg(A::mul(tau, A::add(da, A::mul(vs, db))));
+        A::st(st.T + (size_t)i * mm + j, t);
+        A::st(st.TT + (size_t)j * mm + i, t);
+        const T cnew = A::neg(A::div(A::ldg(st.d1 + j), beta));   // R_S^{-1}(j, i)
+        A::st(st.RinvT + (size_t)j * mm + i, cnew);
+        if (sol) {
+            const double xj = A::to_d(A::add(A::ldg(st.d2 + j), A::mul(cnew, ypi)));
+            st.R[(size_t)a.xcol * st.ldr + j] = xj;
+            st.coef[j] = xj * st.sigma[j];
+        }
+    };
+    if (first && lane == 0) finish(gw1, da0, db0);
+    if (warp >= 1)
+        for (int j = gw1 + nw1; j < i; j += nw1) {
+            T da, db;
+            tdots(j, da, db);
+            if (lane == 0) finish(j, da, db);
+        }
     for (int l = gtid; l < k; l += nthreads) {
         const T vl = l < i ? zero : (l == i ? A::one() : A::mul(A::ldg(st.ys + l), vs));
         A::st(st.V + (size_t)i * k + l, vl);
@@ -602,31 +673,6 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             const double xi = A::to_d(A::div(ypi, beta));
             st.R[(size_t)a.xcol * st.ldr + i] = xi;
             st.coef[i] = xi * inv_r;
-        }
-    }
-    const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
-    for (int j = gwarp; j < i; j += nwarps) {
-        // T(j, i) = -tau sum_{j<=l<i} T(j,l) z_l with z_l = V(i,l) + vs zp_l
-        const double* tr = st.TT + (size_t)j * mm;
-        Acc c0 = A::acc0(), c1 = A::acc0();
-        int l = j + lane;
-        for (; l + 32 < i; l += 64) {
-            A::acc(c0, A::ld(tr + l), A::add(A::ld(vrow_i + l), A::mul(vs, A::ldg(st.zp + l))));
-            A::acc(c1, A::ld(tr + l + 32), A::add(A::ld(vrow_i + l + 32), A::mul(vs, A::ldg(st.zp + l + 32))));
-        }
-        if (l < i) A::acc(c0, A::ld(tr + l), A::add(A::ld(vrow_i + l), A::mul(vs, A::ldg(st.zp + l))));
-        const T d = A::wsum(A::add(A::val(c0), A::val(c1)));
-        if (lane == 0) {
-            const T t = A::neg(A::mul(tau, d));
-            A::st(st.T + (size_t)i * mm + j, t);
-            A::st(st.TT + (size_t)j * mm + i, t);
-            const T cnew = A::neg(A::div(A::ldg(st.d1 + j), beta));   // R_S^{-1}(j, i)
-            A::st(st.RinvT + (size_t)j * mm + i, cnew);
-            if (sol) {
-                const double xj = A::to_d(A::add(A::ldg(st.d2 + j), A::mul(cnew, ypi)));
-                st.R[(size_t)a.xcol * st.ldr + j] = xj;
-                st.coef[j] = xj * st.sigma[j];
-            }
         }
     }
     if (trace) trace[7] = globaltimer();
