@@ -231,18 +231,22 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     return A::from_d((v0 + v1) + (v2 + v3));
 }
 
-// Sum over g in [0, ng) of first-level group sums red[g * k + l] (type A::T, this launch).
+// Sum over g in [0, ng) of first-level group sums red[g * k + l] (type A::T, this launch):
+// the loads of up to 16 groups are issued before the adds.
 template <class A>
 __device__ __forceinline__ typename A::T group_total(const double* red, int ng, int k, int l) {
     using T = typename A::T;
     T v0 = A::zero(), v1 = A::zero();
-    int g = 0;
-#pragma unroll 4
-    for (; g + 1 < ng; g += 2) {
-        v0 = A::add(v0, A::ldg(red + (size_t)g * k + l));
-        v1 = A::add(v1, A::ldg(red + (size_t)(g + 1) * k + l));
+    for (int g0 = 0; g0 < ng; g0 += 16) {
+        T v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = g0 + q < ng ? A::ldg(red + (size_t)(g0 + q) * k + l) : A::zero();
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+            if (g0 + q < ng) v0 = A::add(v0, v[q]);
+            if (g0 + q + 1 < ng) v1 = A::add(v1, v[q + 1]);
+        }
     }
-    if (g < ng) v0 = A::add(v0, A::ldg(red + (size_t)g * k + l));
     return A::add(v0, v1);
 }
 
@@ -329,75 +333,83 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     __syncthreads();
     const T s_scale = scT[6], p_scale = scT[7];
 
-    // ---- phase 0b: a warp per 32 rows (lane = row), each lane summing the groups (or partials)
-    //      of its row in order: s', p and their squared norms (FP64); and M(:, i-1)
+    // ---- phase 0b: items (32-row segment, vector s' or p), a warp each with lane = row, sum
+    //      the groups (or partials) of their rows in order and the squared norms (FP64); the
+    //      warps of the other rows of warps form M(:, i-1), one row each
     {
-        double nrm[2] = {0.0, 0.0};
+        double nrm = 0.0;
         const int nseg = (k + 31) / 32;
-        const bool busy = gwarp < nseg;
-        for (int seg = gwarp; seg < nseg; seg += nwarps) {
+        const int nitems = nseg * 2;
+        for (int it = gwarp; it < nitems; it += nwarps) {
+            const int seg = it >> 1, vec = it & 1;       // vec 0: s', vec 1: p
             const int l = seg * 32 + lane;
-            if (l >= k) continue;
-            if (app) {
-                const T v = A::mul(level1 ? group_total<A>(st.red, sgroups, k, l)
-                                          : part_sum<A>(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l),
-                                   s_scale);
-                A::st(st.sbuf + l, v);
+            if (vec == 0 ? !app : !sol) continue;
+            if (l < k) {
+                T v;
+                if (vec == 0) {
+                    v = A::mul(level1 ? group_total<A>(st.red, sgroups, k, l)
+                                      : part_sum<A>(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l), s_scale);
+                    A::st(st.sbuf + l, v);
+                } else {
+                    v = A::mul(!p_parts ? A::from_d(a.p_vec[l])
+                               : level1 ? group_total<A>(st.red + (size_t)sgroups * k, pgroups, k, l)
+                                        : part_sum<A>(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l), p_scale);
+                    A::st(st.pbuf + l, v);
+                }
                 const double vd = A::to_d(v);
-                nrm[0] = fma(vd, vd, nrm[0]);
-            }
-            if (sol) {
-                const T v = A::mul(!p_parts ? A::from_d(a.p_vec[l])
-                                   : level1 ? group_total<A>(st.red + (size_t)sgroups * k, pgroups, k, l)
-                                            : part_sum<A>(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l),
-                                   p_scale);
-                A::st(st.pbuf + l, v);
-                const double vd = A::to_d(v);
-                if (a.p_store) a.p_store[l] = vd;
-                nrm[1] = fma(vd, vd, nrm[1]);
+                if (vec == 1 && a.p_store) a.p_store[l] = vd;
+                nrm = fma(vd, vd, nrm);
             }
         }
+        // the squared norms: per warp, then per CTA (slot 0: s', slot 1: p)
+        const bool busy = gwarp < nitems;              // idle warps skip the FP64 shuffles
+        if (busy) nrm = warp_sum(nrm);
+        double nv[2] = {busy && (gwarp & 1) == 0 ? nrm : 0.0, busy && (gwarp & 1) == 1 ? nrm : 0.0};
         if (i > 0) {
             // M(:, i-1) = V(:, 0:i) T(0:i, i-1): T's column i-1 was completed by the previous
             // launch; warp per row of the row-major copy VT, lanes over the columns
             const double* tc = st.T + (size_t)(i - 1) * mm;
-            for (int l = gwarp; l < k; l += nwarps) {
+            const int first = min(nitems, nwarps - 1);     // warps after the items' warps (if any)
+            const int mw = nwarps - first;
+            for (int l = gwarp - first; l < k; l += mw) {
+                if (l < 0) break;
                 T d, unused;
                 warp_row_dot2<A>(st.VT + (size_t)l * mm, tc, tc, min(i, l + 1), true, false, d, unused);
                 if (lane == 0) A::st(st.M + (size_t)(i - 1) * k + l, d);
             }
         }
-        if (busy) {                                    // idle warps skip the FP64 shuffles
-            nrm[0] = warp_sum(nrm[0]);
-            nrm[1] = warp_sum(nrm[1]);
-        }
-        block_sum_lane0<FineF64, 2>(nrm, shd);
-        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm[0]; st.blk[blockIdx.x * 4 + 1] = nrm[1]; }
+        block_sum_lane0<FineF64, 2>(nv, shd);
+        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nv[0]; st.blk[blockIdx.x * 4 + 1] = nv[1]; }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[2] = globaltimer();
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
-    // Warp 0 reads the squared norms' totals and thread 0 forms the phase's scalars (one thread:
-    // an FP64 square root or division is a long sequence on the FP64 pipe) while warps 4..15,
-    // three quads of one warp per SM sub-partition, compute the column dots; the quads' sums are
-    // scaled once both are done.
+    // Warp 0 reads the squared norms' totals and forms the phase's scalars (FP64 square roots
+    // and divisions are long sequences on the FP64 pipe, so no other warp repeats them) while
+    // warps 4..15, three quads of one warp per SM sub-partition, compute the column dots; the
+    // quads' sums are scaled once both are done.
     const int warp = tid >> 5;
     if (warp == 0) {
         double tn0, tn1;
         warp_total2<FineF64>(st.blk, 0, tn0, tn1);
+        // One instruction stream for the warp: the square root of ||s'||^2 (lanes 0, 1) and of
+        // ||p||^2 (lane 2) together, then 1/r_ii (the same rounded root: sigma_i is exactly
+        // 1/r_ii); lane 0 keeps r_ii and the breakdown test, lane 1 sigma_i and its A::T form.
+        const double y = sqrt(lane == 2 ? tn1 : tn0);
+        const double ir = app ? 1.0 / y : 1.0;
         if (lane == 0) {
-            const double r0 = sqrt(tn0);
-            int code = 0;                              // 1: non-finite r_ii, 2: breakdown
-            if (app) code = !isfinite(r0) ? 1 : (!(r0 > 16.0 * 0x1p-53 * pref) ? 2 : 0);
-            const double ir = code == 0 ? 1.0 / r0 : 1.0;
-            sc[0] = r0;
-            sc[1] = app ? ir : 1.0;
-            sc[2] = (app && a.p_lag) ? ir : 1.0;
-            sc[3] = sol ? sqrt(tn1) : 0.0;
+            const int code = !app ? 0 : (!isfinite(y) ? 1 : (!(y > 16.0 * 0x1p-53 * pref) ? 2 : 0));
+            sc[0] = y;
             sc[4] = (double)code;
-            scT[0] = A::from_d(sc[1]);
-            scT[1] = A::from_d(sc[2]);
+        } else if (lane == 1) {
+            sc[1] = ir;
+            sc[2] = a.p_lag ? ir : 1.0;
+            const T irT = A::from_d(ir);
+            scT[0] = irT;
+            scT[1] = a.p_lag ? irT : A::one();
+        } else if (lane == 2) {
+            sc[3] = sol ? y : 0.0;
         }
     }
     {
