@@ -691,31 +691,36 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
 }
 
 // Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
-// Block b handles column b: sums of squares of (I - S^T S)(0:m, b) and (P - S R)(:, b).
+// Block t handles the columns b = t and b = m-1-t (equal total work per block): the entries
+// (I - S^T S)(a, b) for a <= b (the matrix is symmetric, so the off-diagonal squares count twice)
+// and the column (P - S R)(:, b), accumulated as sums of squares.
 __global__ void __launch_bounds__(256) cert_kernel(const double* S, int k, int m, const double* R, int64_t ldr,
                                                    const double* P, double* work) {
     __shared__ double sh[256];
-    const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double g2 = 0.0;
-    for (int a = w; a < m; a += 8) {
-        double d = 0.0;
-        for (int l = lane; l < k; l += 32) d = fma(S[(size_t)a * k + l], S[(size_t)b * k + l], d);
-        d = warp_sum(d);
-        const double e = (a == b ? 1.0 : 0.0) - d;
-        g2 += lane == 0 ? e * e : 0.0;
-    }
-    double e2 = 0.0, p2 = 0.0;
-    for (int l = threadIdx.x; l < k; l += 256) {
-        double v = P[(size_t)b * k + l];
-        p2 += v * v;
-        for (int j = 0; j <= b; ++j) v = fma(-S[(size_t)j * k + l], R[(size_t)b * ldr + j], v);
-        e2 += v * v;
+    double g2 = 0.0, e2 = 0.0, p2 = 0.0;
+    const int t = blockIdx.x;
+    for (int h = 0; h < 2; ++h) {
+        const int b = h == 0 ? t : m - 1 - t;
+        if (h == 1 && b == t) break;
+        for (int a = w; a <= b; a += 8) {
+            double d = 0.0;
+            for (int l = lane; l < k; l += 32) d = fma(S[(size_t)a * k + l], S[(size_t)b * k + l], d);
+            d = warp_sum(d);
+            const double e = (a == b ? 1.0 : 0.0) - d;
+            g2 += lane == 0 ? (a == b ? e * e : 2.0 * (e * e)) : 0.0;
+        }
+        for (int l = threadIdx.x; l < k; l += 256) {
+            double v = P[(size_t)b * k + l];
+            p2 += v * v;
+            for (int j = 0; j <= b; ++j) v = fma(-S[(size_t)j * k + l], R[(size_t)b * ldr + j], v);
+            e2 += v * v;
+        }
     }
     g2 = block_sum<256>(g2, sh);
     e2 = block_sum<256>(e2, sh);
     p2 = block_sum<256>(p2, sh);
-    if (threadIdx.x == 0) { work[3 * b] = g2; work[3 * b + 1] = e2; work[3 * b + 2] = p2; }
+    if (threadIdx.x == 0) { work[3 * t] = g2; work[3 * t + 1] = e2; work[3 * t + 2] = p2; }
 }
 
 __global__ void cert_final_kernel(const double* work, int m, double* out) {
@@ -785,9 +790,10 @@ int rgs_ls_max_blocks(int num_sms) {
 
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
                              const double* P, double* out2, double* work) {
-    cert_kernel<<<m, 256, 0, ctx->stream>>>(S, k, m, R, ldr, P, work);
+    const int nb = (m + 1) / 2;                     // block t: columns t and m-1-t
+    cert_kernel<<<nb, 256, 0, ctx->stream>>>(S, k, m, R, ldr, P, work);
     RGS_CUDA(cudaGetLastError());
-    cert_final_kernel<<<1, 256, 0, ctx->stream>>>(work, m, out2);
+    cert_final_kernel<<<1, 256, 0, ctx->stream>>>(work, nb, out2);
     RGS_CUDA(cudaGetLastError());
     ctx->launches += 2;
 }
