@@ -329,7 +329,7 @@ void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n
 
 // spmv.cu
 void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* out);
-int rgs_spmv_nparts(const rgs_context* ctx, int64_t n);
+int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm);
 int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
                     const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale = nullptr);
 int rgs_norm_grid(const rgs_context* ctx, int64_t n);

@@ -56,64 +56,97 @@ struct SpmvParams {
     const int* ctl;
 };
 
-// (A x)_r for one row, stored to w and returned.  The column indices and values of up to
-// RB nonzeros are loaded together, then the gathers of x, then the products (two independent
-// accumulation chains), so a row costs three memory round trips instead of one per nonzero.
+// (A x) for the rows rbase + threadIdx.x + 256 e (e = 0..3) of a tile, stored to w and returned
+// in z[e].  Lanes take consecutive rows, so a warp's row pointers, column indices, values and
+// stores of w are contiguous.  PR rows at a time go through three stages: the column indices
+// and values of their first RB nonzeros, the gathers of x, the products (two accumulation chains
+// per row); a pair of rows thus costs three memory round trips.  Entries past the first RB of a
+// row (none for the stencil operators of the workloads) are added one by one afterwards.
 constexpr int RB = 8;
 
 template <typename TX, bool DFM>
-__device__ __forceinline__ typename std::conditional<DFM, df, double>::type row_product(const SpmvParams& p,
-                                                                                       const TX* x, int64_t r) {
+struct SpmvArith {
     using V = typename std::conditional<DFM, df, double>::type;
-    if (r >= p.n) return FW<V>::zero();
-    const int b0 = __ldg(p.rowptr + r), b1 = __ldg(p.rowptr + r + 1);
-    V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
-    for (int q0 = b0; q0 < b1; q0 += RB) {
-        int c[RB];
-        V v[RB];
-        float xs[RB];
-        double xd[RB];
+    using XV = typename std::conditional<DFM, float, double>::type;
+    __device__ static XV xload(const TX* x, int c) {
+        if constexpr (DFM) return xf(x, c);
+        else return (double)x[c];
+    }
+    __device__ static V vload(const SpmvParams& p, int q) {
+        if constexpr (DFM) return p.vdf[q];
+        else return __ldg(p.val + q);
+    }
+    __device__ static V madd(V acc, V v, XV xv) {
+        if constexpr (DFM) return df_add(acc, df_mul_f(v, xv));
+        else return fma(v, xv, acc);
+    }
+};
+
+template <typename TX, bool DFM, int PR>
+__device__ __forceinline__ void tile_rows(const SpmvParams& p, const TX* x, int64_t rbase,
+                                          typename std::conditional<DFM, df, double>::type z[4]) {
+    using AR = SpmvArith<TX, DFM>;
+    using V = typename AR::V;
+    using XV = typename AR::XV;
+    int b0[4], b1[4];
 #pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            if (q0 + t < b1) {
-                c[t] = __ldg(p.colind + q0 + t);
-                if constexpr (DFM) v[t] = p.vdf[q0 + t];
-                else v[t] = __ldg(p.val + q0 + t);
-            }
-        }
+    for (int e = 0; e < 4; ++e) {
+        const int64_t r = rbase + threadIdx.x + (int64_t)TILE_THREADS * e;
+        b0[e] = r < p.n ? __ldg(p.rowptr + r) : 0;
+        b1[e] = r < p.n ? __ldg(p.rowptr + r + 1) : 0;
+    }
 #pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            if (q0 + t < b1) {
-                if constexpr (DFM) xs[t] = xf(x, c[t]);
-                else xd[t] = (double)x[c[t]];
-            }
-        }
+    for (int e0 = 0; e0 < 4; e0 += PR) {
+        int c[PR][RB];
+        V v[PR][RB];
+        XV xv[PR][RB];
 #pragma unroll
-        for (int t = 0; t < RB; ++t) {
-            if (q0 + t < b1) {
-                if constexpr (DFM) {
-                    const df pr = df_mul_f(v[t], xs[t]);
-                    if (t & 1) acc1 = df_add(acc1, pr); else acc0 = df_add(acc0, pr);
-                } else {
-                    if (t & 1) acc1 = fma(v[t], xd[t], acc1); else acc0 = fma(v[t], xd[t], acc0);
+        for (int h = 0; h < PR; ++h)
+#pragma unroll
+            for (int t = 0; t < RB; ++t) {
+                const int q = b0[e0 + h] + t;
+                if (q < b1[e0 + h]) {
+                    c[h][t] = __ldg(p.colind + q);
+                    v[h][t] = AR::vload(p, q);
                 }
             }
+#pragma unroll
+        for (int h = 0; h < PR; ++h)
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+                if (b0[e0 + h] + t < b1[e0 + h]) xv[h][t] = AR::xload(x, c[h][t]);
+#pragma unroll
+        for (int h = 0; h < PR; ++h) {
+            const int e = e0 + h;
+            V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+                if (b0[e] + t < b1[e]) {
+                    if (t & 1) acc1 = AR::madd(acc1, v[h][t], xv[h][t]);
+                    else acc0 = AR::madd(acc0, v[h][t], xv[h][t]);
+                }
+            for (int q = b0[e] + RB; q < b1[e]; ++q) acc0 = AR::madd(acc0, AR::vload(p, q), AR::xload(x, __ldg(p.colind + q)));
+            z[e] = FW<V>::add(acc0, acc1);
         }
     }
-    if constexpr (DFM) {
-        const df a = df_add(acc0, acc1);
-        reinterpret_cast<df*>(p.w)[r] = a;
-        return a;
-    } else {
-        double a = acc0 + acc1;
-        if (p.yscale) a *= *p.yscale;
-        reinterpret_cast<double*>(p.w)[r] = a;
-        return a;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int64_t r = rbase + threadIdx.x + (int64_t)TILE_THREADS * e;
+        if (r < p.n) {
+            if constexpr (DFM) {
+                reinterpret_cast<df*>(p.w)[r] = z[e];
+            } else {
+                if (p.yscale) z[e] *= *p.yscale;
+                reinterpret_cast<double*>(p.w)[r] = z[e];
+            }
+        } else {
+            z[e] = FW<V>::zero();
+        }
     }
 }
 
 template <typename TX, bool DFM, bool SRHT>
-__global__ void __launch_bounds__(TILE_THREADS, 3) spmv_sketch_kernel(SpmvParams p) {
+__global__ void __launch_bounds__(TILE_THREADS, DFM ? 2 : 3) spmv_sketch_kernel(SpmvParams p) {
     using V = typename std::conditional<DFM, df, double>::type;
     using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
@@ -127,11 +160,19 @@ __global__ void __launch_bounds__(TILE_THREADS, 3) spmv_sketch_kernel(SpmvParams
         __syncthreads();
     }
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-        const int64_t r0 = (int64_t)tile * TILE + threadIdx.x * 4;
+        const int64_t rbase = (int64_t)tile * TILE;
         V z[4];
+        tile_rows<TX, DFM, DFM ? 2 : 1>(p, x, rbase, z);
+        if (SRHT) {
+            // the transform takes rows 4t .. 4t+3 in thread t: transpose through shared memory
+            __syncthreads();                           // the previous tile's readers of zt are done
 #pragma unroll
-        for (int e = 0; e < 4; ++e) z[e] = row_product<TX, DFM>(p, x, r0 + e);
-        if (SRHT) srht_tile<V>(z, r0, p.n, tile, p.signbits, srow, p.k, zt, part);
+            for (int e = 0; e < 4; ++e) zt[threadIdx.x + TILE_THREADS * e] = z[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 4; ++e) z[e] = zt[threadIdx.x * 4 + e];
+            srht_tile<V>(z, rbase + threadIdx.x * 4, p.n, tile, p.signbits, srow, p.k, zt, part);
+        }
     }
     if (SRHT) {
         __syncthreads();
@@ -363,9 +404,11 @@ void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* ou
     ctx->launches++;
 }
 
-int rgs_spmv_nparts(const rgs_context* ctx, int64_t n) {
+// One wave of resident CTAs: 3 per SM with FP64 products (80 registers), 2 with double-float
+// products (two rows in flight per thread: 128 registers).
+int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm) {
     const int ntiles = (int)((n + TILE - 1) / TILE);
-    return std::max(1, std::min(ntiles, ctx->num_sms * 3));     // 3 resident CTAs per SM (80 registers)
+    return std::max(1, std::min(ntiles, ctx->num_sms * (dfm ? 2 : 3)));
 }
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
@@ -390,7 +433,7 @@ int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const v
         p.k = sk->k;
         p.partials = partials;
     }
-    const int grid = rgs_spmv_nparts(ctx, A.n);
+    const int grid = rgs_spmv_nparts(ctx, A.n, dfm != 0);
     const size_t smem = srht ? TILE * 8 + (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 + 16 : 16;
     if (dfm) {
         RGS_REQUIRE(xtype != RGS_F64, "double-float product needs an FP32 or BF16 vector");
