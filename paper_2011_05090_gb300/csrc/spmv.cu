@@ -58,10 +58,10 @@ struct SpmvParams {
 
 // (A x) for the rows rbase + threadIdx.x + 256 e (e = 0..3) of a tile, stored to w and returned
 // in z[e].  Lanes take consecutive rows, so a warp's row pointers, column indices, values and
-// stores of w are contiguous.  PR rows at a time go through three stages: the column indices
-// and values of their first RB nonzeros, the gathers of x, the products (two accumulation chains
-// per row); a pair of rows thus costs three memory round trips.  Entries past the first RB of a
-// row (none for the stencil operators of the workloads) are added one by one afterwards.
+// stores of w are contiguous.  PR rows at a time (one, in the launches below) go through three
+// stages: the column indices and values of their first RB nonzeros, the gathers of x, the
+// products (two accumulation chains per row).  Entries past the first RB of a row (none for
+// the stencil operators of the workloads) are added one by one afterwards.
 constexpr int RB = 8;
 
 template <typename TX, bool DFM>
@@ -146,7 +146,7 @@ __device__ __forceinline__ void tile_rows(const SpmvParams& p, const TX* x, int6
 }
 
 template <typename TX, bool DFM, bool SRHT>
-__global__ void __launch_bounds__(TILE_THREADS, DFM ? 2 : 3) spmv_sketch_kernel(SpmvParams p) {
+__global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams p) {
     using V = typename std::conditional<DFM, df, double>::type;
     using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(TILE_THREADS, DFM ? 2 : 3) spmv_sketch_kernel(
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         const int64_t rbase = (int64_t)tile * TILE;
         V z[4];
-        tile_rows<TX, DFM, DFM ? 2 : 1>(p, x, rbase, z);
+        tile_rows<TX, DFM, 1>(p, x, rbase, z);
         if (SRHT) {
             // the transform takes rows 4t .. 4t+3 in thread t: transpose through shared memory
             __syncthreads();                           // the previous tile's readers of zt are done
@@ -404,11 +404,14 @@ void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* ou
     ctx->launches++;
 }
 
-// One wave of resident CTAs: 3 per SM with FP64 products (80 registers), 2 with double-float
-// products (two rows in flight per thread: 128 registers).
+// One wave of resident CTAs: 4 per SM (64 registers).  Measured on the 128^3 RGMRES step:
+// one row at a time at 4 CTAs per SM 178.0 us per step, at 3 CTAs per SM 184.7-185.5; two rows
+// in flight at 2 CTAs per SM (128 registers) 193.1, two rows at 3 CTAs per SM (spilling) 197.6,
+// four rows at 1 CTA per SM 226.8: occupancy hides the gathers better than rows in flight.
 int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm) {
+    (void)dfm;
     const int ntiles = (int)((n + TILE - 1) / TILE);
-    return std::max(1, std::min(ntiles, ctx->num_sms * (dfm ? 2 : 3)));
+    return std::max(1, std::min(ntiles, ctx->num_sms * 4));
 }
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.

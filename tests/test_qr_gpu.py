@@ -266,3 +266,52 @@ def test_objects_may_outlive_their_handle():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
+
+
+# ------------------------------------------------------------------ the bench workload, full size
+def test_c2_full_size_sampled_parity(h):
+    """The 2^20 x 500 factorization of the benchmark (cond 1e10, SRHT k = 2000, FP32 basis, the
+    bench's tuned launch shape), checked on sampled columns against what the oracle computes one
+    column at a time from the GPU's own outputs: the sketches Theta q'_i (steps 4-6), the
+    sketched least-squares solutions (step 2, oracle Householder on the computed S), the FP32
+    update chain (step 3, oracle emulation), plus Delta_m and ||W - QR|| as properties."""
+    n, m, k = 1 << 20, 500, 2000
+    W = synth.gdw_matrix(n, m, 1e10, 0, device="cuda").T
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 0)
+    rgs.rgs_autotune_update(h, sk, m // 2, torch.float32)
+    Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
+    R = rgs.colmajor_empty(m, m)
+    S = rgs.colmajor_empty(k, m)
+    qs = torch.empty(m, dtype=torch.float64, device="cuda")
+    info = rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, S=S)
+    torch.cuda.synchronize()
+    Rh, Sh, sig = R.cpu().numpy(), S.cpu().numpy(), qs.cpu().numpy()
+    osk = Sketch("srht", n, k, 0)
+    cols = [0, 1, 7, 100, 250, 499]
+    Wc = W[:, cols].cpu().numpy()
+    Qc = Q[:, cols].double().cpu().numpy()
+    P, Sq = osk.apply(Wc), osk.apply(Qc)
+    for c, i in enumerate(cols):
+        r_or = np.linalg.norm(Sq[:, c])                      # r_ii = ||Theta q'_i||
+        assert abs(Rh[i, i] - r_or) <= 1e-12 * r_or, i
+        assert rel(Sh[:, i], Sq[:, c] / r_or) <= 1e-12, i    # s_i
+        if i > 0:
+            x = orgs.ls_householder(Sh[:, :i], P[:, c])      # step 2 on the computed S
+            assert rel(Rh[:i, i], x) <= 1e-10, i
+    # step 3: the FP32 chain q'_i = fl32(w_i) - sum_j c_j q'_j, c_j = fl32(R(j, i) sigma_j)
+    for i in (7, 100):
+        Qp = Q[:, :i].double().cpu().numpy()
+        ref = orgs.update_fp32(W[:, i].cpu().numpy(), Qp, Rh[:i, i] * sig[:i])
+        got = Q[:, i].double().cpu().numpy()
+        same = np.mean(got == ref)
+        print(f"column {i}: step-3 chain bit-identical in {same:.6f} of the rows, "
+              f"rel diff {rel(got, ref):.2e}")
+        assert same >= 0.999 and rel(got, ref) <= 1e-6
+    # properties of the whole factorization
+    d = np.linalg.norm(np.eye(m) - Sh.T @ Sh)
+    assert abs(d - info["delta"]) <= 1e-8 * d
+    E = W - (Q.double() * qs[None, :]) @ R
+    err = (torch.linalg.norm(E) / torch.linalg.norm(W)).item()
+    del E
+    print(f"full size: ||W - QR||/||W|| = {err:.3e}, Delta_m = {info['delta']:.3e}")
+    assert err <= 1e-6
