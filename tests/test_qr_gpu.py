@@ -315,3 +315,23 @@ def test_c2_full_size_sampled_parity(h):
     del E
     print(f"full size: ||W - QR||/||W|| = {err:.3e}, Delta_m = {info['delta']:.3e}")
     assert err <= 1e-6
+
+
+@pytest.mark.parametrize("scale", [2.0 ** 100, 2.0 ** -80])
+def test_double_float_least_squares_on_scaled_inputs(h, scale):
+    """FP32 basis (double-float least squares, FP64 squared norms), W scaled by 2^100 (1.3e30) or
+    2^-80 (8.3e-25): every step is equivariant under a power-of-two scaling while no value leaves
+    FP32's exponent range, so R scales by the same factor and the basis is unchanged, up to
+    rounding at most (no overflow, underflow or loss of the double-float low words)."""
+    n, m, k = 20000, 30, 120
+    A = synth.gdw_matrix(n, m, 1e6, 14).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 5)
+    ref = run_qr(h, sk, to_gpu(A), qdtype=torch.float32, qscale=True)
+    g = run_qr(h, sk, to_gpu(A * scale), qdtype=torch.float32, qscale=True)
+    Qr = ref["Q"] * ref["qscale"][None, :]
+    Qg = g["Q"] * g["qscale"][None, :]
+    assert np.all(np.isfinite(g["R"])) and np.all(np.isfinite(Qg))
+    print(f"scale {scale:.3e}: R {rel(g['R'] / scale, ref['R']):.2e}, Q {rel(Qg, Qr):.2e}, "
+          f"bit-identical R: {np.array_equal(g['R'], ref['R'] * scale)}")
+    assert rel(g["R"] / scale, ref["R"]) <= 1e-12
+    assert rel(Qg, Qr) <= 1e-12
