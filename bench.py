@@ -586,7 +586,10 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32/df/f64",
+               "dtype_detail": "basis and update in f32; sketch and least squares in double-float "
+                               "(f32 pairs); squared norms, R and the returned scales in f64",
+               "data": "synthetic",
                "config": {"workload": WORKLOAD if m == M_COLS else f"profiling case m={m}", "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
                           "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}",
                           "tuning": tuning},

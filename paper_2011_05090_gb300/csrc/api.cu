@@ -291,6 +291,13 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             dR = reinterpret_cast<double*>(base + wb + qb);
             if (pipelined) {
                 if (!h->copy_stream) RGS_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+                // a previous call that failed midway may have left copies in flight on the copy
+                // stream: the bound stream waits for them before the staging is written again
+                cudaEvent_t prev_ev;
+                RGS_CUDA(cudaEventCreateWithFlags(&prev_ev, cudaEventDisableTiming));
+                qdone.push_back(prev_ev);                        // (destroyed with the others)
+                RGS_CUDA(cudaEventRecord(prev_ev, h->copy_stream));
+                RGS_CUDA(cudaStreamWaitEvent(st, prev_ev, 0));
                 cudaEvent_t start_ev;
                 RGS_CUDA(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
                 wready.push_back(start_ev);                      // (destroyed with the others)

@@ -418,20 +418,25 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
     const int k = I.k, m = I.m, ld = m + 1;
     const int t = threadIdx.x;
     __shared__ int sh_stop, sh_bad;
+    // the step's scalars (square roots, reciprocals) come from thread 0 through shared memory:
+    // FP64 square roots and divisions are long sequences on this GPU's FP64 pipe
+    __shared__ double sh_sc[4];
     double a = 0.0;
     for (int l = t; l < k; l += BT) a = fma(ss[l], ss[l], a);
-    const double rii = sqrt(cta_sum(a, red));
-    const double pn = __ldcg(I.scal + 3);
+    const double sum_s = cta_sum(a, red);
     if (t == 0) {
+        const double r0 = sqrt(sum_s);
+        sh_sc[0] = r0;
+        sh_sc[1] = r0 > 0.0 ? 1.0 / r0 : 0.0;
         sh_stop = 0;
-        sh_bad = !isfinite(rii) ? 1 : 0;
+        sh_bad = !isfinite(r0) ? 1 : 0;
         // r_ii at the rounding level of ||p_i||: the Krylov space is invariant (happy breakdown)
-        if (i > 0 && !(rii > 16.0 * 0x1p-53 * pn)) sh_stop = i;
-        if (i == 0 && !(rii > 0.0)) sh_bad = 1;
+        if (i > 0 && !(r0 > 16.0 * 0x1p-53 * __ldcg(I.scal + 3))) sh_stop = i;
+        if (i == 0 && !(r0 > 0.0)) sh_bad = 1;
     }
     __syncthreads();
     if (sh_bad) return false;
-    const double sig = rii > 0.0 ? 1.0 / rii : 0.0;
+    const double rii = sh_sc[0], sig = sh_sc[1];
     if (t == 0) I.sigma[i] = sig;
     // Givens rotation of Hessenberg column i-1 = [R(0:i-1, i); r_ii]
     if (i == 0) {
@@ -457,9 +462,16 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
         }
         a = 0.0;
         for (int l = t; l < k; l += BT) a = fma(ss[l], ss[l], a);
-        const double rho = sqrt(cta_sum(a, red));
+        const double sum_r = cta_sum(a, red);
+        if (t == 0) {
+            const double r0 = sqrt(sum_r);
+            sh_sc[2] = r0;
+            sh_sc[3] = 1.0 / r0;
+        }
+        __syncthreads();
+        const double rho = sh_sc[2], irho = sh_sc[3];
         if (!(rho > 0.0) || !isfinite(rho)) return false;
-        for (int l = t; l < k; l += BT) Ui[l] = ss[l] / rho;
+        for (int l = t; l < k; l += BT) Ui[l] = ss[l] * irho;
         // R_S(0:i, i) and the new column of its inverse: Rinv(0:i-1, i) = -Rinv(0:i-1, 0:i-1) R_S(0:i-1, i) / rho
         double* RSc = I.RS + (size_t)i * ld;
         double* RIc = I.RSi + (size_t)i * ld;
@@ -472,17 +484,17 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
                 double s = 0.0;
                 for (int j = q + lane; j < i; j += 32) s = fma(I.RSi[(size_t)j * ld + q], RSc[j], s);
                 s = warp_sum(s);
-                if (lane == 0) RIc[q] = -s / rho;
+                if (lane == 0) RIc[q] = -s * irho;
             }
         }
-        if (t == 0) RIc[i] = 1.0 / rho;
+        if (t == 0) RIc[i] = irho;
         __syncthreads();
         // next coefficients: c = argmin ||S_{0:i} c - p_{i+1}||, p_{i+1} = sigma_i Theta A q'_i
         for (int l = t; l < k; l += BT) pp[l] *= sig;
         __syncthreads();
         a = 0.0;
         for (int l = t; l < k; l += BT) a = fma(pp[l], pp[l], a);
-        const double pnn = sqrt(cta_sum(a, red));
+        const double sum_p = cta_sum(a, red);
         cta_dots(I.U, k, i + 1, pp, h1);
         double* Rn = I.R + (size_t)(i + 1) * (m + 2);
         {
@@ -497,7 +509,7 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
                 }
             }
         }
-        if (t == 0) I.scal[3] = pnn;
+        if (t == 0) I.scal[3] = sqrt(sum_p);
     }
     __syncthreads();
     if (t == 0) {
@@ -508,14 +520,18 @@ __device__ bool leader_step(const BInst& I, int i, double stop_tol, double* ss, 
     return true;
 }
 
-// y = Hr(0:j, 0:j)^{-1} g(0:j), stored as sigma .* y (one warp)
-__device__ void hess_solve_warp(const BInst& I, int j, double* gs) {
+// y = Hr(0:j, 0:j)^{-1} g(0:j), stored as sigma .* y (one warp); the reciprocals of the diagonal
+// are formed by the lanes in parallel first, so the back substitution has no division in its chain
+__device__ void hess_solve_warp(const BInst& I, int j, double* gs, double* dinv) {
     const int lane = threadIdx.x;
     const int ld = I.m + 1;
-    for (int q = lane; q < j; q += 32) gs[q] = I.g[q];
+    for (int q = lane; q < j; q += 32) {
+        gs[q] = I.g[q];
+        dinv[q] = 1.0 / I.Hr[(size_t)q * ld + q];
+    }
     __syncwarp();
     for (int r = j - 1; r >= 0; --r) {
-        const double yr = gs[r] / I.Hr[(size_t)r * ld + r];
+        const double yr = gs[r] * dinv[r];
         for (int q = lane; q < r; q += 32) gs[q] = fma(-I.Hr[(size_t)r * ld + q], yr, gs[q]);
         if (lane == 0) I.y[r] = yr * I.sigma[r];
         __syncwarp();
@@ -744,7 +760,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
         }
         // H: y; X: x += Q' (sigma .* y)
         if (leader && t < 32) {
-            hess_solve_warp(I, steps, h1);
+            hess_solve_warp(I, steps, h1, h2);
             if (t == 0) {
                 I.flags[2] = steps;
                 I.out[2] += steps;
