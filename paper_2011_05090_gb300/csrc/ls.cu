@@ -37,8 +37,6 @@ constexpr int NW = LT / 32;    // warps per CTA
 constexpr int GS = 32;         // partial sketches summed per warp in the first reduction level
 constexpr int kTotMax = 8;     // per-CTA totals are read for up to 32 * kTotMax CTAs at once
 
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-
 // ------------------------------------------------------------------ arithmetic types
 struct FineF64 {
     using T = double;
