@@ -64,3 +64,31 @@ def test_missing_library_fails_loudly(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     assert "raised:" in out.stdout and "is missing" in out.stdout
+
+
+def _header_constants():
+    """Integer constants of the header: #define NAME <int> (or another constant), enum NAME = <int>."""
+    text = open(os.path.join(ROOT, "include", "librgs.h")).read()
+    consts = {}
+    for name, val in re.findall(r"^#define\s+(RGS_[A-Z0-9_]+)\s+([A-Za-z0-9_]+)\b", text, re.M):
+        if re.fullmatch(r"\d+", val):
+            consts[name] = int(val)
+        elif val in consts:
+            consts[name] = consts[val]
+    for name, val in re.findall(r"\b(RGS_[A-Z0-9_]+)\s*=\s*(\d+)", text):
+        consts[name] = int(val)
+    m = re.search(r"#define\s+RGS_NOALLOC_SCRATCH_BYTES\s+\(\(size_t\)(\d+)\s*<<\s*(\d+)\)", text)
+    if m:
+        consts["RGS_NOALLOC_SCRATCH_BYTES"] = int(m.group(1)) << int(m.group(2))
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    consts = _header_constants()
+    for must in ("RGS_OK", "RGS_ERR_BREAKDOWN", "RGS_F32", "RGS_SKETCH_SRHT", "RGS_QR_FP64_FINE",
+                 "RGS_QR_FP64_SKETCH", "RGS_PRECOND_LEARNED_CONV", "RGS_NOALLOC_SCRATCH_BYTES"):
+        assert must in consts, must
+    for name, val in consts.items():
+        if hasattr(rgs, name):
+            assert getattr(rgs, name) == val, name
+    assert all(hasattr(rgs, n) for n in consts if n.startswith(("RGS_ERR_", "RGS_QR_", "RGS_SKETCH_")))
