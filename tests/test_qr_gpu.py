@@ -177,6 +177,23 @@ def test_breakdown_reported_with_column(h):
     run_qr(h, sk, to_gpu(A))
 
 
+@pytest.mark.parametrize("kind,qdtype", [("srht", torch.float32), ("gaussian", torch.float64)])
+def test_nonfinite_input_reported(h, kind, qdtype):
+    """A NaN in column 3 of W: the sketched norm of that column is not finite, the call returns
+    RGS_ERR_NONFINITE naming the column, and the handle stays usable."""
+    n, m, k = 3000, 8, 40
+    A = synth.gdw_matrix(n, m, 10.0, 6).numpy().T.copy()
+    A[100, 3] = np.nan
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 2)
+    with pytest.raises(rgs.RgsError) as e:
+        run_qr(h, sk, to_gpu(A), qdtype=qdtype)
+    assert e.value.status == rgs.RGS_ERR_NONFINITE
+    assert "column 3" in str(e.value)
+    A[100, 3] = 0.5
+    g = run_qr(h, sk, to_gpu(A), qdtype=qdtype)
+    assert np.all(np.isfinite(g["R"]))
+
+
 @pytest.mark.parametrize("kind", ["srht", "gaussian"])
 @pytest.mark.parametrize("qdtype,qscale,pin", [(torch.float64, False, True), (torch.float32, True, True),
                                                (torch.float32, True, False), (torch.bfloat16, False, True)])
