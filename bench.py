@@ -547,7 +547,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qh)
             e_times.append(time.perf_counter() - t0)
-        e_s = statistics.median(e_times)
+        e_s = max_over_ranks(1e3 * statistics.median(e_times), world, "cuda") * 1e-3   # slowest rank
         e2e = {"value": world * total / e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n * m,
                "d2h_bytes_per_step": 4 * n * m + 8 * m * m + 8 * m, "ms_per_step": 1e3 * e_s,
                "ms_per_step_mean": 1e3 * sum(e_times) / len(e_times), "steps": len(e_times)}
