@@ -185,8 +185,8 @@ def test_large_norm_operator_no_overflow(h, solver):
 
 @pytest.mark.parametrize("solver", ["rgmres", "cgs2"])
 def test_7_point_operator_full_tiles(h, solver):
-    # 3D 7-point operator: 1024-row tiles hold ~7,000 nonzeros (the SpMV stages a tile's column
-    # indices in shared memory); one fixed cycle in FP64 against the oracle
+    # 3D 7-point operator: every 1024-row tile holds ~7,000 nonzeros; one fixed cycle in FP64
+    # against the oracle
     csr = synth.convdiff_3d(20, 30.0, 1.0, 3, 4)
     A = sp.csr_matrix((csr[2], csr[1], csr[0]))
     n = A.shape[0]
@@ -203,3 +203,21 @@ def test_7_point_operator_full_tiles(h, solver):
     assert rel(x.cpu().numpy(), ref.x) <= 1e-10
     y = rgs.rgs_csr_matvec(h, C, dev(b))
     assert np.allclose(y.cpu().numpy(), A @ b, rtol=1e-13, atol=1e-12 * np.abs(A @ b).max())
+
+
+def test_c3_full_size_true_residual(h):
+    """The benchmark's 128^3 convection-diffusion solve (n = 2,097,152; RGMRES(100), SRHT k = 400,
+    FP32 basis, the bench's launch shapes) to 1e-8: convergence and the residual the solver
+    reports, checked against b - A x recomputed in FP64 on the CPU from the same CSR matrix."""
+    csr = synth.convdiff_3d(128, 50.0, 1.0, 8, 0)
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    n = A.shape[0]
+    b = synth.rhs(n, 0)
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, "srht", n, 400, 0)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=100, rtol=1e-8, max_cycles=400, qdtype=torch.float32)
+    true_rel = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+    print(f"128^3: {res['total_steps']} steps, reported {res['rel_residual']:.3e}, recomputed {true_rel:.3e}")
+    assert res["converged"] and true_rel <= 1e-8
+    assert abs(true_rel - res["rel_residual"]) <= 1e-3 * true_rel
