@@ -127,3 +127,25 @@ def test_invalid_arguments(h):
         run(h, [I], [10], [200])                   # k beyond 192
     with pytest.raises(rgs.RgsError):
         run(h, [I], [10], [10])                    # k < restart + 1
+
+
+def test_c4_full_size_sampled_residuals(h):
+    """The benchmark's batch at full size (256 instances, sides U[64, 512], Pe U[1, 100] at an
+    angle U[0, 2 pi), restart U{30..80}, Gaussian k = 2 restart, FP32 basis, two fixed cycles in
+    one launch): for sampled instances the residual the solver reports equals b - A x recomputed
+    in FP64 on the CPU, and it went down."""
+    insts, restarts = [], []
+    for i in range(256):
+        g = np.random.default_rng(i)
+        nx, ny = int(g.integers(64, 513)), int(g.integers(64, 513))
+        ang, pe, m = float(g.uniform(0, 2 * np.pi)), float(g.uniform(1, 100)), int(g.integers(30, 81))
+        insts.append(instance(nx, ny, pe, ang, i))
+        restarts.append(m)
+    res, xs = run(h, insts, restarts, [2 * m for m in restarts], qdtype=torch.float32, max_cycles=2,
+                  fixed_steps=True)
+    for i in (0, 17, 128, 255):
+        I = insts[i]
+        true_rel = np.linalg.norm(I["b"] - I["A"] @ xs[i]) / np.linalg.norm(I["b"])
+        assert res[i]["cycles"] == 2 and res[i]["total_steps"] == 2 * restarts[i]
+        assert abs(true_rel - res[i]["rel_residual"]) <= 1e-8 * true_rel, i
+        assert true_rel < 1.0
