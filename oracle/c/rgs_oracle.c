@@ -167,6 +167,36 @@ static double round_storage(double v, int storage) {
     return round_bf16(v);
 }
 
+/* acc - c q for FP32 values acc, c, q, rounded once to FP32 as one fused multiply-add does.
+ * c q is exact in FP64 (48 significant bits at most).  s = fl64(acc - c q) and its rounding
+ * error e (Knuth's TwoSum) hold the exact difference s + e.  Every FP32 rounding boundary is
+ * an FP64 number, so none lies strictly between s + e and s: s rounds to the right FP32 value
+ * unless s sits exactly on a boundary (halfway between two FP32 neighbours), where e decides;
+ * e = 0 there is a true tie, which the conversion resolves to even. */
+static double fma32_once(double acc, double c, double q) {
+    double prod = c * q;
+    double s = acc - prod;
+    double bb = s - acc;
+    double e = (acc - (s - bb)) + (-prod - bb);
+    float r = (float)s;
+    if (e != 0.0 && (double)r != s) {
+        float other = nextafterf(r, s > (double)r ? INFINITY : -INFINITY);
+        if (0.5 * ((double)r + (double)other) == s && ((e > 0.0) == ((double)other > (double)r))) r = other;
+    }
+    return (double)r;
+}
+
+/* Step 3 in FP32 for rows [0, n): out = fl32(w) - sum_j fl32(c_j) Qp(:, j), one fused
+ * multiply-add per term in column order.  Exported for the tests of the emulation. */
+void orc_update_fp32(int64_t n, int ncols, const double* w, const double* Qp, int64_t ldq, const double* c,
+                     double* out) {
+    for (int64_t r = 0; r < n; ++r) {
+        double acc = (double)(float)w[r];
+        for (int j = 0; j < ncols; ++j) acc = fma32_once(acc, (double)(float)c[j], Qp[(size_t)j * ldq + r]);
+        out[r] = acc;
+    }
+}
+
 /* ---------------- incremental Householder QR of S (k x cols) ---------------- */
 typedef struct {
     int k, mmax, cols;
@@ -299,7 +329,7 @@ static int rgs_step(rgs_state* st, orc_sketch* sk, int i, const double* w, const
             double acc = (double)(float)w[r];
             for (int j = 0; j < i; ++j) {
                 double c = (double)(float)(st->x[j] * st->sigma[j]);
-                acc = (double)(float)(acc - c * st->Qp[(size_t)j * n + r]);
+                acc = fma32_once(acc, c, st->Qp[(size_t)j * n + r]);
             }
             st->qp[r] = round_storage(acc, st->storage);
         }

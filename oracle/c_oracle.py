@@ -19,11 +19,12 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the C oracle (plain -O2, no architecture-specific flags)."""
+    """Compile the C oracle (plain -O2, no architecture-specific flags; no contraction of a
+    multiply and an add into a fused multiply-add, so x86 and Arm builds round alike)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-                               _SRC, "-o", _OUT, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-D_DEFAULT_SOURCE", "-fPIC",
+                               "-shared", _SRC, "-o", _OUT, "-lm"])
     return _OUT
 
 
@@ -47,6 +48,7 @@ def lib():
         L.orc_rgmres.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, P, P]
+        L.orc_update_fp32.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, ctypes.c_int64, P, P]
         L.orc_cgs2_gmres.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P]
     return _lib
@@ -54,6 +56,17 @@ def lib():
 
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def update_fp32(w, Qp, c):
+    """Step 3 in FP32 (one rounding per fused multiply-add term), the C oracle's emulation."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Qp = np.asfortranarray(Qp, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    n, ncols = Qp.shape
+    out = np.empty(n)
+    lib().orc_update_fp32(n, ncols, _p(w), _p(Qp), max(1, n), _p(c), _p(out))
+    return out
 
 
 KIND = {"gaussian": 0, "srht": 1}

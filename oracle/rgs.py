@@ -26,8 +26,9 @@ else in FP64.  Step 7 is required to carry only u_fine error, so the basis is
 kept as the stored q'_i together with the FP64 factor 1/r_ii (``Qp``, ``sigma``);
 the FP64 product ``Q = Qp * sigma`` is the basis the algorithm defines.
 Storage ``"f32"``/``"bf16"`` rounds q'_i to that format and runs step 3 as an
-FP32 fused multiply-add chain (emulated exactly: an FP32 product is exact in
-FP64), summed over j = 1..i-1 in order.
+FP32 fused multiply-add chain summed over j = 1..i-1 in order, each multiply-add
+rounded once (``fma32``: the FP32 product is exact in FP64, the difference is
+carried exactly as a TwoSum pair and that pair is rounded to FP32 once).
 """
 from __future__ import annotations
 
@@ -79,12 +80,39 @@ def ls_richardson(S, p, sweeps=2):
     return x
 
 
+def fma32(acc, c, q):
+    """One FP32 fused multiply-add acc - c q, rounded once to FP32 (round to nearest even).
+
+    acc, c, q hold FP32 values (as FP64 arrays).  The product c q has at most 48 significant
+    bits, so it is exact in FP64.  The difference acc - c q is carried exactly as the
+    unevaluated pair (s, e) of Knuth's TwoSum (s = fl64(acc - c q), e the rounding error).
+    Rounding that pair to FP32: s rounds correctly unless s lies exactly halfway between two
+    FP32 neighbours (both are FP64 numbers, so no FP32 rounding boundary lies strictly between
+    the exact value and s); there the sign of e says on which side the exact value lies, and
+    e = 0 is a true tie, which FP32 conversion resolves to even.
+    """
+    acc = np.asarray(acc, dtype=np.float64)
+    prod = np.asarray(c, dtype=np.float64) * np.asarray(q, dtype=np.float64)
+    s = acc - prod
+    bb = s - acc
+    e = (acc - (s - bb)) + (-prod - bb)
+    r = s.astype(np.float32)
+    rd = r.astype(np.float64)
+    toward = np.where(s > rd, np.float32(np.inf), np.float32(-np.inf)).astype(np.float32)
+    other = np.nextafter(r, toward)
+    od = other.astype(np.float64)
+    tie = (e != 0.0) & (rd != s) & (0.5 * (rd + od) == s)
+    pick_other = tie & ((e > 0.0) == (od > rd))
+    return np.where(pick_other, other, r).astype(np.float64)
+
+
 def update_fp32(w, Qp, c):
-    """Step 3 in FP32: acc = fl32(w); acc = fma32(-c_j, q'_j, acc) for j = 1..i-1."""
+    """Step 3 in FP32: acc = fl32(w); acc = fma32(-c_j, q'_j, acc) for j = 1..i-1, with
+    c_j = fl32(c) and every multiply-add rounded once, as a fused multiply-add does."""
     acc = np.asarray(w, dtype=np.float32).astype(np.float64)
     c32 = np.asarray(c, dtype=np.float32).astype(np.float64)
     for j in range(Qp.shape[1]):
-        acc = (acc - c32[j] * Qp[:, j]).astype(np.float32).astype(np.float64)
+        acc = fma32(acc, c32[j], Qp[:, j])
     return acc
 
 
