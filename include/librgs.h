@@ -82,22 +82,27 @@ RGS_API rgs_status rgs_sketch_create(rgs_handle h, rgs_sketch_kind kind, int64_t
                              uint64_t seed, rgs_sketch* out);
 RGS_API rgs_status rgs_sketch_destroy(rgs_sketch s);
 
-/* Y (k x ncols, ldy >= k) = Theta X (n x ncols, ldx >= n), FP64, device pointers.
- * The sketch of Alg. 2 step 1 / step 4 applied to a block of vectors. */
+/* Y (k x ncols, ldy >= k) = Theta X (n x ncols, ldx >= n), FP64, device pointers (host memory
+ * is rejected with RGS_ERR_INVALID_ARG).  The sketch of Alg. 2 step 1 / step 4 applied to a block
+ * of vectors; any number of columns (launched in groups of at most 65535). */
 RGS_API rgs_status rgs_sketch_apply(rgs_handle h, rgs_sketch s, int32_t ncols, const double* X, int64_t ldx,
                             double* Y, int64_t ldy);
 
 /* Y = Theta X exactly like rgs_sketch_apply, but without allocating device memory during the
  * call, for callers that cannot allow an allocation there: cudaMalloc synchronises the device
  * (a stall inside a latency-critical loop), and an application whose framework allocator holds
- * nearly all free device memory would see it fail.  (The paper has no counterpart: this is an
- * interface variant of the sketch of Sec. 2.1.)
- *  - The partial sketches live in a fixed device array of RGS_NOALLOC_SCRATCH_BYTES (8 MiB),
- *    reserved on every device that loads the library until the process exits.
+ * nearly all free device memory would see it fail.  The paper has no counterpart: this is an
+ * interface variant of rgs_sketch_apply.
+ *  - The partial sketches live in a fixed device array of RGS_NOALLOC_SCRATCH_BYTES (8 MiB).
+ *    rgs_create loads it on the handle's device and looks up its address there, so the 8 MiB
+ *    are reserved when the handle is created (the CUDA runtime may load a library's device
+ *    code lazily) and stay reserved until the process exits.  Calls make no further
+ *    reservation on a device that has a handle.
  *  - Requires k * ncols <= RGS_NOALLOC_SCRATCH_BYTES / 8; larger calls return
- *    RGS_ERR_INVALID_ARG (split the columns).  The handle's device must be current.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *    make that first call before any stream capture.
+ *    RGS_ERR_INVALID_ARG (split the columns).  More than 65535 columns are processed in
+ *    launches of at most 65535 columns each, one after another on the stream.
+ *  - X and Y must be device pointers (host memory is rejected with RGS_ERR_INVALID_ARG) on
+ *    the handle's device, which must be current.
  *  - Every call shares the array: calls whose work overlaps on the GPU (other streams or
  *    host threads) race and must be serialised by the caller.
  *  - Calls no cudaMalloc / cudaFree; work is queued on the handle's stream. */

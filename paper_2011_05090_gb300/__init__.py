@@ -197,8 +197,9 @@ def colmajor_empty(rows, cols, dtype=torch.float64, device="cuda", pin=False):
 
 
 class Handle:
-    def __init__(self, ptr):
+    def __init__(self, ptr, device=0):
         self.ptr = ptr
+        self.device = device
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None and not _exiting:
@@ -223,7 +224,7 @@ def rgs_create(stream=None):
         stream = torch.cuda.current_stream()
     out = ctypes.c_void_p()
     _check(L.rgs_create(ctypes.byref(out), ctypes.c_void_p(stream.cuda_stream)))
-    return Handle(out.value)
+    return Handle(out.value, torch.cuda.current_device())
 
 
 def rgs_set_stream(h, stream):
@@ -236,6 +237,17 @@ def rgs_sketch_create(h, kind, n, k, seed):
     return Sketch(out.value, h, kind, int(n), int(k), int(seed))
 
 
+def _sketch_operands(h, X, Y):
+    """X and Y of a sketch application: FP64 CUDA tensors on the handle's device."""
+    for name, t in (("X", X), ("Y", Y)):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != h.device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the handle on cuda:{h.device}")
+
+
 def rgs_sketch_apply(h, sk, X, Y=None):
     """Y (k x ncols) = Theta X for a column-major FP64 X (n x ncols) on the GPU."""
     if X.dim() == 1:
@@ -243,6 +255,7 @@ def rgs_sketch_apply(h, sk, X, Y=None):
     ncols = X.shape[1]
     if Y is None:
         Y = colmajor_empty(sk.k, ncols, device=X.device)
+    _sketch_operands(h, X, Y)
     px, ldx = _colmajor(X, sk.n, ncols)
     py, ldy = _colmajor(Y, sk.k, ncols)
     _check(load().rgs_sketch_apply(h.ptr, sk.ptr, ncols, px, ldx, py, ldy), h)
@@ -255,6 +268,7 @@ def rgs_sketch_apply_noalloc(h, sk, X, Y):
     if X.dim() == 1:
         X = X[:, None]
     ncols = X.shape[1]
+    _sketch_operands(h, X, Y)
     px, ldx = _colmajor(X, sk.n, ncols)
     py, ldy = _colmajor(Y, sk.k, ncols)
     _check(load().rgs_sketch_apply_noalloc(h.ptr, sk.ptr, ncols, px, ldx, py, ldy), h)

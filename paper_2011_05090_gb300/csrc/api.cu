@@ -63,15 +63,7 @@ void scale_columns(rgs_context* ctx, void* Q, int qtype, int64_t n, int m, int64
 
 size_t dtype_size(int t) { return t == RGS_F64 ? 8 : (t == RGS_F32 ? 4 : 2); }
 
-bool is_host_pointer(const void* p) {
-    if (p == nullptr) return false;
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-        cudaGetLastError();
-        return true;
-    }
-    return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
-}
+bool is_host_pointer(const void* p) { return rgs_is_host_pointer(p); }
 
 void reset_ctl(rgs_context* ctx) {
     RGS_CUDA(cudaMemsetAsync(ctx->ctl.ptr, 0, kCtlWords * sizeof(int), ctx->stream));
@@ -83,7 +75,7 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
     const int k = sk->k;
     const double scale = sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)k) : 1.0;
     const size_t budget = (size_t)256 << 20;
-    int batch = ncols;
+    int batch = std::min(ncols, kMaxGridY);
     while (batch > 1 && (size_t)batch * rgs_update_nparts(ctx, sk, sk->n, batch) * k * 8 > budget) batch = (batch + 1) / 2;
     for (int c0 = 0; c0 < ncols; c0 += batch) {
         const int nc = std::min(batch, ncols - c0);
@@ -105,6 +97,16 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
 }
 
 }  // namespace
+
+bool rgs_is_host_pointer(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
 
 extern "C" {
 
@@ -140,6 +142,7 @@ rgs_status rgs_create(rgs_handle* out, void* stream) {
         ctx->ctl.ensure(kCtlWords * sizeof(int));
         RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, kCtlWords * sizeof(int)));
         ctx->ls_blocks = rgs_ls_max_blocks(ctx->num_sms);
+        rgs_noalloc_reserve(ctx->device);
     });
     if (st != RGS_OK) {
         delete ctx;
@@ -231,6 +234,7 @@ rgs_status rgs_sketch_apply(rgs_handle h, rgs_sketch s, int32_t ncols, const dou
         RGS_REQUIRE(ncols >= 0, "ncols must be >= 0");
         RGS_REQUIRE(ncols == 0 || (X && Y), "null X or Y");
         RGS_REQUIRE(ldx >= s->n && ldy >= s->k, "leading dimension too small");
+        RGS_REQUIRE(ncols == 0 || (!is_host_pointer(X) && !is_host_pointer(Y)), "X and Y must be device pointers");
         if (ncols == 0) return;
         sketch_block(h, s, ncols, X, ldx, Y, ldy);
     });

@@ -318,6 +318,12 @@ struct UpdateLaunch {
 };
 // Number of partial sketches (per input column) the next update/sketch launch will write.
 int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, int wcols);
+// Largest gridDim.y of a launch: launches with one CTA row per column take at most this many.
+constexpr int kMaxGridY = 65535;
+// cudaPointerGetAttributes says host memory (or an address CUDA does not know).
+bool rgs_is_host_pointer(const void* p);
+// Loads the no-allocation scratch array on `device` (current) and records its address.
+void rgs_noalloc_reserve(int device);
 int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L,
                              double* partials, int* nparts, const int* ctl);
 void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols,
