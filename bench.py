@@ -4,9 +4,11 @@
 Workload (one "step" = one full rgs_qr call):
     A = G D W with n = 2^20 rows, m = 500 columns, D log-spaced from 1 to 1e-10,
     G iid N(0,1), W Haar orthogonal; SRHT sketch with k = 2000 over 2^20;
-    basis stored in FP32 with FP32 update arithmetic, sketches / least squares
-    in FP64.  Inputs (4.2 GB) are far larger than L2 (129 MB), so no flush is
-    needed between steps.
+    basis stored in FP32 with FP32 update arithmetic; the sketch's transform sums and
+    the sketched least squares (steps 2, 5, 6) in FP64 (RGS_FP64_FINE).  The same
+    factorization with double-float (FP32-pair) fine arithmetic is reported beside it
+    ("double_float_fine").  Inputs (4.2 GB) are far larger than L2 (129 MB), so no
+    flush is needed between steps.
 
 Metric: whole-job algorithmic HBM throughput of the QR in GB/s, i.e.
     bytes = 8 n m                    (step 1, one pass over W)
@@ -15,11 +17,15 @@ divided by the measured time.  With --gpus N (torchrun), every rank factors
 its own independent matrix (weak scaling, no collective on the data path).
 
 The second half of the metric is reported in the same line ("rgmres"): restarted
-RGMRES(100) with RGS-Arnoldi (SRHT k = 400, FP32 basis, FP64 least squares and
-restart residual) against FP64 CGS2-GMRES(100) on the same GPU, time to a relative
-residual of 1e-8 on a 3D convection-diffusion operator: 128^3 grid (n = 2,097,152,
-7-point CSR, FP64 values), log-normal diffusion (sigma = 1, correlation length 8
-cells), Peclet number 50, iid N(0,1) right-hand side.
+RGMRES(100) with RGS-Arnoldi (SRHT k = 400, FP32 basis; FP64 sketch sums, products,
+least squares, Givens and restart residual) against FP64 CGS2-GMRES(100) on the same
+GPU, time to a relative residual of 1e-8 on a 3D convection-diffusion operator: 128^3
+grid (n = 2,097,152, 7-point CSR, FP64 values), log-normal diffusion (sigma = 1,
+correlation length 8 cells), Peclet number 50, iid N(0,1) right-hand side.  The
+double-float and BF16-basis variants are reported beside it.
+
+"c1": the small FP64 factorization (n = 10,000, m = 100, cond 1e8, Gaussian k = 300),
+latency-bound, reported as time per call.
 
 "batched" in the same line: 256 independent 2D convection-diffusion RGMRES solves in one
 persistent launch (rgmres_solve_batched, FP32 basis, Gaussian k = 2 restart) against the
@@ -73,14 +79,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic():
+def profile_traffic(variant="fp64_fine"):
     """Mean per-launch DRAM traffic (bytes) of the fused update kernel over the m = 500 step, from the
-    committed ncu summary (measured on one launch, scaled by the launch's algorithmic bytes)."""
+    committed ncu summary of the same kernel variant (measured on one launch, scaled by the launch's
+    algorithmic bytes); None when no capture of that variant is committed."""
     path = os.path.join(ROOT, "profiles", "rgs_update_sketch_c2.txt")
+    key = f"traffic_bytes_per_launch_full_step_{variant}:"
     try:
         with open(path) as f:
             for line in f:
-                if line.startswith("traffic_bytes_per_launch_full_step:"):
+                if line.startswith(key):
                     return float(line.split(":")[1])
     except OSError:
         pass
@@ -151,17 +159,26 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_sample_gbps(A_cols_host, n, k, storage="f32"):
-    """Time the C oracle on the first columns of the workload; returns (GB/s, seconds, columns)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_sample_gbps(A_cols_host, n, k, storage="f32", threads=0):
+    """Time the C oracle on the first columns of the workload with `threads` threads (0: all host
+    cores); returns (GB/s, seconds, columns, threads used)."""
     from oracle import c_oracle
     c_oracle.build()
+    used = c_oracle.set_threads(threads if threads > 0 else host_cores())
     sk = c_oracle.CSketch("srht", n, k, SEED)
     msub = A_cols_host.shape[1]
     t0 = time.perf_counter()
     c_oracle.rgs_qr(A_cols_host, sk, ls="householder", storage=storage)
     dt = time.perf_counter() - t0
     total, _ = qr_bytes(n, msub)
-    return total / dt / 1e9, dt, msub
+    return total / dt / 1e9, dt, msub, used
 
 
 def run_reference(args):
@@ -177,24 +194,27 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_sample_gbps(A, N_ROWS, K_SKETCH)
     vals, secs = [], []
+    used = 1
     for _ in range(args.steps):
-        v, dt, _ = cpu_sample_gbps(A, N_ROWS, K_SKETCH)
+        v, dt, _, used = cpu_sample_gbps(A, N_ROWS, K_SKETCH)
         vals.append(v)
         secs.append(dt)
     total, _ = qr_bytes(N_ROWS, msub)
     value = total * len(secs) / sum(secs) / 1e9
-    sample = f"first {msub} of {M_COLS} columns of the workload (n=2^20, SRHT k=2000, f32 storage emulation)"
+    sample = (f"first {msub} of {M_COLS} columns of the workload (n=2^20, SRHT k=2000, f32 storage emulation), "
+              f"C oracle -O3 with OpenMP on {used} host threads")
     out = {"metric": METRIC, "value": value, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_columns": msub},
-           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": used, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_bf16", "cgs2")):
-    """Time-to-1e-8 of RGMRES (FP32 basis) and FP64 CGS2-GMRES on the 3D convection-diffusion system."""
+def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_df", "rgmres_bf16", "cgs2")):
+    """Time-to-1e-8 of RGMRES (FP32 basis; FP64 fine arithmetic, and double-float beside it) and
+    FP64 CGS2-GMRES on the 3D convection-diffusion system."""
     import torch
     import synth
     csr = synth.convdiff_3d(N, 50.0, 1.0, 8, 0)
@@ -204,14 +224,17 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_bf16"
     sk = rgs.rgs_sketch_create(h, "srht", n, 400, 0)
     # warm-up on a few cycles (kernels loaded, allocator primed)
     xw = torch.zeros(n, dtype=torch.float64, device="cuda")
-    rgs.rgmres_solve(h, sk, C, b, xw, restart=100, max_cycles=1)
+    rgs.rgmres_solve(h, sk, C, b, xw, restart=100, max_cycles=1, fine64=True)
+    rgs.rgmres_solve(h, sk, C, b, xw.zero_(), restart=100, max_cycles=1)
     rgs.cgs2_gmres_solve(h, C, b, xw.zero_(), restart=100, max_cycles=1)
     out = {"config": "convdiff3d 128^3 n=2097152 nnz=%d Pe=50 sigma=1 corr=8 restart=100 rtol=1e-8" % len(csr[1])}
-    runs = (("rgmres_f32_srht400", "rgmres", lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8,
-                                                                    max_cycles=max_cycles, qdtype=torch.float32)),
-            ("rgmres_bf16_srht400", "rgmres_bf16",
-             lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8, max_cycles=max_cycles,
-                                        qdtype=torch.bfloat16)),
+
+    def rg(qd, fine):
+        return lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8, max_cycles=max_cycles, qdtype=qd,
+                                          fine64=fine)
+    runs = (("rgmres_f32_fp64fine_srht400", "rgmres", rg(torch.float32, True)),
+            ("rgmres_f32_df_srht400", "rgmres_df", rg(torch.float32, False)),
+            ("rgmres_bf16_fp64fine_srht400", "rgmres_bf16", rg(torch.bfloat16, True)),
             ("cgs2_gmres_f64", "cgs2", lambda x: rgs.cgs2_gmres_solve(h, C, b, x, restart=100, rtol=1e-8,
                                                                      max_cycles=max_cycles)))
     for name, key, fn in runs:
@@ -226,10 +249,39 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_bf16"
         out[name] = {"seconds": dt, "converged": res["converged"], "rel_residual": res["rel_residual"],
                      "cycles": res["cycles"], "arnoldi_steps": res["total_steps"],
                      "us_per_step": 1e6 * dt / max(1, res["total_steps"])}
-    if "rgmres_f32_srht400" in out and "cgs2_gmres_f64" in out:
-        a, c = out["rgmres_f32_srht400"], out["cgs2_gmres_f64"]
-        out["speedup_vs_cgs2_fp64"] = c["seconds"] / a["seconds"]
+    c = out.get("cgs2_gmres_f64")
+    if c and "rgmres_f32_fp64fine_srht400" in out:
+        out["speedup_vs_cgs2_fp64"] = c["seconds"] / out["rgmres_f32_fp64fine_srht400"]["seconds"]
+    if c and "rgmres_f32_df_srht400" in out:
+        out["speedup_vs_cgs2_fp64_double_float"] = c["seconds"] / out["rgmres_f32_df_srht400"]["seconds"]
     return out
+
+
+def run_c1(rgs, h, reps=20):
+    """The small FP64 factorization (n = 10,000, m = 100, cond 1e8, Gaussian k = 300 seed 0):
+    latency-bound, so the time per call is reported (mean of `reps` calls after warm-up)."""
+    import torch
+    import synth
+    n, m, k = 10000, 100, 300
+    W = synth.gdw_matrix(n, m, 1e8, 0).cuda().T                  # (n, m) column-major
+    sk = rgs.rgs_sketch_create(h, "gaussian", n, k, 0)
+    Q = rgs.colmajor_empty(n, m)
+    R = rgs.colmajor_empty(m, m)
+    for _ in range(3):
+        info = rgs.rgs_qr(h, sk, W, Q, R)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        info = rgs.rgs_qr(h, sk, W, Q, R)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    E = W - Q @ R
+    err = (torch.linalg.norm(E) / torch.linalg.norm(W)).item()
+    return {"config": "rgs_qr n=10000 m=100 cond=1e8 gaussian k=300 seed 0, f64 basis", "ms_per_call": ms,
+            "calls": reps, "delta": info["delta"], "delta_tilde": info["delta_tilde"], "rel_err_A_minus_QR": err,
+            "launches_per_call": info["launches"]}
 
 
 def c4_instances(rgs, NB, lo, hi, seed0):
@@ -477,7 +529,8 @@ def run_ours(args):
     Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
     R = rgs.colmajor_empty(m, m)
     qs = torch.empty(m, dtype=torch.float64, device="cuda")
-    flags = rgs.RGS_QR_TIMINGS
+    fine = rgs.RGS_FP64_FINE                  # steps 1-2 and 4-6 in FP64 (u_fine) for the FP32 basis
+    flags = rgs.RGS_QR_TIMINGS | fine
     tuning = rgs.rgs_autotune_update(h, sk, m // 2, torch.float32)     # launch shape of the update pass
 
     for _ in range(args.warmup):
@@ -496,7 +549,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         start.record()
         for _ in range(args.steps):
-            infos.append(rgs.rgs_qr(h, sk, W, Q, R, qscale=qs))
+            infos.append(rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=fine))
         stop.record()
         torch.cuda.synchronize()
         if world > 1:
@@ -517,7 +570,7 @@ def run_ours(args):
     traffic_full = profile_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_full if (traffic_full and m == M_COLS) else None,
-                "kernel": "update_sketch_kernel<float,SRHT>",
+                "kernel": "update_sketch_kernel<float,SRHT,FP64 transform>",
                 "bytes_per_launch": upd / m, "launches_per_step": m,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "timing": "CUDA events around each launch on the library stream, over the K steps that follow "
@@ -537,30 +590,53 @@ def run_ours(args):
         Qh = rgs.colmajor_empty(n, m, dtype=torch.float32, pin=True)
         Rh = rgs.colmajor_empty(m, m, pin=True)
         qh = torch.empty(m, dtype=torch.float64, pin_memory=True)
-        rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qh)
+        rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qh, flags=fine)
         torch.cuda.synchronize()
         # each call copies W in and Q', R, sigma out (pinned host buffers) and returns after its
-        # stream synchronisation; the median over the steps is reported (host-link bandwidth on a
-        # shared machine varies from call to call), the mean beside it
+        # stream synchronisation; the value is the mean over the same K steps as the device-timed
+        # value, the median beside it (host-link bandwidth on a shared machine varies by call)
         e_times = []
-        for _ in range(max(1, min(args.steps, 5))):
+        if world > 1:
+            dist.barrier()
+        for _ in range(args.steps):
             t0 = time.perf_counter()
-            rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qh)
+            rgs.rgs_qr(h, sk, Wh, Qh, Rh, qscale=qh, flags=fine)
             e_times.append(time.perf_counter() - t0)
-        e_s = max_over_ranks(1e3 * statistics.median(e_times), world, "cuda") * 1e-3   # slowest rank
+        e_s = max_over_ranks(1e3 * sum(e_times) / len(e_times), world, "cuda") * 1e-3   # slowest rank
         e2e = {"value": world * total / e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n * m,
                "d2h_bytes_per_step": 4 * n * m + 8 * m * m + 8 * m, "ms_per_step": 1e3 * e_s,
-               "ms_per_step_mean": 1e3 * sum(e_times) / len(e_times), "steps": len(e_times)}
+               "ms_per_step_median": 1e3 * statistics.median(e_times), "steps": len(e_times)}
+        del Wh, Qh
 
-    # the BF16-storage variant of the same factorization: time, throughput, certificates
-    bf16 = None
+    # the same factorization with double-float fine arithmetic (FP32 pairs, about 2^-48 per
+    # operation): time, throughput, and its difference from the FP64-fine R and certificates
+    dfv = None
     if rank == 0:
-        Qb = rgs.colmajor_empty(n, m, dtype=torch.bfloat16)
-        rgs.rgs_qr(h, sk, W, Qb, R, qscale=qs)
+        R64 = R.clone()
+        Rd = rgs.colmajor_empty(m, m)
+        rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs)
         torch.cuda.synchronize()
         start.record()
         for _ in range(3):
-            ib = rgs.rgs_qr(h, sk, W, Qb, R, qscale=qs)
+            idf = rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs)
+        stop.record()
+        torch.cuda.synchronize()
+        td = start.elapsed_time(stop) / 3e3
+        dfv = {"ms": 1e3 * td, "GB/s": total / td / 1e9, "hbm_frac": total / td / 1e9 / peaks()[0],
+               "delta": idf["delta"], "delta_tilde": idf["delta_tilde"],
+               "rel_diff_R_vs_fp64_fine": (torch.linalg.norm(Rd - R64) / torch.linalg.norm(R64)).item()}
+        del Rd, R64
+
+    # the BF16-storage variant of the same factorization (FP64 fine arithmetic): time, throughput,
+    # certificates
+    bf16 = None
+    if rank == 0:
+        Qb = rgs.colmajor_empty(n, m, dtype=torch.bfloat16)
+        rgs.rgs_qr(h, sk, W, Qb, R, qscale=qs, flags=fine)
+        torch.cuda.synchronize()
+        start.record()
+        for _ in range(3):
+            ib = rgs.rgs_qr(h, sk, W, Qb, R, qscale=qs, flags=fine)
         stop.record()
         torch.cuda.synchronize()
         tb = start.elapsed_time(stop) / 3e3
@@ -575,20 +651,28 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = run_batched_c4(rgs, h)
+    c1 = run_c1(rgs, h) if rank == 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        # the C oracle (-O3, OpenMP over independent rows and butterflies) on all host cores, and
+        # on one core beside it, each on a sample of the first columns of the same matrix
         msub = 100
-        v, dt, _ = cpu_sample_gbps(W[:, :msub].cpu().numpy(), n, k)
-        cpu = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {msub} of {m} columns (n=2^20, SRHT k=2000, f32 storage emulation), {dt:.1f} s"}
+        Wc = W[:, :msub].cpu().numpy()
+        v, dt, _, used = cpu_sample_gbps(Wc, n, k, threads=0)
+        v1, dt1, _, _ = cpu_sample_gbps(Wc[:, :40].copy(), n, k, threads=1)
+        cpu = {"value": v, "unit": "GB/s", "cores": used, "kind": "oracle",
+               "sample": f"first {msub} of {m} columns (n=2^20, SRHT k=2000, f32 storage emulation), "
+                         f"{dt:.1f} s on {used} threads",
+               "single_thread": {"value": v1, "unit": "GB/s", "cores": 1,
+                                 "sample": f"first 40 of {m} columns, {dt1:.1f} s"}}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32/df/f64",
-               "dtype_detail": "basis and update in f32; sketch and least squares in double-float "
-                               "(f32 pairs); squared norms, R and the returned scales in f64",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+               "dtype_detail": "basis and update in f32 (u_crs); sketch transform sums and the sketched least "
+                               "squares (steps 2, 5, 6), R and the scales in f64 (u_fine, RGS_FP64_FINE)",
                "data": "synthetic",
                "config": {"workload": WORKLOAD if m == M_COLS else f"profiling case m={m}", "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
                           "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}",
@@ -596,7 +680,7 @@ def run_ours(args):
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "phases_ms": phases,
                "certificates": {"delta": last["delta"], "delta_tilde": last["delta_tilde"]},
-               "rgmres": gm, "batched": batched, "bf16_basis": bf16,
+               "rgmres": gm, "batched": batched, "bf16_basis": bf16, "double_float_fine": dfv, "c1": c1,
                "hbm_frac_whole_job": value / world / peak}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -67,6 +67,13 @@ typedef struct rgs_arnoldi_obj* rgs_arnoldi;
 RGS_API rgs_status rgs_create(rgs_handle* out, void* stream);
 RGS_API rgs_status rgs_destroy(rgs_handle h);
 RGS_API rgs_status rgs_set_stream(rgs_handle h, void* stream);
+/* Clock-cycle budget of every device-side wait of the handle's kernels (grid and team barriers;
+ * no counterpart in the paper).  A wait that runs past it records RGS_ERR_TIMEOUT, every CTA of
+ * the launch leaves at its next barrier, later launches of the call do nothing, and the call
+ * returns RGS_ERR_TIMEOUT; the next call on the handle starts afresh.  cycles <= 0 restores the
+ * default of 4e9 cycles (about two seconds at GB300's clock).  A tiny budget makes the
+ * timeout path run on purpose (used by the tests); the setting persists until changed. */
+RGS_API rgs_status rgs_set_wait_budget(rgs_handle h, int64_t cycles);
 RGS_API const char* rgs_status_string(rgs_status s);
 RGS_API const char* rgs_last_error(rgs_handle h);
 
@@ -136,8 +143,12 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
 #define RGS_QR_NO_CERTIFICATES 1
 #define RGS_QR_TIMINGS 2         /* bit 1: time each phase with CUDA events (fills the *_ms fields) */
-#define RGS_QR_FP64_FINE 4       /* bit 2: FP64 transform sums and least squares for every storage */
-#define RGS_QR_FP64_SKETCH RGS_QR_FP64_FINE
+#define RGS_FP64_FINE 4          /* bit 2: fine precision u_fine = FP64 for every storage type: the SRHT's
+                                    transform sums, the products with A (Arnoldi) and the least-squares
+                                    steps 2, 5, 6 (and Givens) in FP64 (rgs_qr, rgs_arnoldi_create,
+                                    rgmres_opts.flags) */
+#define RGS_QR_FP64_FINE RGS_FP64_FINE
+#define RGS_QR_FP64_SKETCH RGS_FP64_FINE
 typedef struct {
     double delta;          /* Delta_m  = ||I - S^T S||_F            (Alg. 2 step 8) */
     double delta_tilde;    /* Delta~_m = ||P - S R||_F / ||P||_F    (Alg. 2 step 8) */
@@ -166,7 +177,9 @@ typedef struct {
  * time; H_j = R_j(1:j, 2:j) (Sec. 4.1).  The object owns the basis (n x mmax in
  * qtype, stored as q'_i with scale 1/r_ii), S, R, the Householder factors of S
  * and a work vector.  The least-squares steps run in FP64 for an FP64 basis and
- * in double-float arithmetic (about 2^-48) for FP32 / BF16 bases, as in rgs_qr.
+ * in double-float arithmetic (about 2^-48) for FP32 / BF16 bases, as in rgs_qr; with
+ * flags = RGS_FP64_FINE they, the SRHT transform sums and the products with A run in FP64
+ * for every basis type (flags: 0 or RGS_FP64_FINE).
  *   rgs_arnoldi_start: iteration 1 with w_1 (device FP64, n).
  *   rgs_arnoldi_step:  next iteration with w_i = A q_{i-1} (A given, FP64 SpMV),
  *                      or with the caller's w (device FP64) when A is NULL.
@@ -176,7 +189,7 @@ typedef struct {
  * A step after a breakdown returns RGS_ERR_BREAKDOWN (happy breakdown in
  * GMRES terms). */
 RGS_API rgs_status rgs_arnoldi_create(rgs_handle h, rgs_sketch s, int64_t n, int32_t mmax, rgs_dtype qtype,
-                              rgs_arnoldi* out);
+                              int32_t flags, rgs_arnoldi* out);
 RGS_API rgs_status rgs_arnoldi_destroy(rgs_arnoldi a);
 RGS_API rgs_status rgs_arnoldi_start(rgs_handle h, rgs_arnoldi a, const double* w1);
 RGS_API rgs_status rgs_arnoldi_step(rgs_handle h, rgs_arnoldi a, const rgs_csr* A, const double* w);
@@ -203,7 +216,8 @@ typedef struct {
                                cycles after it */
     rgs_dtype qtype;        /* basis storage (RGS only) */
     int32_t fixed_steps;    /* 1: always run `restart` steps per cycle */
-    int32_t reserved;
+    int32_t flags;          /* 0, or RGS_FP64_FINE: FP64 sketch sums, products with A, least squares
+                               and Givens for FP32 / BF16 bases too (RGS only) */
 } rgmres_opts;
 
 typedef struct {

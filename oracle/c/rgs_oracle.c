@@ -19,6 +19,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -138,16 +141,35 @@ void orc_sketch_apply(orc_sketch* sk, const double* x, double* y) {
         return;
     }
     double* z = sk->work;
-    for (int64_t c = 0; c < sk->s; ++c) z[c] = c < sk->n ? sk->signs[c] * x[c] : 0.0;
-    for (int64_t h = 1; h < sk->s; h *= 2)
-        for (int64_t a = 0; a < sk->s; a += 2 * h)
-            for (int64_t b = a; b < a + h; ++b) {
-                double u = z[b], v = z[b + h];
-                z[b] = u + v;
-                z[b + h] = u - v;
-            }
+    const int64_t s = sk->s;
+#pragma omp parallel for schedule(static) if (s >= 65536)
+    for (int64_t c = 0; c < s; ++c) z[c] = c < sk->n ? sk->signs[c] * x[c] : 0.0;
+    /* stage h: the butterflies (b, b + h) for b with bit h clear; they are independent, so a
+     * stage may be split across threads without changing any sum */
+    for (int64_t h = 1; h < s; h *= 2) {
+#pragma omp parallel for schedule(static) if (s >= 65536)
+        for (int64_t t = 0; t < s / 2; ++t) {
+            const int64_t b = (t / h) * 2 * h + t % h;
+            double u = z[b], v = z[b + h];
+            z[b] = u + v;
+            z[b + h] = u - v;
+        }
+    }
     double scale = 1.0 / sqrt((double)sk->k);
     for (int j = 0; j < sk->k; ++j) y[j] = z[sk->rows[j]] * scale;
+}
+
+/* Threads of the parallel loops (0 or less: leave the OpenMP default); returns the count in use,
+ * 1 without OpenMP.  Only loops over independent rows or butterflies run in parallel, so every
+ * result is the same for any thread count. */
+int orc_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }
 
 /* ---------------- precision emulation ---------------- */
@@ -317,14 +339,16 @@ static int rgs_step(rgs_state* st, orc_sketch* sk, int i, const double* w, const
         if (st->ls == 0) hh_solve(&st->hh, p, st->x, st->work);
         else richardson_solve(st->S, k, i, p, st->sweeps, st->x, st->work);
     }
-    /* step 3 */
+    /* step 3 (rows are independent) */
     if (st->storage == 0) {
+#pragma omp parallel for schedule(static) if (n >= 65536)
         for (int64_t r = 0; r < n; ++r) {
             double acc = w[r];
             for (int j = 0; j < i; ++j) acc -= st->Qp[(size_t)j * n + r] * (st->x[j] * st->sigma[j]);
             st->qp[r] = acc;
         }
     } else {
+#pragma omp parallel for schedule(static) if (n >= 65536)
         for (int64_t r = 0; r < n; ++r) {
             double acc = (double)(float)w[r];
             for (int j = 0; j < i; ++j) {

@@ -45,14 +45,16 @@ RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
 RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
 RGS_QR_NO_CERTIFICATES = 1
 RGS_QR_TIMINGS = 2
-RGS_QR_FP64_FINE = 4            # FP64 transform sums and least squares for every storage
-RGS_QR_FP64_SKETCH = RGS_QR_FP64_FINE
+RGS_FP64_FINE = 4               # FP64 transform sums, products and least squares for every storage
+RGS_QR_FP64_FINE = RGS_FP64_FINE
+RGS_QR_FP64_SKETCH = RGS_FP64_FINE
 RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
 
 _DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF16}
 _KIND = {"gaussian": RGS_SKETCH_GAUSSIAN, "srht": RGS_SKETCH_SRHT}
 
-EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_status_string", "rgs_last_error",
+EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_set_wait_budget", "rgs_status_string",
+            "rgs_last_error",
             "rgs_sketch_create", "rgs_sketch_destroy", "rgs_sketch_apply", "rgs_sketch_apply_noalloc", "rgs_qr",
             "rgs_arnoldi_create", "rgs_arnoldi_destroy", "rgs_arnoldi_start", "rgs_arnoldi_step",
             "rgs_arnoldi_get", "rgs_arnoldi_basis", "rgs_csr_matvec", "rgmres_solve", "cgs2_gmres_solve",
@@ -82,7 +84,7 @@ class CSR(ctypes.Structure):
 class GmresOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("inner_factor", ctypes.c_double), ("qtype", ctypes.c_int32), ("fixed_steps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 class GmresInfo(ctypes.Structure):
@@ -124,6 +126,7 @@ def load():
         "rgs_create": [ctypes.POINTER(P), P],
         "rgs_destroy": [P],
         "rgs_set_stream": [P, P],
+        "rgs_set_wait_budget": [P, I64],
         "rgs_status_string": [ctypes.c_int],
         "rgs_last_error": [P],
         "rgs_sketch_create": [P, ctypes.c_int, I64, I32, ctypes.c_uint64, ctypes.POINTER(P)],
@@ -131,7 +134,7 @@ def load():
         "rgs_sketch_apply": [P, P, I32, P, I64, P, I64],
         "rgs_sketch_apply_noalloc": [P, P, I32, P, I64, P, I64],
         "rgs_qr": [P, P, I64, I32, P, I64, P, ctypes.c_int, I64, P, P, I64, P, I64, I32, ctypes.POINTER(QRInfo)],
-        "rgs_arnoldi_create": [P, P, I64, I32, ctypes.c_int, ctypes.POINTER(P)],
+        "rgs_arnoldi_create": [P, P, I64, I32, ctypes.c_int, I32, ctypes.POINTER(P)],
         "rgs_arnoldi_destroy": [P],
         "rgs_arnoldi_start": [P, P, P],
         "rgs_arnoldi_step": [P, P, ctypes.POINTER(CSR), P],
@@ -225,6 +228,11 @@ def rgs_create(stream=None):
     out = ctypes.c_void_p()
     _check(L.rgs_create(ctypes.byref(out), ctypes.c_void_p(stream.cuda_stream)))
     return Handle(out.value, torch.cuda.current_device())
+
+
+def rgs_set_wait_budget(h, cycles):
+    """Clock-cycle budget of every device-side wait (0: the default, about two seconds)."""
+    _check(load().rgs_set_wait_budget(h.ptr, int(cycles)), h)
 
 
 def rgs_set_stream(h, stream):
@@ -325,9 +333,11 @@ class _DeviceArray:
                                          "data": (ptr, False), "version": 2}
 
 
-def rgs_arnoldi_create(h, sk, n, mmax, qdtype=torch.float64):
+def rgs_arnoldi_create(h, sk, n, mmax, qdtype=torch.float64, fine64=False):
+    """RGS-Arnoldi object; fine64 selects FP64 fine arithmetic for FP32 / BF16 bases (RGS_FP64_FINE)."""
     out = ctypes.c_void_p()
-    _check(load().rgs_arnoldi_create(h.ptr, sk.ptr, int(n), int(mmax), _DTYPE[qdtype], ctypes.byref(out)), h)
+    _check(load().rgs_arnoldi_create(h.ptr, sk.ptr, int(n), int(mmax), _DTYPE[qdtype],
+                                     RGS_FP64_FINE if fine64 else 0, ctypes.byref(out)), h)
     return Arnoldi(out.value, h, sk, int(n), int(mmax), qdtype)
 
 
@@ -369,9 +379,9 @@ def rgs_arnoldi_basis(a, ncols=None):
     return torch.as_tensor(arr, device="cuda").T
 
 
-def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps):
+def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64=False):
     return GmresOpts(int(restart), int(max_cycles), float(rtol), float(inner_factor), _DTYPE[qdtype],
-                     1 if fixed_steps else 0, 0)
+                     1 if fixed_steps else 0, RGS_FP64_FINE if fine64 else 0)
 
 
 def _gmres_result(st, info, hist, h):
@@ -388,9 +398,10 @@ def _gmres_result(st, info, hist, h):
 
 
 def rgmres_solve(h, sk, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_factor=0.5,
-                 qdtype=torch.float32, fixed_steps=False):
-    """Restarted randomized GMRES; x (FP64, CUDA) holds x0 and receives the solution."""
-    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps)
+                 qdtype=torch.float32, fixed_steps=False, fine64=False):
+    """Restarted randomized GMRES; x (FP64, CUDA) holds x0 and receives the solution.  fine64:
+    FP64 sketch sums, products with A, least squares and Givens for FP32 / BF16 bases."""
+    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64)
     hist = (ctypes.c_double * (max_cycles + 2))()
     info = GmresInfo()
     info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))

@@ -139,8 +139,8 @@ rgs_status rgs_create(rgs_handle* out, void* stream) {
         RGS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
         RGS_REQUIRE(coop, "device does not support cooperative launches");
         ctx->stream = (cudaStream_t)stream;
-        ctx->ctl.ensure(kCtlWords * sizeof(int));
-        RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, kCtlWords * sizeof(int)));
+        ctx->ctl.ensure(kCtlAlloc * sizeof(int));
+        RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, kCtlAlloc * sizeof(int)));
         ctx->ls_blocks = rgs_ls_max_blocks(ctx->num_sms);
         rgs_noalloc_reserve(ctx->device);
     });
@@ -157,6 +157,15 @@ rgs_status rgs_destroy(rgs_handle h) {
     cudaStreamSynchronize(h->stream);
     delete h;
     return RGS_OK;
+}
+
+rgs_status rgs_set_wait_budget(rgs_handle h, int64_t cycles) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const long long v = cycles > 0 ? (long long)cycles : 0;
+        RGS_CUDA(cudaMemcpyAsync(h->ctl.as<int>() + kBudgetWord, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+    });
 }
 
 rgs_status rgs_set_stream(rgs_handle h, void* stream) {

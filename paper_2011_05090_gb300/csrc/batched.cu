@@ -115,18 +115,20 @@ __device__ bool team_barrier(unsigned* word, int T, int rank, int* ctl) {
         int ok = 1;
         if (T > 1) {
             const unsigned add = rank == 0 ? 0x80000000u - (unsigned)(T - 1) : 1u;
+            const long long budget = wait_budget(ctl);
             const unsigned old = atom_add_acq_rel(word, add);
             const long long start = clock64();
             unsigned spins = 0;
             while (((old ^ ld_acquire(word)) & 0x80000000u) == 0u) {
-                if ((++spins & 63u) == 0) {
-                    if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
-                    if (clock64() - start > 4000000000LL) {
-                        atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
-                        atomicExch(ctl + kAbortWord, 1);
-                        ok = 0;
-                        break;
-                    }
+                if (clock64() - start > budget) {
+                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                    atomicExch(ctl + kAbortWord, 1);
+                    ok = 0;
+                    break;
+                }
+                if ((++spins & 63u) == 0 && *reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) {
+                    ok = 0;
+                    break;
                 }
             }
         } else {

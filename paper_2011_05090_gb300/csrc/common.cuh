@@ -156,7 +156,17 @@ constexpr int kFlagWord = 7;     // set-up checks (e.g. a zero diagonal for Jaco
 constexpr int kBarCount = 32;     // the barrier word
 constexpr int kBarGen = 64;       // unused (kept free)
 constexpr int kAbortWord = 96;
-constexpr int kCtlWords = 128;
+constexpr int kCtlWords = 128;   // words cleared at the start of every call
+// After the cleared words: the clock-cycle budget of every device-side wait (int64; 0 = the
+// default of 4e9 cycles, about two seconds), kept across calls (rgs_set_wait_budget).
+constexpr int kBudgetWord = kCtlWords;
+constexpr int kCtlAlloc = kCtlWords + 32;
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ long long wait_budget(const int* ctl) {
+    const long long b = *reinterpret_cast<const volatile long long*>(ctl + kBudgetWord);
+    return b > 0 ? b : kDefaultWaitCycles;
+}
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies.
 __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -252,14 +262,19 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
 // nobody waits for: CTA 0 adds 2^31 - (G-1), the others 1, so the sum over one barrier is
 // exactly 2^31 and the top bit flips when the last CTA arrives.  Thread 0 of each CTA reads the
 // top bit once, before its first arrival (the bit cannot change before that arrival), and then
-// polls with acquire loads for the alternating value.  Every wait is bounded: after about two
-// seconds the waiting CTA records RGS_ERR_TIMEOUT, raises the abort word and returns false,
-// and every other CTA then leaves at its next barrier.
+// polls with acquire loads for the alternating value.  Every wait is bounded: after the wait
+// budget (by default 4e9 cycles, about two seconds) the waiting CTA records RGS_ERR_TIMEOUT,
+// raises the abort word and returns false, and every other CTA then leaves at its next barrier.
 struct GridBarrier {
     unsigned* word;
     unsigned expect;                       // thread 0: the top bit that completes the next barrier
-    __device__ explicit GridBarrier(int* ctl) : word(reinterpret_cast<unsigned*>(ctl + kBarCount)), expect(0u) {
-        if (threadIdx.x == 0) expect = (ld_relaxed(word) & 0x80000000u) ^ 0x80000000u;
+    long long budget;                      // thread 0: clock cycles a wait may take
+    __device__ explicit GridBarrier(int* ctl)
+        : word(reinterpret_cast<unsigned*>(ctl + kBarCount)), expect(0u), budget(kDefaultWaitCycles) {
+        if (threadIdx.x == 0) {
+            expect = (ld_relaxed(word) & 0x80000000u) ^ 0x80000000u;
+            budget = wait_budget(ctl);
+        }
     }
     __device__ bool sync(int* ctl) {
         __shared__ int ok_sh;
@@ -270,14 +285,15 @@ struct GridBarrier {
             const long long start = clock64();
             unsigned spins = 0;
             while ((ld_acquire(word) & 0x80000000u) != expect) {
-                if ((++spins & 63u) == 0) {
-                    if (*reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) { ok = 0; break; }
-                    if (clock64() - start > 4000000000LL) {
-                        atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
-                        atomicExch(ctl + kAbortWord, 1);
-                        ok = 0;
-                        break;
-                    }
+                if (clock64() - start > budget) {
+                    atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_TIMEOUT);
+                    atomicExch(ctl + kAbortWord, 1);
+                    ok = 0;
+                    break;
+                }
+                if ((++spins & 63u) == 0 && *reinterpret_cast<volatile int*>(ctl + kAbortWord) != 0) {
+                    ok = 0;
+                    break;
                 }
             }
             expect ^= 0x80000000u;

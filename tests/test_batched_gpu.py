@@ -55,6 +55,25 @@ def test_one_cycle_matches_oracle(h):
         assert abs(r["history"][1] - ref.true_residuals[1] / ref.true_residuals[0]) <= 1e-10
 
 
+def test_one_cycle_fp32_within_emulated_oracle(h):
+    """FP32 basis: one fixed cycle per instance against the oracle's FP32-storage emulation with
+    the same bf16-rounded Gaussian sketch; the GPU's x lies within 10x of the emulation's own
+    distance from the FP64 method."""
+    shapes = [(20, 30, 10.0, 0.3, 1), (33, 17, 40.0, 2.0, 2), (48, 48, 5.0, 4.0, 3), (16, 64, 80.0, 1.0, 4)]
+    insts = [instance(*s) for s in shapes]
+    restarts, ks = [12, 25, 30, 7], [24, 60, 61, 20]
+    res, xs = run(h, insts, restarts, ks, qdtype=torch.float32, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
+        n = I["A"].shape[0]
+        skb = Sketch("gaussian_bf16", n, k, 5)
+        emu = og.rgmres(I["A"], I["b"], skb, restart=m, max_cycles=1, fixed_steps=True, storage="f32")
+        ex = og.rgmres(I["A"], I["b"], skb, restart=m, max_cycles=1, fixed_steps=True)
+        d_gpu, d_emu = rel(x, emu.x), rel(emu.x, ex.x)
+        print(f"n={n} m={m}: ||x-x_emu||/||x_emu|| {d_gpu:.2e}, emulation vs FP64 {d_emu:.2e}")
+        assert r["cycles"] == 1 and r["total_steps"] == m
+        assert d_gpu <= 10 * d_emu
+
+
 @pytest.mark.parametrize("qdtype", [torch.float64, torch.float32])
 def test_batch_converges_like_the_oracle(h, qdtype):
     g = np.random.default_rng(0)

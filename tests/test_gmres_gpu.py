@@ -90,6 +90,33 @@ def test_rgmres_fp64_one_cycle_matches_oracle(h, kind):
     assert abs(res["history"][1] - ref.true_residuals[1]) <= 1e-10 * ref.true_residuals[0]
 
 
+@pytest.mark.parametrize("fine64", [True, False])
+@pytest.mark.parametrize("qdtype,storage", [(torch.float32, "f32"), (torch.bfloat16, "bf16")])
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_rgmres_reduced_precision_one_cycle_vs_emulated_oracle(h, kind, qdtype, storage, fine64):
+    """One fixed cycle of RGMRES(20) with an FP32 / BF16 basis against the oracle's emulation of
+    the same storage (FP32 step 3 with one rounding per fused multiply-add, FP64 elsewhere): the
+    GPU's x lies within 10x of the emulation's own distance from the FP64 method, element by
+    element in the 2-norm, and so does the true residual after the cycle."""
+    csr, A, b = system(24, 25, 30.0, 2)
+    n, m, k = A.shape[0], 20, 70
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 9)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=m, max_cycles=1, qdtype=qdtype, fixed_steps=True,
+                           fine64=fine64)
+    emu = og.rgmres(A, b, Sketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True, storage=storage)
+    ex = og.rgmres(A, b, Sketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True)
+    xg = x.cpu().numpy()
+    d_gpu, d_emu = rel(xg, emu.x), rel(emu.x, ex.x)
+    r_gpu, r_emu, r_ex = res["history"][1], emu.true_residuals[1], ex.true_residuals[1]
+    print(f"{kind}/{storage}/fine64={fine64}: ||x-x_emu||/||x_emu|| {d_gpu:.2e} (emulation vs FP64 {d_emu:.2e}); "
+          f"residual gpu {r_gpu:.6e} emulated {r_emu:.6e} fp64 {r_ex:.6e}")
+    assert res["cycles"] == 1 and res["total_steps"] == m
+    assert d_gpu <= 10 * d_emu
+    assert abs(r_gpu - r_emu) <= 10 * abs(r_emu - r_ex) + 1e-12
+
+
 @pytest.mark.parametrize("qdtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("kind", ["srht", "gaussian"])
 def test_rgmres_converges_to_1e8(h, qdtype, kind):
