@@ -4,10 +4,11 @@
 Workload (one "step" = one full rgs_qr call):
     A = G D W with n = 2^20 rows, m = 500 columns, D log-spaced from 1 to 1e-10,
     G iid N(0,1), W Haar orthogonal; SRHT sketch with k = 2000 over 2^20;
-    basis stored in FP32 with FP32 update arithmetic; the sketch's transform sums and
-    the sketched least squares (steps 2, 5, 6) in FP64 (RGS_FP64_FINE).  The same
-    factorization with double-float (FP32-pair) fine arithmetic is reported beside it
-    ("double_float_fine").  Inputs (4.2 GB) are far larger than L2 (129 MB), so no
+    basis stored in FP32 with FP32 update arithmetic; the sketched least squares
+    (steps 2, 5, 6) in FP64 (RGS_FP64_LS); the SRHT's transform sums in double-float
+    (FP32 pairs, about 2^-48: finer than the FP32 accumulation the workload allows).
+    The same factorization with everything fine in FP64 ("fp64_fine") and with
+    double-float least squares ("double_float_fine") is reported beside it.  Inputs (4.2 GB) are far larger than L2 (129 MB), so no
     flush is needed between steps.
 
 Metric: whole-job algorithmic HBM throughput of the QR in GB/s, i.e.
@@ -17,12 +18,12 @@ divided by the measured time.  With --gpus N (torchrun), every rank factors
 its own independent matrix (weak scaling, no collective on the data path).
 
 The second half of the metric is reported in the same line ("rgmres"): restarted
-RGMRES(100) with RGS-Arnoldi (SRHT k = 400, FP32 basis; FP64 sketch sums, products,
-least squares, Givens and restart residual) against FP64 CGS2-GMRES(100) on the same
+RGMRES(100) with RGS-Arnoldi (SRHT k = 400, FP32 basis; FP64 least squares, Givens and
+restart residual; double-float sketch sums and products) against FP64 CGS2-GMRES(100) on the same
 GPU, time to a relative residual of 1e-8 on a 3D convection-diffusion operator: 128^3
 grid (n = 2,097,152, 7-point CSR, FP64 values), log-normal diffusion (sigma = 1,
 correlation length 8 cells), Peclet number 50, iid N(0,1) right-hand side.  The
-double-float and BF16-basis variants are reported beside it.
+all-FP64-fine, all-double-float and BF16-basis variants are reported beside it.
 
 "c1": the small FP64 factorization (n = 10,000, m = 100, cond 1e8, Gaussian k = 300),
 latency-bound, reported as time per call.
@@ -212,9 +213,10 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_df", "rgmres_bf16", "cgs2")):
-    """Time-to-1e-8 of RGMRES (FP32 basis; FP64 fine arithmetic, and double-float beside it) and
-    FP64 CGS2-GMRES on the 3D convection-diffusion system."""
+def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_f64", "rgmres_df", "rgmres_bf16",
+                                                          "cgs2")):
+    """Time-to-1e-8 of RGMRES (FP32 basis; FP64 least squares, and the all-FP64 and all-double-float
+    fine arithmetics beside it) and FP64 CGS2-GMRES on the 3D convection-diffusion system."""
     import torch
     import synth
     csr = synth.convdiff_3d(N, 50.0, 1.0, 8, 0)
@@ -224,17 +226,19 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_df", 
     sk = rgs.rgs_sketch_create(h, "srht", n, 400, 0)
     # warm-up on a few cycles (kernels loaded, allocator primed)
     xw = torch.zeros(n, dtype=torch.float64, device="cuda")
-    rgs.rgmres_solve(h, sk, C, b, xw, restart=100, max_cycles=1, fine64=True)
+    rgs.rgmres_solve(h, sk, C, b, xw, restart=100, max_cycles=1, ls64=True)
+    rgs.rgmres_solve(h, sk, C, b, xw.zero_(), restart=100, max_cycles=1, fine64=True)
     rgs.rgmres_solve(h, sk, C, b, xw.zero_(), restart=100, max_cycles=1)
     rgs.cgs2_gmres_solve(h, C, b, xw.zero_(), restart=100, max_cycles=1)
     out = {"config": "convdiff3d 128^3 n=2097152 nnz=%d Pe=50 sigma=1 corr=8 restart=100 rtol=1e-8" % len(csr[1])}
 
-    def rg(qd, fine):
+    def rg(qd, fine64=False, ls64=False):
         return lambda x: rgs.rgmres_solve(h, sk, C, b, x, restart=100, rtol=1e-8, max_cycles=max_cycles, qdtype=qd,
-                                          fine64=fine)
-    runs = (("rgmres_f32_fp64fine_srht400", "rgmres", rg(torch.float32, True)),
-            ("rgmres_f32_df_srht400", "rgmres_df", rg(torch.float32, False)),
-            ("rgmres_bf16_fp64fine_srht400", "rgmres_bf16", rg(torch.bfloat16, True)),
+                                          fine64=fine64, ls64=ls64)
+    runs = (("rgmres_f32_fp64ls_srht400", "rgmres", rg(torch.float32, ls64=True)),
+            ("rgmres_f32_fp64fine_srht400", "rgmres_f64", rg(torch.float32, fine64=True)),
+            ("rgmres_f32_df_srht400", "rgmres_df", rg(torch.float32)),
+            ("rgmres_bf16_fp64ls_srht400", "rgmres_bf16", rg(torch.bfloat16, ls64=True)),
             ("cgs2_gmres_f64", "cgs2", lambda x: rgs.cgs2_gmres_solve(h, C, b, x, restart=100, rtol=1e-8,
                                                                      max_cycles=max_cycles)))
     for name, key, fn in runs:
@@ -250,10 +254,11 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_df", 
                      "cycles": res["cycles"], "arnoldi_steps": res["total_steps"],
                      "us_per_step": 1e6 * dt / max(1, res["total_steps"])}
     c = out.get("cgs2_gmres_f64")
-    if c and "rgmres_f32_fp64fine_srht400" in out:
-        out["speedup_vs_cgs2_fp64"] = c["seconds"] / out["rgmres_f32_fp64fine_srht400"]["seconds"]
-    if c and "rgmres_f32_df_srht400" in out:
-        out["speedup_vs_cgs2_fp64_double_float"] = c["seconds"] / out["rgmres_f32_df_srht400"]["seconds"]
+    for name, key in (("rgmres_f32_fp64ls_srht400", "speedup_vs_cgs2_fp64"),
+                      ("rgmres_f32_fp64fine_srht400", "speedup_vs_cgs2_fp64_all_fp64_fine"),
+                      ("rgmres_f32_df_srht400", "speedup_vs_cgs2_fp64_double_float")):
+        if c and name in out:
+            out[key] = c["seconds"] / out[name]["seconds"]
     return out
 
 
@@ -440,8 +445,8 @@ def run_profile_case(args):
     """Small cases for ncu captures (no bench line): 'convnet' runs three training steps and one
     forward pass of the network on a batch of four 256 x 256 grids; 'batched' runs 16 instances
     (sides 32..64) of the batched solver for two fixed cycles; 'ls' runs one RGS QR of a 2^16 x 500
-    matrix with an SRHT of k = 2000 rows and an FP32 basis (the least-squares launches have the
-    bench workload's k and m; only the row count is smaller)."""
+    matrix with an SRHT of k = 2000 rows, an FP32 basis and FP64 least squares (the least-squares
+    launches have the bench workload's k, m and arithmetic; only the row count is smaller)."""
     import torch
     import synth
     import paper_2011_05090_gb300 as rgs
@@ -468,7 +473,7 @@ def run_profile_case(args):
         Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
         R = rgs.colmajor_empty(m, m)
         qs = torch.empty(m, dtype=torch.float64, device="cuda")
-        rgs.rgs_qr(h, sk, W, Q, R, qscale=qs)
+        rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=rgs.RGS_FP64_LS)
     else:
         insts = c4_instances(rgs, 16, 32, 64, 0)
         xs = [torch.zeros(I["n"], dtype=torch.float64, device="cuda") for I in insts]
@@ -529,7 +534,7 @@ def run_ours(args):
     Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
     R = rgs.colmajor_empty(m, m)
     qs = torch.empty(m, dtype=torch.float64, device="cuda")
-    fine = rgs.RGS_FP64_FINE                  # steps 1-2 and 4-6 in FP64 (u_fine) for the FP32 basis
+    fine = rgs.RGS_FP64_LS                    # least-squares steps 2, 5, 6 in FP64 for the FP32 basis
     flags = rgs.RGS_QR_TIMINGS | fine
     tuning = rgs.rgs_autotune_update(h, sk, m // 2, torch.float32)     # launch shape of the update pass
 
@@ -567,10 +572,10 @@ def run_ours(args):
     upd_ms = sum(i["update_ms"] for i in tinfos) / len(tinfos)
     peak, peak_kind = peaks()
     achieved = upd / (upd_ms * 1e-3) / 1e9
-    traffic_full = profile_traffic()
+    traffic_full = profile_traffic("double_float")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_full if (traffic_full and m == M_COLS) else None,
-                "kernel": "update_sketch_kernel<float,SRHT,FP64 transform>",
+                "kernel": "update_sketch_kernel<float,SRHT,double-float transform>",
                 "bytes_per_launch": upd / m, "launches_per_step": m,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "timing": "CUDA events around each launch on the library stream, over the K steps that follow "
@@ -608,26 +613,28 @@ def run_ours(args):
                "ms_per_step_median": 1e3 * statistics.median(e_times), "steps": len(e_times)}
         del Wh, Qh
 
-    # the same factorization with double-float fine arithmetic (FP32 pairs, about 2^-48 per
-    # operation): time, throughput, and its difference from the FP64-fine R and certificates
-    dfv = None
+    # the same factorization with the other fine arithmetics: everything fine in FP64, and
+    # everything fine in double-float (FP32 pairs, about 2^-48 per operation); time, throughput,
+    # certificates and the difference from the headline's R
+    variants = {}
     if rank == 0:
-        R64 = R.clone()
+        Rref = R.clone()
         Rd = rgs.colmajor_empty(m, m)
-        rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs)
-        torch.cuda.synchronize()
-        start.record()
-        for _ in range(3):
-            idf = rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs)
-        stop.record()
-        torch.cuda.synchronize()
-        td = start.elapsed_time(stop) / 3e3
-        dfv = {"ms": 1e3 * td, "GB/s": total / td / 1e9, "hbm_frac": total / td / 1e9 / peaks()[0],
-               "delta": idf["delta"], "delta_tilde": idf["delta_tilde"],
-               "rel_diff_R_vs_fp64_fine": (torch.linalg.norm(Rd - R64) / torch.linalg.norm(R64)).item()}
-        del Rd, R64
+        for vname, vflags in (("fp64_fine", rgs.RGS_FP64_FINE), ("double_float_fine", 0)):
+            rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs, flags=vflags)
+            torch.cuda.synchronize()
+            start.record()
+            for _ in range(3):
+                iv = rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs, flags=vflags)
+            stop.record()
+            torch.cuda.synchronize()
+            td = start.elapsed_time(stop) / 3e3
+            variants[vname] = {"ms": 1e3 * td, "GB/s": total / td / 1e9, "hbm_frac": total / td / 1e9 / peaks()[0],
+                               "delta": iv["delta"], "delta_tilde": iv["delta_tilde"],
+                               "rel_diff_R_vs_headline": (torch.linalg.norm(Rd - Rref) / torch.linalg.norm(Rref)).item()}
+        del Rd, Rref
 
-    # the BF16-storage variant of the same factorization (FP64 fine arithmetic): time, throughput,
+    # the BF16-storage variant of the same factorization (FP64 least squares): time, throughput,
     # certificates
     bf16 = None
     if rank == 0:
@@ -671,8 +678,9 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
-               "dtype_detail": "basis and update in f32 (u_crs); sketch transform sums and the sketched least "
-                               "squares (steps 2, 5, 6), R and the scales in f64 (u_fine, RGS_FP64_FINE)",
+               "dtype_detail": "basis and update in f32 (u_crs); sketched least squares (steps 2, 5, 6), squared "
+                               "norms, R and the scales in f64 (RGS_FP64_LS); SRHT transform sums in double-float "
+                               "(f32 pairs, ~2^-48)",
                "data": "synthetic",
                "config": {"workload": WORKLOAD if m == M_COLS else f"profiling case m={m}", "n": n, "m": m, "k": k, "sketch": "srht", "qtype": "f32",
                           "cond": COND, "l2": "inputs 4.2 GB > L2, no flush", "parallelism": f"replicas{world}",
@@ -680,7 +688,7 @@ def run_ours(args):
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "phases_ms": phases,
                "certificates": {"delta": last["delta"], "delta_tilde": last["delta_tilde"]},
-               "rgmres": gm, "batched": batched, "bf16_basis": bf16, "double_float_fine": dfv, "c1": c1,
+               "rgmres": gm, "batched": batched, "bf16_basis": bf16, "fine_variants": variants, "c1": c1,
                "hbm_frac_whole_job": value / world / peak}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -136,8 +136,8 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  *   R      m x m, ldr >= m (strictly lower part set to 0).
  *   S      optional (NULL): k x m, lds >= k, receives S = Theta Q (FP64).
  *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings;
- *          RGS_QR_FP64_FINE (= RGS_QR_FP64_SKETCH): FP64 transform sums and least
- *          squares in every storage mode.
+ *          RGS_QR_FP64_FINE (= RGS_FP64_FINE): FP64 transform sums and least squares in every
+ *          storage mode; RGS_FP64_LS: FP64 least squares, double-float transform sums.
  *   info   optional host struct: step-8 certificates and breakdown column.
  * W, Q, R, S, qscale may be all device or all host pointers.  Returns
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
@@ -147,6 +147,10 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
                                     transform sums, the products with A (Arnoldi) and the least-squares
                                     steps 2, 5, 6 (and Givens) in FP64 (rgs_qr, rgs_arnoldi_create,
                                     rgmres_opts.flags) */
+#define RGS_FP64_LS 8            /* bit 3: the sketched least-squares steps 2, 5, 6 (and the Givens
+                                    rotations of GMRES) in FP64 for every storage type, while the SRHT
+                                    transform sums and the products with A of FP32 / BF16 bases stay in
+                                    double-float (about 2^-48, finer than FP32 accumulation) */
 #define RGS_QR_FP64_FINE RGS_FP64_FINE
 #define RGS_QR_FP64_SKETCH RGS_FP64_FINE
 typedef struct {
@@ -178,8 +182,8 @@ typedef struct {
  * qtype, stored as q'_i with scale 1/r_ii), S, R, the Householder factors of S
  * and a work vector.  The least-squares steps run in FP64 for an FP64 basis and
  * in double-float arithmetic (about 2^-48) for FP32 / BF16 bases, as in rgs_qr; with
- * flags = RGS_FP64_FINE they, the SRHT transform sums and the products with A run in FP64
- * for every basis type (flags: 0 or RGS_FP64_FINE).
+ * flags = RGS_FP64_LS they run in FP64 for every basis type, and with RGS_FP64_FINE the SRHT
+ * transform sums and the products with A do too (flags: 0, RGS_FP64_LS or RGS_FP64_FINE).
  *   rgs_arnoldi_start: iteration 1 with w_1 (device FP64, n).
  *   rgs_arnoldi_step:  next iteration with w_i = A q_{i-1} (A given, FP64 SpMV),
  *                      or with the caller's w (device FP64) when A is NULL.
@@ -216,8 +220,8 @@ typedef struct {
                                cycles after it */
     rgs_dtype qtype;        /* basis storage (RGS only) */
     int32_t fixed_steps;    /* 1: always run `restart` steps per cycle */
-    int32_t flags;          /* 0, or RGS_FP64_FINE: FP64 sketch sums, products with A, least squares
-                               and Givens for FP32 / BF16 bases too (RGS only) */
+    int32_t flags;          /* 0, RGS_FP64_LS (FP64 least squares and Givens) or RGS_FP64_FINE (also
+                               FP64 sketch sums and products with A) for FP32 / BF16 bases (RGS only) */
 } rgmres_opts;
 
 typedef struct {

@@ -46,6 +46,7 @@ RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
 RGS_QR_NO_CERTIFICATES = 1
 RGS_QR_TIMINGS = 2
 RGS_FP64_FINE = 4               # FP64 transform sums, products and least squares for every storage
+RGS_FP64_LS = 8                 # FP64 least squares (and Givens); double-float transform sums
 RGS_QR_FP64_FINE = RGS_FP64_FINE
 RGS_QR_FP64_SKETCH = RGS_FP64_FINE
 RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
@@ -333,11 +334,16 @@ class _DeviceArray:
                                          "data": (ptr, False), "version": 2}
 
 
-def rgs_arnoldi_create(h, sk, n, mmax, qdtype=torch.float64, fine64=False):
-    """RGS-Arnoldi object; fine64 selects FP64 fine arithmetic for FP32 / BF16 bases (RGS_FP64_FINE)."""
+def _fine_flags(fine64, ls64):
+    return (RGS_FP64_FINE if fine64 else 0) | (RGS_FP64_LS if ls64 else 0)
+
+
+def rgs_arnoldi_create(h, sk, n, mmax, qdtype=torch.float64, fine64=False, ls64=False):
+    """RGS-Arnoldi object; for FP32 / BF16 bases ls64 selects FP64 least squares (RGS_FP64_LS) and
+    fine64 all-FP64 fine arithmetic (RGS_FP64_FINE)."""
     out = ctypes.c_void_p()
-    _check(load().rgs_arnoldi_create(h.ptr, sk.ptr, int(n), int(mmax), _DTYPE[qdtype],
-                                     RGS_FP64_FINE if fine64 else 0, ctypes.byref(out)), h)
+    _check(load().rgs_arnoldi_create(h.ptr, sk.ptr, int(n), int(mmax), _DTYPE[qdtype], _fine_flags(fine64, ls64),
+                                     ctypes.byref(out)), h)
     return Arnoldi(out.value, h, sk, int(n), int(mmax), qdtype)
 
 
@@ -379,9 +385,9 @@ def rgs_arnoldi_basis(a, ncols=None):
     return torch.as_tensor(arr, device="cuda").T
 
 
-def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64=False):
+def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64=False, ls64=False):
     return GmresOpts(int(restart), int(max_cycles), float(rtol), float(inner_factor), _DTYPE[qdtype],
-                     1 if fixed_steps else 0, RGS_FP64_FINE if fine64 else 0)
+                     1 if fixed_steps else 0, _fine_flags(fine64, ls64))
 
 
 def _gmres_result(st, info, hist, h):
@@ -398,10 +404,10 @@ def _gmres_result(st, info, hist, h):
 
 
 def rgmres_solve(h, sk, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_factor=0.5,
-                 qdtype=torch.float32, fixed_steps=False, fine64=False):
-    """Restarted randomized GMRES; x (FP64, CUDA) holds x0 and receives the solution.  fine64:
-    FP64 sketch sums, products with A, least squares and Givens for FP32 / BF16 bases."""
-    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64)
+                 qdtype=torch.float32, fixed_steps=False, fine64=False, ls64=False):
+    """Restarted randomized GMRES; x (FP64, CUDA) holds x0 and receives the solution.  For FP32 /
+    BF16 bases, ls64: FP64 least squares and Givens; fine64: also FP64 sketch sums and products."""
+    opts = _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fine64, ls64)
     hist = (ctypes.c_double * (max_cycles + 2))()
     info = GmresInfo()
     info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))

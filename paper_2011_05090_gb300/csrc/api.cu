@@ -350,7 +350,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         // workspaces: Householder engine, P = Theta W, partial sketches, certificates
         LSState ls{};
         rgs_ls_alloc(h->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm,
-                     qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH), &ls);
+                     qtype != RGS_F64 && !(flags & (RGS_FP64_FINE | RGS_FP64_LS)), &ls);
         ls.ctl = h->ctl.as<int>();
         ls.R = dR;
         ls.ldr = dldr;
@@ -375,7 +375,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         // step 1: P = Theta W in one pass over W (Gaussian), or only p_1 (SRHT; the other
         // columns are sketched inside the update passes)
         timer.start(0);
-        const bool df = qtype != RGS_F64 && !(flags & RGS_QR_FP64_SKETCH);
+        const bool df = qtype != RGS_F64 && !(flags & RGS_FP64_FINE);     // double-float transform sums
         need_w(fused_p ? 0 : m - 1);
         sketch_block(h, s, fused_p ? 1 : m, dW, dldw, P, k, df);
         timer.stop(0);

@@ -28,6 +28,7 @@ struct rgs_arnoldi_obj {
     int mmax = 0;
     int qtype = 0;
     int fine64 = 0;          // RGS_FP64_FINE: FP64 transform sums, products and least squares for any qtype
+    int ls64 = 0;            // RGS_FP64_LS: FP64 least squares (and Givens) for any qtype
     int64_t ldq = 0;
     int ncols = 0;           // columns appended so far (public step-by-step interface)
     DevBuf Q;                // n x mmax in qtype
@@ -76,8 +77,8 @@ void arnoldi_alloc(rgs_arnoldi_obj* a) {
     const int k = a->sk->k, m = a->mmax;
     a->ldq = (a->n + 7) & ~(int64_t)7;
     a->Q.ensure(dsize(a->qtype) * (size_t)a->ldq * m);
-    rgs_ls_alloc(a->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm, a->qtype != RGS_F64 && !a->fine64,
-                 &a->ls);
+    rgs_ls_alloc(a->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm,
+                 a->qtype != RGS_F64 && !a->fine64 && !a->ls64, &a->ls);
     a->R.ensure(sizeof(double) * (size_t)m * m);
     a->gv.ensure(sizeof(double) * (4 * (size_t)m + 2 + (size_t)m * m + 2 * (size_t)m));
     double* g = a->gv.as<double>();
@@ -222,13 +223,14 @@ rgs_status rgs_arnoldi_create(rgs_handle h, rgs_sketch s, int64_t n, int32_t mma
         RGS_REQUIRE(qtype == RGS_F64 || qtype == RGS_F32 || qtype == RGS_BF16, "unknown qtype");
         RGS_REQUIRE(n == s->n, "n differs from the sketch's n");
         RGS_REQUIRE(mmax >= 1 && mmax <= s->k && mmax <= 1024 && mmax <= n, "need 1 <= mmax <= min(k, n, 1024)");
-        RGS_REQUIRE((flags & ~RGS_FP64_FINE) == 0, "unknown flags");
+        RGS_REQUIRE((flags & ~(RGS_FP64_FINE | RGS_FP64_LS)) == 0, "unknown flags");
         a->h = h;
         a->sk = s;
         a->n = n;
         a->mmax = mmax;
         a->qtype = qtype;
         a->fine64 = (flags & RGS_FP64_FINE) ? 1 : 0;
+        a->ls64 = (flags & RGS_FP64_LS) ? 1 : 0;
         arnoldi_alloc(a);
     });
     if (st != RGS_OK) {
@@ -380,7 +382,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         RGS_REQUIRE(opts->restart >= 1 && opts->restart + 1 <= s->k && opts->restart < 1024,
                     "need 1 <= restart < min(k, 1024)");
         RGS_REQUIRE(opts->max_cycles >= 0 && opts->rtol >= 0.0, "bad max_cycles or rtol");
-        RGS_REQUIRE((opts->flags & ~RGS_FP64_FINE) == 0, "unknown flags");
+        RGS_REQUIRE((opts->flags & ~(RGS_FP64_FINE | RGS_FP64_LS)) == 0, "unknown flags");
         const int m = opts->restart;
         rgs_arnoldi_obj obj;
         obj.h = h;
@@ -389,6 +391,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         obj.mmax = m + 1;
         obj.qtype = opts->qtype;
         obj.fine64 = (opts->flags & RGS_FP64_FINE) ? 1 : 0;
+        obj.ls64 = (opts->flags & RGS_FP64_LS) ? 1 : 0;
         arnoldi_alloc(&obj);
         // Right preconditioning A M, x = x0 + M (Q y) (Sec. 5.3 preconditions A_f P_f from the right).
         // Jacobi, M = D^{-1}: the Arnoldi operator is A D^{-1} (column-scaled values), and the

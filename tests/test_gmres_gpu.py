@@ -90,31 +90,40 @@ def test_rgmres_fp64_one_cycle_matches_oracle(h, kind):
     assert abs(res["history"][1] - ref.true_residuals[1]) <= 1e-10 * ref.true_residuals[0]
 
 
-@pytest.mark.parametrize("fine64", [True, False])
+@pytest.mark.parametrize("fine", ["ls64", "f64", "df"])
 @pytest.mark.parametrize("qdtype,storage", [(torch.float32, "f32"), (torch.bfloat16, "bf16")])
 @pytest.mark.parametrize("kind", ["srht", "gaussian"])
-def test_rgmres_reduced_precision_one_cycle_vs_emulated_oracle(h, kind, qdtype, storage, fine64):
+def test_rgmres_reduced_precision_one_cycle_vs_emulated_oracle(h, kind, qdtype, storage, fine):
     """One fixed cycle of RGMRES(20) with an FP32 / BF16 basis against the oracle's emulation of
-    the same storage (FP32 step 3 with one rounding per fused multiply-add, FP64 elsewhere): the
-    GPU's x lies within 10x of the emulation's own distance from the FP64 method, element by
-    element in the 2-norm, and so does the true residual after the cycle."""
+    the same storage (FP32 step 3 with one rounding per fused multiply-add, FP64 elsewhere).
+    With FP64 fine arithmetic (all of it, or the least squares with the Gaussian sketch, whose
+    sums are FP64 anyway) the GPU takes the emulation's roundings: x agrees to 1e-10.  Where
+    double-float sums or products enter, some FP32 roundings of q' differ, so x lies within 10x of
+    the emulation's own distance from the FP64 method, and the true residual after the cycle
+    within 10x of the emulation's distance plus ten FP32 storage roundings of it."""
     csr, A, b = system(24, 25, 30.0, 2)
     n, m, k = A.shape[0], 20, 70
     (rp, ci, va), C = rgs.csr_to_device(*csr)
     sk = rgs.rgs_sketch_create(h, kind, n, k, 9)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=m, max_cycles=1, qdtype=qdtype, fixed_steps=True,
-                           fine64=fine64)
+                           fine64=fine == "f64", ls64=fine == "ls64")
     emu = og.rgmres(A, b, Sketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True, storage=storage)
     ex = og.rgmres(A, b, Sketch(kind, n, k, 9), restart=m, max_cycles=1, fixed_steps=True)
     xg = x.cpu().numpy()
     d_gpu, d_emu = rel(xg, emu.x), rel(emu.x, ex.x)
     r_gpu, r_emu, r_ex = res["history"][1], emu.true_residuals[1], ex.true_residuals[1]
-    print(f"{kind}/{storage}/fine64={fine64}: ||x-x_emu||/||x_emu|| {d_gpu:.2e} (emulation vs FP64 {d_emu:.2e}); "
+    print(f"{kind}/{storage}/{fine}: ||x-x_emu||/||x_emu|| {d_gpu:.2e} (emulation vs FP64 {d_emu:.2e}); "
           f"residual gpu {r_gpu:.6e} emulated {r_emu:.6e} fp64 {r_ex:.6e}")
     assert res["cycles"] == 1 and res["total_steps"] == m
-    assert d_gpu <= 10 * d_emu
-    assert abs(r_gpu - r_emu) <= 10 * abs(r_emu - r_ex) + 1e-12
+    same_roundings = fine == "f64" or (fine == "ls64" and kind == "gaussian")
+    if same_roundings:
+        assert d_gpu <= 1e-10
+        assert abs(r_gpu - r_emu) <= 1e-10 * r_emu
+    else:
+        u_crs = 2.0 ** -24 if storage == "f32" else 2.0 ** -8
+        assert d_gpu <= 10 * d_emu
+        assert abs(r_gpu - r_ex) <= 10 * abs(r_emu - r_ex) + 10 * u_crs * r_ex
 
 
 @pytest.mark.parametrize("qdtype", [torch.float64, torch.float32, torch.bfloat16])
