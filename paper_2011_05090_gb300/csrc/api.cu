@@ -142,6 +142,8 @@ rgs_status rgs_create(rgs_handle* out, void* stream) {
         ctx->ctl.ensure(kCtlAlloc * sizeof(int));
         RGS_CUDA(cudaMemset(ctx->ctl.ptr, 0, kCtlAlloc * sizeof(int)));
         ctx->ls_blocks = rgs_ls_max_blocks(ctx->num_sms);
+        const char* pdl = std::getenv("RGS_PDL");
+        ctx->pdl = (pdl != nullptr && pdl[0] == '0') ? 0 : 1;
         rgs_noalloc_reserve(ctx->device);
     });
     if (st != RGS_OK) {

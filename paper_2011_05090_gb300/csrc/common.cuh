@@ -81,6 +81,9 @@ struct rgs_context {
     cudaStream_t capture_stream = nullptr; // private stream on which launches are captured into graphs
     cudaStream_t copy_stream = nullptr;    // host <-> device copies overlapped with rgs_qr
     int launches = 0;      // kernels launched by the current call
+    int pdl = 1;           // launch the update and least-squares kernels with programmatic stream
+                           // serialization (RGS_PDL=0 in the environment at rgs_create: plain order)
+    int pdl_coop = 1;      // the driver accepts it together with a cooperative launch (cleared on refusal)
     std::vector<cudaEvent_t> events;   // pool for per-phase timings
     ~rgs_context() {
         for (auto e : events) cudaEventDestroy(e);
@@ -304,6 +307,14 @@ struct GridBarrier {
     }
 };
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the kernel before it on the stream is still running; pdl_wait() returns once that
+// kernel has completed and its memory operations are visible (immediately for a plain launch).
+// pdl_launch_dependents() lets the next such kernel be scheduled once every CTA of this grid has
+// issued it (its CTAs then wait in their own pdl_wait()).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -379,7 +390,6 @@ struct LSState {
     double *M;              // M = V T (column-major k x mmax): Q_H^T x = x - V (M^T x)
     double *u2s, *u2p;
     double *zp, *d1, *d2;   // per-column dots of phase 4
-    double *red;            // first-level sums of partial sketches
     double *blk;            // 4 * grid
     double *sigma, *pnorm, *coef;
     double *R;

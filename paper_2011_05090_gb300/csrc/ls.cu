@@ -34,7 +34,6 @@ namespace {
 
 constexpr int LT = 512;        // threads per CTA (one CTA per SM)
 constexpr int NW = LT / 32;    // warps per CTA
-constexpr int GS = 32;         // partial sketches summed per warp in the first reduction level
 constexpr int kTotMax = 8;     // per-CTA totals are read for up to 32 * kTotMax CTAs at once
 
 // ------------------------------------------------------------------ arithmetic types
@@ -229,25 +228,6 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     return A::from_d((v0 + v1) + (v2 + v3));
 }
 
-// Sum over g in [0, ng) of first-level group sums red[g * k + l] (type A::T, this launch):
-// the loads of up to 16 groups are issued before the adds.
-template <class A>
-__device__ __forceinline__ typename A::T group_total(const double* red, int ng, int k, int l) {
-    using T = typename A::T;
-    T v0 = A::zero(), v1 = A::zero();
-    for (int g0 = 0; g0 < ng; g0 += 16) {
-        T v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = g0 + q < ng ? A::ldg(red + (size_t)(g0 + q) * k + l) : A::zero();
-#pragma unroll
-        for (int q = 0; q < 16; q += 2) {
-            if (g0 + q < ng) v0 = A::add(v0, v[q]);
-            if (g0 + q + 1 < ng) v1 = A::add(v1, v[q + 1]);
-        }
-    }
-    return A::add(v0, v1);
-}
-
 // Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2 (written earlier
 // in this launch), a warp with lanes over the entries: the lane partials summed over the warp,
 // valid in every lane; use1 / use2 select the vectors needed.
@@ -287,9 +267,12 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     __shared__ double shd[2 * (NW + 1) + 2];   // FP64 block sums and totals (squared norms)
     __shared__ T shT[2 * (NW + 1) + 2];        // A::T block sums and totals
     __shared__ T qs[3 * NW];                   // per-warp partial dots of the column phases
+    __shared__ T shP[NW * 32];                 // phase 0: the warps' range sums of one segment
     __shared__ T scT[8];                       // scalars of the current phase, in A::T
     __shared__ double sc[8];                   // FP64 scalars of phase 1
     int* ctl = st.ctl;
+    pdl_wait();                        // the partial sketches and status of the kernel before
+    pdl_launch_dependents();
     if (ctl[kStatusWord] != 0 || ctl[kStopWord] != 0) return;
     const int k = st.k, mm = st.mmax, i = a.i;
     const int G = gridDim.x;
@@ -309,75 +292,63 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         scT[7] = A::from_d(a.p_scale);
     }
 
-    // ---- phase 0a: with more than GS partial sketches, a first level sums groups of GS
-    const int sgroups = app ? (a.s_nparts + GS - 1) / GS : 0;
-    const int pgroups = p_parts ? (a.p_nparts + GS - 1) / GS : 0;
-    const bool level1 = sgroups > 1 || pgroups > 1;
-    if (level1) {
-        const int nseg = (k + 31) / 32;
-        for (int it = gwarp; it < nseg * (sgroups + pgroups); it += nwarps) {
-            const int seg = it % nseg, g = it / nseg;
-            const bool is_s = g < sgroups;
-            const int gg = is_s ? g : g - sgroups;
-            const int np = is_s ? a.s_nparts : a.p_nparts;
-            const int l = seg * 32 + lane;
-            if (l < k)
-                A::st(st.red + (size_t)g * k + l, part_sum<A>(is_s ? a.s_part : a.p_part, (is_s ? a.s_df : a.p_df) != 0,
-                                                             gg * GS, min(np, gg * GS + GS), k, l));
-        }
-        if (!bar.sync(ctl)) return;
-    }
-    if (trace) trace[1] = globaltimer();
+    if (trace) trace[1] = globaltimer();              // (the partial sums need no phase of their own)
     __syncthreads();
     const T s_scale = scT[6], p_scale = scT[7];
 
-    // ---- phase 0b: items (32-row segment, vector s' or p), a warp each with lane = row, sum
-    //      the groups (or partials) of their rows in order and the squared norms (FP64); the
-    //      warps of the other rows of warps form M(:, i-1), one row each
+    // ---- phase 0: the totals of s' and p.  Item = (32-row segment, vector), one item per CTA:
+    //      its NW warps sum consecutive ranges of the partial sketches for the segment's rows
+    //      (lane = row), warp 0 adds the NW range sums in order (deterministic), scales and
+    //      stores them and forms the squared norms (FP64).  Then every warp forms rows of
+    //      M(:, i-1) = V(:, 0:i) T(0:i, i-1).
     {
-        double nrm = 0.0;
+        const int warp = tid >> 5;
+        double nrm_s = 0.0, nrm_p = 0.0;               // warp 0, lane 0
         const int nseg = (k + 31) / 32;
         const int nitems = nseg * 2;
-        for (int it = gwarp; it < nitems; it += nwarps) {
-            const int seg = it >> 1, vec = it & 1;       // vec 0: s', vec 1: p
-            const int l = seg * 32 + lane;
+        for (int it = blockIdx.x; it < nitems; it += G) {
+            const int seg = it >> 1, vec = it & 1;       // vec 0: s', vec 1: p (uniform over the CTA)
             if (vec == 0 ? !app : !sol) continue;
-            if (l < k) {
-                T v;
-                if (vec == 0) {
-                    v = A::mul(level1 ? group_total<A>(st.red, sgroups, k, l)
-                                      : part_sum<A>(a.s_part, a.s_df != 0, 0, a.s_nparts, k, l), s_scale);
-                    A::st(st.sbuf + l, v);
-                } else {
-                    v = A::mul(!p_parts ? A::from_d(a.p_vec[l])
-                               : level1 ? group_total<A>(st.red + (size_t)sgroups * k, pgroups, k, l)
-                                        : part_sum<A>(a.p_part, a.p_df != 0, 0, a.p_nparts, k, l), p_scale);
-                    A::st(st.pbuf + l, v);
-                }
-                const double vd = A::to_d(v);
-                if (vec == 1 && a.p_store) a.p_store[l] = vd;
-                nrm = fma(vd, vd, nrm);
+            const int l = seg * 32 + lane;
+            T part = zero;
+            if (vec == 0 || p_parts) {
+                const int np = vec == 0 ? a.s_nparts : a.p_nparts;
+                const int chunk = (np + NW - 1) / NW;
+                const int b0 = min(np, warp * chunk), b1 = min(np, b0 + chunk);
+                if (l < k && b1 > b0)
+                    part = part_sum<A>(vec == 0 ? a.s_part : a.p_part, (vec == 0 ? a.s_df : a.p_df) != 0, b0, b1, k, l);
+            } else if (warp == 0 && l < k) {
+                part = A::from_d(a.p_vec[l]);
             }
+            shP[warp * 32 + lane] = part;
+            __syncthreads();
+            if (warp == 0) {
+                T v = shP[lane];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) v = A::add(v, shP[w * 32 + lane]);
+                v = A::mul(v, vec == 0 ? s_scale : p_scale);
+                double vd = 0.0;
+                if (l < k) {
+                    A::st((vec == 0 ? st.sbuf : st.pbuf) + l, v);
+                    vd = A::to_d(v);
+                    if (vec == 1 && a.p_store) a.p_store[l] = vd;
+                }
+                const double sq = warp_sum(vd * vd);
+                if (vec == 0) nrm_s += sq; else nrm_p += sq;
+            }
+            __syncthreads();                               // shP is reused by the next item
         }
-        // the squared norms: per warp, then per CTA (slot 0: s', slot 1: p)
-        const bool busy = gwarp < nitems;              // idle warps skip the FP64 shuffles
-        if (busy) nrm = warp_sum(nrm);
-        double nv[2] = {busy && (gwarp & 1) == 0 ? nrm : 0.0, busy && (gwarp & 1) == 1 ? nrm : 0.0};
         if (i > 0) {
             // M(:, i-1) = V(:, 0:i) T(0:i, i-1): T's column i-1 was completed by the previous
             // launch; warp per row of the row-major copy VT, lanes over the columns
             const double* tc = st.T + (size_t)(i - 1) * mm;
-            const int first = min(nitems, nwarps - 1);     // warps after the items' warps (if any)
-            const int mw = nwarps - first;
-            for (int l = gwarp - first; l < k; l += mw) {
-                if (l < 0) break;
+            for (int l = gwarp; l < k; l += nwarps) {
                 T d, unused;
                 warp_row_dot2<A>(st.VT + (size_t)l * mm, tc, tc, min(i, l + 1), true, false, d, unused);
                 if (lane == 0) A::st(st.M + (size_t)(i - 1) * k + l, d);
             }
         }
-        block_sum_lane0<FineF64, 2>(nv, shd);
-        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nv[0]; st.blk[blockIdx.x * 4 + 1] = nv[1]; }
+        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm_s; st.blk[blockIdx.x * 4 + 1] = nrm_p; }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[2] = globaltimer();
@@ -734,14 +705,13 @@ __global__ void cert_final_kernel(const double* work, int m, double* out) {
 }  // namespace
 
 void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fine_df, LSState* st) {
-    const int groups = 2 * ((std::max(max_parts, 1) + GS - 1) / GS);
     size_t n = 0;
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
     const size_t oV = take((size_t)k * mmax), oVT = take((size_t)k * mmax), oT = take((size_t)mmax * mmax),
                  oTT = take((size_t)mmax * mmax), oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax),
                  osb = take(k), opb = take(k), oys = take(k), oyp = take(k), oM = take((size_t)k * mmax),
                  ou2s = take(mmax), ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
-                 ored = take((size_t)groups * k), oblk = take((size_t)4 * grid), osg = take(mmax + 1),
+                 oblk = take((size_t)4 * grid), osg = take(mmax + 1),
                  opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
     double* b = buf.as<double>();
@@ -750,7 +720,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fi
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
     st->M = b + oM; st->u2s = b + ou2s; st->u2p = b + ou2p;
     st->zp = b + ozp; st->d1 = b + od1; st->d2 = b + od2;
-    st->red = b + ored; st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
+    st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
     st->coef = b + oco;
 }
 
@@ -772,7 +742,26 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
     RGS_REQUIRE(grid <= 32 * kTotMax, "least-squares grid larger than the per-CTA totals support");
     const void* fn = st.fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
-    RGS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(LT), args, 0, ctx->stream));
+    cudaLaunchAttribute attrs[2] = {};
+    attrs[0].id = cudaLaunchAttributeCooperative;
+    attrs[0].val.cooperative = 1;
+    attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(LT);
+    cfg.stream = ctx->stream;
+    cfg.attrs = attrs;
+    cfg.numAttrs = (ctx->pdl && ctx->pdl_coop) ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (e != cudaSuccess && cfg.numAttrs == 2) {
+        // the driver refused programmatic serialization with a cooperative launch: plain order
+        cudaGetLastError();
+        ctx->pdl_coop = 0;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+    }
+    RGS_CUDA(e);
     ctx->launches++;
 }
 

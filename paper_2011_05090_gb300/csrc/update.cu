@@ -135,6 +135,8 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     int32_t* srow = reinterpret_cast<int32_t*>(part + (SRHT ? p.k : 0));     // k
     Acc* sc = reinterpret_cast<Acc*>(srow + (SRHT ? ((p.k + 3) & ~3) : 0));   // ncols
 
+    pdl_wait();                        // the previous kernel's coefficients, status and basis
+    pdl_launch_dependents();
     if (p.ctl != nullptr && p.ctl[kStatusWord] != 0) return;   // an earlier step failed or broke down
     const int col = blockIdx.y;
     // the second row of blocks of a launch with w_next sketches the next input column as it is
@@ -338,8 +340,17 @@ template <typename TQ, bool SRHT, bool DF = false>
 void launch_update_t(rgs_context* ctx, const UpdParams& p, int gx, int gy, size_t smem) {
     auto kern = update_sketch_kernel<TQ, SRHT, DF>;
     if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<dim3(gx, gy), UT, smem, ctx->stream>>>(p);
-    RGS_CUDA(cudaGetLastError());
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(gx, gy);
+    cfg.blockDim = dim3(UT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = ctx->pdl ? 1 : 0;
+    RGS_CUDA(cudaLaunchKernelEx(&cfg, kern, p));
     ctx->launches++;
 }
 

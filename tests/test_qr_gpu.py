@@ -367,9 +367,11 @@ def test_c2_full_size_sampled_parity(h, fine):
 @pytest.mark.parametrize("scale", [2.0 ** 100, 2.0 ** -80])
 def test_double_float_least_squares_on_scaled_inputs(h, scale):
     """FP32 basis (double-float least squares, FP64 squared norms), W scaled by 2^100 (1.3e30) or
-    2^-80 (8.3e-25): every step is equivariant under a power-of-two scaling while no value leaves
-    FP32's exponent range, so R scales by the same factor and the basis is unchanged, up to
-    rounding at most (no overflow, underflow or loss of the double-float low words)."""
+    2^-80 (8.3e-25): the steps commute with a power-of-two scaling while no value leaves FP32's
+    exponent range, so R scales by the same factor (to 1e-12: the runs are not bit-identical, a
+    difference of 1e-14 to 1e-12 in R was measured) and the basis agrees to FP32 rounding (such a
+    difference can flip the FP32 rounding of a step-3 coefficient); an overflow, underflow or
+    loss of the double-float low words would show as orders of magnitude more."""
     n, m, k = 20000, 30, 120
     A = synth.gdw_matrix(n, m, 1e6, 14).numpy().T.copy()
     sk = rgs.rgs_sketch_create(h, "srht", n, k, 5)
@@ -381,4 +383,4 @@ def test_double_float_least_squares_on_scaled_inputs(h, scale):
     print(f"scale {scale:.3e}: R {rel(g['R'] / scale, ref['R']):.2e}, Q {rel(Qg, Qr):.2e}, "
           f"bit-identical R: {np.array_equal(g['R'], ref['R'] * scale)}")
     assert rel(g["R"] / scale, ref["R"]) <= 1e-12
-    assert rel(Qg, Qr) <= 1e-12
+    assert rel(Qg, Qr) <= 1e-6
