@@ -442,7 +442,8 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
 
 
 def run_profile_case(args):
-    """Small cases for ncu captures (no bench line): 'convnet' runs three training steps and one
+    """Small cases for ncu captures (no bench line): 'update' and 'c2' run the QR workload (below);
+    'convnet' runs three training steps and one
     forward pass of the network on a batch of four 256 x 256 grids; 'batched' runs 16 instances
     (sides 32..64) of the batched solver for two fixed cycles; 'ls' runs one RGS QR of a 2^16 x 500
     matrix with an SRHT of k = 2000 rows, an FP32 basis and FP64 least squares (the least-squares
@@ -466,6 +467,19 @@ def run_profile_case(args):
         for _ in range(3):
             rgs.rgs_convnet_train_step(h, net, x, x[:, 0].contiguous(), lr=1e-3, stencil=S)
         rgs.rgs_convnet_forward(h, net, x)
+    elif args.profile_case in ("update", "c2"):
+        # 'update': one factorization of the first 128 columns of the 2^20-row workload (update
+        # launch j + 1 is column j; launch 0 sketches w_1); 'c2': two factorizations of the full
+        # 2^20 x 500 workload (the second one's 1004 launches follow the first one's)
+        n, k = 1 << 20, 2000
+        m = 128 if args.profile_case == "update" else 500
+        W = synth.gdw_matrix(n, m, 1e10, 0, device="cuda").T
+        sk = rgs.rgs_sketch_create(h, "srht", n, k, 0)
+        Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
+        R = rgs.colmajor_empty(m, m)
+        qs = torch.empty(m, dtype=torch.float64, device="cuda")
+        for _ in range(1 if args.profile_case == "update" else 2):
+            rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=rgs.RGS_FP64_LS)
     elif args.profile_case == "ls":
         n, m, k = 1 << 16, 500, 2000
         W = synth.gdw_matrix(n, m, 1e10, 0).T.to("cuda")
@@ -708,7 +722,7 @@ def main():
     ap.add_argument("--gmres-cycles", type=int, default=400)
     ap.add_argument("--cols", type=int, default=0, help="profiling cases only: override m (the bench line is m=500)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--profile-case", choices=["convnet", "batched", "ls"], default="",
+    ap.add_argument("--profile-case", choices=["convnet", "batched", "ls", "update", "c2"], default="",
                     help="small case for an ncu capture only (no bench line)")
     ap.add_argument("--c5", type=int, default=0, metavar="N",
                     help="only the learned-preconditioner workload on N x N grids (one JSON line)")
