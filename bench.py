@@ -28,6 +28,9 @@ all-FP64-fine, all-double-float and BF16-basis variants are reported beside it.
 "c1": the small FP64 factorization (n = 10,000, m = 100, cond 1e8, Gaussian k = 300),
 latency-bound, reported as time per call.
 
+"embedding_certificate": Sec. 3.2's a posteriori certificate omega_bar (eps* = 0.05) for the
+factorization's basis and for one RGS-Arnoldi cycle's basis on the 128^3 operator.
+
 "batched" in the same line: 256 independent 2D convection-diffusion RGMRES solves in one
 persistent launch (rgmres_solve_batched, FP32 basis, Gaussian k = 2 restart) against the
 same 256 systems solved one after another with FP64 CGS2-GMRES, at the full sizes (sides
@@ -259,6 +262,46 @@ def run_gmres_c3(rgs, h, N=128, max_cycles=400, solvers=("rgmres", "rgmres_f64",
                       ("rgmres_f32_df_srht400", "speedup_vs_cgs2_fp64_double_float")):
         if c and name in out:
             out[key] = c["seconds"] / out[name]["seconds"]
+    return out
+
+
+def run_certificates(rgs, h, W, sk, n, m, k):
+    """Sec. 3.2's embedding certificate omega_bar (eps* = 0.05, Phi an SRHT of Theta's size with
+    another seed) for (a) the basis of the 2^20 x 500 factorization and (b) the Arnoldi basis of one
+    RGMRES(100) cycle on the 128^3 convection-diffusion operator (FP32 bases, FP64 least squares)."""
+    import torch
+    import synth
+    out = {}
+    Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
+    R = rgs.colmajor_empty(m, m)
+    S = rgs.colmajor_empty(k, m)
+    qs = torch.empty(m, dtype=torch.float64, device="cuda")
+    rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, S=S, flags=rgs.RGS_FP64_LS)
+    phi = rgs.rgs_sketch_create(h, "srht", n, k, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = rgs.rgs_certify_embedding(h, sk, phi, Q, 0.05, vscale=qs, VTheta=S)
+    torch.cuda.synchronize()
+    out["qr_2e20x500_srht2000"] = {**c, "eps_star": 0.05, "ms": 1e3 * (time.perf_counter() - t0)}
+    del Q, S
+    N = 128
+    csr = synth.convdiff_3d(N, 50.0, 1.0, 8, 0)
+    n3 = N ** 3
+    arrays, C = rgs.csr_to_device(*csr)
+    b = torch.tensor(synth.rhs(n3, 0), device="cuda")
+    th3 = rgs.rgs_sketch_create(h, "srht", n3, 400, 0)
+    ph3 = rgs.rgs_sketch_create(h, "srht", n3, 400, 1)
+    a = rgs.rgs_arnoldi_create(h, th3, n3, 101, torch.float32, ls64=True)
+    rgs.rgs_arnoldi_start(h, a, b)
+    for _ in range(100):
+        rgs.rgs_arnoldi_step(h, a, csr=C)
+    _, _, qs3 = rgs.rgs_arnoldi_get(h, a)
+    Q3 = rgs.rgs_arnoldi_basis(a, 101)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c3 = rgs.rgs_certify_embedding(h, th3, ph3, Q3, 0.05, vscale=torch.tensor(qs3, device="cuda"))
+    torch.cuda.synchronize()
+    out["arnoldi_128cube_srht400_101cols"] = {**c3, "eps_star": 0.05, "ms": 1e3 * (time.perf_counter() - t0)}
     return out
 
 
@@ -673,6 +716,7 @@ def run_ours(args):
     if rank == 0 and not args.no_batched:
         batched = run_batched_c4(rgs, h)
     c1 = run_c1(rgs, h) if rank == 0 else None
+    certs = run_certificates(rgs, h, W, sk, n, m, k) if (rank == 0 and m == M_COLS) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -703,6 +747,7 @@ def run_ours(args):
                "clocks": clk.summary(), "phases_ms": phases,
                "certificates": {"delta": last["delta"], "delta_tilde": last["delta_tilde"]},
                "rgmres": gm, "batched": batched, "bf16_basis": bf16, "fine_variants": variants, "c1": c1,
+               "embedding_certificate": certs,
                "hbm_frac_whole_job": value / world / peak}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -51,7 +51,8 @@ typedef enum {
     RGS_ERR_NOT_CONVERGED = 5,   /* solver stopped at max_cycles above the tolerance; x is the last iterate */
     RGS_ERR_TIMEOUT = 6,         /* a device-side grid barrier gave up waiting */
     RGS_ERR_NONFINITE = 7,       /* NaN or Inf met in a sketched norm */
-    RGS_ERR_NOT_IMPLEMENTED = 8
+    RGS_ERR_NOT_IMPLEMENTED = 8,
+    RGS_ERR_CERT_FAILED = 9      /* rgs_certify_embedding: omega_bar >= 1, no embedding certificate */
 } rgs_status;
 
 typedef enum { RGS_F64 = 0, RGS_F32 = 1, RGS_BF16 = 2 } rgs_dtype;
@@ -166,6 +167,29 @@ typedef struct {
 RGS_API rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double* W, int64_t ldw,
                   void* Q, rgs_dtype qtype, int64_t ldq, double* qscale, double* R, int64_t ldr,
                   double* S, int64_t lds, int32_t flags, rgs_qr_info* info);
+
+/* ---------------------------------------------------------------- embedding certificate
+ * Sec. 3.2, Prop. cert01: an a posteriori certificate that Theta is an omega_bar-embedding for
+ * range(V) (V n x m), from the sketches V^Theta = Theta V and V^Phi = Phi V, with Phi a second
+ * sketch drawn independently of V and Theta (for instance the same kind and size, another seed):
+ *     omega_bar = max(1 - (1 - eps_star) s_min^2, (1 + eps_star) s_max^2 - 1),
+ * s the singular values of V^Theta X with V^Phi X orthonormal.  It holds with probability at
+ * least 1 - delta* when Phi is an (eps_star, delta*, 1) oblivious embedding.  Everything is
+ * FP64 on the GPU: Phi V (and Theta V when not given), the Gram matrices G_Phi and G_Theta, the
+ * Cholesky factor L of G_Phi, C = L^{-1} G_Theta L^{-T} (eigenvalues s^2), Lanczos with full
+ * (two-pass) reorthogonalisation on C until its extreme Ritz values settle (at most m steps),
+ * and multisection with Sturm counts on the Lanczos tridiagonal matrix.
+ *   V       device, n x m in vtype, ld ldv; column j multiplied by vscale[j] if vscale != NULL
+ *           (pass rgs_qr's Q' and qscale to certify the basis Q).
+ *   VTheta  NULL (Theta V is computed), or Theta V on the device, k x m FP64, ld ldvt (rgs_qr's S).
+ *   out     host double[3]: omega_bar, s_min, s_max.
+ * Requires 1 <= m <= min(1024, k of theta, k of phi), phi->n == theta->n == n.  Returns
+ * RGS_ERR_CERT_FAILED when omega_bar >= 1 (out is filled), RGS_ERR_NONFINITE when G_Phi is not
+ * numerically positive definite.  Synchronises the handle's stream; allocates workspace on the
+ * handle (about 8 (kmax + 4 m) m bytes and one chunk of FP64 columns). */
+RGS_API rgs_status rgs_certify_embedding(rgs_handle h, rgs_sketch theta, rgs_sketch phi, int64_t n, int32_t m,
+                                         const void* V, rgs_dtype vtype, int64_t ldv, const double* vscale,
+                                         const double* VTheta, int64_t ldvt, double eps_star, double* out);
 
 /* ---------------------------------------------------------------- sparse operator */
 typedef struct {

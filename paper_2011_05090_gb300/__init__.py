@@ -40,6 +40,7 @@ RGS_ERR_NOT_CONVERGED = 5
 RGS_ERR_TIMEOUT = 6
 RGS_ERR_NONFINITE = 7
 RGS_ERR_NOT_IMPLEMENTED = 8
+RGS_ERR_CERT_FAILED = 9
 
 RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
 RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
@@ -62,7 +63,7 @@ EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_set_wait_budget"
             "rgmres_set_preconditioner", "rgs_convnet_num_params", "rgs_convnet_create", "rgs_convnet_destroy",
             "rgs_convnet_get_params", "rgs_convnet_set_params", "rgs_convnet_forward", "rgs_convnet_loss_grad",
             "rgs_convnet_train_step", "rgmres_solve_batched", "rgs_get_tuning", "rgs_set_tuning",
-            "rgs_autotune_update", "rgs_autotune_batched"]
+            "rgs_autotune_update", "rgs_autotune_batched", "rgs_certify_embedding"]
 
 
 class RgsError(RuntimeError):
@@ -128,6 +129,7 @@ def load():
         "rgs_destroy": [P],
         "rgs_set_stream": [P, P],
         "rgs_set_wait_budget": [P, I64],
+        "rgs_certify_embedding": [P, P, P, I64, I32, P, ctypes.c_int, I64, P, P, I64, D, P],
         "rgs_status_string": [ctypes.c_int],
         "rgs_last_error": [P],
         "rgs_sketch_create": [P, ctypes.c_int, I64, I32, ctypes.c_uint64, ctypes.POINTER(P)],
@@ -285,6 +287,25 @@ def rgs_sketch_apply_noalloc(h, sk, X, Y):
 
 
 RGS_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def rgs_certify_embedding(h, theta, phi, V, eps_star=0.05, vscale=None, VTheta=None):
+    """Sec. 3.2's certificate omega_bar for range(V diag(vscale)) (V: n x m CUDA tensor, FP64 / FP32 /
+    BF16, column-major; VTheta: optional Theta V, k x m FP64).  Returns a dict with omega_bar,
+    s_min, s_max and certified (omega_bar < 1)."""
+    n, m = V.shape
+    pv, ldv = _colmajor(V, n, m)
+    for name, t in (("vscale", vscale), ("VTheta", VTheta)):
+        if t is not None and (t.dtype != torch.float64 or not t.is_cuda):
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+    pt, ldt = (_colmajor(VTheta, theta.k, m) if VTheta is not None else (None, theta.k))
+    out = (ctypes.c_double * 3)()
+    st = load().rgs_certify_embedding(h.ptr, theta.ptr, phi.ptr, int(n), int(m), pv, _DTYPE[V.dtype], ldv,
+                                      vscale.data_ptr() if vscale is not None else None, pt, ldt, float(eps_star),
+                                      out)
+    if st not in (RGS_OK, RGS_ERR_CERT_FAILED):
+        _check(st, h)
+    return {"omega_bar": out[0], "s_min": out[1], "s_max": out[2], "certified": st == RGS_OK}
 
 
 def rgs_qr(h, sk, W, Q, R, qscale=None, S=None, flags=0):

@@ -98,6 +98,11 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
 
 }  // namespace
 
+void rgs_sketch_columns(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const double* X, int64_t ldx,
+                        double* Y, int64_t ldy) {
+    sketch_block(ctx, sk, ncols, X, ldx, Y, ldy, false);
+}
+
 bool rgs_is_host_pointer(const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes attr;
@@ -121,6 +126,7 @@ const char* rgs_status_string(rgs_status s) {
         case RGS_ERR_TIMEOUT: return "device barrier timeout";
         case RGS_ERR_NONFINITE: return "non-finite value";
         case RGS_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case RGS_ERR_CERT_FAILED: return "no embedding certificate (omega_bar >= 1)";
     }
     return "unknown status";
 }

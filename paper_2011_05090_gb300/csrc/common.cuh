@@ -63,6 +63,8 @@ struct rgs_context {
     DevBuf scratch;        // staging for host-pointer calls
     DevBuf lsbuf;          // Householder factors and vectors of the least-squares engine
     DevBuf work;           // P = Theta W, certificates
+    DevBuf cert;           // rgs_certify_embedding: sketches, Gram matrices, Cholesky factor, Lanczos basis
+    DevBuf cert_cols;      // rgs_certify_embedding: a chunk of V's columns in FP64
     int upd_blocks_per_sm = 4;             // tuning: CTAs per SM of the update / sketch pass (<= kUpdMaxBlocksPerSm)
     int ls_blocks = 0;     // cooperative grid of the least-squares kernel (at most num_sms)
     int ls_blocks_tuned = 0;   // tuning: 0 = one CTA per SM
@@ -349,6 +351,9 @@ int rgs_update_nparts(const rgs_context* ctx, const rgs_sketch_obj* sk, int64_t 
 constexpr int kMaxGridY = 65535;
 // cudaPointerGetAttributes says host memory (or an address CUDA does not know).
 bool rgs_is_host_pointer(const void* p);
+// Y (k x ncols, ld ldy) = Theta X for FP64 device columns X (n x ncols, ld ldx), FP64 transform.
+void rgs_sketch_columns(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const double* X, int64_t ldx,
+                        double* Y, int64_t ldy);
 // Loads the no-allocation scratch array on `device` (current) and records its address.
 void rgs_noalloc_reserve(int device);
 int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L,
