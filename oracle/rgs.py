@@ -120,16 +120,30 @@ class QRResult:
     pass
 
 
-def rgs_qr(W, sketch, ls="householder", sweeps=2, storage="f64", P=None):
+def ls_householder_f32(S, p):
+    """argmin ||S y - p|| with every operation in FP32 (LAPACK sgeqrf and an FP32 triangular solve)."""
+    if S.shape[1] == 0:
+        return np.zeros(0)
+    Qh, Rh = np.linalg.qr(np.asarray(S, dtype=np.float32), mode="reduced")
+    y = scipy.linalg.solve_triangular(Rh, Qh.T @ np.asarray(p, dtype=np.float32), lower=False)
+    return np.asarray(y, dtype=np.float32).astype(np.float64)
+
+
+def rgs_qr(W, sketch, ls="householder", sweeps=2, storage="f64", P=None, fine="f64"):
     """Alg. 2 on the n x m matrix W with sketch ``sketch`` (an ``oracle.sketch.Sketch``).
 
+    fine="f32" is the unique-precision setting of Sec. 5.1 (u_fine = u_crs = FP32, with an FP32
+    basis): the sketches, the least-squares problem, r_ii, s_i and 1/r_ii in FP32 arithmetic.
     Returns an object with Q (FP64 basis), Qp (stored q'), sigma (1/r_ii), R, S,
     P, delta (Delta_m), delta_tilde (Delta~_m).
     """
     W = np.asarray(W, dtype=np.float64)
     n, m = W.shape
+    up = fine == "f32"
+    if up and storage == "f64":
+        raise ValueError("the unique-precision setting needs an FP32 or BF16 basis")
     if P is None:
-        P = sketch.apply(round_storage(W, "f64"))            # step 1, all columns
+        P = sketch.apply_f32(W) if up else sketch.apply(round_storage(W, "f64"))   # step 1, all columns
     k = P.shape[0]
     if m > k:
         raise ValueError("Alg. 2 needs m <= k")
@@ -140,7 +154,9 @@ def rgs_qr(W, sketch, ls="householder", sweeps=2, storage="f64", P=None):
     S = np.zeros((k, m))
     for i in range(m):
         p = P[:, i]
-        if ls == "householder":
+        if up:
+            x = ls_householder_f32(S[:, :i], p)              # step 2 in FP32
+        elif ls == "householder":
             x = ls_householder(S[:, :i], p)                  # step 2
         elif ls == "richardson":
             x = ls_richardson(S[:, :i], p, sweeps)
@@ -151,13 +167,23 @@ def rgs_qr(W, sketch, ls="householder", sweeps=2, storage="f64", P=None):
         else:
             qp = update_fp32(W[:, i], Qp[:, :i], x * sigma[:i])
         qp = round_storage(qp, storage)
-        sp = sketch.apply(qp)                                # step 4
-        r = np.linalg.norm(sp)                               # step 5
-        if not r > BREAKDOWN_FACTOR * U_FINE * np.linalg.norm(p):
-            raise BreakdownError(i)
-        S[:, i] = sp / r                                     # step 6
+        if up:
+            sp = sketch.apply_f32(qp)                        # step 4 in FP32
+            r = float(np.linalg.norm(sp.astype(np.float32)))  # step 5: FP32 norm
+            # the breakdown rule keeps its FP64 threshold: it detects exactly dependent columns,
+            # and numerically dependent ones continue, as in Sec. 5.1's unique-precision run
+            if not r > BREAKDOWN_FACTOR * U_FINE * float(np.linalg.norm(p.astype(np.float32))):
+                raise BreakdownError(i)
+            S[:, i] = (sp.astype(np.float32) / np.float32(r)).astype(np.float64)   # step 6
+            sigma[i] = float(np.float32(1.0) / np.float32(r))
+        else:
+            sp = sketch.apply(qp)                            # step 4
+            r = np.linalg.norm(sp)                           # step 5
+            if not r > BREAKDOWN_FACTOR * U_FINE * np.linalg.norm(p):
+                raise BreakdownError(i)
+            S[:, i] = sp / r                                 # step 6
+            sigma[i] = 1.0 / r
         Qp[:, i] = qp
-        sigma[i] = 1.0 / r
         Q[:, i] = qp * sigma[i]                              # step 7
         R[:i, i] = x
         R[i, i] = r

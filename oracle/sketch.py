@@ -30,9 +30,10 @@ def next_pow2(n):
     return s
 
 
-def fwht(x):
-    """Unnormalised Walsh-Hadamard transform along axis 0 (length must be a power of two)."""
-    y = np.array(x, dtype=np.float64, copy=True)
+def fwht(x, dtype=np.float64):
+    """Unnormalised Walsh-Hadamard transform along axis 0 (length must be a power of two), every
+    butterfly computed in ``dtype``."""
+    y = np.array(x, dtype=dtype, copy=True)
     s = y.shape[0]
     if s & (s - 1):
         raise ValueError("length must be a power of two")
@@ -80,6 +81,26 @@ class Sketch:
             Z = np.zeros((self.s, X.shape[1]))
             Z[: self.n] = self.signs[:, None] * X
             Y = fwht(Z)[self.rows] / np.sqrt(self.k)
+        return Y[:, 0] if vec else Y
+
+    def apply_f32(self, X):
+        """Theta @ X with every operation in FP32 (the unique-precision setting of Sec. 5.1): X
+        rounded to FP32, Theta's Gaussian entries rounded to FP32 and an FP32 product, or the
+        SRHT's signs, FP32 butterflies and an FP32 1/sqrt(k) scale.  Returned as FP64."""
+        X = np.asarray(X, dtype=np.float64)
+        vec = X.ndim == 1
+        if vec:
+            X = X[:, None]
+        if X.shape[0] != self.n:
+            raise ValueError("row count mismatch")
+        X32 = X.astype(np.float32)
+        if self.kind in ("gaussian", "gaussian_bf16"):
+            Y = self._theta.astype(np.float32) @ X32
+        else:
+            Z = np.zeros((self.s, X.shape[1]), dtype=np.float32)
+            Z[: self.n] = self.signs.astype(np.float32)[:, None] * X32
+            Y = fwht(Z, np.float32)[self.rows] * np.float32(1.0 / np.sqrt(self.k))
+        Y = Y.astype(np.float64)
         return Y[:, 0] if vec else Y
 
     def dense(self):
