@@ -484,6 +484,74 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
             "held_out_fields": ntest, "summary": summary, "per_field": res}
 
 
+def run_ex1(args):
+    """Sec. 5.1, Ex. 1: the f_mu functions, n = 10^6 points, m = 300 parameters, P-SRHT sketches of
+    k = 1500 and 5000 rows (10^6 is not a power of two).  RGS through rgs_qr with an FP32 basis in
+    the unique-precision setting (RGS_FP32_FINE: everything in FP32) and in the paper's mixed
+    precision (RGS_FP64_FINE: step 3 in FP32, everything else in FP64).  For i = 10, 20, ..., 300:
+    cond(Q_i) and ||W_i - Q_i R_i||_F / ||W_i||_F (Q_i, R_i the leading blocks of the final factors,
+    which RGS never changes after column i).  The C oracle's emulation of the mixed-precision run
+    (FP32 step 3 with one rounding per fused multiply-add, FP64 elsewhere) is tabulated beside it."""
+    import torch
+    import paper_2011_05090_gb300 as rgs
+    import synth
+    from paper_2011_05090_gb300 import build as libbuild
+    libbuild.build()
+    h = rgs.rgs_create()
+    n, m = 1000000, 300
+    W = synth.f_mu_matrix(n, m, device="cuda").T                      # (n, m) column-major
+    grid = list(range(10, m + 1, 10))
+
+    def curves(Qb, R, Wd):
+        G = (Qb.T @ Qb).cpu().numpy()
+        cond = []
+        for i in grid:
+            ev = np.linalg.eigvalsh(G[:i, :i])              # cond(Q_i)^2 from the Gram matrix
+            cond.append(float(np.sqrt(ev[-1] / ev[0])))
+        E = Wd - Qb @ R
+        ce = torch.cumsum((E * E).sum(dim=0), 0).cpu().numpy()
+        cw = torch.cumsum((Wd * Wd).sum(dim=0), 0).cpu().numpy()
+        err = [float(np.sqrt(ce[i - 1] / cw[i - 1])) for i in grid]
+        return cond, err
+
+    out = {"experiment": "Sec. 5.1 Ex. 1: f_mu(x) = sin(10(mu+x)) / (cos(100(mu-x)) + 1.1)",
+           "config": {"n": n, "m": m, "sketch": "P-SRHT (s = 2^20)", "basis": "f32", "i": grid}, "runs": {}}
+    for k in (1500, 5000):
+        sk = rgs.rgs_sketch_create(h, "srht", n, k, 0)
+        for name, flags in (("unique_fp32", rgs.RGS_FP32_FINE), ("mixed_fp32_fp64", rgs.RGS_FP64_FINE)):
+            Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
+            R = rgs.colmajor_empty(m, m)
+            qs = torch.empty(m, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=flags)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            cond, err = curves(Q.double() * qs[None, :], R, W)
+            out["runs"][f"k{k}_{name}"] = {"ms": 1e3 * dt, "delta": info["delta"], "cond_Q": cond, "rel_err": err}
+            del Q
+    if not args.no_cpu:
+        from oracle import c_oracle
+        c_oracle.build()
+        c_oracle.set_threads(host_cores())
+        Wh = W.cpu().numpy()
+        for k in (1500,):
+            t0 = time.perf_counter()
+            ref = c_oracle.rgs_qr(Wh, c_oracle.CSketch("srht", n, k, 0), storage="f32")
+            dt = time.perf_counter() - t0
+            Qb = torch.tensor(ref.Qp * ref.sigma[None, :], device="cuda")
+            cond, err = curves(Qb, torch.tensor(ref.R, device="cuda"), W)
+            out["runs"][f"k{k}_mixed_fp32_fp64_oracle"] = {"s": dt, "cores": host_cores(), "delta": ref.delta,
+                                                            "cond_Q": cond, "rel_err": err}
+    r = out["runs"]
+    out["checks"] = {
+        "mixed_cond_max": max(max(r["k1500_mixed_fp32_fp64"]["cond_Q"]), max(r["k5000_mixed_fp32_fp64"]["cond_Q"])),
+        "unique_cond_final_k1500": r["k1500_unique_fp32"]["cond_Q"][-1],
+        "unique_cond_final_k5000": r["k5000_unique_fp32"]["cond_Q"][-1],
+        "k5000_does_not_help_unique": r["k5000_unique_fp32"]["cond_Q"][-1] >= r["k1500_unique_fp32"]["cond_Q"][-1]}
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_case(args):
     """Small cases for ncu captures (no bench line): 'update' and 'c2' run the QR workload (below);
     'convnet' runs three training steps and one
@@ -777,8 +845,11 @@ def main():
     ap.add_argument("--c5-cycles", type=int, default=400)
     ap.add_argument("--c5-val", type=int, default=0, help="validation fields for model selection (0: none)")
     ap.add_argument("--c5-eval-every", type=int, default=1000)
+    ap.add_argument("--ex1", action="store_true", help="only the reproduction of Sec. 5.1's Ex. 1 (one JSON line)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ex1:
+        run_ex1(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.profile_case:
         run_profile_case(args)

@@ -138,7 +138,8 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  *   S      optional (NULL): k x m, lds >= k, receives S = Theta Q (FP64).
  *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings;
  *          RGS_QR_FP64_FINE (= RGS_FP64_FINE): FP64 transform sums and least squares in every
- *          storage mode; RGS_FP64_LS: FP64 least squares, double-float transform sums.
+ *          storage mode; RGS_FP64_LS: FP64 least squares, double-float transform sums;
+ *          RGS_FP32_FINE: everything in FP32 (the unique-precision comparison run of Sec. 5.1).
  *   info   optional host struct: step-8 certificates and breakdown column.
  * W, Q, R, S, qscale may be all device or all host pointers.  Returns
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
@@ -152,6 +153,9 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
                                     rotations of GMRES) in FP64 for every storage type, while the SRHT
                                     transform sums and the products with A of FP32 / BF16 bases stay in
                                     double-float (about 2^-48, finer than FP32 accumulation) */
+#define RGS_FP32_FINE 16         /* bit 4, rgs_qr only: the unique-precision setting of Sec. 5.1 (u_fine =
+                                    u_crs = FP32): FP32 transform sums, FP32 least squares and FP32
+                                    squared norms; needs an FP32 / BF16 basis and an SRHT sketch */
 #define RGS_QR_FP64_FINE RGS_FP64_FINE
 #define RGS_QR_FP64_SKETCH RGS_FP64_FINE
 typedef struct {

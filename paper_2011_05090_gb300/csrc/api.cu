@@ -70,8 +70,9 @@ void reset_ctl(rgs_context* ctx) {
 }
 
 // Y (k x ncols) = Theta X, in column batches whose partial sketches fit a fixed budget.
+// fine: transform sums 0 FP64, 1 double-float, 2 FP32 (SRHT).
 void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const double* X, int64_t ldx, double* Y,
-                  int64_t ldy, bool df = false) {
+                  int64_t ldy, int df = 0) {
     const int k = sk->k;
     const double scale = sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)k) : 1.0;
     const size_t budget = (size_t)256 << 20;
@@ -88,11 +89,11 @@ void sketch_block(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, const d
         L.w = X + (int64_t)c0 * ldx;
         L.ldw = ldx;
         L.wcols = nc;
-        L.df_sketch = df ? 1 : 0;
+        L.df_sketch = df;
         int nparts = 0;
         rgs_launch_update_sketch(ctx, sk, L, ctx->partials.as<double>(), &nparts, nullptr);
         rgs_launch_reduce_partials(ctx, ctx->partials.as<double>(), nparts, k, nc, scale, Y + (int64_t)c0 * ldy, ldy,
-                                   df && sk->kind == RGS_SKETCH_SRHT);
+                                   df != 0 && sk->kind == RGS_SKETCH_SRHT);
     }
 }
 
@@ -271,6 +272,9 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
     return guarded(h, [&] {
         RGS_REQUIRE(qtype == RGS_F64 || qtype == RGS_F32 || qtype == RGS_BF16, "unknown qtype");
         RGS_REQUIRE(n == s->n, "n differs from the sketch's n");
+        RGS_REQUIRE(!(flags & RGS_FP32_FINE) || (qtype != RGS_F64 && s->kind == RGS_SKETCH_SRHT &&
+                                                 !(flags & (RGS_FP64_FINE | RGS_FP64_LS))),
+                    "RGS_FP32_FINE needs an FP32 / BF16 basis, an SRHT sketch and no FP64 fine flag");
         RGS_REQUIRE(m >= 1 && m <= s->k, "need 1 <= m <= k (Alg. 2 assumes m <= k)");
         RGS_REQUIRE(m <= n, "need m <= n");
         RGS_REQUIRE(W && Q && R, "null W, Q or R");
@@ -357,8 +361,9 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
 
         // workspaces: Householder engine, P = Theta W, partial sketches, certificates
         LSState ls{};
+        const bool up = (flags & RGS_FP32_FINE) != 0;     // unique precision: fine arithmetic in FP32
         rgs_ls_alloc(h->lsbuf, k, m, h->num_sms, h->num_sms * kUpdMaxBlocksPerSm,
-                     qtype != RGS_F64 && !(flags & (RGS_FP64_FINE | RGS_FP64_LS)), &ls);
+                     up ? 2 : (qtype != RGS_F64 && !(flags & (RGS_FP64_FINE | RGS_FP64_LS)) ? 1 : 0), &ls);
         ls.ctl = h->ctl.as<int>();
         ls.R = dR;
         ls.ldr = dldr;
@@ -383,7 +388,8 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         // step 1: P = Theta W in one pass over W (Gaussian), or only p_1 (SRHT; the other
         // columns are sketched inside the update passes)
         timer.start(0);
-        const bool df = qtype != RGS_F64 && !(flags & RGS_FP64_FINE);     // double-float transform sums
+        // transform sums: FP32 (unique precision), double-float (FP32 / BF16 bases), else FP64
+        const int df = up ? 2 : (qtype != RGS_F64 && !(flags & RGS_FP64_FINE) ? 1 : 0);
         need_w(fused_p ? 0 : m - 1);
         sketch_block(h, s, fused_p ? 1 : m, dW, dldw, P, k, df);
         timer.stop(0);
@@ -402,7 +408,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             L.wcols = 1;
             L.coef = ls.coef;
             L.qout = static_cast<char*>(dQ) + esz * (size_t)i * dldq;
-            L.df_sketch = df ? 1 : 0;
+            L.df_sketch = df;
             L.w_next = (fused_p && i + 1 < m) ? dW + (int64_t)(i + 1) * dldw : nullptr;
             int nparts = 0;
             need_w(i + 1);
@@ -427,7 +433,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             a.s_part = h->partials.as<double>();
             a.s_nparts = nparts;
             a.s_scale = s_scale;
-            a.s_df = (df && s->kind == RGS_SKETCH_SRHT) ? 1 : 0;
+            a.s_df = (df != 0 && s->kind == RGS_SKETCH_SRHT) ? 1 : 0;
             a.solve = (i + 1 < m) ? 1 : 0;                     // step 2 of the next column
             a.xcol = i + 1;
             if (fused_p) {

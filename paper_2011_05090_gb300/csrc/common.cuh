@@ -340,7 +340,7 @@ struct UpdateLaunch {
     int w_df;               // w holds double-float pairs (float2) instead of FP64
     const double* coef;     // ncols FP64 coefficients (device)
     void* qout;             // optional stored result column (qtype)
-    int df_sketch;          // SRHT transform in double-float (FP32 pairs) instead of FP64
+    int df_sketch;          // SRHT transform sums: 0 FP64, 1 double-float (FP32 pairs), 2 FP32
     int max_parts;          // 0, or an upper bound on the partial sketches per column
     const double* w_next;   // SRHT, wcols == 1: also sketch this FP64 column (no update) into the
                             // second block of partials (step 1 of the next column in the same pass)
@@ -401,7 +401,7 @@ struct LSState {
     int64_t ldr;
     double *cs, *sn, *g, *Hr;       // Givens state of the Hessenberg problem (GMRES); Hr ld mmax
     int max_parts;
-    int fine_df;            // internal arrays hold double-float values (FP32 / BF16 bases), else FP64
+    int fine_df;            // arithmetic of the internal arrays: 0 FP64, 1 double-float (FP32 / BF16 bases), 2 FP32
     int* ctl;
 };
 struct LSStep {
@@ -425,7 +425,7 @@ struct LSStep {
     int arnoldi;            // a vanishing r_ii ends the cycle (happy breakdown) instead of failing
     double stop_tol;        // GMRES: stop the cycle when the rotated residual falls to this value
 };
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fine_df, LSState* st);
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fine_df, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a);
 int rgs_ls_max_blocks(int num_sms);

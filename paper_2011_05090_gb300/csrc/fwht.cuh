@@ -11,7 +11,7 @@ constexpr int TILE = 1024;
 constexpr int LOG_TILE = 10;
 constexpr int TILE_THREADS = 256;    // 4 consecutive rows per thread
 
-// Arithmetic of the transform for its two value types (FP64, or double-float pairs).
+// Arithmetic of the transform for its value types (FP64, double-float pairs, or FP32).
 template <typename V> struct FW;
 template <> struct FW<double> {
     __device__ static double add(double a, double b) { return a + b; }
@@ -22,6 +22,16 @@ template <> struct FW<double> {
     __device__ static double from_float(float x) { return (double)x; }
     __device__ static double to_double(double a) { return a; }
     __device__ static double zero() { return 0.0; }
+};
+template <> struct FW<float> {        // the unique-precision setting: every butterfly in FP32
+    __device__ static float add(float a, float b) { return a + b; }
+    __device__ static float sub(float a, float b) { return a - b; }
+    __device__ static float neg(float a) { return -a; }
+    __device__ static float shfl(float a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+    __device__ static float from(double x) { return __double2float_rn(x); }
+    __device__ static float from_float(float x) { return x; }
+    __device__ static double to_double(float a) { return (double)a; }
+    __device__ static float zero() { return 0.f; }
 };
 template <> struct FW<df> {
     __device__ static df add(df a, df b) { return df_add(a, b); }

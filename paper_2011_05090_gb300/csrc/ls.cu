@@ -61,6 +61,8 @@ struct FineF64 {
     __device__ static Acc acc0() { return {0.0}; }
     __device__ static void acc(Acc& s, T a, T b) { s.v = fma(a, b, s.v); }
     __device__ static T val(Acc s) { return s.v; }
+    __device__ static double round_d(double x) { return x; }            // a scalar as this arithmetic keeps it
+    __device__ static double recip_d(double y) { return 1.0 / y; }
 };
 
 __device__ __forceinline__ df df_two_sum(float a, float b) {
@@ -144,6 +146,43 @@ struct FineDF {
         s.c = __fadd_rn(s.c, __fadd_rn(t.l, e));
     }
     __device__ static T val(Acc s) { return df_fast(s.s, s.c); }
+    __device__ static double round_d(double x) { return x; }
+    __device__ static double recip_d(double y) { return 1.0 / y; }
+};
+
+// FP32 storage and arithmetic: the unique-precision setting of Sec. 5.1 (u_fine = u_crs = FP32).
+// Values live in the first four bytes of the 8-byte slots; the squared norms are FP32 sums too,
+// and r_ii, its reciprocal and ||p|| are FP32 numbers.
+struct FineF32 {
+    using T = float;
+    struct Acc {
+        float v;
+    };
+    __device__ static T zero() { return 0.f; }
+    __device__ static T one() { return 1.f; }
+    __device__ static T from_d(double x) { return __double2float_rn(x); }
+    __device__ static double to_d(T x) { return (double)x; }
+    __device__ static T add(T a, T b) { return __fadd_rn(a, b); }
+    __device__ static T sub(T a, T b) { return __fsub_rn(a, b); }
+    __device__ static T mul(T a, T b) { return __fmul_rn(a, b); }
+    __device__ static T neg(T a) { return -a; }
+    __device__ static T div(T a, T b) { return __fdiv_rn(a, b); }
+    __device__ static T sqrt_(T a) { return sqrtf(a); }
+    __device__ static bool is_zero(T a) { return a == 0.f; }
+    __device__ static bool nonneg(T a) { return a >= 0.f; }
+    __device__ static T wsum(T v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+    __device__ static T ld(const double* p) { return *reinterpret_cast<const float*>(p); }
+    __device__ static T ldg(const double* p) { return __ldcg(reinterpret_cast<const float*>(p)); }
+    __device__ static void st(double* p, T v) { *reinterpret_cast<float*>(p) = v; }
+    __device__ static Acc acc0() { return {0.f}; }
+    __device__ static void acc(Acc& s, T a, T b) { s.v = __fmaf_rn(a, b, s.v); }
+    __device__ static T val(Acc s) { return s.v; }
+    __device__ static double round_d(double x) { return (double)__double2float_rn(x); }
+    __device__ static double recip_d(double y) { return (double)__fdiv_rn(1.f, __double2float_rn(y)); }
 };
 
 // ------------------------------------------------------------------ reductions
@@ -196,6 +235,24 @@ __device__ void warp_total2(const double* blk, int off, typename A::T& t0, typen
 // written by an earlier launch, in the arithmetic of A.
 template <class A>
 __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
+    if constexpr (std::is_same<typename A::T, float>::value) {
+        // unique precision: the FP32 partials (high words of the pairs) summed in FP32
+        const df* d = reinterpret_cast<const df*>(src);
+        float t0 = 0.f, t1 = 0.f;
+        for (int bb = b0; bb < b1; bb += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                v[q] = bb + q < b1 ? (sdf ? d[(size_t)(bb + q) * k + l].h : __double2float_rn(src[(size_t)(bb + q) * k + l]))
+                                   : 0.f;
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) {
+                t0 = __fadd_rn(t0, v[q]);
+                t1 = __fadd_rn(t1, v[q + 1]);
+            }
+        }
+        return __fadd_rn(t0, t1);
+    }
     if (sdf) {
         const df* d = reinterpret_cast<const df*>(src);
         df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
@@ -303,7 +360,9 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     //      M(:, i-1) = V(:, 0:i) T(0:i, i-1).
     {
         const int warp = tid >> 5;
+        constexpr bool f32 = std::is_same<T, float>::value;   // unique precision: FP32 squared norms
         double nrm_s = 0.0, nrm_p = 0.0;               // warp 0, lane 0
+        float nrm_sf = 0.f, nrm_pf = 0.f;
         const int nseg = (k + 31) / 32;
         const int nitems = nseg * 2;
         for (int it = blockIdx.x; it < nitems; it += G) {
@@ -333,8 +392,14 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                     vd = A::to_d(v);
                     if (vec == 1 && a.p_store) a.p_store[l] = vd;
                 }
-                const double sq = warp_sum(vd * vd);
-                if (vec == 0) nrm_s += sq; else nrm_p += sq;
+                if constexpr (f32) {
+                    const float vf = l < k ? (float)vd : 0.f;
+                    const float sq = A::wsum(__fmul_rn(vf, vf));
+                    if (vec == 0) nrm_sf = __fadd_rn(nrm_sf, sq); else nrm_pf = __fadd_rn(nrm_pf, sq);
+                } else {
+                    const double sq = warp_sum(vd * vd);
+                    if (vec == 0) nrm_s += sq; else nrm_p += sq;
+                }
             }
             __syncthreads();                               // shP is reused by the next item
         }
@@ -348,7 +413,15 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 if (lane == 0) A::st(st.M + (size_t)(i - 1) * k + l, d);
             }
         }
-        if (tid == 0) { st.blk[blockIdx.x * 4 + 0] = nrm_s; st.blk[blockIdx.x * 4 + 1] = nrm_p; }
+        if (tid == 0) {
+            if constexpr (f32) {
+                A::st(st.blk + blockIdx.x * 4 + 0, nrm_sf);
+                A::st(st.blk + blockIdx.x * 4 + 1, nrm_pf);
+            } else {
+                st.blk[blockIdx.x * 4 + 0] = nrm_s;
+                st.blk[blockIdx.x * 4 + 1] = nrm_p;
+            }
+        }
     }
     if (!bar.sync(ctl)) return;
     if (trace) trace[2] = globaltimer();
@@ -361,12 +434,19 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const int warp = tid >> 5;
     if (warp == 0) {
         double tn0, tn1;
-        warp_total2<FineF64>(st.blk, 0, tn0, tn1);
+        if constexpr (std::is_same<T, float>::value) {
+            float a0, a1;
+            warp_total2<FineF32>(st.blk, 0, a0, a1);
+            tn0 = a0;
+            tn1 = a1;
+        } else {
+            warp_total2<FineF64>(st.blk, 0, tn0, tn1);
+        }
         // One instruction stream for the warp: the square root of ||s'||^2 (lanes 0, 1) and of
         // ||p||^2 (lane 2) together, then 1/r_ii (the same rounded root: sigma_i is exactly
         // 1/r_ii); lane 0 keeps r_ii and the breakdown test, lane 1 sigma_i and its A::T form.
-        const double y = sqrt(lane == 2 ? tn1 : tn0);
-        const double ir = app ? 1.0 / y : 1.0;
+        const double y = A::round_d(sqrt(lane == 2 ? tn1 : tn0));
+        const double ir = app ? A::recip_d(y) : 1.0;
         if (lane == 0) {
             const int code = !app ? 0 : (!isfinite(y) ? 1 : (!(y > 16.0 * 0x1p-53 * pref) ? 2 : 0));
             sc[0] = y;
@@ -704,7 +784,7 @@ __global__ void cert_final_kernel(const double* work, int m, double* out) {
 
 }  // namespace
 
-void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fine_df, LSState* st) {
+void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fine_df, LSState* st) {
     size_t n = 0;
     auto take = [&](size_t cnt) { size_t off = n; n += (cnt + 31) & ~(size_t)31; return off; };
     const size_t oV = take((size_t)k * mmax), oVT = take((size_t)k * mmax), oT = take((size_t)mmax * mmax),
@@ -715,7 +795,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, bool fi
                  opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
     double* b = buf.as<double>();
-    st->k = k; st->mmax = mmax; st->max_parts = max_parts; st->fine_df = fine_df ? 1 : 0;
+    st->k = k; st->mmax = mmax; st->max_parts = max_parts; st->fine_df = fine_df;
     st->V = b + oV; st->VT = b + oVT; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
     st->M = b + oM; st->u2s = b + ou2s; st->u2p = b + ou2p;
@@ -741,7 +821,8 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     void* args[] = {&s, &p};
     const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
     RGS_REQUIRE(grid <= 32 * kTotMax, "least-squares grid larger than the per-CTA totals support");
-    const void* fn = st.fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
+    const void* fn = st.fine_df == 2 ? (const void*)ls_kernel<FineF32>
+                     : st.fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
     cudaLaunchAttribute attrs[2] = {};
     attrs[0].id = cudaLaunchAttributeCooperative;
     attrs[0].val.cooperative = 1;
@@ -767,7 +848,7 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
 
 // One CTA of LT threads per SM (its registers fill the SM), so the cooperative grid is the SM count.
 int rgs_ls_max_blocks(int num_sms) {
-    for (const void* fn : {(const void*)ls_kernel<FineF64>, (const void*)ls_kernel<FineDF>}) {
+    for (const void* fn : {(const void*)ls_kernel<FineF64>, (const void*)ls_kernel<FineDF>, (const void*)ls_kernel<FineF32>}) {
         int per_sm = 0;
         RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LT, 0));
         RGS_REQUIRE(per_sm >= 1, "the least-squares kernel does not fit on an SM");

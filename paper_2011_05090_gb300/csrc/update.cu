@@ -123,11 +123,13 @@ struct UpdParams {
     const int* ctl;
 };
 
-template <typename TQ, bool SRHT, bool DF>
+// FM: arithmetic of the transform sums: 0 FP64, 1 double-float, 2 FP32 (partials written as
+// double-float pairs with a zero low word, the layout the least-squares kernel reads).
+template <typename TQ, bool SRHT, int FM>
 __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     using IO = QIO<TQ>;
     using Acc = typename IO::Acc;
-    using V = typename std::conditional<DF, df, double>::type;     // transform arithmetic
+    using V = typename std::conditional<FM == 1, df, typename std::conditional<FM == 2, float, double>::type>::type;
     using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
     V* zt = reinterpret_cast<V*>(smem);                  // TILE
@@ -251,8 +253,14 @@ __global__ void __launch_bounds__(UT, 4) update_sketch_kernel(UpdParams p) {
     }
     if (SRHT) {
         __syncthreads();
-        V* out = reinterpret_cast<V*>(p.partials) + ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
-        for (int j = threadIdx.x; j < p.k; j += UT) out[j] = part[j];
+        const int64_t o = ((int64_t)col * gridDim.x + blockIdx.x) * p.k;
+        if constexpr (FM == 2) {
+            df* out = reinterpret_cast<df*>(p.partials) + o;
+            for (int j = threadIdx.x; j < p.k; j += UT) out[j] = df{part[j], 0.f};
+        } else {
+            V* out = reinterpret_cast<V*>(p.partials) + o;
+            for (int j = threadIdx.x; j < p.k; j += UT) out[j] = part[j];
+        }
     }
 }
 
@@ -336,9 +344,9 @@ __global__ void gaussian_theta_kernel(double* theta, int k, int64_t n, uint32_t 
     if (2 * pr + 1 < k) theta[c * k + 2 * pr + 1] = rad * sn * scale;
 }
 
-template <typename TQ, bool SRHT, bool DF = false>
+template <typename TQ, bool SRHT, int FM = 0>
 void launch_update_t(rgs_context* ctx, const UpdParams& p, int gx, int gy, size_t smem) {
-    auto kern = update_sketch_kernel<TQ, SRHT, DF>;
+    auto kern = update_sketch_kernel<TQ, SRHT, FM>;
     if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchAttribute attr{};
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -418,11 +426,17 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     size_t smem = TILE * 8 + (srht ? (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 : 0) + (size_t)L.ncols * accsz + 16;
     if (L.ncols > 0 || L.qout || srht) {
         const int gy = L.w_next ? 2 : L.wcols;
-        if (srht && L.df_sketch) {
+        if (srht && L.df_sketch == 2) {
             switch (L.qtype) {
-                case RGS_F64: launch_update_t<double, true, true>(ctx, p, gx, gy, smem); break;
-                case RGS_F32: launch_update_t<float, true, true>(ctx, p, gx, gy, smem); break;
-                default: launch_update_t<__nv_bfloat16, true, true>(ctx, p, gx, gy, smem); break;
+                case RGS_F64: launch_update_t<double, true, 2>(ctx, p, gx, gy, smem); break;
+                case RGS_F32: launch_update_t<float, true, 2>(ctx, p, gx, gy, smem); break;
+                default: launch_update_t<__nv_bfloat16, true, 2>(ctx, p, gx, gy, smem); break;
+            }
+        } else if (srht && L.df_sketch) {
+            switch (L.qtype) {
+                case RGS_F64: launch_update_t<double, true, 1>(ctx, p, gx, gy, smem); break;
+                case RGS_F32: launch_update_t<float, true, 1>(ctx, p, gx, gy, smem); break;
+                default: launch_update_t<__nv_bfloat16, true, 1>(ctx, p, gx, gy, smem); break;
             }
         } else if (srht) {
             switch (L.qtype) {

@@ -384,3 +384,44 @@ def test_double_float_least_squares_on_scaled_inputs(h, scale):
           f"bit-identical R: {np.array_equal(g['R'], ref['R'] * scale)}")
     assert rel(g["R"] / scale, ref["R"]) <= 1e-12
     assert rel(Qg, Qr) <= 1e-6
+
+
+# ------------------------------------------------------------------ unique precision (Sec. 5.1)
+def test_unique_precision_within_emulated_oracle(h):
+    """RGS_FP32_FINE (FP32 transform sums and least squares, FP32 basis) against the oracle's
+    unique-precision emulation: errors within 10x of the emulation's."""
+    n, m, k = 20000, 40, 120
+    A = synth.gdw_matrix(n, m, 1e6, 3).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 8)
+    g = run_qr(h, sk, to_gpu(A), qdtype=torch.float32, qscale=True, flags=rgs.RGS_FP32_FINE)
+    Qg = g["Q"] * g["qscale"][None, :]
+    emu = orgs.rgs_qr(A, Sketch("srht", n, k, 8), storage="f32", fine="f32")
+    exact = orgs.rgs_qr(A, Sketch("srht", n, k, 8))
+    e_gpu, e_emu = rel(A, Qg @ g["R"]), rel(A, emu.Q @ emu.R)
+    r_gpu, r_emu = rel(g["R"], exact.R), rel(emu.R, exact.R)
+    print(f"unique FP32: ||A-QR||/||A|| gpu {e_gpu:.3e} emulated {e_emu:.3e}; ||R-R_fp64||/||R_fp64|| gpu "
+          f"{r_gpu:.3e} emulated {r_emu:.3e}; cond(Q) gpu {np.linalg.cond(Qg):.3f} emulated {np.linalg.cond(emu.Q):.3f}")
+    assert e_gpu <= 10 * e_emu and r_gpu <= 10 * r_emu
+    assert np.linalg.cond(Qg) <= 10 * np.linalg.cond(emu.Q)
+    with pytest.raises(rgs.RgsError):                       # FP64 basis: not the unique-precision setting
+        run_qr(h, sk, to_gpu(A), qdtype=torch.float64, flags=rgs.RGS_FP32_FINE)
+
+
+def test_unique_precision_degrades_where_mixed_precision_does_not(h):
+    """Sec. 5.1 on the f_mu functions (P-SRHT, n not a power of two): past i = 150, where W_i is
+    numerically singular, the unique-FP32 basis loses conditioning and the mixed-precision one
+    (FP32 step 3, FP64 elsewhere) stays near 1 + O(epsilon)."""
+    n, m, k = 100000, 250, 1500
+    W = synth.f_mu_matrix(n, m, device="cuda").T
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 6)
+    out = {}
+    for name, flags in (("unique", rgs.RGS_FP32_FINE), ("mixed", rgs.RGS_FP64_FINE)):
+        Q = rgs.colmajor_empty(n, m, dtype=torch.float32)
+        R = rgs.colmajor_empty(m, m)
+        qs = torch.empty(m, dtype=torch.float64, device="cuda")
+        rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=flags)
+        Qb = Q.double() * qs[None, :]
+        out[name] = [float(torch.linalg.cond(Qb[:, :i]).item()) for i in (100, 250)]
+    print(f"cond(Q_100), cond(Q_250): unique FP32 {out['unique']}, mixed precision {out['mixed']}")
+    assert abs(out["unique"][0] - out["mixed"][0]) <= 0.02 * out["mixed"][0]
+    assert out["mixed"][1] < 3.0 and out["unique"][1] > 5 * out["mixed"][1]
