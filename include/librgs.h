@@ -371,18 +371,22 @@ RGS_API rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_
  *   batch_min_team_work  rows x (k + restart) per CTA below which a batched instance gets no
  *                        further CTA for its team.
  *   ls_blocks            CTAs of the cooperative least-squares kernel (0: one per SM).
+ *   batch_rows_per_thread  rows per thread of the batched kernel (2 or 4): a tile shape, one
+ *                        compiled kernel per value.
  * rgs_autotune_update times the update pass of an n-row basis of ncols columns (s->n rows, SRHT s)
  * for upd_blocks_per_sm in 2..4 and keeps the fastest; ms (optional, 3 entries) receives the
  * mean launch times.  rgs_autotune_batched times `cycles` fixed cycles of the given batch for
- * batch_blocks_per_sm in {occupancy limit, one less} x batch_min_team_work in {2^17, 2^19, 2^21}
- * and keeps the fastest; ms (optional, 6 entries) receives the times (unused entries 0).  Both leave the choice on the handle and
+ * batch_rows_per_thread in {4, 2} x batch_blocks_per_sm in {occupancy limit, one less} x
+ * batch_min_team_work in {2^17, 2^19, 2^21} and keeps the fastest; ms (optional, 12 entries, in
+ * that nesting order) receives the times (0 for a candidate that was not run).  Both leave the choice on the handle and
  * copy it to out (optional). */
 typedef struct {
     int32_t upd_blocks_per_sm;
     int32_t batch_blocks_per_sm;
     double batch_min_team_work;
     int32_t ls_blocks;            /* CTAs of the least-squares kernel of step 2 (0: one per SM) */
-    int32_t reserved;
+    int32_t batch_rows_per_thread;  /* rows per thread (2 or 4; 0 = 4) of the batched kernel's streaming
+                                       phases and of its tensor-core sketch tile: two kernel builds */
 } rgs_tuning;
 RGS_API rgs_status rgs_get_tuning(rgs_handle h, rgs_tuning* out);
 RGS_API rgs_status rgs_set_tuning(rgs_handle h, const rgs_tuning* t);

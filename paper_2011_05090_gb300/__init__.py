@@ -106,7 +106,7 @@ class BatchOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("upd_blocks_per_sm", ctypes.c_int32), ("batch_blocks_per_sm", ctypes.c_int32),
                 ("batch_min_team_work", ctypes.c_double), ("ls_blocks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("batch_rows_per_thread", ctypes.c_int32)]
 
 
 class LearnedPrecond(ctypes.Structure):
@@ -484,7 +484,8 @@ def rgmres_solve_batched(h, csrs, bs, xs, restarts, ks, rtol=1e-8, max_cycles=10
 
 def _tuning_dict(t):
     return {"upd_blocks_per_sm": t.upd_blocks_per_sm, "batch_blocks_per_sm": t.batch_blocks_per_sm,
-            "batch_min_team_work": t.batch_min_team_work, "ls_blocks": t.ls_blocks}
+            "batch_min_team_work": t.batch_min_team_work, "ls_blocks": t.ls_blocks,
+            "batch_rows_per_thread": t.batch_rows_per_thread}
 
 
 def rgs_get_tuning(h):
@@ -493,8 +494,10 @@ def rgs_get_tuning(h):
     return _tuning_dict(t)
 
 
-def rgs_set_tuning(h, upd_blocks_per_sm, batch_blocks_per_sm, batch_min_team_work, ls_blocks=0):
-    t = Tuning(int(upd_blocks_per_sm), int(batch_blocks_per_sm), float(batch_min_team_work), int(ls_blocks), 0)
+def rgs_set_tuning(h, upd_blocks_per_sm, batch_blocks_per_sm, batch_min_team_work, ls_blocks=0,
+                   batch_rows_per_thread=0):
+    t = Tuning(int(upd_blocks_per_sm), int(batch_blocks_per_sm), float(batch_min_team_work), int(ls_blocks),
+               int(batch_rows_per_thread))
     _check(load().rgs_set_tuning(h.ptr, ctypes.byref(t)), h)
 
 
@@ -514,7 +517,7 @@ def rgs_autotune_batched(h, csrs, bs, restarts, ks, cycles=1, qdtype=torch.float
     opts = (BatchOpts * nb)(*[BatchOpts(int(restarts[i]), int(ks[i]), 1, _DTYPE[qdtype], 1e-8, 0.5, 1, 0)
                               for i in range(nb)])
     t = Tuning()
-    ms = (ctypes.c_float * 6)()
+    ms = (ctypes.c_float * 12)()
     _check(load().rgs_autotune_batched(h.ptr, nb, A, bp, opts, int(sketch_seed), int(cycles), ctypes.byref(t), ms), h)
     return {**_tuning_dict(t), "ms": list(ms)}
 

@@ -45,7 +45,7 @@ void fill_tuning(const rgs_context* h, rgs_tuning* t) {
     t->batch_blocks_per_sm = h->batch_blocks_per_sm;
     t->batch_min_team_work = h->batch_min_team_work;
     t->ls_blocks = h->ls_blocks_tuned;
-    t->reserved = 0;
+    t->batch_rows_per_thread = h->batch_rr;
 }
 
 __global__ void fill_kernel(double* q, int64_t n) {
@@ -71,7 +71,10 @@ rgs_status rgs_set_tuning(rgs_handle h, const rgs_tuning* t) {
         RGS_REQUIRE(t->batch_blocks_per_sm >= 0 && t->batch_blocks_per_sm <= 4, "batch_blocks_per_sm must be in [0, 4]");
         RGS_REQUIRE(t->batch_min_team_work > 0.0, "batch_min_team_work must be positive");
         RGS_REQUIRE(t->ls_blocks >= 0 && t->ls_blocks <= h->num_sms, "ls_blocks must be in [0, SMs]");
+        RGS_REQUIRE(t->batch_rows_per_thread == 0 || t->batch_rows_per_thread == 2 || t->batch_rows_per_thread == 4,
+                    "batch_rows_per_thread must be 0 (4), 2 or 4");
         h->ls_blocks_tuned = t->ls_blocks;
+        h->batch_rr = t->batch_rows_per_thread == 0 ? 4 : t->batch_rows_per_thread;
         h->upd_blocks_per_sm = t->upd_blocks_per_sm;
         h->batch_blocks_per_sm = t->batch_blocks_per_sm;
         h->batch_min_team_work = t->batch_min_team_work;
@@ -159,18 +162,25 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
             xp[i] = xs.as<double>() + off;
             off += (size_t)A[i].n;
         }
-        const int saved_b = h->batch_blocks_per_sm;
+        const int saved_b = h->batch_blocks_per_sm, saved_rr = h->batch_rr;
         const double saved_w = h->batch_min_team_work;
+        const int rrs[2] = {4, 2};
         const int occ = rgs_batched_max_blocks_per_sm(opts[0].qtype);
         const int bpm[2] = {occ, std::max(1, occ - 1)};
         const double tw[3] = {131072.0, 524288.0, 2097152.0};
         Events ev;
         float best = INFINITY;
-        int best_b = saved_b;
+        int best_b = saved_b, best_rr = saved_rr;
         double best_w = saved_w;
-        int c = 0;
-        for (int bi = 0; bi < (bpm[1] < bpm[0] ? 2 : 1); ++bi)
-            for (int wi = 0; wi < 3; ++wi, ++c) {
+        for (int ri = 0; ri < 2; ++ri)
+        for (int bi = 0; bi < 2; ++bi)
+            for (int wi = 0; wi < 3; ++wi) {
+                const int c = (ri * 2 + bi) * 3 + wi;
+                if (bi == 1 && !(bpm[1] < bpm[0])) {
+                    if (ms) ms[c] = 0.f;
+                    continue;
+                }
+                h->batch_rr = rrs[ri];
                 h->batch_blocks_per_sm = bpm[bi];
                 h->batch_min_team_work = tw[wi];
                 RGS_CUDA(cudaMemsetAsync(xs.ptr, 0, xs.bytes, h->stream));
@@ -179,6 +189,7 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
                 if (st != RGS_OK) {
                     h->batch_blocks_per_sm = saved_b;
                     h->batch_min_team_work = saved_w;
+                    h->batch_rr = saved_rr;
                     throw RgsError{st, "batched solve failed while tuning: " + h->last_error};
                 }
                 RGS_CUDA(cudaEventRecord(ev.b, h->stream));
@@ -190,10 +201,12 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
                     best = t;
                     best_b = bpm[bi];
                     best_w = tw[wi];
+                    best_rr = rrs[ri];
                 }
             }
         h->batch_blocks_per_sm = best_b;
         h->batch_min_team_work = best_w;
+        h->batch_rr = best_rr;
         if (out) fill_tuning(h, out);
     });
 }

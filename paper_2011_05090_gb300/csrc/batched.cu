@@ -44,7 +44,9 @@ constexpr int MB_MAX = 127;              // restart length of one instance
 constexpr int GROUPS = 4;                // row groups of the sketch accumulation
 constexpr int GL = BT / GROUPS;          // threads per group; a thread owns sketch rows tl + GL j
 constexpr int LPT = KB_MAX / GL;         // sketch rows per thread
-constexpr int RR = 4;                    // rows per thread in the streaming phases
+// RR, the rows per thread of the streaming phases (and of the tensor-core sketch's tile of grid
+// rows), is a template parameter: kernels for RR = 2 and RR = 4 are built and the autotuner
+// chooses between them.
 
 // Device-side description of one instance and its workspace.
 struct BInst {
@@ -145,15 +147,16 @@ __device__ __forceinline__ double cta_sum(double v, double* red) { return block_
 
 // Partial sketches of the CTA's rows [r0, r1).  MODE 0: vector b.  MODE 1: q'_i and
 // w = A q'_i (w stored).  MODE 2: q'_i.  Writes part[rank*2k + l] and part[rank*2k + k + l].
+template <int RR>
 struct SketchSmem {
     float2 sv0[BT], sv1[BT];                 // double-float split of the tile's vectors
     df red0[GROUPS][KB_MAX], red1[GROUPS][KB_MAX];
     __align__(16) bf16 pc[8][RR * BT + 8];   // tensor-core path: bf16 pieces of the two vectors
 };
 
-template <typename TQ, int MODE>
+template <typename TQ, int MODE, int RR>
 __device__ void sketch_phase(const BatchParams& P, const BInst& I, int i, int64_t r0, int64_t r1, int rank,
-                             SketchSmem& S) {
+                             SketchSmem<RR>& S) {
     float2* sv0 = S.sv0;
     float2* sv1 = S.sv1;
     auto& red0 = S.red0;
@@ -256,9 +259,9 @@ __device__ __forceinline__ void split3(double v, bf16& p0, bf16& p1, bf16& p2) {
 // and the B operand is a 16 x 8 block of G (grid rows x sketch rows), one 32-bit word per
 // column pair of the interleaved layout.  Products are exact; the FP32 accumulator is flushed
 // into double-float sums every 64 grid rows; the pieces are added at the end.
-template <int MODE>
+template <int MODE, int RR>
 __device__ void sketch_phase_tc(const BatchParams& P, const BInst& I, int i, int64_t r0, int64_t r1, int rank,
-                                SketchSmem& S) {
+                                SketchSmem<RR>& S) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
     const int k = I.k, ntiles = (k + 7) / 8;
     const float* qcol = static_cast<const float*>(I.Q) + (size_t)i * I.ldq;
@@ -368,11 +371,11 @@ __device__ void sketch_phase_tc(const BatchParams& P, const BInst& I, int i, int
         }
 }
 
-template <typename TQ, int MODE>
+template <typename TQ, int MODE, int RR>
 __device__ __forceinline__ void sketch_any(const BatchParams& P, const BInst& I, int i, int64_t r0, int64_t r1,
-                                           int rank, SketchSmem& S) {
-    if constexpr (sizeof(TQ) == 4) sketch_phase_tc<MODE>(P, I, i, r0, r1, rank, S);
-    else sketch_phase<TQ, MODE>(P, I, i, r0, r1, rank, S);
+                                           int rank, SketchSmem<RR>& S) {
+    if constexpr (sizeof(TQ) == 4) sketch_phase_tc<MODE, RR>(P, I, i, r0, r1, rank, S);
+    else sketch_phase<TQ, MODE, RR>(P, I, i, r0, r1, rank, S);
 }
 
 // The first CTA: sum of the team's partial vectors into dst (length len, offset off).
@@ -542,7 +545,7 @@ __device__ void hess_solve_warp(const BInst& I, int j, double* gs, double* dinv)
 
 // q'_i = sg w - Q'_{0:i} cy over rows [r0, r1): RR rows per thread, the loads of 8 columns
 // issued before their products; each row's FMA chain runs over j = 0 .. i-1 in order.
-template <typename TQ>
+template <typename TQ, int RR>
 __device__ void update_rows(TQ* Q, int64_t ldq, const double* w, double sg, const double* cy, int i, int64_t r0,
                             int64_t r1) {
     using A = TQ;
@@ -580,7 +583,7 @@ __device__ void update_rows(TQ* Q, int64_t ldq, const double* w, double sg, cons
 }
 
 // x += Q'_{0:steps} cy (FP64 sums, columns in order), RR rows per thread
-template <typename TQ>
+template <typename TQ, int RR>
 __device__ void solution_rows(const TQ* Q, int64_t ld, const double* cy, int steps, double* x, int64_t r0,
                               int64_t r1) {
     for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)BT * RR) {
@@ -616,7 +619,7 @@ __device__ void solution_rows(const TQ* Q, int64_t ld, const double* cy, int ste
 }
 
 // r = b - A x over rows [r0, r1), stored as q'_0 (TQ); returns the thread's sum of r^2
-template <typename TQ>
+template <typename TQ, int RR>
 __device__ double residual_rows(const BInst& I, TQ* Q, int64_t r0, int64_t r1) {
     double a = 0.0;
     for (int64_t base = r0 + threadIdx.x; base < r1; base += (int64_t)BT * RR) {
@@ -651,13 +654,13 @@ __device__ double residual_rows(const BInst& I, TQ* Q, int64_t r0, int64_t r1) {
     return a;
 }
 
-template <typename TQ>
+template <typename TQ, int RR>
 __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T) {
     __shared__ double red[BT / 32 + 1];
     __shared__ double ss[KB_MAX], pp[KB_MAX], h1[MB_MAX + 1], h2[MB_MAX + 1];
     __shared__ double cy[MB_MAX + 1];
     __shared__ int sh_flag[2];
-    __shared__ SketchSmem sks;
+    __shared__ SketchSmem<RR> sks;
     const int k = I.k, m = I.m, t = threadIdx.x;
     const bool leader = rank == 0;
     const int64_t chunk = ((I.n + T - 1) / T + 31) & ~(int64_t)31;
@@ -669,7 +672,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
         double a = 0.0;
         for (int64_t c = r0 + t; c < r1; c += BT) a = fma(I.b[c], I.b[c], a);
         a = cta_sum(a, red);
-        sketch_any<TQ, 0>(P, I, 0, r0, r1, rank, sks);
+        sketch_any<TQ, 0, RR>(P, I, 0, r0, r1, rank, sks);
         if (t == 0) I.part[(size_t)rank * 2 * k + k] = a;
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
         if (leader) {
@@ -693,7 +696,7 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
     }
     for (int cycle = 0;; ++cycle) {
         // R: r = b - A x, q'_0 = r, ||r||^2
-        double a = residual_rows<TQ>(I, Q, r0, r1);
+        double a = residual_rows<TQ, RR>(I, Q, r0, r1);
         a = cta_sum(a, red);
         if (t == 0) I.part[(size_t)rank * 2 * k + k] = a;
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
@@ -733,12 +736,12 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
                 const double sg = __ldcg(I.sigma + i - 1);
                 for (int j = t; j < i; j += BT) cy[j] = __ldcg(I.coef + j);
                 __syncthreads();
-                update_rows<TQ>(Q, I.ldq, I.w, sg, cy, i, r0, r1);
+                update_rows<TQ, RR>(Q, I.ldq, I.w, sg, cy, i, r0, r1);
                 if (!team_barrier(I.bar, T, rank, ctl)) return false;
             }
             // S: w = A q'_i with the sketches of q'_i and w
-            if (i < m) sketch_any<TQ, 1>(P, I, i, r0, r1, rank, sks);
-            else sketch_any<TQ, 2>(P, I, i, r0, r1, rank, sks);
+            if (i < m) sketch_any<TQ, 1, RR>(P, I, i, r0, r1, rank, sks);
+            else sketch_any<TQ, 2, RR>(P, I, i, r0, r1, rank, sks);
             if (!team_barrier(I.bar, T, rank, ctl)) return false;
             if (leader) {
                 reduce_parts(I, T, 0, k, ss);
@@ -772,19 +775,19 @@ __device__ bool solve_one(const BatchParams& P, const BInst& I, int rank, int T)
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
         for (int j = t; j < steps; j += BT) cy[j] = __ldcg(I.y + j);
         __syncthreads();
-        solution_rows<TQ>(Q, I.ldq, cy, steps, I.x, r0, r1);
+        solution_rows<TQ, RR>(Q, I.ldq, cy, steps, I.x, r0, r1);
         if (!team_barrier(I.bar, T, rank, ctl)) return false;
     }
     return true;
 }
 
-template <typename TQ>
+template <typename TQ, int RR>
 __global__ void __launch_bounds__(BT) rgmres_batched_kernel(BatchParams P) {
     const int team = P.cta_team[blockIdx.x];
     if (team < 0) return;
     const int rank = P.cta_rank[blockIdx.x], T = P.team_size[team];
     for (int li = P.team_begin[team]; li < P.team_begin[team + 1]; ++li) {
-        if (!solve_one<TQ>(P, P.inst[P.team_list[li]], rank, T)) return;
+        if (!solve_one<TQ, RR>(P, P.inst[P.team_list[li]], rank, T)) return;
     }
 }
 
@@ -829,14 +832,25 @@ rgs_status guarded(rgs_handle h, F&& f) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+using BatchedKernel = void (*)(BatchParams);
+
+// The kernel for a basis type and a rows-per-thread choice (2 or 4; anything else means 4).
+BatchedKernel batched_kernel_for(int qtype, int rr) {
+    if (qtype == RGS_F64) return rr == 2 ? rgmres_batched_kernel<double, 2> : rgmres_batched_kernel<double, 4>;
+    return rr == 2 ? rgmres_batched_kernel<float, 2> : rgmres_batched_kernel<float, 4>;
+}
+
 }  // namespace
 
 // Resident CTAs per SM of the batched kernel for a basis type (the cooperative grid's limit).
 int rgs_batched_max_blocks_per_sm(int qtype) {
-    auto kern = qtype == RGS_F64 ? rgmres_batched_kernel<double> : rgmres_batched_kernel<float>;
-    int per_sm = 0;
-    RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, 0));
-    return std::min(per_sm, 4);
+    int lim = 4;
+    for (int rr : {2, 4}) {
+        int per_sm = 0;
+        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(qtype, rr), BT, 0));
+        lim = std::min(lim, per_sm);
+    }
+    return lim;
 }
 
 extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, const double* const* b,
@@ -878,7 +892,7 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
             ctx->batch_theta_n = ncols;
         }
         // grid and teams: every CTA resident (cooperative launch)
-        auto kern = qtype == RGS_F64 ? rgmres_batched_kernel<double> : rgmres_batched_kernel<float>;
+        const BatchedKernel kern = batched_kernel_for(qtype, ctx->batch_rr);
         int per_sm = 0;
         RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, 0));
         RGS_REQUIRE(per_sm >= 1, "batched kernel does not fit on an SM");

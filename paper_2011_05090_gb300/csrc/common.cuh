@@ -77,6 +77,7 @@ struct rgs_context {
     int batch_theta_k = 0;
     int64_t batch_theta_n = 0;
     int batch_blocks_per_sm = 0;           // tuning: 0 = the occupancy limit, at most 4
+    int batch_rr = 4;                      // tuning: rows per thread of the batched kernel (2 or 4)
     double batch_min_team_work = 8192.0 * 64.0;   // tuning: rows x (k + restart) per CTA worth an extra CTA
     DevBuf batch_ws;       // per-instance workspaces of the batched solve
     DevBuf batch_desc;     // instance descriptors and team tables

@@ -41,12 +41,21 @@ def run(h, insts, restarts, ks, qdtype=torch.float64, x0=None, **kw):
     return res, [x.cpu().numpy() for x in xs]
 
 
-def test_one_cycle_matches_oracle(h):
-    # uneven sizes, restarts and sketch sizes in one launch; FP64 basis, fixed steps
+@pytest.mark.parametrize("rr", [4, 2])
+def test_one_cycle_matches_oracle(h, rr):
+    # uneven sizes, restarts and sketch sizes in one launch; FP64 basis, fixed steps; both
+    # compiled tile shapes (rows per thread)
     shapes = [(20, 30, 10.0, 0.3, 1), (33, 17, 40.0, 2.0, 2), (48, 48, 5.0, 4.0, 3), (16, 64, 80.0, 1.0, 4)]
     insts = [instance(*s) for s in shapes]
     restarts, ks = [12, 25, 30, 7], [24, 60, 61, 20]
-    res, xs = run(h, insts, restarts, ks, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    t0 = rgs.rgs_get_tuning(h)
+    rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"],
+                       t0["ls_blocks"], rr)
+    try:
+        res, xs = run(h, insts, restarts, ks, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    finally:
+        rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"],
+                           t0["ls_blocks"], t0["batch_rows_per_thread"])
     for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
         n = I["A"].shape[0]
         ref = og.rgmres(I["A"], I["b"], Sketch("gaussian_bf16", n, k, 5), restart=m, max_cycles=1, fixed_steps=True)
@@ -55,14 +64,22 @@ def test_one_cycle_matches_oracle(h):
         assert abs(r["history"][1] - ref.true_residuals[1] / ref.true_residuals[0]) <= 1e-10
 
 
-def test_one_cycle_fp32_within_emulated_oracle(h):
+@pytest.mark.parametrize("rr", [4, 2])
+def test_one_cycle_fp32_within_emulated_oracle(h, rr):
     """FP32 basis: one fixed cycle per instance against the oracle's FP32-storage emulation with
     the same bf16-rounded Gaussian sketch; the GPU's x lies within 10x of the emulation's own
-    distance from the FP64 method."""
+    distance from the FP64 method (both compiled tile shapes)."""
     shapes = [(20, 30, 10.0, 0.3, 1), (33, 17, 40.0, 2.0, 2), (48, 48, 5.0, 4.0, 3), (16, 64, 80.0, 1.0, 4)]
     insts = [instance(*s) for s in shapes]
     restarts, ks = [12, 25, 30, 7], [24, 60, 61, 20]
-    res, xs = run(h, insts, restarts, ks, qdtype=torch.float32, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    t0 = rgs.rgs_get_tuning(h)
+    rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"],
+                       t0["ls_blocks"], rr)
+    try:
+        res, xs = run(h, insts, restarts, ks, qdtype=torch.float32, max_cycles=1, fixed_steps=True, sketch_seed=5)
+    finally:
+        rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"],
+                           t0["ls_blocks"], t0["batch_rows_per_thread"])
     for I, m, k, r, x in zip(insts, restarts, ks, res, xs):
         n = I["A"].shape[0]
         skb = Sketch("gaussian_bf16", n, k, 5)

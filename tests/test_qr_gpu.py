@@ -425,3 +425,41 @@ def test_unique_precision_degrades_where_mixed_precision_does_not(h):
     print(f"cond(Q_100), cond(Q_250): unique FP32 {out['unique']}, mixed precision {out['mixed']}")
     assert abs(out["unique"][0] - out["mixed"][0]) <= 0.02 * out["mixed"][0]
     assert out["mixed"][1] < 3.0 and out["unique"][1] > 5 * out["mixed"][1]
+
+
+def test_c2_full_size_errors_vs_fp64_oracle(h):
+    """The bench's 2^20 x 500 factorization (cond 1e10, SRHT k = 2000) against the C oracle run in
+    full on the host cores: FP64 (the reference R) and its FP32-storage emulation.  The errors of
+    the FP32 basis (FP64 and double-float least squares) and of the BF16 basis are stated against
+    the FP64 oracle, and the FP32 ones must lie within 10x of the emulation's."""
+    import os
+    n, m, k = 1 << 20, 500, 2000
+    W = synth.gdw_matrix(n, m, 1e10, 0, device="cuda").T
+    Wh = W.cpu().numpy()
+    c_oracle.set_threads(len(os.sched_getaffinity(0)))
+    csk = c_oracle.CSketch("srht", n, k, 0)
+    ref = c_oracle.rgs_qr(Wh, csk)
+    emu = c_oracle.rgs_qr(Wh, csk, storage="f32")
+    nW = np.linalg.norm(Wh)
+    e_emu = np.linalg.norm(Wh - (emu.Qp * emu.sigma[None, :]) @ emu.R) / nW
+    r_emu = rel(emu.R, ref.R)
+    del emu
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 0)
+    out = {}
+    for name, qd, flags in (("f32_fp64ls", torch.float32, rgs.RGS_FP64_LS), ("f32_df", torch.float32, 0),
+                            ("bf16_fp64ls", torch.bfloat16, rgs.RGS_FP64_LS)):
+        Q = rgs.colmajor_empty(n, m, dtype=qd)
+        R = rgs.colmajor_empty(m, m)
+        qs = torch.empty(m, dtype=torch.float64, device="cuda")
+        info = rgs.rgs_qr(h, sk, W, Q, R, qscale=qs, flags=flags)
+        torch.cuda.synchronize()
+        E = W - (Q.double() * qs[None, :]) @ R
+        out[name] = (rel(R.cpu().numpy(), ref.R), (torch.linalg.norm(E) / torch.linalg.norm(W)).item(), info["delta"])
+        del Q, E
+    print(f"FP64 oracle at full size: Delta_m {ref.delta:.3e}; FP32 emulation: ||R-R_or||/||R_or|| {r_emu:.3e}, "
+          f"||W-QR||/||W|| {e_emu:.3e}")
+    for name, (r, e, d) in out.items():
+        print(f"{name}: ||R-R_or||/||R_or|| {r:.3e}  ||W-QR||/||W|| {e:.3e}  Delta_m {d:.3e}")
+    for name in ("f32_fp64ls", "f32_df"):
+        assert out[name][0] <= 10 * r_emu and out[name][1] <= 10 * e_emu
+    assert out["bf16_fp64ls"][1] <= 1e-2

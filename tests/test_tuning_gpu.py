@@ -75,6 +75,7 @@ def test_batched_autotune_then_solve(h):
     out = rgs.rgs_autotune_batched(h, csrs, bs, ms_, ks, cycles=1)
     print(out)
     assert 1 <= out["batch_blocks_per_sm"] <= 4 and out["batch_min_team_work"] in (131072.0, 524288.0, 2097152.0)
+    assert out["batch_rows_per_thread"] in (2, 4) and len(out["ms"]) == 12
     assert min(t for t in out["ms"] if t > 0) > 0
     xs = [torch.zeros(b.numel(), dtype=torch.float64, device="cuda") for b in bs]
     res = rgs.rgmres_solve_batched(h, csrs, bs, xs, ms_, ks, rtol=1e-8, max_cycles=300)
