@@ -165,15 +165,17 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
         const int saved_b = h->batch_blocks_per_sm, saved_rr = h->batch_rr;
         const double saved_w = h->batch_min_team_work;
         const int rrs[2] = {4, 2};
-        const int occ = rgs_batched_max_blocks_per_sm(opts[0].qtype);
-        const int bpm[2] = {occ, std::max(1, occ - 1)};
+
         const double tw[3] = {131072.0, 524288.0, 2097152.0};
         Events ev;
         float best = INFINITY;
         int best_b = saved_b, best_rr = saved_rr;
         double best_w = saved_w;
-        for (int ri = 0; ri < 2; ++ri)
-        for (int bi = 0; bi < 2; ++bi)
+        for (int ri = 0; ri < 2; ++ri) {
+            // each compiled tile shape at its own occupancy limit and one below
+            const int occ = rgs_batched_max_blocks_per_sm(opts[0].qtype, rrs[ri]);
+            const int bpm[2] = {occ, std::max(1, occ - 1)};
+            for (int bi = 0; bi < 2; ++bi)
             for (int wi = 0; wi < 3; ++wi) {
                 const int c = (ri * 2 + bi) * 3 + wi;
                 if (bi == 1 && !(bpm[1] < bpm[0])) {
@@ -204,6 +206,7 @@ rgs_status rgs_autotune_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, 
                     best_rr = rrs[ri];
                 }
             }
+        }
         h->batch_blocks_per_sm = best_b;
         h->batch_min_team_work = best_w;
         h->batch_rr = best_rr;

@@ -842,15 +842,12 @@ BatchedKernel batched_kernel_for(int qtype, int rr) {
 
 }  // namespace
 
-// Resident CTAs per SM of the batched kernel for a basis type (the cooperative grid's limit).
-int rgs_batched_max_blocks_per_sm(int qtype) {
-    int lim = 4;
-    for (int rr : {2, 4}) {
-        int per_sm = 0;
-        RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(qtype, rr), BT, 0));
-        lim = std::min(lim, per_sm);
-    }
-    return lim;
+// Resident CTAs per SM of the batched kernel for a basis type and rows per thread (the
+// cooperative grid's limit; at most 4).
+int rgs_batched_max_blocks_per_sm(int qtype, int rr) {
+    int per_sm = 0;
+    RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(qtype, rr), BT, 0));
+    return std::min(per_sm, 4);
 }
 
 extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const rgs_csr* A, const double* const* b,

@@ -379,7 +379,7 @@ void rgs_launch_jacobi_setup(rgs_context* ctx, const rgs_csr& A, double* dinv, d
 void rgs_convnet_apply_precond(rgs_context* ctx, void* net, const double* logkappa, const void* x, int xtype, float* z);
 int64_t rgs_convnet_grid_points(const void* net);     // H x W of the network's grid
 // batched.cu
-int rgs_batched_max_blocks_per_sm(int qtype);
+int rgs_batched_max_blocks_per_sm(int qtype, int rr);
 void rgs_launch_hess_solve(rgs_context* ctx, const double* Hr, int ldh, const double* g, const double* colscale,
                            int jmax, double* y, double* cy, int* ctl);
 int rgs_multidot_grid(const rgs_context* ctx, int64_t n);

@@ -34,11 +34,14 @@ def test_tuning_roundtrip_and_checks(h):
     t0 = rgs.rgs_get_tuning(h)
     rgs.rgs_set_tuning(h, 3, 1, 1e6)
     assert rgs.rgs_get_tuning(h) == {"upd_blocks_per_sm": 3, "batch_blocks_per_sm": 1, "batch_min_team_work": 1e6,
-                                     "ls_blocks": 0}
-    for bad in [(0, 1, 1e6), (5, 1, 1e6), (2, 5, 1e6), (2, 1, 0.0)]:
+                                     "ls_blocks": 0, "batch_rows_per_thread": 4}
+    rgs.rgs_set_tuning(h, 3, 1, 1e6, 0, 2)
+    assert rgs.rgs_get_tuning(h)["batch_rows_per_thread"] == 2
+    for bad in [(0, 1, 1e6), (5, 1, 1e6), (2, 5, 1e6), (2, 1, 0.0), (2, 1, 1e6, 0, 3)]:
         with pytest.raises(rgs.RgsError):
             rgs.rgs_set_tuning(h, *bad)
-    rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"])
+    rgs.rgs_set_tuning(h, t0["upd_blocks_per_sm"], t0["batch_blocks_per_sm"], t0["batch_min_team_work"],
+                       t0["ls_blocks"], t0["batch_rows_per_thread"])
 
 
 def test_update_autotune_keeps_the_factorization(h):
