@@ -342,6 +342,7 @@ struct UpdateLaunch {
     const double* coef;     // ncols FP64 coefficients (device)
     void* qout;             // optional stored result column (qtype)
     int df_sketch;          // SRHT transform sums: 0 FP64, 1 double-float (FP32 pairs), 2 FP32
+    int no_gauss;           // Gaussian sketch with qout: store q'_i only (sketched later with another vector)
     int max_parts;          // 0, or an upper bound on the partial sketches per column
     const double* w_next;   // SRHT, wcols == 1: also sketch this FP64 column (no update) into the
                             // second block of partials (step 1 of the next column in the same pass)
@@ -359,6 +360,10 @@ void rgs_sketch_columns(rgs_context* ctx, const rgs_sketch_obj* sk, int ncols, c
 void rgs_noalloc_reserve(int device);
 int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const UpdateLaunch& L,
                              double* partials, int* nparts, const int* ctl);
+// Gaussian sketch partials of x1 (n entries, type x1type) and of the FP64 x2 in one pass over Theta;
+// returns the partials per vector (the same count and values as two one-column launches).
+int rgs_launch_gauss_sketch2(rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, const void* x1, int x1type,
+                             const double* x2, double* part1, double* part2, const int* ctl);
 void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int nparts, int k, int ncols,
                                 double scale, double* Y, int64_t ldy, bool df = false);
 void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed);

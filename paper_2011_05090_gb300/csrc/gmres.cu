@@ -115,7 +115,8 @@ bool sketch_is_df(const rgs_arnoldi_obj* a) {
 double s_scale(const rgs_sketch_obj* sk) { return sk->kind == RGS_SKETCH_SRHT ? 1.0 / std::sqrt((double)sk->k) : 1.0; }
 
 // Steps 3-4 for column i from the input column w (FP64 or double-float) scaled by *wscale, into spart.
-int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const double* wscale = nullptr) {
+int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const double* wscale = nullptr,
+                  bool no_gauss = false) {
     UpdateLaunch L{};
     L.n = a->n;
     L.ncols = i;
@@ -130,6 +131,7 @@ int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const doub
     L.coef = a->ls.coef;
     L.qout = a->Q.as<char>() + dsize(a->qtype) * (size_t)i * a->ldq;
     L.df_sketch = sketch_is_df(a) ? 1 : 0;
+    L.no_gauss = no_gauss ? 1 : 0;
     int np = 0;
     rgs_launch_update_sketch(a->h, a->sk, L, a->spart.as<double>(), &np, a->h->ctl.as<int>());
     return np;
@@ -137,7 +139,8 @@ int launch_update(rgs_arnoldi_obj* a, int i, const void* w, int w_df, const doub
 
 // w' = A v (+ sketch of w' into ppart) for v = q'_col (or the vector v of type vtype when
 // given); returns the number of partial sketches.
-int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v = nullptr, int vtype = -1) {
+int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v = nullptr, int vtype = -1,
+                   bool sketch = true) {
     rgs_context* h = a->h;
     const void* x = v ? v : a->Q.as<char>() + dsize(a->qtype) * (size_t)col * a->ldq;
     const int xtype = v ? vtype : a->qtype;
@@ -147,6 +150,7 @@ int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v 
                                h->ctl.as<int>());
     }
     rgs_launch_spmv(h, A, nullptr, x, xtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
+    if (!sketch) return 0;
     UpdateLaunch L{};
     L.n = a->n;
     L.qtype = RGS_F64;
@@ -429,21 +433,36 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         double prev_rel = INFINITY;
         int fallback_cycle = -1;
         // w' = A M q'_i (or A q'_i once the preconditioner is off), with its sketch
-        auto product = [&](int i) -> int {
+        auto product = [&](int i, bool sketch) -> int {
             if (use_pc && learned) {
                 float* z = obj.Z.as<float>() + (size_t)i * obj.ldq;
                 rgs_convnet_apply_precond(h, h->precond_net, h->precond_field,
                                           obj.Q.as<char>() + dsize(obj.qtype) * (size_t)i * obj.ldq, obj.qtype, z);
-                return launch_product(&obj, *A, i, z, RGS_F32);
+                return launch_product(&obj, *A, i, z, RGS_F32, sketch);
             }
             if (use_pc) {
                 void* keep = obj.vdf.ptr;
                 if (vdf_pc.ptr) obj.vdf.ptr = vdf_pc.ptr;
-                const int np = launch_product(&obj, Apc, i);
+                const int np = launch_product(&obj, Apc, i, nullptr, -1, sketch);
                 obj.vdf.ptr = keep;
                 return np;
             }
-            return launch_product(&obj, *A, i);
+            return launch_product(&obj, *A, i, nullptr, -1, sketch);
+        };
+        // Gaussian sketch: Theta q'_i and Theta (A q'_i) in one pass over Theta (Sec. 2.4's single
+        // synchronisation per step; the k x n matrix is read once per step instead of twice)
+        const bool gauss2 = s->kind == RGS_SKETCH_GAUSSIAN;
+        auto step = [&](int i, const void* w, int w_df, const double* wscale, bool with_product, int& sp, int& pp) {
+            if (gauss2 && with_product) {
+                launch_update(&obj, i, w, w_df, wscale, true);
+                product(i, false);
+                const void* qi = obj.Q.as<char>() + dsize(obj.qtype) * (size_t)i * obj.ldq;
+                sp = pp = rgs_launch_gauss_sketch2(h, s, s->n, qi, obj.qtype, obj.wbuf.as<double>(),
+                                                   obj.spart.as<double>(), obj.ppart.as<double>(), h->ctl.as<int>());
+            } else {
+                sp = launch_update(&obj, i, w, w_df, wscale);
+                if (with_product) pp = product(i, true);
+            }
         };
         Scalars sc = scalars(&obj);
         h->launches = 0;
@@ -495,12 +514,11 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             prev_rel = rel;
             reset_cycle(&obj);
             // Arnoldi step 0: q'_0 from r, w'_1 = A M q'_0, column 0 appended and p_1 solved
-            int sp = launch_update(&obj, 0, sc.r, 0);
-            int pp = product(0);
+            int sp = 0, pp = 0;
+            step(0, sc.r, 0, nullptr, true, sp, pp);
             launch_ls(&obj, 0, sp, m >= 1, pp, true, stop_tol);
             for (int i = 1; i <= m; ++i) {
-                sp = launch_update(&obj, i, obj.wbuf.ptr, sketch_is_df(&obj) ? 1 : 0, obj.ls.sigma + (i - 1));
-                if (i < m) pp = product(i);
+                step(i, obj.wbuf.ptr, sketch_is_df(&obj) ? 1 : 0, obj.ls.sigma + (i - 1), i < m, sp, pp);
                 launch_ls(&obj, i, sp, i < m, pp, true, stop_tol);
             }
             rgs_launch_hess_solve(h, obj.ls.Hr, obj.mmax, obj.ls.g, obj.ls.sigma, m, y_buf(&obj), cy_buf(&obj),

@@ -307,6 +307,61 @@ __global__ void __launch_bounds__(256) gauss_sketch_kernel(const double* __restr
     }
 }
 
+// Two columns in one pass over Theta (the one-synchronisation RGS-Arnoldi of Sec. 2.4 with a
+// Gaussian sketch: Theta q'_i and Theta A q'_i are formed together, a two-column product, instead
+// of reading the k x n matrix once per vector).  Rows, blocks and the order of every sum are those
+// of gauss_sketch_kernel, so each column's partials are bit-identical to a one-column launch.
+template <typename TX>
+__global__ void __launch_bounds__(256) gauss_sketch2_kernel(const double* __restrict__ theta, int k, int64_t n,
+                                                            const TX* __restrict__ x1, const double* __restrict__ x2,
+                                                            double* __restrict__ part1, double* __restrict__ part2,
+                                                            const int* ctl) {
+    constexpr int CH = 256;
+    __shared__ double xs1[CH], xs2[CH];
+    if (ctl != nullptr && ctl[kStatusWord] != 0) return;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per;
+    const int64_t c1 = min(n, c0 + per);
+    double* o1 = part1 + (int64_t)blockIdx.x * k;
+    double* o2 = part2 + (int64_t)blockIdx.x * k;
+    for (int lb = 0; lb < k; lb += 1024) {
+        double a1[4] = {0.0, 0.0, 0.0, 0.0}, a2[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t cb = c0; cb < c1; cb += CH) {
+            const int len = (int)min((int64_t)CH, c1 - cb);
+            __syncthreads();
+            if (threadIdx.x < len) {
+                if constexpr (sizeof(TX) == 2) xs1[threadIdx.x] = (double)__bfloat162float(x1[cb + threadIdx.x]);
+                else xs1[threadIdx.x] = (double)x1[cb + threadIdx.x];
+                xs2[threadIdx.x] = x2[cb + threadIdx.x];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int l = lb + threadIdx.x + 256 * t;
+                if (l < k) {
+                    const double* th = theta + cb * k + l;
+                    double u = a1[t], v = a2[t];
+                    for (int c = 0; c < len; ++c) {
+                        const double tc = __ldg(th + (int64_t)c * k);
+                        u = fma(tc, xs1[c], u);
+                        v = fma(tc, xs2[c], v);
+                    }
+                    a1[t] = u;
+                    a2[t] = v;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int l = lb + threadIdx.x + 256 * t;
+            if (l < k) {
+                o1[l] = a1[t];
+                o2[l] = a2[t];
+            }
+        }
+    }
+}
+
 template <bool DF>
 __global__ void reduce_partials_kernel(const double* __restrict__ partials, int nparts, int k, double scale,
                                        double* __restrict__ Y, int64_t ldy) {
@@ -459,6 +514,10 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
     // Gaussian: sketch the stored column (or the input columns when nothing is stored)
     int gg = rgs_update_nparts(ctx, sk, n, L.wcols);
     if (L.max_parts > 0) gg = std::min(gg, L.max_parts);
+    if (L.qout && L.no_gauss) {
+        *nparts = 0;                 // the caller sketches q'_i later, together with another vector
+        return 0;
+    }
     if (L.qout) {
         switch (L.qtype) {
             case RGS_F64: launch_gauss_t<double>(ctx, sk->theta.as<double>(), sk->k, n, L.qout, L.ldq, 1, partials, gg, ctl); break;
@@ -469,6 +528,22 @@ int rgs_launch_update_sketch(rgs_context* ctx, const rgs_sketch_obj* sk, const U
         launch_gauss_t<double>(ctx, sk->theta.as<double>(), sk->k, n, L.w, L.ldw, L.wcols, partials, gg, ctl);
     }
     *nparts = gg;
+    return gg;
+}
+
+int rgs_launch_gauss_sketch2(rgs_context* ctx, const rgs_sketch_obj* sk, int64_t n, const void* x1, int x1type,
+                             const double* x2, double* part1, double* part2, const int* ctl) {
+    const int gg = rgs_update_nparts(ctx, sk, n, 1);
+    const double* th = sk->theta.as<double>();
+    if (x1type == RGS_F64)
+        gauss_sketch2_kernel<double><<<gg, 256, 0, ctx->stream>>>(th, sk->k, n, (const double*)x1, x2, part1, part2, ctl);
+    else if (x1type == RGS_F32)
+        gauss_sketch2_kernel<float><<<gg, 256, 0, ctx->stream>>>(th, sk->k, n, (const float*)x1, x2, part1, part2, ctl);
+    else
+        gauss_sketch2_kernel<__nv_bfloat16><<<gg, 256, 0, ctx->stream>>>(th, sk->k, n, (const __nv_bfloat16*)x1, x2,
+                                                                        part1, part2, ctl);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
     return gg;
 }
 
