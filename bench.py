@@ -792,7 +792,8 @@ def run_ours(args):
     if rank == 0:
         Rref = R.clone()
         Rd = rgs.colmajor_empty(m, m)
-        for vname, vflags in (("fp64_fine", rgs.RGS_FP64_FINE), ("double_float_fine", 0)):
+        for vname, vflags in (("fp64_fine", rgs.RGS_FP64_FINE), ("double_float_fine", 0),
+                              ("richardson_fp64ls", rgs.RGS_FP64_LS | rgs.RGS_LS_RICHARDSON)):
             rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs, flags=vflags)
             torch.cuda.synchronize()
             start.record()
@@ -804,6 +805,14 @@ def run_ours(args):
             variants[vname] = {"ms": 1e3 * td, "GB/s": total / td / 1e9, "hbm_frac": total / td / 1e9 / peaks()[0],
                                "delta": iv["delta"], "delta_tilde": iv["delta_tilde"],
                                "rel_diff_R_vs_headline": (torch.linalg.norm(Rd - Rref) / torch.linalg.norm(Rref)).item()}
+            if vflags & rgs.RGS_LS_RICHARDSON:
+                # Sec. 2.3's normal-equations alternative on this ill-conditioned matrix: its
+                # least-squares time and the factorization error it leaves
+                ti = rgs.rgs_qr(h, sk, W, Q, Rd, qscale=qs, flags=vflags | rgs.RGS_QR_TIMINGS)
+                E = W - (Q.double() * qs[None, :]) @ Rd
+                variants[vname]["ls_ms"] = ti["ls_ms"]
+                variants[vname]["rel_err_W_minus_QR"] = (torch.linalg.norm(E) / torch.linalg.norm(W)).item()
+                del E
         del Rd, Rref
 
     # the BF16-storage variant of the same factorization (FP64 least squares): time, throughput,

@@ -139,7 +139,8 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
  *   flags  RGS_QR_NO_CERTIFICATES: skip step 8; RGS_QR_TIMINGS: per-phase event timings;
  *          RGS_QR_FP64_FINE (= RGS_FP64_FINE): FP64 transform sums and least squares in every
  *          storage mode; RGS_FP64_LS: FP64 least squares, double-float transform sums;
- *          RGS_FP32_FINE: everything in FP32 (the unique-precision comparison run of Sec. 5.1).
+ *          RGS_FP32_FINE: everything in FP32 (the unique-precision comparison run of Sec. 5.1);
+ *          RGS_LS_RICHARDSON: step 2 by two Richardson sweeps on the normal equations.
  *   info   optional host struct: step-8 certificates and breakdown column.
  * W, Q, R, S, qscale may be all device or all host pointers.  Returns
  * RGS_ERR_BREAKDOWN (info->breakdown_col set) if some r_ii vanishes. */
@@ -156,6 +157,10 @@ RGS_API rgs_status rgs_sketch_apply_noalloc(rgs_handle h, rgs_sketch s, int32_t 
 #define RGS_FP32_FINE 16         /* bit 4, rgs_qr only: the unique-precision setting of Sec. 5.1 (u_fine =
                                     u_crs = FP32): FP32 transform sums, FP32 least squares and FP32
                                     squared norms; needs an FP32 / BF16 basis and an SRHT sketch */
+#define RGS_LS_RICHARDSON 32     /* bit 5, rgs_qr only: step 2 by the normal equations S^T S x = S^T p with
+                                    two Richardson sweeps from x = 0 (the alternative of Sec. 2.3) instead
+                                    of Householder; needs FP64 least squares (an FP64 basis, RGS_FP64_LS or
+                                    RGS_FP64_FINE).  Accurate only while S stays close to orthonormal. */
 #define RGS_QR_FP64_FINE RGS_FP64_FINE
 #define RGS_QR_FP64_SKETCH RGS_FP64_FINE
 typedef struct {

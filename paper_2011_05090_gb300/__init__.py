@@ -49,6 +49,7 @@ RGS_QR_TIMINGS = 2
 RGS_FP64_FINE = 4               # FP64 transform sums, products and least squares for every storage
 RGS_FP64_LS = 8                 # FP64 least squares (and Givens); double-float transform sums
 RGS_FP32_FINE = 16              # rgs_qr: unique precision, FP32 transform sums and least squares
+RGS_LS_RICHARDSON = 32          # rgs_qr: step 2 by two Richardson sweeps on the normal equations
 RGS_QR_FP64_FINE = RGS_FP64_FINE
 RGS_QR_FP64_SKETCH = RGS_FP64_FINE
 RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2

@@ -272,6 +272,8 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
     return guarded(h, [&] {
         RGS_REQUIRE(qtype == RGS_F64 || qtype == RGS_F32 || qtype == RGS_BF16, "unknown qtype");
         RGS_REQUIRE(n == s->n, "n differs from the sketch's n");
+        RGS_REQUIRE(!(flags & RGS_LS_RICHARDSON) || qtype == RGS_F64 || (flags & (RGS_FP64_LS | RGS_FP64_FINE)),
+                    "RGS_LS_RICHARDSON needs FP64 least squares (an FP64 basis, RGS_FP64_LS or RGS_FP64_FINE)");
         RGS_REQUIRE(!(flags & RGS_FP32_FINE) || (qtype != RGS_F64 && s->kind == RGS_SKETCH_SRHT &&
                                                  !(flags & (RGS_FP64_FINE | RGS_FP64_LS))),
                     "RGS_FP32_FINE needs an FP32 / BF16 basis, an SRHT sketch and no FP64 fine flag");
@@ -447,6 +449,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
                 a.p_scale = 1.0;
             }
             a.pnorm_idx = i + 1;
+            a.rich = (flags & RGS_LS_RICHARDSON) ? 1 : 0;
             a.trace = trace ? h->trace.as<unsigned long long>() + 10 * (size_t)i : nullptr;
             timer.start(2);
             rgs_launch_ls(h, ls, a);

@@ -430,6 +430,7 @@ struct LSStep {
     int givens;             // GMRES: rotate H(:, i-1) = sigma_{i-1} R(0:i+1, i) once r_ii is known
     int arnoldi;            // a vanishing r_ii ends the cycle (happy breakdown) instead of failing
     double stop_tol;        // GMRES: stop the cycle when the rotated residual falls to this value
+    int rich;               // step 2 by two Richardson sweeps on the normal equations (FP64 only)
 };
 void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fine_df, LSState* st);
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);

@@ -317,6 +317,67 @@ __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y
               : A::zero();
 }
 
+// Step 2 by the normal equations S^T S x = S^T p with two Richardson sweeps from x = 0 (the
+// alternative Sec. 2.3 names for larger S): x1 = S^T p, x2 = x1 + S^T (p - S x1), FP64.  Entered
+// after phase 1 with r_ii known; S(:, i) = s'_i / r_ii is appended here, with a row-major copy in
+// the V^T slot (unused in this mode) for the row products.  Three grid phases:
+//   1b: S(:, i) and its row copy; x1_j = S(:, j) . p for j < i and x1_i = (s' . p) / r_ii (warp per j)
+//   2:  r_l = p_l - S(l, 0:i+1) x1 (warp per row)
+//   3:  x2_j = x1_j + S(:, j) . r (warp per j), written to R(:, xcol) and the step-3 coefficients.
+__device__ __forceinline__ void richardson_phases(const LSState& st, const LSStep& a, GridBarrier& bar, int* ctl,
+                                               double inv_r, double pmul, unsigned long long* trace) {
+    const int k = st.k, mm = st.mmax, i = a.i;
+    const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31;
+    const int nthreads = G * LT, gtid = blockIdx.x * LT + tid;
+    const int gwarp = blockIdx.x + G * (tid >> 5), nwarps = nthreads >> 5;
+    const bool app = a.append != 0, sol = a.solve != 0;
+    auto coldot = [&](const double* u, const double* v) {     // sum_l u_l v_l over k rows, a warp
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int l = lane;
+        for (; l + 96 < k; l += 128) {
+            s0 = fma(__ldcg(u + l), __ldcg(v + l), s0);
+            s1 = fma(__ldcg(u + l + 32), __ldcg(v + l + 32), s1);
+            s2 = fma(__ldcg(u + l + 64), __ldcg(v + l + 64), s2);
+            s3 = fma(__ldcg(u + l + 96), __ldcg(v + l + 96), s3);
+        }
+        for (; l < k; l += 32) s0 = fma(__ldcg(u + l), __ldcg(v + l), s0);
+        return warp_sum((s0 + s1) + (s2 + s3));
+    };
+    if (app)
+        for (int l = gtid; l < k; l += nthreads) {
+            const double sl = __ldcg(st.sbuf + l) * inv_r;
+            st.S[(size_t)i * k + l] = sl;
+            st.VT[(size_t)l * mm + i] = sl;
+        }
+    if (sol)
+        for (int j = gwarp; j <= i; j += nwarps) {
+            const double d = j < i ? coldot(st.S + (size_t)j * k, st.pbuf) : coldot(st.sbuf, st.pbuf) * inv_r;
+            if (lane == 0) st.u2p[j] = d * pmul;
+        }
+    if (!bar.sync(ctl)) return;
+    if (trace) trace[3] = trace[4] = globaltimer();
+    if (!sol) {
+        if (trace) trace[5] = trace[6] = trace[7] = globaltimer();
+        return;
+    }
+    for (int l = gwarp; l < k; l += nwarps) {
+        double d, unused;
+        warp_row_dot2<FineF64>(st.VT + (size_t)l * mm, st.u2p, st.u2p, i + 1, true, false, d, unused);
+        if (lane == 0) st.yp[l] = __ldcg(st.pbuf + l) * pmul - d;
+    }
+    if (!bar.sync(ctl)) return;
+    if (trace) trace[5] = trace[6] = globaltimer();
+    for (int j = gwarp; j <= i; j += nwarps) {
+        const double d = coldot(st.S + (size_t)j * k, st.yp);
+        if (lane == 0) {
+            const double x = __ldcg(st.u2p + j) + d;
+            st.R[(size_t)a.xcol * st.ldr + j] = x;
+            st.coef[j] = x * __ldcg(st.sigma + j);
+        }
+    }
+    if (trace) trace[7] = globaltimer();
+}
+
 template <class A>
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     using T = typename A::T;
@@ -461,7 +522,9 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             sc[3] = sol ? y : 0.0;
         }
     }
-    {
+    constexpr bool f64 = std::is_same<A, FineF64>::value;
+    const bool rich = f64 && a.rich != 0;               // Richardson sweeps instead of the reflectors
+    if (!rich) {
         const int quad = warp / 4 - 1, qw = warp & 3;  // quads 0..2; warps 0..3 take no column
         const int seg = (k + 3) / 4;
         for (int base = 0; base < i; base += G * 3) {
@@ -534,6 +597,12 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     }
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
+    if constexpr (f64) {
+        if (rich) {
+            richardson_phases(st, a, bar, ctl, inv_r, pmul, trace);
+            return;
+        }
+    }
     if (!bar.sync(ctl)) return;
     if (trace) trace[3] = globaltimer();
     if (trace) trace[4] = trace[3];                  // (no separate T^T u phase: M holds V T)

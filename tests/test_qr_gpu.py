@@ -463,3 +463,41 @@ def test_c2_full_size_errors_vs_fp64_oracle(h):
     for name in ("f32_fp64ls", "f32_df"):
         assert out[name][0] <= 10 * r_emu and out[name][1] <= 10 * e_emu
     assert out["bf16_fp64ls"][1] <= 1e-2
+
+
+# ------------------------------------------------------------------ step 2 by Richardson (Sec. 2.3)
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_richardson_least_squares_matches_oracle(h, kind):
+    """RGS_LS_RICHARDSON: step 2 by two Richardson sweeps on the normal equations, FP64 basis,
+    against the oracle's ls="richardson" (the NumPy and C oracles bound the rounding-order floor)."""
+    n, m, k = 20000, 30, 120
+    A = synth.gdw_matrix(n, m, 1e2, 31).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, kind, n, k, 4)
+    g = run_qr(h, sk, to_gpu(A), qdtype=torch.float64, flags=rgs.RGS_LS_RICHARDSON)
+    ref = orgs.rgs_qr(A, Sketch(kind, n, k, 4), ls="richardson", sweeps=2)
+    refc = c_oracle.rgs_qr(A, c_oracle.CSketch(kind, n, k, 4), ls="richardson", sweeps=2)
+    hh = orgs.rgs_qr(A, Sketch(kind, n, k, 4))
+    floor = max(1e-12, 10 * rel(refc.R, ref.R))
+    print(f"{kind}: ||R-R_or||/||R_or|| {rel(g['R'], ref.R):.3e} (floor {floor:.1e}); Richardson vs Householder "
+          f"oracle {rel(ref.R, hh.R):.3e}; Delta_m gpu {g['info']['delta']:.3e} oracle {ref.delta:.3e}")
+    assert rel(g["R"], ref.R) <= floor
+    assert abs(g["info"]["delta"] - ref.delta) <= 1e-8 + 1e-6 * ref.delta
+
+
+def test_richardson_with_fp32_basis_within_emulated_oracle(h):
+    """FP32 basis with FP64 least squares by Richardson against the oracle's FP32 emulation with
+    the same solver; without FP64 least squares the flag is rejected."""
+    n, m, k = 20000, 30, 120
+    A = synth.gdw_matrix(n, m, 1e2, 32).numpy().T.copy()
+    sk = rgs.rgs_sketch_create(h, "srht", n, k, 5)
+    g = run_qr(h, sk, to_gpu(A), qdtype=torch.float32, qscale=True, flags=rgs.RGS_LS_RICHARDSON | rgs.RGS_FP64_LS)
+    Qg = g["Q"] * g["qscale"][None, :]
+    emu = orgs.rgs_qr(A, Sketch("srht", n, k, 5), ls="richardson", sweeps=2, storage="f32")
+    exact = orgs.rgs_qr(A, Sketch("srht", n, k, 5), ls="richardson", sweeps=2)
+    e_gpu, e_emu = rel(A, Qg @ g["R"]), rel(A, emu.Q @ emu.R)
+    r_gpu, r_emu = rel(g["R"], exact.R), rel(emu.R, exact.R)
+    print(f"Richardson FP32 basis: ||A-QR|| gpu {e_gpu:.3e} emulated {e_emu:.3e}; ||R-R_fp64|| gpu {r_gpu:.3e} "
+          f"emulated {r_emu:.3e}")
+    assert e_gpu <= 10 * e_emu and r_gpu <= 10 * r_emu
+    with pytest.raises(rgs.RgsError):
+        run_qr(h, sk, to_gpu(A), qdtype=torch.float32, flags=rgs.RGS_LS_RICHARDSON)
