@@ -474,7 +474,7 @@ def run_learned_c5(rgs, h, N=256, ell=16.0, nfields=40, rhs_per_field=8, cycles=
     for f in range(nfields):
         csr, lk = synth.diffusion_2d(N, 1.5, ell, 1000 + f)
         arrays, C = rgs.csr_to_device(*csr)
-        stencils[f] = learned.stencil_from_csr(*arrays, N, N)
+        stencils[f] = learned.stencil_from_csr(h, C, N, N)
         g = np.random.default_rng(f)
         for j in range(rhs_per_field):
             corr = float(g.choice([0.0, 1.0, 2.0, 4.0, 8.0])) * N / 32
@@ -620,8 +620,8 @@ def run_profile_case(args):
         g.manual_seed(0)
         x = torch.randn(B, 2, N, N, generator=g).cuda()
         csr, _ = synth.diffusion_2d(N, 1.5, 16, 0)
-        arrays, _ = rgs.csr_to_device(*csr)
-        S = learned.stencil_from_csr(*arrays, N, N).expand(B, 5, N, N).contiguous()
+        arrays, C = rgs.csr_to_device(*csr)
+        S = learned.stencil_from_csr(h, C, N, N).expand(B, 5, N, N).contiguous()
         for _ in range(3):
             rgs.rgs_convnet_train_step(h, net, x, x[:, 0].contiguous(), lr=1e-3, stencil=S)
         rgs.rgs_convnet_forward(h, net, x)

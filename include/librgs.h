@@ -272,6 +272,11 @@ typedef struct {
  * that Alg. 3 applies to each basis vector, exported for callers that form right-hand sides
  * b = A y or residuals themselves. */
 RGS_API rgs_status rgs_csr_matvec(rgs_handle h, const rgs_csr* A, const double* x, double* y);
+/* r = b - A x in FP64 (device arrays of A->n entries; r must not alias x): the restart residual of
+ * Sec. 4.2's restarted solver, exported for callers that harvest residuals.  rnorm: NULL, or a host
+ * double receiving ||r|| (then the stream is synchronised). */
+RGS_API rgs_status rgs_csr_residual(rgs_handle h, const rgs_csr* A, const double* x, const double* b, double* r,
+                                    double* rnorm);
 
 RGS_API rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const double* b, double* x,
                         const rgmres_opts* opts, rgmres_info* info);
@@ -321,6 +326,14 @@ RGS_API rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind
  * eps 1e-8) on the batch; rgs_convnet_loss_grad: loss and the FP32 gradient (host) without
  * updating.  max_batch bounds the batch of every call (it sizes the saved activations). */
 RGS_API int64_t rgs_convnet_num_params(void);
+/* The network's input for one grid (device arrays; n = H W points): out[0:n] = r / rms(r),
+ * out[n:2n] = log kappa, FP32, with rms(r) = ||r|| / sqrt(n) summed in FP64 (rms 0 gives a zero
+ * channel).  The same scaling the preconditioner applies inside flexible RGMRES. */
+RGS_API rgs_status rgs_convnet_input(rgs_handle h, int64_t n, const double* r, const double* logkappa, float* out);
+/* out (device, 5 x H x W FP32): the 5-point stencil of A (n = H W, x fastest) in the loss's layout
+ * (centre, west, east, north, south coefficients of each row; repeated entries add).  Returns
+ * RGS_ERR_INVALID_ARG if an entry lies at another offset.  Synchronises the stream. */
+RGS_API rgs_status rgs_csr_to_stencil(rgs_handle h, const rgs_csr* A, int32_t H, int32_t W, float* out);
 /* rgs_convnet_create: weights drawn U(-1/sqrt(9 c_in), 1/sqrt(9 c_in)) from Philox (key = seed,
  * counter (parameter index, 0, 0, 8)), biases 0. */
 RGS_API rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32_t max_batch, uint64_t seed,

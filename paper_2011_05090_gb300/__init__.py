@@ -65,7 +65,8 @@ EXPORTED = ["rgs_create", "rgs_destroy", "rgs_set_stream", "rgs_set_wait_budget"
             "rgmres_set_preconditioner", "rgs_convnet_num_params", "rgs_convnet_create", "rgs_convnet_destroy",
             "rgs_convnet_get_params", "rgs_convnet_set_params", "rgs_convnet_forward", "rgs_convnet_loss_grad",
             "rgs_convnet_train_step", "rgmres_solve_batched", "rgs_get_tuning", "rgs_set_tuning",
-            "rgs_autotune_update", "rgs_autotune_batched", "rgs_certify_embedding"]
+            "rgs_autotune_update", "rgs_autotune_batched", "rgs_certify_embedding", "rgs_csr_residual",
+            "rgs_convnet_input", "rgs_csr_to_stencil"]
 
 
 class RgsError(RuntimeError):
@@ -132,6 +133,9 @@ def load():
         "rgs_set_stream": [P, P],
         "rgs_set_wait_budget": [P, I64],
         "rgs_certify_embedding": [P, P, P, I64, I32, P, ctypes.c_int, I64, P, P, I64, D, P],
+        "rgs_csr_residual": [P, ctypes.POINTER(CSR), P, P, P, P],
+        "rgs_convnet_input": [P, I64, P, P, P],
+        "rgs_csr_to_stencil": [P, ctypes.POINTER(CSR), I32, I32, P],
         "rgs_status_string": [ctypes.c_int],
         "rgs_last_error": [P],
         "rgs_sketch_create": [P, ctypes.c_int, I64, I32, ctypes.c_uint64, ctypes.POINTER(P)],
@@ -448,6 +452,39 @@ def cgs2_gmres_solve(h, csr, b, x, restart, rtol=1e-8, max_cycles=100, inner_fac
     st = load().cgs2_gmres_solve(h.ptr, ctypes.byref(csr), b.data_ptr(), x.data_ptr(), ctypes.byref(opts),
                                  ctypes.byref(info))
     return _gmres_result(st, info, hist, h)
+
+
+def rgs_csr_residual(h, csr, x, b, r=None):
+    """r = b - A x (FP64 CUDA vectors); returns (r, ||r||)."""
+    if r is None:
+        r = torch.empty_like(b)
+    nrm = ctypes.c_double()
+    _check(load().rgs_csr_residual(h.ptr, ctypes.byref(csr), x.data_ptr(), b.data_ptr(), r.data_ptr(),
+                                   ctypes.byref(nrm)), h)
+    return r, nrm.value
+
+
+def rgs_convnet_input(h, r, logkappa, out=None):
+    """The network input (2, n) FP32 for one grid: r / rms(r) and log kappa (FP64 CUDA vectors)."""
+    n = r.numel()
+    if r.dtype != torch.float64 or logkappa.dtype != torch.float64 or not r.is_cuda or not logkappa.is_cuda:
+        raise ValueError("r and logkappa must be float64 CUDA tensors")
+    if logkappa.numel() != n:
+        raise ValueError("r and logkappa differ in size")
+    if out is None:
+        out = torch.empty(2, n, dtype=torch.float32, device=r.device)
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != 2 * n:
+        raise ValueError("out must be a contiguous float32 tensor of 2 n entries")
+    _check(load().rgs_convnet_input(h.ptr, n, r.contiguous().data_ptr(), logkappa.contiguous().data_ptr(),
+                                    out.data_ptr()), h)
+    return out
+
+
+def rgs_csr_to_stencil(h, csr, H, W):
+    """(5, H, W) FP32 coefficients of a 5-point operator (centre, west, east, north, south)."""
+    out = torch.empty(5, H, W, dtype=torch.float32, device="cuda")
+    _check(load().rgs_csr_to_stencil(h.ptr, ctypes.byref(csr), int(H), int(W), out.data_ptr()), h)
+    return out
 
 
 def rgs_csr_matvec(h, csr, x, y=None):

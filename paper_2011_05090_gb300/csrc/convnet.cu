@@ -614,6 +614,45 @@ void pack_training_input(rgs_convnet_obj* net, int B, const float* in) {
     net->h->launches++;
 }
 
+// out[0:n] = r / rms(r), out[n:2n] = log kappa (FP32), with rms(r) = ||r|| / sqrt(n) summed in FP64
+// by one CTA (the grids of the learned preconditioner are at most a few hundred thousand points).
+__global__ void __launch_bounds__(1024) convnet_input_kernel(int64_t n, const double* __restrict__ r,
+                                                             const double* __restrict__ lk, float* __restrict__ out) {
+    __shared__ double sh[33];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s = fma(r[i], r[i], s);
+    s = block_sum<1024>(s, sh);
+    const double rms = sqrt(s / (double)n);
+    const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        out[i] = (float)(r[i] * inv);
+        out[n + i] = (float)lk[i];
+    }
+}
+
+// out[c][row] (5 x n FP32): the coefficients of each row of a 5-point operator on an H x W grid (x
+// fastest) by offset, c = 0 centre, 1 west (-1), 2 east (+1), 3 north (-W), 4 south (+W); a thread
+// per row sums its entries per channel (repeated entries add).  An entry at another offset sets
+// *bad.
+__global__ void csr_stencil_kernel(int64_t n, int W, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ colind, const double* __restrict__ val,
+                                   float* __restrict__ out, int* bad) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = rowptr[row]; q < rowptr[row + 1]; ++q) {
+        const int64_t d = (int64_t)colind[q] - row;
+        const int ch = d == 0 ? 0 : d == -1 ? 1 : d == 1 ? 2 : d == -W ? 3 : d == W ? 4 : -1;
+        if (ch < 0) {
+            atomicExch(bad, 1);
+            continue;
+        }
+        c[ch] += val[q];
+    }
+#pragma unroll
+    for (int t = 0; t < 5; ++t) out[t * n + row] = (float)c[t];
+}
+
 template <class F>
 rgs_status guarded(rgs_handle h, F&& f) {
     try {
@@ -671,6 +710,35 @@ void rgs_convnet_apply_precond(rgs_context* ctx, void* netp, const double* logka
 extern "C" {
 
 int64_t rgs_convnet_num_params(void) { return total_params(); }
+
+rgs_status rgs_convnet_input(rgs_handle h, int64_t n, const double* r, const double* logkappa, float* out) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(n >= 1 && r && logkappa && out, "need n >= 1 and r, logkappa, out");
+        RGS_REQUIRE(!rgs_is_host_pointer(r) && !rgs_is_host_pointer(logkappa) && !rgs_is_host_pointer(out),
+                    "r, logkappa and out must be device pointers");
+        convnet_input_kernel<<<1, 1024, 0, h->stream>>>(n, r, logkappa, out);
+        RGS_CUDA(cudaGetLastError());
+    });
+}
+
+rgs_status rgs_csr_to_stencil(rgs_handle h, const rgs_csr* A, int32_t H, int32_t W, float* out) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(A && A->rowptr && A->colind && A->val && out, "null CSR array or out");
+        RGS_REQUIRE(H >= 1 && W >= 1 && A->n == (int64_t)H * W, "the operator's n differs from H x W");
+        RGS_REQUIRE(!rgs_is_host_pointer(out), "out must be a device pointer");
+        int* bad = h->ctl.as<int>() + kFlagWord;
+        RGS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+        csr_stencil_kernel<<<(unsigned)((A->n + 255) / 256), 256, 0, h->stream>>>(A->n, W, A->rowptr, A->colind, A->val,
+                                                                                 out, bad);
+        RGS_CUDA(cudaGetLastError());
+        int hb = 0;
+        RGS_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        RGS_CUDA(cudaStreamSynchronize(h->stream));
+        RGS_REQUIRE(hb == 0, "not a 5-point operator on this grid");
+    });
+}
 
 rgs_status rgs_convnet_create(rgs_handle h, int32_t height, int32_t width, int32_t max_batch, uint64_t seed,
                               rgs_convnet* out) {

@@ -697,6 +697,25 @@ rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const 
     });
 }
 
+rgs_status rgs_csr_residual(rgs_handle h, const rgs_csr* A, const double* x, const double* b, double* r,
+                            double* rnorm) {
+    if (!h) return RGS_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        RGS_REQUIRE(A != nullptr, "null CSR");
+        check_csr(A, A->n);
+        RGS_REQUIRE(A->n >= 1 && x && b && r, "need n >= 1 and x, b, r");
+        RGS_REQUIRE(r != x, "r and x must not alias");
+        const int grid = rgs_norm_grid(h, A->n);
+        h->work.ensure(sizeof(double) * ((size_t)grid + 1));
+        double* part = h->work.as<double>();
+        rgs_launch_residual(h, *A, x, b, r, part, part + grid);
+        if (rnorm) {
+            RGS_CUDA(cudaMemcpyAsync(rnorm, part + grid, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            RGS_CUDA(cudaStreamSynchronize(h->stream));
+        }
+    });
+}
+
 rgs_status rgs_csr_matvec(rgs_handle h, const rgs_csr* A, const double* x, double* y) {
     if (!h) return RGS_ERR_INVALID_ARG;
     return guarded(h, [&] {

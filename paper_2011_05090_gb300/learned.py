@@ -12,8 +12,8 @@ cycles), the range of vectors a flexible solver later applies M to.  Arnoldi bas
 of the cycles can be added as further inputs.
 
 Inputs are scaled to unit root mean square, rms(v) = ||v|| / sqrt(n), like the network's
-input inside the solver; the operators travel as 5-point stencils (centre, west, east,
-north, south coefficients of each row).
+input inside the solver (rgs_convnet_input); the operators travel as 5-point stencils (centre,
+west, east, north, south coefficients of each row; rgs_csr_to_stencil).
 
 Everything numerical runs in librgs (the solver, the products with A, the network's forward,
 backward and Adam kernels); this module only moves tensors between those calls.
@@ -25,30 +25,13 @@ import math
 import torch
 
 from . import (rgmres_set_preconditioner, rgmres_solve, rgs_arnoldi_basis, rgs_arnoldi_create, rgs_arnoldi_start,
-               rgs_arnoldi_step, rgs_convnet_train_step, rgs_csr_matvec)
+               rgs_arnoldi_step, rgs_convnet_input, rgs_convnet_train_step, rgs_csr_residual, rgs_csr_to_stencil)
 
 
-def _rms(v):
-    return torch.linalg.vector_norm(v.double()) / math.sqrt(v.numel())
-
-
-def stencil_from_csr(rowptr, colind, val, H, W):
-    """(5, H, W) FP32 coefficients of a 5-point operator on an H x W grid (x fastest) from its
-    CSR arrays (torch tensors on one device); raises if a row reaches another neighbour."""
-    n = H * W
-    if rowptr.numel() != n + 1:
-        raise ValueError(f"the operator has {rowptr.numel() - 1} rows, the grid {n} points")
-    counts = rowptr[1:].long() - rowptr[:-1].long()
-    rows = torch.repeat_interleave(torch.arange(n, device=rowptr.device), counts)
-    d = colind.long() - rows
-    chan = torch.full_like(d, -1)
-    for c, off in enumerate((0, -1, 1, -W, W)):
-        chan[d == off] = c
-    if bool((chan < 0).any()):
-        raise ValueError("not a 5-point operator on this grid")
-    S = torch.zeros(5, n, dtype=torch.float64, device=rowptr.device)
-    S.index_put_((chan, rows), val.double(), accumulate=True)
-    return S.view(5, H, W).float()
+def stencil_from_csr(h, csr, H, W):
+    """(5, H, W) FP32 coefficients of a 5-point operator on an H x W grid (x fastest) from its CSR
+    (the library's rgs_csr_to_stencil); raises if a row reaches another neighbour."""
+    return rgs_csr_to_stencil(h, csr, H, W)
 
 
 def harvest(h, sk, csr, logkappa, b, inputs, start=0, cycles=100, restart=50, qdtype=torch.float32,
@@ -59,7 +42,7 @@ def harvest(h, sk, csr, logkappa, b, inputs, start=0, cycles=100, restart=50, qd
     of an RGS-Arnoldi process started from r_j.  Stops after ``cycles`` residuals, when the
     solve reaches 1e-10, or when ``inputs`` is full.  Returns the number of rows written."""
     H, W = logkappa.shape
-    lk = logkappa.float()
+    lk = logkappa.reshape(-1).double().contiguous()
     x = torch.zeros_like(b)
     N = inputs.shape[0]
     w = start
@@ -67,19 +50,17 @@ def harvest(h, sk, csr, logkappa, b, inputs, start=0, cycles=100, restart=50, qd
     if basis_cols:
         arn = rgs_arnoldi_create(h, sk, H * W, max(basis_cols) + 1, qdtype)
 
-    def put(v):
+    def put(v, nonzero=True):
         nonlocal w
-        rr = _rms(v)
-        if w >= N or not rr > 0:
+        if w >= N or not nonzero:
             return False
-        inputs[w, 0] = (v.double() / rr).view(H, W).float()
-        inputs[w, 1] = lk
+        rgs_convnet_input(h, v, lk, inputs[w].view(2, H * W))
         w += 1
         return True
 
     for j in range(cycles):
-        r = b - rgs_csr_matvec(h, csr, x)
-        if not put(r):
+        r, rnorm = rgs_csr_residual(h, csr, x, b)
+        if not put(r, rnorm > 0):
             break
         if arn is not None:
             rgs_arnoldi_start(h, arn, r)
@@ -87,7 +68,7 @@ def harvest(h, sk, csr, logkappa, b, inputs, start=0, cycles=100, restart=50, qd
                 rgs_arnoldi_step(h, arn, csr=csr)
             Q = rgs_arnoldi_basis(arn, max(basis_cols) + 1)
             for c in basis_cols:
-                if not put(Q[:, c].contiguous()):
+                if not put(Q[:, c].double().contiguous()):
                     break
         res = rgmres_solve(h, sk, csr, b, x, restart=restart, rtol=1e-10, max_cycles=1, qdtype=qdtype)
         if res["converged"] or w >= N:

@@ -153,19 +153,3 @@ def test_residual_loss_grad_matches_finite_differences():
         f = lambda q: oc.loss(oc.stencil_apply(S, oc.forward(q, x)[0]), t)
         fd = (f(pp) - f(pm)) / (2 * eps)
         assert abs(fd - grad[i]) <= 1e-6 * max(abs(grad[i]), 1e-3 * np.abs(grad).max()), i
-
-
-def test_package_stencil_extraction_matches_the_oracle():
-    # the training pipeline's CSR -> 5-point stencil rearrangement (torch, CPU here) against the
-    # oracle's own loop over the rows
-    import torch
-    from paper_2011_05090_gb300 import learned
-    H, W = 8, 16
-    csr = synth.convdiff_csr((H, W), np.exp(rng(14).standard_normal((H, W))), np.array([2.0, -1.0]))
-    S = learned.stencil_from_csr(torch.tensor(csr[0]), torch.tensor(csr[1]), torch.tensor(csr[2]), H, W)
-    assert np.allclose(S.numpy().astype(np.float64), oc.stencil_from_csr(csr, H, W), rtol=1e-6, atol=0)
-    t = [torch.tensor(a) for a in csr]
-    with pytest.raises(ValueError):
-        learned.stencil_from_csr(*t, W, H)            # same n, transposed grid: other neighbour offsets
-    with pytest.raises(ValueError):
-        learned.stencil_from_csr(*t, H, 2 * W)        # wrong number of points

@@ -6,6 +6,7 @@ import scipy.sparse as sp
 import torch
 
 import paper_2011_05090_gb300 as rgs
+from paper_2011_05090_gb300 import learned
 import synth
 from oracle import convnet as oc
 from oracle import gmres as og
@@ -130,8 +131,8 @@ def test_residual_loss_grad_matches_oracle(h):
     for b in range(B):
         csr = synth.convdiff_csr((H, W), np.exp(np.random.default_rng(b).standard_normal((H, W))),
                                  np.array([4.0 * b, -3.0]))
-        (rp, ci, va), _ = rgs.csr_to_device(*csr)
-        Sd = learned.stencil_from_csr(rp, ci, va, H, W) / (H + 1) ** 2
+        (rp, ci, va), Cb = rgs.csr_to_device(*csr)
+        Sd = learned.stencil_from_csr(h, Cb, H, W) / (H + 1) ** 2
         assert np.allclose(Sd.cpu().numpy().astype(np.float64), oc.stencil_from_csr(csr, H, W) / (H + 1) ** 2,
                            rtol=1e-6)
         S.append(Sd)
@@ -383,7 +384,7 @@ def test_trained_network_beats_jacobi_and_none(h):
     for f in range(nfields):
         csr, lk = synth.diffusion_2d(N, 1.5, 2, 100 + f)
         (rp, ci, va), C = rgs.csr_to_device(*csr)
-        stencils[f] = learned.stencil_from_csr(rp, ci, va, N, N)
+        stencils[f] = learned.stencil_from_csr(h, C, N, N)
         g = np.random.default_rng(f)
         for j in range(per):
             corr = [0, 1, 2, 4, 8][j % 5]
@@ -410,3 +411,29 @@ def test_trained_network_beats_jacobi_and_none(h):
             steps[pc].append(res["total_steps"])
     print(steps)
     assert sum(steps["learned"]) < sum(steps["jacobi"]) < sum(steps["none"])
+
+
+def test_stencil_input_and_residual_entry_points_match_the_oracle(h):
+    """rgs_csr_to_stencil against the oracle's loop over the rows (and its rejections),
+    rgs_convnet_input against r / rms(r) in FP64, rgs_csr_residual against b - A x on the CPU."""
+    H, W = 8, 16
+    csr = synth.convdiff_csr((H, W), np.exp(np.random.default_rng(14).standard_normal((H, W))), np.array([2.0, -1.0]))
+    arrays, C = rgs.csr_to_device(*csr)
+    S = learned.stencil_from_csr(h, C, H, W)
+    assert np.allclose(S.cpu().numpy().astype(np.float64), oc.stencil_from_csr(csr, H, W), rtol=1e-6, atol=0)
+    with pytest.raises(rgs.RgsError):
+        learned.stencil_from_csr(h, C, W, H)            # same n, transposed grid: other neighbour offsets
+    with pytest.raises(rgs.RgsError):
+        learned.stencil_from_csr(h, C, H, 2 * W)        # wrong number of points
+    n = H * W
+    g = np.random.default_rng(3)
+    r, lk = g.standard_normal(n) * 7.5, g.standard_normal(n)
+    out = rgs.rgs_convnet_input(h, dev(r), dev(lk)).cpu().numpy().astype(np.float64)
+    rms = np.linalg.norm(r) / np.sqrt(n)
+    assert np.allclose(out[0], r / rms, rtol=1e-6, atol=1e-7) and np.allclose(out[1], lk, rtol=1e-6, atol=1e-7)
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    x, b = g.standard_normal(n), g.standard_normal(n)
+    res, nrm = rgs.rgs_csr_residual(h, C, dev(x), dev(b))
+    want = b - A @ x
+    assert np.allclose(res.cpu().numpy(), want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+    assert abs(nrm - np.linalg.norm(want)) <= 1e-12 * np.linalg.norm(want)
