@@ -361,8 +361,16 @@ __device__ __forceinline__ void richardson_phases(const LSState& st, const LSSte
         return;
     }
     for (int l = gwarp; l < k; l += nwarps) {
-        double d, unused;
-        warp_row_dot2<FineF64>(st.VT + (size_t)l * mm, st.u2p, st.u2p, i + 1, true, false, d, unused);
+        // the row copy's entry i was written above in this launch: L2 loads, not L1
+        const double* row = st.VT + (size_t)l * mm;
+        double s0 = 0.0, s1 = 0.0;
+        int j = lane;
+        for (; j + 32 <= i; j += 64) {
+            s0 = fma(__ldcg(row + j), __ldcg(st.u2p + j), s0);
+            s1 = fma(__ldcg(row + j + 32), __ldcg(st.u2p + j + 32), s1);
+        }
+        if (j <= i) s0 = fma(__ldcg(row + j), __ldcg(st.u2p + j), s0);
+        const double d = warp_sum(s0 + s1);
         if (lane == 0) st.yp[l] = __ldcg(st.pbuf + l) * pmul - d;
     }
     if (!bar.sync(ctl)) return;
@@ -400,6 +408,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     const int gwarp = blockIdx.x + G * (tid >> 5), nwarps = nthreads >> 5;
     const bool app = a.append != 0, sol = a.solve != 0;
     const bool p_parts = sol && a.p_vec == nullptr;
+    constexpr bool f64 = std::is_same<A, FineF64>::value;
+    const bool rich = f64 && a.rich != 0;               // Richardson sweeps instead of the reflectors
     const T zero = A::zero();
     unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
     if (trace) trace[0] = globaltimer();
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             __syncthreads();                               // shP is reused by the next item
         }
-        if (i > 0) {
+        if (i > 0 && !rich) {
             // M(:, i-1) = V(:, 0:i) T(0:i, i-1): T's column i-1 was completed by the previous
             // launch; warp per row of the row-major copy VT, lanes over the columns
             const double* tc = st.T + (size_t)(i - 1) * mm;
@@ -522,8 +532,6 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             sc[3] = sol ? y : 0.0;
         }
     }
-    constexpr bool f64 = std::is_same<A, FineF64>::value;
-    const bool rich = f64 && a.rich != 0;               // Richardson sweeps instead of the reflectors
     if (!rich) {
         const int quad = warp / 4 - 1, qw = warp & 3;  // quads 0..2; warps 0..3 take no column
         const int seg = (k + 3) / 4;
@@ -561,8 +569,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             __syncthreads();
         }
-        __syncthreads();                               // the scalars, also when no column was dotted
     }
+    __syncthreads();                                   // warp 0's scalars, also when no column was dotted
     const double r = sc[0], pn = sc[3];
     const int code = (int)sc[4];
     const double inv_r = sc[1], pmul = sc[2];
