@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <utility>
+#include <vector>
 
 using namespace rgsdev;
 
@@ -112,6 +113,71 @@ bool rgs_is_host_pointer(const void* p) {
         return true;
     }
     return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
+
+// RGS_TRACE summary of the least-squares launches in microseconds, as means over the launches of
+// each range of 50 columns: the spread of the CTAs' start times; per phase the median CTA's work
+// (from leaving the previous barrier to arriving at the next), how long after the median CTA the
+// last one arrived, and the barrier's own latency (from the last arrival to the median
+// departure); the last phase up to the last CTA's end; the launch's first start to last end.
+void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
+    const size_t stride = (size_t)grid * kLsTraceSlots;
+    std::vector<unsigned long long> t(stride * (size_t)m);
+    RGS_CUDA(cudaMemcpy(t.data(), h->trace.ptr, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    constexpr int kBucket = 50;
+    const int nbk = (m + kBucket - 1) / kBucket;
+    struct Acc {
+        double start = 0, work[4] = {0}, skew[4] = {0}, lat[4] = {0}, tail = 0, total = 0;
+        int n = 0, nq[4] = {0};
+    };
+    std::vector<Acc> acc(nbk);
+    auto median = [](std::vector<double> v) {
+        std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+        return v[v.size() / 2];
+    };
+    std::vector<double> a(grid), d(grid), prev(grid), w(grid);
+    for (int i = 0; i < m; ++i) {
+        const unsigned long long* ti = t.data() + stride * (size_t)i;
+        auto at = [&](int b, int slot) { return ti[(size_t)b * kLsTraceSlots + slot]; };
+        if (at(0, 0) == 0) continue;                               // not launched (early stop)
+        Acc& c = acc[i / kBucket];
+        ++c.n;
+        unsigned long long t0 = at(0, 0), t1 = at(0, 0), e1 = 0;
+        for (int b = 0; b < grid; ++b) {
+            t0 = std::min(t0, at(b, 0));
+            t1 = std::max(t1, at(b, 0));
+            e1 = std::max(e1, at(b, 9));
+        }
+        c.start += (double)(t1 - t0) * 1e-3;
+        for (int b = 0; b < grid; ++b) prev[b] = (double)(at(b, 0) - t0);
+        for (int q = 0; q < 4; ++q) {
+            if (at(0, 1 + 2 * q) == 0) break;                      // this launch had fewer barriers
+            for (int b = 0; b < grid; ++b) {
+                a[b] = (double)(at(b, 1 + 2 * q) - t0);
+                d[b] = (double)(at(b, 2 + 2 * q) - t0);
+                w[b] = a[b] - prev[b];
+            }
+            const double amax = *std::max_element(a.begin(), a.end());
+            c.work[q] += median(w) * 1e-3;
+            c.skew[q] += (amax - median(a)) * 1e-3;
+            c.lat[q] += (median(d) - amax) * 1e-3;
+            ++c.nq[q];
+            prev = d;
+        }
+        c.tail += ((double)(e1 - t0) - median(prev)) * 1e-3;
+        c.total += (double)(e1 - t0) * 1e-3;
+    }
+    for (int bk = 0; bk < nbk; ++bk) {
+        const Acc& c = acc[bk];
+        if (c.n == 0) continue;
+        std::fprintf(stderr, "[rgs trace] least squares, columns [%d,%d), %d CTAs (us): start spread %.2f",
+                     bk * kBucket, std::min(m, (bk + 1) * kBucket), grid, c.start / c.n);
+        for (int q = 0; q < 4; ++q)
+            if (c.nq[q] > 0)
+                std::fprintf(stderr, "; phase %d work %.2f, last arrival +%.2f, barrier %.2f", q, c.work[q] / c.nq[q],
+                             c.skew[q] / c.nq[q], c.lat[q] / c.nq[q]);
+        std::fprintf(stderr, "; last phase %.2f; launch %.2f\n", c.tail / c.n, c.total / c.n);
+    }
 }
 
 extern "C" {
@@ -381,7 +447,12 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
         PhaseTimer timer(h, (flags & RGS_QR_TIMINGS) != 0);
         // RGS_TRACE=1 in the environment: per-phase device timestamps of the least-squares kernel
         const bool trace = std::getenv("RGS_TRACE") != nullptr;
-        if (trace) h->trace.ensure(sizeof(unsigned long long) * 10 * (size_t)m);
+        const int ls_grid = rgs_ls_grid(h);
+        const size_t tstride = (size_t)ls_grid * kLsTraceSlots;
+        if (trace) {
+            h->trace.ensure(sizeof(unsigned long long) * tstride * (size_t)m);
+            RGS_CUDA(cudaMemsetAsync(h->trace.ptr, 0, sizeof(unsigned long long) * tstride * (size_t)m, st));
+        }
         h->launches = 0;
         reset_ctl(h);
         rgs_ls_reset(h, ls);
@@ -450,7 +521,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
             }
             a.pnorm_idx = i + 1;
             a.rich = (flags & RGS_LS_RICHARDSON) ? 1 : 0;
-            a.trace = trace ? h->trace.as<unsigned long long>() + 10 * (size_t)i : nullptr;
+            a.trace = trace ? h->trace.as<unsigned long long>() + tstride * (size_t)i : nullptr;
             timer.start(2);
             rgs_launch_ls(h, ls, a);
             timer.stop(2);
@@ -498,16 +569,7 @@ rgs_status rgs_qr(rgs_handle h, rgs_sketch s, int64_t n, int32_t m, const double
                 info->ls_ms = timer.total_ms(2);
             }
         }
-        if (trace) {
-            std::vector<unsigned long long> t(10 * (size_t)m);
-            RGS_CUDA(cudaMemcpy(t.data(), h->trace.ptr, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-            double ph[7] = {0};
-            for (int i = 0; i < m; ++i)
-                for (int p = 0; p < 7; ++p) ph[p] += (double)(t[10 * (size_t)i + p + 1] - t[10 * (size_t)i + p]) * 1e-3;
-            std::fprintf(stderr, "[rgs trace] least-squares phase means (us):");
-            for (int p = 0; p < 7; ++p) std::fprintf(stderr, " %.2f", ph[p] / m);
-            std::fprintf(stderr, "\n");
-        }
+        if (trace) rgs_print_ls_trace(h, m, ls_grid);
         if (ctl[0] != 0)
             throw RgsError{(rgs_status)ctl[0], std::string("device status ") + rgs_status_string((rgs_status)ctl[0]) +
                                                    " at column " + std::to_string(ctl[1])};

@@ -263,6 +263,12 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
     return v;
 }
 
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Grid-wide barrier for a cooperative launch on one word (the control word kBarCount, zero in
 // its low 31 bits between barriers).  Every CTA arrives with a release reduction, whose reply
 // nobody waits for: CTA 0 adds 2^31 - (G-1), the others 1, so the sum over one barrier is
@@ -282,10 +288,12 @@ struct GridBarrier {
             budget = wait_budget(ctl);
         }
     }
-    __device__ bool sync(int* ctl) {
+    // ts (thread 0, optional): ts[0] = arrival of the whole CTA, ts[1] = departure (ns)
+    __device__ bool sync(int* ctl, unsigned long long* ts = nullptr) {
         __shared__ int ok_sh;
         __syncthreads();                   // the CTA's writes are ordered before thread 0's release
         if (threadIdx.x == 0) {
+            if (ts) ts[0] = globaltimer();
             int ok = 1;
             red_add_release(word, blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u);
             const long long start = clock64();
@@ -303,6 +311,7 @@ struct GridBarrier {
                 }
             }
             expect ^= 0x80000000u;
+            if (ts) ts[1] = globaltimer();
             ok_sh = ok;
         }
         __syncthreads();
@@ -317,12 +326,6 @@ struct GridBarrier {
 // issued it (its CTAs then wait in their own pdl_wait()).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 }  // namespace rgsdev
 
@@ -426,7 +429,7 @@ struct LSStep {
     int p_lag;              // divide p by the r_ii of the appended column (Arnoldi lag)
     int s_df, p_df;         // partial sketches stored as double-float pairs (float2) instead of FP64
     int pnorm_idx;          // where to record ||p||
-    unsigned long long* trace;  // optional: 8 timestamps (ns) at the phase boundaries, written by CTA 0
+    unsigned long long* trace;  // optional: kLsTraceSlots timestamps (ns) per CTA, CTA b at trace + b * kLsTraceSlots
     int givens;             // GMRES: rotate H(:, i-1) = sigma_{i-1} R(0:i+1, i) once r_ii is known
     int arnoldi;            // a vanishing r_ii ends the cycle (happy breakdown) instead of failing
     double stop_tol;        // GMRES: stop the cycle when the rotated residual falls to this value
@@ -436,5 +439,10 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fin
 void rgs_ls_reset(rgs_context* ctx, const LSState& st);
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a);
 int rgs_ls_max_blocks(int num_sms);
+int rgs_ls_grid(const rgs_context* ctx);
+// RGS_TRACE: summary of the least-squares timestamps of launches 0..m-1 on stderr
+void rgs_print_ls_trace(rgs_context* h, int m, int grid);
+// least-squares trace per CTA: start, (arrival, departure) at each of up to four grid barriers, end
+constexpr int kLsTraceSlots = 10;
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
                              const double* P, double* out2 /* device: delta, delta_tilde */, double* work);

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 #include <vector>
 
@@ -42,6 +43,8 @@ struct rgs_arnoldi_obj {
     DevBuf work;             // r (n), norm partials, scalars
     DevBuf jac;              // Jacobi: diag(A)^{-1} (n) and the values of A D^{-1} (nnz)
     DevBuf Z;                // flexible preconditioning: z'_i = M(q'_i), n x mmax FP32
+    unsigned long long* trace = nullptr;   // RGS_TRACE: least-squares timestamps of step i at
+    size_t tstride = 0;                    // trace + i * tstride (the latest cycle's steps)
 };
 
 namespace {
@@ -191,6 +194,7 @@ void launch_ls(rgs_arnoldi_obj* a, int i, int sparts, bool solve, int pparts, bo
     s.givens = gmres ? 1 : 0;
     s.arnoldi = 1;
     s.stop_tol = stop_tol;
+    s.trace = a->trace ? a->trace + a->tstride * (size_t)i : nullptr;
     rgs_launch_ls(a->h, a->ls, s);
 }
 
@@ -465,6 +469,14 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             }
         };
         Scalars sc = scalars(&obj);
+        const bool trace = std::getenv("RGS_TRACE") != nullptr;
+        if (trace) {
+            obj.tstride = (size_t)rgs_ls_grid(h) * kLsTraceSlots;
+            h->trace.ensure(sizeof(unsigned long long) * obj.tstride * (size_t)(m + 1));
+            RGS_CUDA(cudaMemsetAsync(h->trace.ptr, 0, sizeof(unsigned long long) * obj.tstride * (size_t)(m + 1),
+                                     h->stream));
+            obj.trace = h->trace.as<unsigned long long>();
+        }
         h->launches = 0;
         RGS_CUDA(cudaMemsetAsync(h->ctl.ptr, 0, kCtlWords * sizeof(int), h->stream));
         // ||b|| and ||Theta b|| (the inner stopping test compares the sketched residual with the latter)
@@ -530,6 +542,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
                                       use_pc ? dinv : nullptr);
             ++cycles;
         }
+        if (trace) rgs_print_ls_trace(h, m + 1, rgs_ls_grid(h));
         if (info) {
             info->cycles = cycles;
             info->total_steps = total;

@@ -11,6 +11,13 @@
 //   M(:, i) = V T(:, i) (formed at the start of the next launch).
 // One cooperative launch per column; phases are separated by bounded grid barriers.
 //
+// Loads.  Vectors that every warp of the grid reads (T's new column, s', p, u, y, z) go through
+// L1: a grid barrier ends with a GPU-scope acquire, after which ordinary loads see every write
+// made before it, and none of these vectors is read, rewritten and read again within a launch.
+// Through L2 alone (ld.cg) all 2432 warps fetch the same few lines from one L2 slice, which
+// measured as most of each phase.  The per-CTA totals blk are the exception: rows written in
+// one phase share lines with rows read in an earlier one, so they are read with ld.cg.
+//
 // Fine-precision arithmetic (u_fine).  GB300 runs FP64 at 2 operations per clock per SM, with
 // about 65 cycles between dependent FP64 operations, against 128 FP32 operations per clock and
 // about 5 cycles.  The kernel is therefore written once over an arithmetic type A:
@@ -56,7 +63,7 @@ struct FineF64 {
     __device__ static bool nonneg(T a) { return a >= 0.0; }
     __device__ static T wsum(T v) { return warp_sum(v); }
     __device__ static T ld(const double* p) { return *p; }
-    __device__ static T ldg(const double* p) { return __ldcg(p); }     // written earlier in this launch
+    __device__ static T ldcg(const double* p) { return __ldcg(p); }
     __device__ static void st(double* p, T v) { *p = v; }
     __device__ static Acc acc0() { return {0.0}; }
     __device__ static void acc(Acc& s, T a, T b) { s.v = fma(a, b, s.v); }
@@ -130,7 +137,7 @@ struct FineDF {
         const float2 v = *reinterpret_cast<const float2*>(p);
         return {v.x, v.y};
     }
-    __device__ static T ldg(const double* p) {
+    __device__ static T ldcg(const double* p) {
         const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
         return {v.x, v.y};
     }
@@ -176,7 +183,7 @@ struct FineF32 {
         return v;
     }
     __device__ static T ld(const double* p) { return *reinterpret_cast<const float*>(p); }
-    __device__ static T ldg(const double* p) { return __ldcg(reinterpret_cast<const float*>(p)); }
+    __device__ static T ldcg(const double* p) { return __ldcg(reinterpret_cast<const float*>(p)); }
     __device__ static void st(double* p, T v) { *reinterpret_cast<float*>(p) = v; }
     __device__ static Acc acc0() { return {0.f}; }
     __device__ static void acc(Acc& s, T a, T b) { s.v = __fmaf_rn(a, b, s.v); }
@@ -220,8 +227,8 @@ __device__ void warp_total2(const double* blk, int off, typename A::T& t0, typen
 #pragma unroll
     for (int q = 0; q < kTotMax; ++q) {
         const int b = lane + 32 * q;
-        a0[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off) : A::zero();
-        a1[q] = b < G ? A::ldg(blk + (size_t)b * 4 + off + 1) : A::zero();
+        a0[q] = b < G ? A::ldcg(blk + (size_t)b * 4 + off) : A::zero();
+        a1[q] = b < G ? A::ldcg(blk + (size_t)b * 4 + off + 1) : A::zero();
     }
     T v0 = A::zero(), v1 = A::zero();
 #pragma unroll
@@ -285,8 +292,7 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     return A::from_d((v0 + v1) + (v2 + v3));
 }
 
-// Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2 (written earlier
-// in this launch), a warp with lanes over the entries: the lane partials summed over the warp,
+// Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2, a warp with lanes over the entries: the lane partials summed over the warp,
 // valid in every lane; use1 / use2 select the vectors needed.
 template <class A>
 __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y1, const double* y2, int jend,
@@ -302,8 +308,8 @@ __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y
             const int j = j0 + 32 * q + lane;
             const bool ok = j < jend;
             v[q] = ok ? A::ld(row + j) : A::zero();
-            w1[q] = (ok && use1) ? A::ldg(y1 + j) : A::zero();
-            w2[q] = (ok && use2) ? A::ldg(y2 + j) : A::zero();
+            w1[q] = (ok && use1) ? A::ld(y1 + j) : A::zero();
+            w2[q] = (ok && use2) ? A::ld(y2 + j) : A::zero();
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -325,7 +331,7 @@ __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y
 //   2:  r_l = p_l - S(l, 0:i+1) x1 (warp per row)
 //   3:  x2_j = x1_j + S(:, j) . r (warp per j), written to R(:, xcol) and the step-3 coefficients.
 __device__ __forceinline__ void richardson_phases(const LSState& st, const LSStep& a, GridBarrier& bar, int* ctl,
-                                               double inv_r, double pmul, unsigned long long* trace) {
+                                               double inv_r, double pmul, unsigned long long* tr) {
     const int k = st.k, mm = st.mmax, i = a.i;
     const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31;
     const int nthreads = G * LT, gtid = blockIdx.x * LT + tid;
@@ -335,17 +341,17 @@ __device__ __forceinline__ void richardson_phases(const LSState& st, const LSSte
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int l = lane;
         for (; l + 96 < k; l += 128) {
-            s0 = fma(__ldcg(u + l), __ldcg(v + l), s0);
-            s1 = fma(__ldcg(u + l + 32), __ldcg(v + l + 32), s1);
-            s2 = fma(__ldcg(u + l + 64), __ldcg(v + l + 64), s2);
-            s3 = fma(__ldcg(u + l + 96), __ldcg(v + l + 96), s3);
+            s0 = fma(u[l], v[l], s0);
+            s1 = fma(u[l + 32], v[l + 32], s1);
+            s2 = fma(u[l + 64], v[l + 64], s2);
+            s3 = fma(u[l + 96], v[l + 96], s3);
         }
-        for (; l < k; l += 32) s0 = fma(__ldcg(u + l), __ldcg(v + l), s0);
+        for (; l < k; l += 32) s0 = fma(u[l], v[l], s0);
         return warp_sum((s0 + s1) + (s2 + s3));
     };
     if (app)
         for (int l = gtid; l < k; l += nthreads) {
-            const double sl = __ldcg(st.sbuf + l) * inv_r;
+            const double sl = st.sbuf[l] * inv_r;
             st.S[(size_t)i * k + l] = sl;
             st.VT[(size_t)l * mm + i] = sl;
         }
@@ -354,43 +360,39 @@ __device__ __forceinline__ void richardson_phases(const LSState& st, const LSSte
             const double d = j < i ? coldot(st.S + (size_t)j * k, st.pbuf) : coldot(st.sbuf, st.pbuf) * inv_r;
             if (lane == 0) st.u2p[j] = d * pmul;
         }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[3] = trace[4] = globaltimer();
+    if (!bar.sync(ctl, tr ? tr + 3 : nullptr)) return;
     if (!sol) {
-        if (trace) trace[5] = trace[6] = trace[7] = globaltimer();
+        if (tr) tr[9] = globaltimer();
         return;
     }
     for (int l = gwarp; l < k; l += nwarps) {
-        // the row copy's entry i was written above in this launch: L2 loads, not L1
         const double* row = st.VT + (size_t)l * mm;
         double s0 = 0.0, s1 = 0.0;
         int j = lane;
         for (; j + 32 <= i; j += 64) {
-            s0 = fma(__ldcg(row + j), __ldcg(st.u2p + j), s0);
-            s1 = fma(__ldcg(row + j + 32), __ldcg(st.u2p + j + 32), s1);
+            s0 = fma(row[j], st.u2p[j], s0);
+            s1 = fma(row[j + 32], st.u2p[j + 32], s1);
         }
-        if (j <= i) s0 = fma(__ldcg(row + j), __ldcg(st.u2p + j), s0);
+        if (j <= i) s0 = fma(row[j], st.u2p[j], s0);
         const double d = warp_sum(s0 + s1);
-        if (lane == 0) st.yp[l] = __ldcg(st.pbuf + l) * pmul - d;
+        if (lane == 0) st.yp[l] = st.pbuf[l] * pmul - d;
     }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[5] = trace[6] = globaltimer();
+    if (!bar.sync(ctl, tr ? tr + 5 : nullptr)) return;
     for (int j = gwarp; j <= i; j += nwarps) {
         const double d = coldot(st.S + (size_t)j * k, st.yp);
         if (lane == 0) {
-            const double x = __ldcg(st.u2p + j) + d;
+            const double x = st.u2p[j] + d;
             st.R[(size_t)a.xcol * st.ldr + j] = x;
-            st.coef[j] = x * __ldcg(st.sigma + j);
+            st.coef[j] = x * st.sigma[j];
         }
     }
-    if (trace) trace[7] = globaltimer();
+    if (tr) tr[9] = globaltimer();
 }
 
 template <class A>
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     using T = typename A::T;
     using Acc = typename A::Acc;
-    __shared__ double shd[2 * (NW + 1) + 2];   // FP64 block sums and totals (squared norms)
     __shared__ T shT[2 * (NW + 1) + 2];        // A::T block sums and totals
     __shared__ T qs[3 * NW];                   // per-warp partial dots of the column phases
     __shared__ T shP[NW * 32];                 // phase 0: the warps' range sums of one segment
@@ -411,8 +413,10 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     constexpr bool f64 = std::is_same<A, FineF64>::value;
     const bool rich = f64 && a.rich != 0;               // Richardson sweeps instead of the reflectors
     const T zero = A::zero();
-    unsigned long long* trace = (a.trace != nullptr && blockIdx.x == 0 && tid == 0) ? a.trace : nullptr;
-    if (trace) trace[0] = globaltimer();
+    // optional timestamps, thread 0 of every CTA: start, then arrival at and departure from each
+    // grid barrier (slots 1, 2 for the first, 3, 4 for the second, ...), end in slot 9
+    unsigned long long* tr = (a.trace != nullptr && tid == 0) ? a.trace + (size_t)blockIdx.x * kLsTraceSlots : nullptr;
+    if (tr) tr[0] = globaltimer();
     GridBarrier bar(ctl);
     const double pref = (app && tid == 0) ? st.pnorm[i] : 0.0;   // ||p_i||, for the breakdown test
     if (tid == 0) {                                              // the partial sketches' scales
@@ -420,7 +424,6 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         scT[7] = A::from_d(a.p_scale);
     }
 
-    if (trace) trace[1] = globaltimer();              // (the partial sums need no phase of their own)
     __syncthreads();
     const T s_scale = scT[6], p_scale = scT[7];
 
@@ -494,8 +497,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
         }
     }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[2] = globaltimer();
+    if (!bar.sync(ctl, tr ? tr + 1 : nullptr)) return;
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
     // Warp 0 reads the squared norms' totals and forms the phase's scalars (FP64 square roots
@@ -547,9 +549,9 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                     for (int q = 0; q < 8; ++q) {
                         const int l = lb + 32 * q + lane;
                         const bool ok = l < l1;
-                        mv[q] = ok ? A::ldg(mc + l) : zero;
-                        sv[q] = (ok && app) ? A::ldg(st.sbuf + l) : zero;
-                        pv[q] = (ok && sol) ? A::ldg(st.pbuf + l) : zero;
+                        mv[q] = ok ? A::ld(mc + l) : zero;
+                        sv[q] = (ok && app) ? A::ld(st.sbuf + l) : zero;
+                        pv[q] = (ok && sol) ? A::ld(st.pbuf + l) : zero;
                     }
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -607,13 +609,11 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (sol && gtid == 0) st.pnorm[a.pnorm_idx] = pn * pmul;
     if constexpr (f64) {
         if (rich) {
-            richardson_phases(st, a, bar, ctl, inv_r, pmul, trace);
+            richardson_phases(st, a, bar, ctl, inv_r, pmul, tr);
             return;
         }
     }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[3] = globaltimer();
-    if (trace) trace[4] = trace[3];                  // (no separate T^T u phase: M holds V T)
+    if (!bar.sync(ctl, tr ? tr + 3 : nullptr)) return;
 
     // ---- phase 3: y = [s, p] - V u2 (the i reflectors applied), warp per row using the
     //      row-major copy VT; s_i is stored (step 6); sums over rows > i for the new reflector
@@ -621,8 +621,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     {
         Acc sg = A::acc0(), cr = A::acc0();
         for (int l = gwarp; l < krows; l += nwarps) {
-            const T sl0 = app ? A::ldg(st.sbuf + l) : zero;     // issued before the row's dots
-            const T pl0 = sol ? A::ldg(st.pbuf + l) : zero;
+            const T sl0 = app ? A::ld(st.sbuf + l) : zero;     // issued before the row's dots
+            const T pl0 = sol ? A::ld(st.pbuf + l) : zero;
             T ws, wp;
             warp_row_dot2<A>(st.VT + (size_t)l * mm, st.u2s, st.u2p, min(i, l + 1), app, sol, ws, wp);
             if (lane == 0) {
@@ -639,8 +639,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         block_sum_lane0<A, 2>(sums, shT);
         if (tid == 0) { A::st(st.blk + blockIdx.x * 4 + 2, sums[0]); A::st(st.blk + blockIdx.x * 4 + 3, sums[1]); }
     }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[5] = globaltimer();
+    if (!bar.sync(ctl, tr ? tr + 5 : nullptr)) return;
 
     if (!app) {
         // pure solve: x = R_S^{-1} y(0:i); row j of R_S^{-1} is column j of RinvT
@@ -653,7 +652,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 st.coef[j] = dd * st.sigma[j];
             }
         }
-        if (trace) { trace[6] = globaltimer(); trace[7] = trace[6]; }
+        if (tr) tr[9] = globaltimer();
         return;
     }
 
@@ -674,7 +673,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                     for (int q = 0; q < 8; ++q) {
                         const int l = lb + 32 * q + lane;
                         vv[q] = l < l1 ? A::ld(v + l) : zero;
-                        yv[q] = l < l1 ? A::ldg(st.ys + l) : zero;
+                        yv[q] = l < l1 ? A::ld(st.ys + l) : zero;
                     }
 #pragma unroll
                     for (int q = 0; q < 8; ++q) A::acc(az, vv[q], yv[q]);
@@ -689,8 +688,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                         const int l = lb + 32 * q + lane;
                         const bool ok = l < r1;
                         rv[q] = ok ? A::ld(rr + l) : zero;
-                        y1[q] = ok ? A::ldg(st.ys + l) : zero;
-                        y2[q] = (ok && sol) ? A::ldg(st.yp + l) : zero;
+                        y1[q] = ok ? A::ld(st.ys + l) : zero;
+                        y2[q] = (ok && sol) ? A::ld(st.yp + l) : zero;
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -717,8 +716,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             __syncthreads();
         }
     }
-    if (!bar.sync(ctl)) return;
-    if (trace) trace[6] = globaltimer();
+    if (!bar.sync(ctl, tr ? tr + 7 : nullptr)) return;
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
     // Warp 0 forms the reflector's scalars (totals SG, CR; alpha, beta, tau, vs) while warps
@@ -727,8 +725,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (warp == 0) {
         T alpha = zero, ypi0 = zero;
         if (lane == 0) {                               // issued before the totals' round trip
-            alpha = A::ldg(st.ys + i);
-            ypi0 = sol ? A::ldg(st.yp + i) : zero;
+            alpha = A::ld(st.ys + i);
+            ypi0 = sol ? A::ld(st.yp + i) : zero;
         }
         T SG, CR;
         warp_total2<A>(st.blk, 2, SG, CR);
@@ -758,7 +756,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 const bool ok = l < i;
                 tv[q] = ok ? A::ld(tr + l) : zero;
                 vv[q] = ok ? A::ld(vrow_i + l) : zero;
-                zv[q] = ok ? A::ldg(st.zp + l) : zero;
+                zv[q] = ok ? A::ld(st.zp + l) : zero;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -783,10 +781,10 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         const T t = A::neg(A::mul(tau, A::add(da, A::mul(vs, db))));
         A::st(st.T + (size_t)i * mm + j, t);
         A::st(st.TT + (size_t)j * mm + i, t);
-        const T cnew = A::neg(A::div(A::ldg(st.d1 + j), beta));   // R_S^{-1}(j, i)
+        const T cnew = A::neg(A::div(A::ld(st.d1 + j), beta));   // R_S^{-1}(j, i)
         A::st(st.RinvT + (size_t)j * mm + i, cnew);
         if (sol) {
-            const double xj = A::to_d(A::add(A::ldg(st.d2 + j), A::mul(cnew, ypi)));
+            const double xj = A::to_d(A::add(A::ld(st.d2 + j), A::mul(cnew, ypi)));
             st.R[(size_t)a.xcol * st.ldr + j] = xj;
             st.coef[j] = xj * st.sigma[j];
         }
@@ -799,7 +797,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             if (lane == 0) finish(j, da, db);
         }
     for (int l = gtid; l < k; l += nthreads) {
-        const T vl = l < i ? zero : (l == i ? A::one() : A::mul(A::ldg(st.ys + l), vs));
+        const T vl = l < i ? zero : (l == i ? A::one() : A::mul(A::ld(st.ys + l), vs));
         A::st(st.V + (size_t)i * k + l, vl);
         if (l >= i) A::st(st.VT + (size_t)l * mm + i, vl);
     }
@@ -813,7 +811,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             st.coef[i] = xi * inv_r;
         }
     }
-    if (trace) trace[7] = globaltimer();
+    if (tr) tr[9] = globaltimer();
 }
 
 // Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
@@ -891,15 +889,23 @@ void rgs_ls_reset(rgs_context* ctx, const LSState& st) {
     RGS_CUDA(cudaMemsetAsync(st.pnorm, 0, sizeof(double) * (size_t)(st.mmax + 2), ctx->stream));
 }
 
+int rgs_ls_grid(const rgs_context* ctx) {
+    return ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
+}
+
+const void* ls_kernel_for(int fine_df) {
+    return fine_df == 2 ? (const void*)ls_kernel<FineF32>
+           : fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
+}
+
 void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
     RGS_REQUIRE(a.s_nparts <= st.max_parts && a.p_nparts <= st.max_parts, "too many partial sketches");
     LSState s = st;
     LSStep p = a;
     void* args[] = {&s, &p};
-    const int grid = ctx->ls_blocks_tuned > 0 ? std::min(ctx->ls_blocks_tuned, ctx->ls_blocks) : ctx->ls_blocks;
+    const int grid = rgs_ls_grid(ctx);
     RGS_REQUIRE(grid <= 32 * kTotMax, "least-squares grid larger than the per-CTA totals support");
-    const void* fn = st.fine_df == 2 ? (const void*)ls_kernel<FineF32>
-                     : st.fine_df ? (const void*)ls_kernel<FineDF> : (const void*)ls_kernel<FineF64>;
+    const void* fn = ls_kernel_for(st.fine_df);
     cudaLaunchAttribute attrs[2] = {};
     attrs[0].id = cudaLaunchAttributeCooperative;
     attrs[0].val.cooperative = 1;
@@ -925,7 +931,8 @@ void rgs_launch_ls(rgs_context* ctx, const LSState& st, const LSStep& a) {
 
 // One CTA of LT threads per SM (its registers fill the SM), so the cooperative grid is the SM count.
 int rgs_ls_max_blocks(int num_sms) {
-    for (const void* fn : {(const void*)ls_kernel<FineF64>, (const void*)ls_kernel<FineDF>, (const void*)ls_kernel<FineF32>}) {
+    for (int f = 0; f < 3; ++f) {
+        const void* fn = ls_kernel_for(f);
         int per_sm = 0;
         RGS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LT, 0));
         RGS_REQUIRE(per_sm >= 1, "the least-squares kernel does not fit on an SM");
