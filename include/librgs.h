@@ -265,6 +265,14 @@ typedef struct {
     double rel_residual;    /* final ||b - A x|| / ||b|| in FP64 */
     double* history;        /* optional host array (max_cycles + 1): residual after each cycle */
     int32_t fallback_cycle; /* cycle at which the preconditioner was switched off, or -1 */
+    int32_t sell;           /* 1: the products with A read it in SELL-32 form (slices of 32 rows,
+                               entry-major; built once per solve when the SRHT sketch is used and
+                               the padding stays within nnz / 4; RGS_SELL=0 in the environment
+                               keeps CSR), 0: CSR.  The two give bit-identical results. */
+    int32_t sketch_refreshes; /* rgmres_solve: cycles after which Theta was redrawn because the cycle
+                                 had not reduced ||b - A x|| by a relative 2^-10 (the r-th redraw
+                                 uses seed + r * 0x9E3779B97F4A7C15 mod 2^64; restarting, and so
+                                 this rule, is outside the paper, which runs one cycle) */
     int32_t reserved;
 } rgmres_info;
 

@@ -17,6 +17,13 @@ Alg. 3 from w_1 = r = b - A x (FP64), adds Q_{j} y to x, and recomputes the
 true FP64 residual.  ``restart`` is the largest number of Arnoldi steps
 (products with A) per cycle, so a cycle's basis has restart + 1 columns.
 
+A restart cycle that leaves the true residual without a relative decrease of 2^-10 draws a new
+Theta for the following cycles, the r-th such draw with seed + r * 0x9E3779B97F4A7C15 (mod 2^64)
+and the caller's kind, n and k.  Each cycle minimises the sketched residual only; after many
+cycles with one Theta the residual is no longer independent of it and can settle where Theta sees
+little of it, when the cycles stop making progress.  (A rule of the restarted solver, like
+restarting itself; ``refresh=False`` turns it off.)
+
 Right preconditioning (Sec. 5, Ex. 3 applies A P): with ``precond`` given,
 the operator is A M and x += M (Q y); with ``flexible=True`` each
 z_j = M(q_j) is stored and x += Z y (a nonlinear M is allowed).
@@ -29,6 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from .sketch import Sketch
 from .rgs import (BREAKDOWN_FACTOR, U_FINE, ls_householder, ls_richardson,
                   round_storage, update_fp32)
 
@@ -118,9 +126,17 @@ class SolveResult:
     pass
 
 
+REFRESH_STRIDE = 0x9E3779B97F4A7C15
+
+
+def refresh_seed(seed, r):
+    """Seed of the r-th redrawn Theta of a restarted solve."""
+    return (int(seed) + int(r) * REFRESH_STRIDE) % (1 << 64)
+
+
 def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="householder",
            sweeps=2, storage="f64", precond=None, flexible=False, inner_factor=0.5,
-           fixed_steps=False):
+           fixed_steps=False, refresh=True):
     """Restarted randomized GMRES with RGS-Arnoldi; ``A`` is anything with ``A @ v``.
 
     Inner stop (unless ``fixed_steps``): sketched residual estimate
@@ -132,6 +148,7 @@ def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="househol
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     bnorm = np.linalg.norm(b)
     sb = np.linalg.norm(sketch.apply(b))
+    base_seed = sketch.seed
     res = SolveResult()
     res.true_residuals = []
     res.steps = []
@@ -142,7 +159,12 @@ def rgmres(A, b, sketch, restart, tol=1e-8, max_cycles=50, x0=None, ls="househol
     converged = res.true_residuals[-1] <= tol
     cycles = 0
     thr = inner_factor * tol * sb
+    res.refreshes = 0
     while not converged and cycles < max_cycles:
+        tr = res.true_residuals
+        if refresh and cycles > 0 and not (tr[-1] < tr[-2] * (1.0 - 2.0 ** -10)):
+            res.refreshes += 1
+            sketch = Sketch(sketch.kind, sketch.n, sketch.k, refresh_seed(base_seed, res.refreshes))
         stop = None if fixed_steps else (lambda rho, j, thr=thr: rho <= thr)
         cyc = rgs_arnoldi(matvec, r, sketch, restart, ls, sweeps, storage,
                           precond=precond, stop=stop)

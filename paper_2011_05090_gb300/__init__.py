@@ -96,7 +96,7 @@ class GmresInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("total_steps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("fallback_cycle", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sell", ctypes.c_int32), ("sketch_refreshes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -420,7 +420,8 @@ def _gmres_opts(restart, max_cycles, rtol, inner_factor, qdtype, fixed_steps, fi
 def _gmres_result(st, info, hist, h):
     res = {"cycles": info.cycles, "total_steps": info.total_steps, "converged": bool(info.converged),
            "status": info.status, "rel_residual": info.rel_residual,
-           "history": [hist[i] for i in range(info.cycles + 1)], "fallback_cycle": info.fallback_cycle}
+           "history": [hist[i] for i in range(info.cycles + 1)], "fallback_cycle": info.fallback_cycle,
+           "sell": bool(info.sell), "sketch_refreshes": info.sketch_refreshes}
     if st not in (RGS_OK, RGS_ERR_NOT_CONVERGED):
         try:
             _check(st, h)

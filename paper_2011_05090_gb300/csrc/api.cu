@@ -127,7 +127,7 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
     constexpr int kBucket = 50;
     const int nbk = (m + kBucket - 1) / kBucket;
     struct Acc {
-        double start = 0, work[4] = {0}, skew[4] = {0}, lat[4] = {0}, tail = 0, total = 0;
+        double start = 0, work[4] = {0}, skew[4] = {0}, lat[4] = {0}, tail = 0, total = 0, psum_med = 0, psum_max = 0;
         int n = 0, nq[4] = {0};
     };
     std::vector<Acc> acc(nbk);
@@ -149,7 +149,12 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
             e1 = std::max(e1, at(b, 9));
         }
         c.start += (double)(t1 - t0) * 1e-3;
-        for (int b = 0; b < grid; ++b) prev[b] = (double)(at(b, 0) - t0);
+        for (int b = 0; b < grid; ++b) {
+            prev[b] = (double)(at(b, 0) - t0);
+            w[b] = (double)(at(b, 10) - at(b, 0));                 // phase 0's partial sums
+        }
+        c.psum_med += median(w) * 1e-3;
+        c.psum_max += *std::max_element(w.begin(), w.end()) * 1e-3;
         for (int q = 0; q < 4; ++q) {
             if (at(0, 1 + 2 * q) == 0) break;                      // this launch had fewer barriers
             for (int b = 0; b < grid; ++b) {
@@ -170,8 +175,9 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
     for (int bk = 0; bk < nbk; ++bk) {
         const Acc& c = acc[bk];
         if (c.n == 0) continue;
-        std::fprintf(stderr, "[rgs trace] least squares, columns [%d,%d), %d CTAs (us): start spread %.2f",
-                     bk * kBucket, std::min(m, (bk + 1) * kBucket), grid, c.start / c.n);
+        std::fprintf(stderr, "[rgs trace] least squares, columns [%d,%d), %d CTAs (us): start spread %.2f; "
+                     "partial sums median %.2f, max %.2f", bk * kBucket, std::min(m, (bk + 1) * kBucket), grid,
+                     c.start / c.n, c.psum_med / c.n, c.psum_max / c.n);
         for (int q = 0; q < 4; ++q)
             if (c.nq[q] > 0)
                 std::fprintf(stderr, "; phase %d work %.2f, last arrival +%.2f, barrier %.2f", q, c.work[q] / c.nq[q],

@@ -1097,6 +1097,8 @@ extern "C" rgs_status rgmres_solve_batched(rgs_handle h, int32_t nbatch, const r
                 info[i].converged = outs[8 * (size_t)i + 3];
                 info[i].rel_residual = sc[8 * (size_t)i + 4];
                 info[i].fallback_cycle = -1;
+                info[i].sell = 0;
+                info[i].sketch_refreshes = 0;
             }
         }
         if (ctlv[kStatusWord] != 0)

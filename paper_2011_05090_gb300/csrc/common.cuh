@@ -281,11 +281,15 @@ struct GridBarrier {
     unsigned* word;
     unsigned expect;                       // thread 0: the top bit that completes the next barrier
     long long budget;                      // thread 0: clock cycles a wait may take
+    unsigned raw_word;                     // thread 0: the two control words as read at construction,
+    long long raw_budget;                  // turned into expect / budget at the first sync, so
+    bool primed;                           // that the kernel's start does not wait for the reads
     __device__ explicit GridBarrier(int* ctl)
-        : word(reinterpret_cast<unsigned*>(ctl + kBarCount)), expect(0u), budget(kDefaultWaitCycles) {
+        : word(reinterpret_cast<unsigned*>(ctl + kBarCount)), expect(0u), budget(kDefaultWaitCycles), raw_word(0u),
+          raw_budget(0), primed(false) {
         if (threadIdx.x == 0) {
-            expect = (ld_relaxed(word) & 0x80000000u) ^ 0x80000000u;
-            budget = wait_budget(ctl);
+            raw_word = ld_relaxed(word);
+            raw_budget = *reinterpret_cast<const volatile long long*>(ctl + kBudgetWord);
         }
     }
     // ts (thread 0, optional): ts[0] = arrival of the whole CTA, ts[1] = departure (ns)
@@ -294,6 +298,11 @@ struct GridBarrier {
         __syncthreads();                   // the CTA's writes are ordered before thread 0's release
         if (threadIdx.x == 0) {
             if (ts) ts[0] = globaltimer();
+            if (!primed) {
+                expect = (raw_word & 0x80000000u) ^ 0x80000000u;
+                budget = raw_budget > 0 ? raw_budget : kDefaultWaitCycles;
+                primed = true;
+            }
             int ok = 1;
             red_add_release(word, blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u);
             const long long start = clock64();
@@ -372,10 +381,34 @@ void rgs_launch_reduce_partials(rgs_context* ctx, const double* partials, int np
 void rgs_launch_gaussian_theta(rgs_context* ctx, double* theta, int k, int64_t n, uint64_t seed);
 
 // spmv.cu
+// A sparse operator in SELL-32 form (sliced ELLPACK, Kreutzer et al. 2014, with slices of 32
+// rows and no sorting): slice s holds rows 32 s .. 32 s + 31 padded to the slice's longest row,
+// entry t of row 32 s + l at off[s] + 32 t + l (padding: value 0, column of a valid row).  A
+// warp's load of entry t of its 32 rows is then one contiguous access.  Built once per solve.
+struct SellView {
+    int64_t nslices = 0;
+    const int64_t* off = nullptr;   // nslices + 1 entry offsets
+    const int32_t* col = nullptr;
+    const void* val = nullptr;      // double-float pairs or FP64, 8 bytes an entry
+};
+struct SellBuf {
+    DevBuf off, col, val;
+    int64_t nslices = 0;
+    int64_t entries = 0;
+};
+// The SELL-32 structure of A and its values (double-float pairs when dfm, else FP64) into sb;
+// false (nothing built) when the padding would exceed a quarter of nnz.
+bool rgs_build_sell(rgs_context* ctx, const rgs_csr& A, int dfm, SellBuf& sb);
+// Values val (nnz, A's pattern) in sb's layout into out (sb.entries x 8 bytes).
+void rgs_fill_sell_values(rgs_context* ctx, const rgs_csr& A, const double* val, int dfm, const SellBuf& sb,
+                          DevBuf& out);
 void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* out);
 int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm);
+// sell (optional, with an SRHT sketch): the product reads A in that layout instead of CSR (the
+// same arithmetic in the same order: bit-identical results)
 int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
-                    const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale = nullptr);
+                    const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale = nullptr,
+                    const SellView* sell = nullptr);
 int rgs_norm_grid(const rgs_context* ctx, int64_t n);
 void rgs_launch_residual(rgs_context* ctx, const rgs_csr& A, const double* x, const double* b, double* r,
                          double* part, double* norm_out);
@@ -442,7 +475,8 @@ int rgs_ls_max_blocks(int num_sms);
 int rgs_ls_grid(const rgs_context* ctx);
 // RGS_TRACE: summary of the least-squares timestamps of launches 0..m-1 on stderr
 void rgs_print_ls_trace(rgs_context* h, int m, int grid);
-// least-squares trace per CTA: start, (arrival, departure) at each of up to four grid barriers, end
-constexpr int kLsTraceSlots = 10;
+// least-squares trace per CTA: start, (arrival, departure) at each of up to four grid barriers, end,
+// end of phase 0's partial sums
+constexpr int kLsTraceSlots = 11;
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
                              const double* P, double* out2 /* device: delta, delta_tilde */, double* work);

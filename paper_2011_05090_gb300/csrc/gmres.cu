@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <new>
 #include <vector>
@@ -43,6 +44,7 @@ struct rgs_arnoldi_obj {
     DevBuf work;             // r (n), norm partials, scalars
     DevBuf jac;              // Jacobi: diag(A)^{-1} (n) and the values of A D^{-1} (nnz)
     DevBuf Z;                // flexible preconditioning: z'_i = M(q'_i), n x mmax FP32
+    const SellView* sell = nullptr;        // A in SELL-32 form for the fused product (rgmres_solve)
     unsigned long long* trace = nullptr;   // RGS_TRACE: least-squares timestamps of step i at
     size_t tstride = 0;                    // trace + i * tstride (the latest cycle's steps)
 };
@@ -150,7 +152,7 @@ int launch_product(rgs_arnoldi_obj* a, const rgs_csr& A, int col, const void* v 
     if (a->sk->kind == RGS_SKETCH_SRHT) {
         const int dfm = sketch_is_df(a) ? 1 : 0;
         return rgs_launch_spmv(h, A, a->vdf.ptr, x, xtype, a->wbuf.ptr, dfm, a->sk, a->ppart.as<double>(),
-                               h->ctl.as<int>());
+                               h->ctl.as<int>(), nullptr, a->sell);
     }
     rgs_launch_spmv(h, A, nullptr, x, xtype, a->wbuf.ptr, 0, nullptr, nullptr, h->ctl.as<int>());
     if (!sketch) return 0;
@@ -379,7 +381,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
                         const rgmres_opts* opts, rgmres_info* info) {
     if (!h || !s || !opts) return RGS_ERR_INVALID_ARG;
     if (info) {
-        info->cycles = info->total_steps = info->converged = 0;
+        info->cycles = info->total_steps = info->converged = info->sell = info->sketch_refreshes = 0;
         info->status = RGS_OK;
         info->rel_residual = NAN;
     }
@@ -425,7 +427,25 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             obj.Z.ensure(sizeof(float) * (size_t)obj.ldq * obj.mmax);
         }
         DevBuf vdf_pc;                       // double-float values of A D^{-1}
-        if (sketch_is_df(&obj)) {
+        // The fused product with the SRHT reads A in SELL-32 form when its padding is small
+        // (RGS_SELL=0 in the environment: CSR); A D^{-1} shares the structure, with its own values.
+        SellBuf sell;
+        SellView sview, sview_pc;
+        const char* sell_env = std::getenv("RGS_SELL");
+        const int dfm = sketch_is_df(&obj) ? 1 : 0;
+        if (s->kind == RGS_SKETCH_SRHT && !(sell_env && sell_env[0] == '0') && rgs_build_sell(h, *A, dfm, sell)) {
+            sview.nslices = sell.nslices;
+            sview.off = sell.off.as<int64_t>();
+            sview.col = sell.col.as<int32_t>();
+            sview.val = sell.val.ptr;
+            sview_pc = sview;
+            if (pk == RGS_PRECOND_JACOBI) {
+                rgs_fill_sell_values(h, *A, Apc.val, dfm, sell, vdf_pc);
+                sview_pc.val = vdf_pc.ptr;
+            }
+            obj.sell = &sview;
+            if (info) info->sell = 1;
+        } else if (dfm) {
             obj.vdf.ensure(8 * (size_t)std::max<int64_t>(A->nnz, 1));
             rgs_csr_split_df(h, A->val, A->nnz, obj.vdf.ptr);
             if (pk == RGS_PRECOND_JACOBI) {
@@ -446,9 +466,11 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             }
             if (use_pc) {
                 void* keep = obj.vdf.ptr;
-                if (vdf_pc.ptr) obj.vdf.ptr = vdf_pc.ptr;
+                if (vdf_pc.ptr && !obj.sell) obj.vdf.ptr = vdf_pc.ptr;
+                if (obj.sell) obj.sell = &sview_pc;
                 const int np = launch_product(&obj, Apc, i, nullptr, -1, sketch);
                 obj.vdf.ptr = keep;
+                if (obj.sell) obj.sell = &sview;
                 return np;
             }
             return launch_product(&obj, *A, i, nullptr, -1, sketch);
@@ -456,12 +478,25 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         // Gaussian sketch: Theta q'_i and Theta (A q'_i) in one pass over Theta (Sec. 2.4's single
         // synchronisation per step; the k x n matrix is read once per step instead of twice)
         const bool gauss2 = s->kind == RGS_SKETCH_GAUSSIAN;
+        const bool trace = std::getenv("RGS_TRACE") != nullptr;
+        PhaseTimer timer(h, trace);          // RGS_TRACE: device time of the update, product and LS launches
         auto step = [&](int i, const void* w, int w_df, const double* wscale, bool with_product, int& sp, int& pp) {
+            if (trace && !(gauss2 && with_product)) {
+                timer.start(0);
+                sp = launch_update(&obj, i, w, w_df, wscale);
+                timer.stop(0);
+                if (with_product) {
+                    timer.start(1);
+                    pp = product(i, true);
+                    timer.stop(1);
+                }
+                return;
+            }
             if (gauss2 && with_product) {
                 launch_update(&obj, i, w, w_df, wscale, true);
                 product(i, false);
                 const void* qi = obj.Q.as<char>() + dsize(obj.qtype) * (size_t)i * obj.ldq;
-                sp = pp = rgs_launch_gauss_sketch2(h, s, s->n, qi, obj.qtype, obj.wbuf.as<double>(),
+                sp = pp = rgs_launch_gauss_sketch2(h, obj.sk, s->n, qi, obj.qtype, obj.wbuf.as<double>(),
                                                    obj.spart.as<double>(), obj.ppart.as<double>(), h->ctl.as<int>());
             } else {
                 sp = launch_update(&obj, i, w, w_df, wscale);
@@ -469,7 +504,6 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             }
         };
         Scalars sc = scalars(&obj);
-        const bool trace = std::getenv("RGS_TRACE") != nullptr;
         if (trace) {
             obj.tstride = (size_t)rgs_ls_grid(h) * kLsTraceSlots;
             h->trace.ensure(sizeof(unsigned long long) * obj.tstride * (size_t)(m + 1));
@@ -499,8 +533,16 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         const double bnorm = hv[1], sbnorm = hv[2];
         RGS_REQUIRE(bnorm > 0.0 && std::isfinite(bnorm), "b must be nonzero and finite");
         double stop_tol = (opts->fixed_steps ? -1.0 : opts->inner_factor * opts->rtol * sbnorm);
-        int cycles = 0, total = 0;
+        int cycles = 0, total = 0, refreshes = 0;
         double rel = NAN;
+        struct SketchOwner {                 // a refreshed Theta, destroyed with the solve
+            rgs_sketch p = nullptr;
+            void reset(rgs_sketch q) {
+                if (p) rgs_sketch_destroy(p);
+                p = q;
+            }
+            ~SketchOwner() { reset(nullptr); }
+        } fresh;
         for (;;) {
             rgs_launch_residual(h, *A, x, b, sc.r, sc.part, sc.val);     // true FP64 residual
             int ctlv[8];
@@ -519,9 +561,24 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             // true residual (by at least a relative 2^-10, so that rounding noise does not count as
             // progress) turns it off; the unpreconditioned method finishes the solve.  A fixed linear
             // preconditioner (Jacobi) is kept: its slow cycles are the restarted method's, not its own.
-            if (use_pc && learned && cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10))) {
+            const bool stalled = cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10));
+            if (use_pc && learned && stalled) {
                 use_pc = false;
                 fallback_cycle = cycles;
+            } else if (stalled) {
+                // A cycle of the restarted method that did not reduce the true residual draws a new
+                // Theta for the following cycles.  Each cycle minimises the sketched residual only,
+                // and after many cycles with one Theta the residual is no longer independent of it:
+                // it can settle where Theta sees little of it (||Theta r|| << ||r||), and the cycles
+                // then make no progress.  The new Theta is the r-th refresh of the caller's seed,
+                // seed + r * 0x9E3779B97F4A7C15 (mod 2^64), with the same kind, n and k.
+                ++refreshes;
+                rgs_sketch ns = nullptr;
+                const uint64_t seed = s->seed + (uint64_t)refreshes * 0x9E3779B97F4A7C15ull;
+                const rgs_status cs = rgs_sketch_create(h, (rgs_sketch_kind)s->kind, s->n, s->k, seed, &ns);
+                if (cs != RGS_OK) throw RgsError{cs, "sketch refresh: " + std::string(rgs_last_error(h))};
+                fresh.reset(ns);
+                obj.sk = ns;
             }
             prev_rel = rel;
             reset_cycle(&obj);
@@ -531,7 +588,9 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             launch_ls(&obj, 0, sp, m >= 1, pp, true, stop_tol);
             for (int i = 1; i <= m; ++i) {
                 step(i, obj.wbuf.ptr, sketch_is_df(&obj) ? 1 : 0, obj.ls.sigma + (i - 1), i < m, sp, pp);
+                timer.start(2);
                 launch_ls(&obj, i, sp, i < m, pp, true, stop_tol);
+                timer.stop(2);
             }
             rgs_launch_hess_solve(h, obj.ls.Hr, obj.mmax, obj.ls.g, obj.ls.sigma, m, y_buf(&obj), cy_buf(&obj),
                                   h->ctl.as<int>());
@@ -542,13 +601,21 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
                                       use_pc ? dinv : nullptr);
             ++cycles;
         }
-        if (trace) rgs_print_ls_trace(h, m + 1, rgs_ls_grid(h));
+        if (trace) {
+            RGS_CUDA(cudaStreamSynchronize(h->stream));
+            const double nst = std::max(1, total);
+            std::fprintf(stderr, "[rgs trace] rgmres, %d steps (us per step, device): update + sketch %.2f, product + "
+                         "sketch %.2f, least squares %.2f\n", total, 1e3 * timer.total_ms(0) / nst,
+                         1e3 * timer.total_ms(1) / nst, 1e3 * timer.total_ms(2) / nst);
+            rgs_print_ls_trace(h, m + 1, rgs_ls_grid(h));
+        }
         if (info) {
             info->cycles = cycles;
             info->total_steps = total;
             info->converged = converged ? 1 : 0;
             info->rel_residual = rel;
             info->fallback_cycle = fallback_cycle;
+            info->sketch_refreshes = refreshes;
         }
     });
     if (info) info->status = st;
@@ -599,7 +666,7 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
                             rgmres_info* info) {
     if (!h || !A || !opts) return RGS_ERR_INVALID_ARG;
     if (info) {
-        info->cycles = info->total_steps = info->converged = 0;
+        info->cycles = info->total_steps = info->converged = info->sell = info->sketch_refreshes = 0;
         info->status = RGS_OK;
         info->rel_residual = NAN;
     }

@@ -62,6 +62,7 @@ struct FineF64 {
     __device__ static bool is_zero(T a) { return a == 0.0; }
     __device__ static bool nonneg(T a) { return a >= 0.0; }
     __device__ static T wsum(T v) { return warp_sum(v); }
+    __device__ static T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     __device__ static T ld(const double* p) { return *p; }
     __device__ static T ldcg(const double* p) { return __ldcg(p); }
     __device__ static void st(double* p, T v) { *p = v; }
@@ -133,6 +134,9 @@ struct FineDF {
         }
         return v;
     }
+    __device__ static T shfl_xor(T v, int o) {
+        return {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    }
     __device__ static T ld(const double* p) {
         const float2 v = *reinterpret_cast<const float2*>(p);
         return {v.x, v.y};
@@ -182,6 +186,7 @@ struct FineF32 {
         for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
         return v;
     }
+    __device__ static T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     __device__ static T ld(const double* p) { return *reinterpret_cast<const float*>(p); }
     __device__ static T ldcg(const double* p) { return __ldcg(reinterpret_cast<const float*>(p)); }
     __device__ static void st(double* p, T v) { *reinterpret_cast<float*>(p) = v; }
@@ -238,20 +243,22 @@ __device__ void warp_total2(const double* blk, int off, typename A::T& t0, typen
     t1 = A::wsum(v1);
 }
 
-// Sum over b in [b0, b1) of the partial sketch entries src[b * k + l] (double-float or FP64),
-// written by an earlier launch, in the arithmetic of A.
+// Sum over b = b0, b0 + step, ... < b1 of the partial sketch entries src[b * k + l] (double-float
+// or FP64), written by an earlier launch, in the arithmetic of A.
 template <class A>
-__device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, int b0, int b1, int k, int l) {
+__device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, int b0, int b1, int step, int k,
+                                                  int l) {
     if constexpr (std::is_same<typename A::T, float>::value) {
         // unique precision: the FP32 partials (high words of the pairs) summed in FP32
         const df* d = reinterpret_cast<const df*>(src);
         float t0 = 0.f, t1 = 0.f;
-        for (int bb = b0; bb < b1; bb += 16) {
+        for (int bb = b0; bb < b1; bb += 16 * step) {
             float v[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-                v[q] = bb + q < b1 ? (sdf ? d[(size_t)(bb + q) * k + l].h : __double2float_rn(src[(size_t)(bb + q) * k + l]))
-                                   : 0.f;
+            for (int q = 0; q < 16; ++q) {
+                const int b = bb + q * step;
+                v[q] = b < b1 ? (sdf ? d[(size_t)b * k + l].h : __double2float_rn(src[(size_t)b * k + l])) : 0.f;
+            }
 #pragma unroll
             for (int q = 0; q < 16; q += 2) {
                 t0 = __fadd_rn(t0, v[q]);
@@ -263,10 +270,13 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     if (sdf) {
         const df* d = reinterpret_cast<const df*>(src);
         df t0 = {0.f, 0.f}, t1 = {0.f, 0.f};
-        for (int bb = b0; bb < b1; bb += 16) {         // 16 loads in flight, then the sums
+        for (int bb = b0; bb < b1; bb += 16 * step) {  // 16 loads in flight, then the sums
             df v[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = bb + q < b1 ? d[(size_t)(bb + q) * k + l] : df{0.f, 0.f};
+            for (int q = 0; q < 16; ++q) {
+                const int b = bb + q * step;
+                v[q] = b < b1 ? d[(size_t)b * k + l] : df{0.f, 0.f};
+            }
 #pragma unroll
             for (int q = 0; q < 16; q += 2) {
                 t0 = df_add(t0, v[q]);
@@ -282,18 +292,19 @@ __device__ __forceinline__ typename A::T part_sum(const double* src, bool sdf, i
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
     int b = b0;
 #pragma unroll 2
-    for (; b + 3 < b1; b += 4) {
+    for (; b + 3 * step < b1; b += 4 * step) {
         v0 += src[(size_t)b * k + l];
-        v1 += src[(size_t)(b + 1) * k + l];
-        v2 += src[(size_t)(b + 2) * k + l];
-        v3 += src[(size_t)(b + 3) * k + l];
+        v1 += src[(size_t)(b + step) * k + l];
+        v2 += src[(size_t)(b + 2 * step) * k + l];
+        v3 += src[(size_t)(b + 3 * step) * k + l];
     }
-    for (; b < b1; ++b) v0 += src[(size_t)b * k + l];
+    for (; b < b1; b += step) v0 += src[(size_t)b * k + l];
     return A::from_d((v0 + v1) + (v2 + v3));
 }
 
-// Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2, a warp with lanes over the entries: the lane partials summed over the warp,
-// valid in every lane; use1 / use2 select the vectors needed.
+// Dot products of a row (stride 1, entries [0, jend)) with vectors y1 and y2, a warp with lanes
+// over the entries: the lane partials summed over the warp, valid in every lane; use1 / use2
+// select the vectors needed.
 template <class A>
 __device__ __forceinline__ void warp_row_dot2(const double* row, const double* y1, const double* y2, int jend,
                                               bool use1, bool use2, typename A::T& o1, typename A::T& o2) {
@@ -427,47 +438,62 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     __syncthreads();
     const T s_scale = scT[6], p_scale = scT[7];
 
-    // ---- phase 0: the totals of s' and p.  Item = (32-row segment, vector), one item per CTA:
-    //      its NW warps sum consecutive ranges of the partial sketches for the segment's rows
-    //      (lane = row), warp 0 adds the NW range sums in order (deterministic), scales and
-    //      stores them and forms the squared norms (FP64).  Then every warp forms rows of
-    //      M(:, i-1) = V(:, 0:i) T(0:i, i-1).
+    // ---- phase 0: the totals of s' and p.  Item = (segment of R rows, vector), R the largest of
+    //      32, 16, 8, 4 that still gives at least G/2 items (small k: shorter segments spread the
+    //      sums over more CTAs; one item per CTA, as each item has a fixed serial part).  The
+    //      item's NW warps sum consecutive ranges of the partial sketches;
+    //      within a warp, lane = (row, slice): slice t of the 32/R takes every (32/R)-th partial
+    //      of the range and the slices are combined by shuffles.  Warp 0 adds the NW range sums
+    //      in a fixed pairwise order (deterministic), scales and stores them and forms the squared norms (FP64).
+    //      Then every warp forms rows of M(:, i-1) = V(:, 0:i) T(0:i, i-1).
     {
         const int warp = tid >> 5;
         constexpr bool f32 = std::is_same<T, float>::value;   // unique precision: FP32 squared norms
         double nrm_s = 0.0, nrm_p = 0.0;               // warp 0, lane 0
         float nrm_sf = 0.f, nrm_pf = 0.f;
-        const int nseg = (k + 31) / 32;
+        int R = 32;
+        while (R > 4 && 2 * 2 * ((k + R - 1) / R) < G) R >>= 1;
+        const int S = 32 / R, rl = lane & (R - 1), sl = lane / R;
+        const int nseg = (k + R - 1) / R;
         const int nitems = nseg * 2;
         for (int it = blockIdx.x; it < nitems; it += G) {
             const int seg = it >> 1, vec = it & 1;       // vec 0: s', vec 1: p (uniform over the CTA)
             if (vec == 0 ? !app : !sol) continue;
-            const int l = seg * 32 + lane;
+            const int l = seg * R + rl;
             T part = zero;
             if (vec == 0 || p_parts) {
                 const int np = vec == 0 ? a.s_nparts : a.p_nparts;
                 const int chunk = (np + NW - 1) / NW;
                 const int b0 = min(np, warp * chunk), b1 = min(np, b0 + chunk);
-                if (l < k && b1 > b0)
-                    part = part_sum<A>(vec == 0 ? a.s_part : a.p_part, (vec == 0 ? a.s_df : a.p_df) != 0, b0, b1, k, l);
+                if (l < k && b0 + sl < b1)
+                    part = part_sum<A>(vec == 0 ? a.s_part : a.p_part, (vec == 0 ? a.s_df : a.p_df) != 0, b0 + sl, b1,
+                                       S, k, l);
+                for (int o = R; o < 32; o <<= 1) part = A::add(part, A::shfl_xor(part, o));
             } else if (warp == 0 && l < k) {
                 part = A::from_d(a.p_vec[l]);
             }
-            shP[warp * 32 + lane] = part;
+            if (sl == 0) shP[warp * 32 + rl] = part;
             __syncthreads();
             if (warp == 0) {
-                T v = shP[lane];
+                const int lw = seg * R + lane;           // lanes 0..R-1: the segment's rows
+                const bool own = lane < R && lw < k;
+                T t[NW];                                 // the NW range sums, added as a pairwise tree
 #pragma unroll
-                for (int w = 1; w < NW; ++w) v = A::add(v, shP[w * 32 + lane]);
+                for (int w = 0; w < NW; ++w) t[w] = lane < R ? shP[w * 32 + lane] : zero;
+#pragma unroll
+                for (int h = 1; h < NW; h *= 2)
+#pragma unroll
+                    for (int w = 0; w + h < NW; w += 2 * h) t[w] = A::add(t[w], t[w + h]);
+                T v = t[0];
                 v = A::mul(v, vec == 0 ? s_scale : p_scale);
                 double vd = 0.0;
-                if (l < k) {
-                    A::st((vec == 0 ? st.sbuf : st.pbuf) + l, v);
+                if (own) {
+                    A::st((vec == 0 ? st.sbuf : st.pbuf) + lw, v);
                     vd = A::to_d(v);
-                    if (vec == 1 && a.p_store) a.p_store[l] = vd;
+                    if (vec == 1 && a.p_store) a.p_store[lw] = vd;
                 }
                 if constexpr (f32) {
-                    const float vf = l < k ? (float)vd : 0.f;
+                    const float vf = own ? (float)vd : 0.f;
                     const float sq = A::wsum(__fmul_rn(vf, vf));
                     if (vec == 0) nrm_sf = __fadd_rn(nrm_sf, sq); else nrm_pf = __fadd_rn(nrm_pf, sq);
                 } else {
@@ -477,6 +503,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             }
             __syncthreads();                               // shP is reused by the next item
         }
+        if (tr) tr[10] = globaltimer();
         if (i > 0 && !rich) {
             // M(:, i-1) = V(:, 0:i) T(0:i, i-1): T's column i-1 was completed by the previous
             // launch; warp per row of the row-major copy VT, lanes over the columns

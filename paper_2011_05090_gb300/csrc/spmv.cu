@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 using namespace rgsdev;
 
@@ -22,6 +23,44 @@ __global__ void csr_split_df_kernel(const double* __restrict__ val, int64_t nnz,
         const double v = val[e];
         const float h = __double2float_rn(v);
         out[e] = {h, __double2float_rn(v - (double)h)};
+    }
+}
+
+// SELL-32 slice widths: the longest row of each slice of 32 rows (rows past n count as empty).
+// The grid-stride loop runs over whole slices, so the 32 lanes of a warp share one slice.
+__global__ void sell_width_kernel(int64_t n, const int32_t* __restrict__ rowptr, int64_t nslices,
+                                  int32_t* __restrict__ width) {
+    const int64_t rows = nslices * 32;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
+        const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        if ((r & 31) == 0) width[r >> 5] = wmax;
+    }
+}
+
+// Fill the SELL-32 arrays: entry t of row r = 32 s + l goes to off[s] + 32 t + l; padding gets the
+// value 0 and the column r (0 past n), a valid index.  col == nullptr: values only.
+template <bool DFM>
+__global__ void sell_fill_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                 const double* __restrict__ val, const int64_t* __restrict__ off, int64_t nslices,
+                                 int32_t* __restrict__ col, void* __restrict__ out) {
+    const int64_t rows = nslices * 32;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = r >> 5, q0 = off[s] + (r & 31);
+        const int width = (int)((off[s + 1] - off[s]) >> 5);
+        const int b0 = r < n ? rowptr[r] : 0, len = r < n ? rowptr[r + 1] - b0 : 0;
+        for (int t = 0; t < width; ++t) {
+            const int64_t q = q0 + 32 * (int64_t)t;
+            const bool real = t < len;
+            if (col) col[q] = real ? colind[b0 + t] : (r < n ? (int32_t)r : 0);
+            const double v = real ? val[b0 + t] : 0.0;
+            if constexpr (DFM) {
+                const float h = __double2float_rn(v);
+                reinterpret_cast<df*>(out)[q] = {h, __double2float_rn(v - (double)h)};
+            } else {
+                reinterpret_cast<double*>(out)[q] = v;
+            }
+        }
     }
 }
 
@@ -54,6 +93,10 @@ struct SpmvParams {
     int ntiles;
     double* partials;
     const int* ctl;
+    int64_t nslices;        // SELL-32 layout (the SELL kernels): slices, entry offsets, columns, values
+    const int64_t* soff;
+    const int32_t* scol;
+    const void* sval;
 };
 
 // (A x) for the rows rbase + threadIdx.x + 256 e (e = 0..3) of a tile, stored to w and returned
@@ -145,7 +188,65 @@ __device__ __forceinline__ void tile_rows(const SpmvParams& p, const TX* x, int6
     }
 }
 
-template <typename TX, bool DFM, bool SRHT>
+// tile_rows on the SELL-32 layout: warp w's 32 rows rbase + 256 e + 32 w + lane are one slice, so
+// every load of entry t is one contiguous access and no row pointers are read.  Entries are
+// multiplied and added exactly as in tile_rows (first RB alternately into two chains, the rest
+// into the first); padding entries (value 0) add exact zeros, so the results are bit-identical.
+template <typename TX, bool DFM>
+__device__ __forceinline__ void tile_rows_sell(const SpmvParams& p, const TX* x, int64_t rbase,
+                                               typename std::conditional<DFM, df, double>::type z[4]) {
+    using AR = SpmvArith<TX, DFM>;
+    using V = typename AR::V;
+    using XV = typename AR::XV;
+    const int lane = threadIdx.x & 31;
+    const V* sval = reinterpret_cast<const V*>(p.sval);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int64_t s = (rbase + (int64_t)TILE_THREADS * e + (threadIdx.x & ~31)) >> 5;   // warp-uniform
+        V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
+        if (s < p.nslices) {
+            const int64_t q0 = __ldg(p.soff + s);
+            const int width = (int)((__ldg(p.soff + s + 1) - q0) >> 5);
+            int c[RB];
+            V v[RB];
+            XV xv[RB];
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+                if (t < width) {
+                    const int64_t q = q0 + 32 * t + lane;
+                    c[t] = __ldg(p.scol + q);
+                    v[t] = sval[q];
+                }
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+                if (t < width) xv[t] = AR::xload(x, c[t]);
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+                if (t < width) {
+                    if (t & 1) acc1 = AR::madd(acc1, v[t], xv[t]);
+                    else acc0 = AR::madd(acc0, v[t], xv[t]);
+                }
+            for (int t = RB; t < width; ++t) {
+                const int64_t q = q0 + 32 * t + lane;
+                acc0 = AR::madd(acc0, sval[q], AR::xload(x, __ldg(p.scol + q)));
+            }
+        }
+        z[e] = FW<V>::add(acc0, acc1);
+        const int64_t r = rbase + threadIdx.x + (int64_t)TILE_THREADS * e;
+        if (r < p.n) {
+            if constexpr (DFM) {
+                reinterpret_cast<df*>(p.w)[r] = z[e];
+            } else {
+                if (p.yscale) z[e] *= *p.yscale;
+                reinterpret_cast<double*>(p.w)[r] = z[e];
+            }
+        } else {
+            z[e] = FW<V>::zero();
+        }
+    }
+}
+
+template <typename TX, bool DFM, bool SRHT, bool SELL = false>
 __global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams p) {
     using V = typename std::conditional<DFM, df, double>::type;
     using F = FW<V>;
@@ -162,7 +263,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         const int64_t rbase = (int64_t)tile * TILE;
         V z[4];
-        tile_rows<TX, DFM, 1>(p, x, rbase, z);
+        if constexpr (SELL) tile_rows_sell<TX, DFM>(p, x, rbase, z);
+        else tile_rows<TX, DFM, 1>(p, x, rbase, z);
         if (SRHT) {
             // the transform takes rows 4t .. 4t+3 in thread t: transpose through shared memory
             __syncthreads();                           // the previous tile's readers of zt are done
@@ -386,9 +488,9 @@ __global__ void jacobi_scale_kernel(int64_t nnz, const int32_t* __restrict__ col
         out[e] = val[e] * dinv[colind[e]];
 }
 
-template <typename TX, bool DFM, bool SRHT>
+template <typename TX, bool DFM, bool SRHT, bool SELL = false>
 void launch_spmv_t(rgs_context* ctx, const SpmvParams& p, int grid, size_t smem) {
-    auto kern = spmv_sketch_kernel<TX, DFM, SRHT>;
+    auto kern = spmv_sketch_kernel<TX, DFM, SRHT, SELL>;
     if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, TILE_THREADS, smem, ctx->stream>>>(p);
     RGS_CUDA(cudaGetLastError());
@@ -416,7 +518,8 @@ int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm) {
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
 int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const void* x, int xtype, void* w, int dfm,
-                    const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale) {
+                    const rgs_sketch_obj* sk, double* partials, const int* ctl, const double* yscale,
+                    const SellView* sell) {
     SpmvParams p{};
     RGS_REQUIRE(!(dfm && yscale), "scaled products are FP64 only");
     p.yscale = yscale;
@@ -438,6 +541,23 @@ int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const v
     }
     const int grid = rgs_spmv_nparts(ctx, A.n, dfm != 0);
     const size_t smem = srht ? TILE * 8 + (size_t)p.k * 8 + (size_t)((p.k + 3) & ~3) * 4 + 16 : 16;
+    if (sell && srht) {
+        RGS_REQUIRE(sell->nslices == (A.n + 31) / 32, "SELL layout of another operator");
+        p.nslices = sell->nslices;
+        p.soff = sell->off;
+        p.scol = sell->col;
+        p.sval = sell->val;
+        if (dfm) {
+            RGS_REQUIRE(xtype != RGS_F64, "double-float product needs an FP32 or BF16 vector");
+            if (xtype == RGS_F32) launch_spmv_t<float, true, true, true>(ctx, p, grid, smem);
+            else launch_spmv_t<__nv_bfloat16, true, true, true>(ctx, p, grid, smem);
+        } else {
+            if (xtype == RGS_F64) launch_spmv_t<double, false, true, true>(ctx, p, grid, smem);
+            else if (xtype == RGS_F32) launch_spmv_t<float, false, true, true>(ctx, p, grid, smem);
+            else launch_spmv_t<__nv_bfloat16, false, true, true>(ctx, p, grid, smem);
+        }
+        return grid;
+    }
     if (dfm) {
         RGS_REQUIRE(xtype != RGS_F64, "double-float product needs an FP32 or BF16 vector");
         if (xtype == RGS_F32) {
@@ -460,6 +580,54 @@ int rgs_launch_spmv(rgs_context* ctx, const rgs_csr& A, const void* vdf, const v
         }
     }
     return grid;
+}
+
+bool rgs_build_sell(rgs_context* ctx, const rgs_csr& A, int dfm, SellBuf& sb) {
+    const int64_t ns = (A.n + 31) / 32;
+    if (ns == 0) return false;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ns * 32 + 255) / 256, 4 * ctx->num_sms));
+    DevBuf wd;
+    wd.ensure(sizeof(int32_t) * (size_t)ns);
+    sell_width_kernel<<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, ns, wd.as<int32_t>());
+    RGS_CUDA(cudaGetLastError());
+    std::vector<int32_t> width((size_t)ns);
+    RGS_CUDA(cudaMemcpyAsync(width.data(), wd.ptr, sizeof(int32_t) * (size_t)ns, cudaMemcpyDeviceToHost, ctx->stream));
+    RGS_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<int64_t> off((size_t)ns + 1);
+    off[0] = 0;
+    for (int64_t q = 0; q < ns; ++q) off[q + 1] = off[q] + 32 * (int64_t)width[q];
+    if (off[ns] > A.nnz + A.nnz / 4) return false;
+    sb.off.ensure(sizeof(int64_t) * (size_t)(ns + 1));
+    RGS_CUDA(cudaMemcpyAsync(sb.off.ptr, off.data(), sizeof(int64_t) * (size_t)(ns + 1), cudaMemcpyHostToDevice,
+                             ctx->stream));
+    sb.col.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(off[ns], 1));
+    sb.val.ensure(8 * (size_t)std::max<int64_t>(off[ns], 1));
+    if (dfm)
+        sell_fill_kernel<true><<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, A.val, sb.off.as<int64_t>(), ns,
+                                                              sb.col.as<int32_t>(), sb.val.ptr);
+    else
+        sell_fill_kernel<false><<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, A.val, sb.off.as<int64_t>(), ns,
+                                                               sb.col.as<int32_t>(), sb.val.ptr);
+    RGS_CUDA(cudaGetLastError());
+    RGS_CUDA(cudaStreamSynchronize(ctx->stream));          // the host offsets are read by the copy
+    ctx->launches += 2;
+    sb.nslices = ns;
+    sb.entries = off[ns];
+    return true;
+}
+
+void rgs_fill_sell_values(rgs_context* ctx, const rgs_csr& A, const double* val, int dfm, const SellBuf& sb,
+                          DevBuf& out) {
+    out.ensure(8 * (size_t)std::max<int64_t>(sb.entries, 1));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((sb.nslices * 32 + 255) / 256, 4 * ctx->num_sms));
+    if (dfm)
+        sell_fill_kernel<true><<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, val, sb.off.as<int64_t>(),
+                                                              sb.nslices, nullptr, out.ptr);
+    else
+        sell_fill_kernel<false><<<grid, 256, 0, ctx->stream>>>(A.n, A.rowptr, A.colind, val, sb.off.as<int64_t>(),
+                                                               sb.nslices, nullptr, out.ptr);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
 }
 
 int rgs_norm_grid(const rgs_context* ctx, int64_t n) {

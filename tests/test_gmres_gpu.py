@@ -257,3 +257,84 @@ def test_c3_full_size_true_residual(h):
     print(f"128^3: {res['total_steps']} steps, reported {res['rel_residual']:.3e}, recomputed {true_rel:.3e}")
     assert res["converged"] and true_rel <= 1e-8
     assert abs(true_rel - res["rel_residual"]) <= 1e-3 * true_rel
+
+
+@pytest.mark.parametrize("qdtype,fine", [(torch.float32, "df"), (torch.float32, "ls64"), (torch.float64, "f64"),
+                                         (torch.bfloat16, "df")])
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_sell_product_bit_identical_to_csr(h, qdtype, fine, jacobi, monkeypatch):
+    """The fused product reads A in SELL-32 form (slices of 32 rows, entry-major, padding within
+    nnz / 4): the same products and sums in the same order as from CSR, so one fixed RGMRES cycle
+    gives bit-identical x whichever layout it read (RGS_SELL=0 keeps CSR), also for A D^{-1}."""
+    csr = synth.convdiff_3d(18, 30.0, 1.0, 3, 5)           # 5832 rows: slices with 4-7 nonzeros
+    A = sp.csr_matrix((csr[2], csr[1], csr[0]))
+    n = A.shape[0]
+    b = dev(synth.rhs(n, 11))
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, "srht", n, 80, 6)
+    rgs.rgmres_set_preconditioner(h, "jacobi" if jacobi else "none")
+    out = {}
+    try:
+        for layout in ("sell", "csr"):
+            if layout == "csr":
+                monkeypatch.setenv("RGS_SELL", "0")
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            res = rgs.rgmres_solve(h, sk, C, b, x, restart=25, max_cycles=2, qdtype=qdtype, fixed_steps=True,
+                                   fine64=fine == "f64" and qdtype != torch.float64, ls64=fine == "ls64")
+            out[layout] = (x.cpu().numpy(), res)
+    finally:
+        rgs.rgmres_set_preconditioner(h, "none")
+    assert out["sell"][1]["sell"] and not out["csr"][1]["sell"]
+    assert np.array_equal(out["sell"][0], out["csr"][0])
+    assert out["sell"][1]["history"] == out["csr"][1]["history"]
+
+
+def test_sell_falls_back_to_csr_for_uneven_rows(h):
+    """Rows of very different lengths (one dense row per slice) would pad SELL-32 past nnz / 4:
+    the solver keeps CSR and still matches the oracle."""
+    n = 640
+    rows, cols = [], []
+    for r in range(n):
+        rows.append(r); cols.append(r)
+        if r % 32 == 0:
+            for c in range(0, n, 7):
+                if c != r:
+                    rows.append(r); cols.append(c)
+        elif r + 1 < n:
+            rows.append(r); cols.append(r + 1)
+    vals = np.where(np.array(rows) == np.array(cols), 4.0, -0.01)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    csr = (A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+    b = synth.rhs(n, 12)
+    (rp, ci, va), C = rgs.csr_to_device(*csr)
+    sk = rgs.rgs_sketch_create(h, "srht", n, 60, 7)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=15, max_cycles=1, qdtype=torch.float64, fixed_steps=True)
+    ref = og.rgmres(A, b, Sketch("srht", n, 60, 7), restart=15, max_cycles=1, fixed_steps=True)
+    assert not res["sell"]
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-10
+
+
+@pytest.mark.parametrize("qdtype,tol", [(torch.float64, 1e-8), (torch.float32, 1e-4)])
+def test_rgmres_redraws_theta_after_a_stalled_cycle(h, qdtype, tol):
+    """From a residual the SRHT cannot see (b - A x0 = D H e_j, j not sampled, plus a small visible
+    part; the oracle's restart pins), the first cycle leaves the true residual where it was, so the
+    solver draws Theta anew with the oracle's seed rule (seed + 0x9E3779B97F4A7C15): the residual
+    after the second cycle matches the oracle's, and the solve converges."""
+    from test_oracle_restart_refresh import stalled_start
+    A, b, sk_o, x0, _ = stalled_start()
+    n = A.shape[0]
+    (rp, ci, va), C = rgs.csr_to_device(A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data)
+    sk = rgs.rgs_sketch_create(h, "srht", n, 60, 3)
+    x = dev(x0)
+    res = rgs.rgmres_solve(h, sk, C, dev(b), x, restart=20, rtol=1e-8, max_cycles=300, qdtype=qdtype)
+    ref = og.rgmres(A, b, sk_o, restart=20, tol=1e-8, max_cycles=300, x0=x0,
+                    storage="f64" if qdtype == torch.float64 else "f32")
+    hist = res["history"]
+    print(f"{qdtype}: gpu cycles {res['cycles']} refreshes {res['sketch_refreshes']} history {hist[:4]}; "
+          f"oracle cycles {ref.cycles} refreshes {ref.refreshes} {ref.true_residuals[:4]}")
+    assert hist[1] >= (1.0 - 2.0 ** -10) * hist[0] and hist[2] < 0.5 * hist[1]
+    assert abs(hist[2] - ref.true_residuals[2]) <= tol * ref.true_residuals[2]
+    assert res["converged"] and res["sketch_refreshes"] >= 1
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
