@@ -20,11 +20,35 @@ __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, dou
     const int lane = threadIdx.x & 31;
     const int T = (j + 31) / 32;                 // rotations per lane
     const int t0 = lane * T, t1 = min(j, t0 + T);
+    const double gj = g[j];                      // issued with the loads below, used at the end
+    constexpr int TR = 4;                        // up to 4 rotations a lane (j <= 128): every load
+    double cr[TR], sr[TR], hr[TR];               // issued at once and kept in registers
+    if (T <= TR) {
+#pragma unroll
+        for (int q = 0; q < TR; ++q) {
+            const int t = t0 + q;
+            const bool ok = t < t1;
+            cr[q] = ok ? cs[t] : 1.0;
+            sr[q] = ok ? sn[t] : 0.0;
+            hr[q] = ok ? hcol(t + 1) : 0.0;
+        }
+    }
+    const double h0 = hcol(0);
     double A = 1.0, B = 0.0;                     // composition of the lane's maps, in order
-    for (int t = t0; t < t1; ++t) {
-        const double a = -sn[t], b = cs[t] * hcol(t + 1);
-        B = fma(a, B, b);
-        A = a * A;
+    if (T <= TR) {
+#pragma unroll
+        for (int q = 0; q < TR; ++q)
+            if (t0 + q < t1) {
+                const double a = -sr[q], b = cr[q] * hr[q];
+                B = fma(a, B, b);
+                A = a * A;
+            }
+    } else {
+        for (int t = t0; t < t1; ++t) {
+            const double a = -sn[t], b = cs[t] * hcol(t + 1);
+            B = fma(a, B, b);
+            A = a * A;
+        }
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {           // inclusive scan: lane L = M_L o ... o M_0
@@ -36,17 +60,25 @@ __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, dou
     }
     double Ae = __shfl_up_sync(FULL, A, 1), Be = __shfl_up_sync(FULL, B, 1);
     if (lane == 0) { Ae = 1.0; Be = 0.0; }
-    double carry = fma(Ae, hcol(0), Be);
-    for (int t = t0; t < t1; ++t) {
-        const double h1 = hcol(t + 1);
-        Hr[(size_t)j * ldh + t] = fma(cs[t], carry, sn[t] * h1);
-        carry = fma(-sn[t], carry, cs[t] * h1);
+    double carry = fma(Ae, h0, Be);
+    if (T <= TR) {
+#pragma unroll
+        for (int q = 0; q < TR; ++q)
+            if (t0 + q < t1) {
+                Hr[(size_t)j * ldh + t0 + q] = fma(cr[q], carry, sr[q] * hr[q]);
+                carry = fma(-sr[q], carry, cr[q] * hr[q]);
+            }
+    } else {
+        for (int t = t0; t < t1; ++t) {
+            const double h1 = hcol(t + 1);
+            Hr[(size_t)j * ldh + t] = fma(cs[t], carry, sn[t] * h1);
+            carry = fma(-sn[t], carry, cs[t] * h1);
+        }
     }
     const double x = __shfl_sync(FULL, carry, 31);   // entry j after G_0..G_{j-1}
     const double y = hcol(j + 1);
     const double d = hypot(x, y);
     const double c = d == 0.0 ? 1.0 : x / d, s = d == 0.0 ? 0.0 : y / d;
-    const double gj = g[j];
     __syncwarp();
     if (lane == 0) {
         cs[j] = c;

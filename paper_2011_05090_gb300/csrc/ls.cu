@@ -400,6 +400,18 @@ __device__ __forceinline__ void richardson_phases(const LSState& st, const LSSte
     if (tr) tr[9] = globaltimer();
 }
 
+// GMRES (one warp): rotates H(:, i-1) = [R(0:i, i); r_ii] by the stored rotations, forms the next
+// one and updates g; sets the stop word when the least-squares residual reaches the tolerance
+// or the launch found a breakdown.
+__device__ __forceinline__ void givens_and_stop(const LSState& st, const LSStep& a, double r, int* ctl,
+                                                bool breakdown) {
+    const int i = a.i;
+    const double* rc = st.R + (size_t)i * st.ldr;
+    auto hcol = [&](int t) { return t < i ? rc[t] : r; };
+    const double res = givens_column_warp(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, st.mmax);
+    if (threadIdx.x == 0 && (breakdown || res <= a.stop_tol)) atomicCAS(ctl + kStopWord, 0, i);
+}
+
 template <class A>
 __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     using T = typename A::T;
@@ -611,14 +623,13 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
         const bool breakdown = code == 2;
         if (a.givens) {
-            // GMRES: H(:, i-1) = R(0:i+1, i) (Sec. 4.1) is complete now that r_ii is known
+            // GMRES: H(:, i-1) = R(0:i+1, i) (Sec. 4.1) is complete now that r_ii is known.  Its
+            // rotation runs in phase 4, on a CTA without columns there while i < G, so that no
+            // phase waits for it; a breakdown ends the launch here, so it runs now.
             if (i == 0) {
                 if (gtid == 0) st.g[0] = r;
-            } else if (blockIdx.x == G - 1 && tid < 32) {
-                const double* rc = st.R + (size_t)i * st.ldr;
-                auto hcol = [&](int t) { return t < i ? rc[t] : r; };
-                const double res = givens_column_warp(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, mm);
-                if (tid == 0 && (breakdown || res <= a.stop_tol)) atomicCAS(ctl + kStopWord, 0, i);
+            } else if (breakdown && blockIdx.x == G - 1 && tid < 32) {
+                givens_and_stop(st, a, r, ctl, true);
             }
         }
         if (breakdown) {
@@ -685,6 +696,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
 
     // ---- phase 4: per column j < i, the dots the new reflector needs that do not depend on beta:
     //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
+    //   (and GMRES's rotation of H(:, i-1), by warp 0 of the last CTA)
+    if (a.givens && i > 0 && blockIdx.x == G - 1 && tid < 32) givens_and_stop(st, a, r, ctl, false);
     {
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
         for (int base = 0; base < i; base += G * (NW / 4)) {

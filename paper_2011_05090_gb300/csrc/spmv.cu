@@ -246,14 +246,17 @@ __device__ __forceinline__ void tile_rows_sell(const SpmvParams& p, const TX* x,
     }
 }
 
+// FP64 values (DFM false) need more registers than 4 CTAs per SM leave (64): 3 CTAs, no spills.
 template <typename TX, bool DFM, bool SRHT, bool SELL = false>
-__global__ void __launch_bounds__(TILE_THREADS, 4) spmv_sketch_kernel(SpmvParams p) {
+__global__ void __launch_bounds__(TILE_THREADS, DFM ? 4 : 3) spmv_sketch_kernel(SpmvParams p) {
     using V = typename std::conditional<DFM, df, double>::type;
     using F = FW<V>;
     extern __shared__ __align__(16) double smem[];
     V* zt = reinterpret_cast<V*>(smem);
     V* part = zt + TILE;
     int32_t* srow = reinterpret_cast<int32_t*>(part + (SRHT ? p.k : 0));
+    pdl_wait();                        // the basis column and status of the kernel before
+    pdl_launch_dependents();
     if (p.ctl != nullptr && (p.ctl[kStatusWord] != 0 || p.ctl[kStopWord] != 0)) return;
     const TX* x = reinterpret_cast<const TX*>(p.x);
     if (SRHT) {
@@ -492,8 +495,19 @@ template <typename TX, bool DFM, bool SRHT, bool SELL = false>
 void launch_spmv_t(rgs_context* ctx, const SpmvParams& p, int grid, size_t smem) {
     auto kern = spmv_sketch_kernel<TX, DFM, SRHT, SELL>;
     if (smem > 48 * 1024) RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, TILE_THREADS, smem, ctx->stream>>>(p);
-    RGS_CUDA(cudaGetLastError());
+    // programmatic serialization: scheduled while the kernel before is finishing (its CTAs wait
+    // in pdl_wait for its completion)
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TILE_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = ctx->pdl ? 1 : 0;
+    RGS_CUDA(cudaLaunchKernelEx(&cfg, kern, p));
     ctx->launches++;
 }
 
@@ -506,14 +520,14 @@ void rgs_csr_split_df(rgs_context* ctx, const double* val, int64_t nnz, void* ou
     ctx->launches++;
 }
 
-// One wave of resident CTAs: 4 per SM (64 registers).  Measured on the 128^3 RGMRES step:
+// One wave of resident CTAs: 4 per SM with double-float values (64 registers), 3 with FP64 values
+// (80 registers: at 64 they spill).  Measured on the 128^3 RGMRES step (double-float):
 // one row at a time at 4 CTAs per SM 178.0 us per step, at 3 CTAs per SM 184.7-185.5; two rows
 // in flight at 2 CTAs per SM (128 registers) 193.1, two rows at 3 CTAs per SM (spilling) 197.6,
 // four rows at 1 CTA per SM 226.8: occupancy hides the gathers better than rows in flight.
 int rgs_spmv_nparts(const rgs_context* ctx, int64_t n, bool dfm) {
-    (void)dfm;
     const int ntiles = (int)((n + TILE - 1) / TILE);
-    return std::max(1, std::min(ntiles, ctx->num_sms * 4));
+    return std::max(1, std::min(ntiles, ctx->num_sms * (dfm ? 4 : 3)));   // one wave (launch bounds)
 }
 
 // w = A x (x in xtype; w FP64, or double-float when dfm), with SRHT partial sketches of w when sk != NULL.
