@@ -14,16 +14,22 @@ namespace rgsdev {
 // Column j of H has entries hcol(0..j+1).  Rotates it by G_0..G_{j-1} (cs, sn), forms G_j,
 // updates g (g[j], g[j+1]) and writes the rotated column to Hr(:, j) (ld ldh).  Returns
 // |g[j+1]|, the residual norm of the least-squares problem after j+1 columns, in every lane.
-template <class HF>
+// REG: for j <= 128, issue every load at once and keep the lane's rotations in registers (for
+// callers with registers to spare; the same arithmetic either way).
+template <bool REG = false, class HF>
 __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, double* g, double* Hr, int ldh) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int T = (j + 31) / 32;                 // rotations per lane
     const int t0 = lane * T, t1 = min(j, t0 + T);
-    const double gj = g[j];                      // issued with the loads below, used at the end
+    double gj = 0.0, h0 = 0.0;
+    if (REG) {                                   // issued with the loads below, used at the end
+        gj = g[j];
+        h0 = hcol(0);
+    }
     constexpr int TR = 4;                        // up to 4 rotations a lane (j <= 128): every load
     double cr[TR], sr[TR], hr[TR];               // issued at once and kept in registers
-    if (T <= TR) {
+    if (REG && T <= TR) {
 #pragma unroll
         for (int q = 0; q < TR; ++q) {
             const int t = t0 + q;
@@ -33,9 +39,8 @@ __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, dou
             hr[q] = ok ? hcol(t + 1) : 0.0;
         }
     }
-    const double h0 = hcol(0);
     double A = 1.0, B = 0.0;                     // composition of the lane's maps, in order
-    if (T <= TR) {
+    if (REG && T <= TR) {
 #pragma unroll
         for (int q = 0; q < TR; ++q)
             if (t0 + q < t1) {
@@ -60,8 +65,8 @@ __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, dou
     }
     double Ae = __shfl_up_sync(FULL, A, 1), Be = __shfl_up_sync(FULL, B, 1);
     if (lane == 0) { Ae = 1.0; Be = 0.0; }
-    double carry = fma(Ae, h0, Be);
-    if (T <= TR) {
+    double carry = fma(Ae, REG ? h0 : hcol(0), Be);
+    if (REG && T <= TR) {
 #pragma unroll
         for (int q = 0; q < TR; ++q)
             if (t0 + q < t1) {
@@ -79,6 +84,7 @@ __device__ double givens_column_warp(int j, HF hcol, double* cs, double* sn, dou
     const double y = hcol(j + 1);
     const double d = hypot(x, y);
     const double c = d == 0.0 ? 1.0 : x / d, s = d == 0.0 ? 0.0 : y / d;
+    if (!REG) gj = g[j];
     __syncwarp();
     if (lane == 0) {
         cs[j] = c;

@@ -408,7 +408,7 @@ __device__ __forceinline__ void givens_and_stop(const LSState& st, const LSStep&
     const int i = a.i;
     const double* rc = st.R + (size_t)i * st.ldr;
     auto hcol = [&](int t) { return t < i ? rc[t] : r; };
-    const double res = givens_column_warp(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, st.mmax);
+    const double res = givens_column_warp<true>(i - 1, hcol, st.cs, st.sn, st.g, st.Hr, st.mmax);
     if (threadIdx.x == 0 && (breakdown || res <= a.stop_tol)) atomicCAS(ctl + kStopWord, 0, i);
 }
 
