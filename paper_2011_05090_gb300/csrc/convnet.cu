@@ -1,10 +1,11 @@
 // The learned preconditioner: six 3x3 convolutions (2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
 // between layers, zero padding) on H x W grids, with hand-written forward and backward kernels.
 //
-//  - conv3x3_mma_kernel: the convolution as an implicit GEMM (pixels x (tap, c_in) times
-//    (tap, c_in) x c_out) on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation).  A CTA
-//    stages an 8 x 16 pixel tile with its one-pixel halo and the layer's weights in shared memory
-//    (channel strides padded so fragment loads are bank-conflict free).  The same kernel computes
+//  - conv3x3_tc_kernel: the convolution as an implicit GEMM (pixels x (tap, c_in) times
+//    (tap, c_in) x c_out) on the tcgen05 tensor cores (BF16 operands from shared memory, FP32
+//    accumulator in TMEM, one M = 128 pixels x N = c_out x K = 16 MMA per tap and channel step).
+//    A CTA stages an 8 x 16 pixel tile's halo (three column-shifted copies, so that every tap's
+//    operand is a plain descriptor into them) and the layer's weights.  The same kernel computes
 //    the backward pass for the activations: the gradient of a layer's input is the convolution of
 //    the output gradient with the taps flipped and c_in / c_out swapped, masked by ReLU'.
 //  - dweight_mma_kernel: weight and bias gradients (sums over all pixels of the batch) as
@@ -40,7 +41,6 @@ int64_t param_offset(int l) {
 }
 int64_t total_params() { return param_offset(NL); }
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -57,96 +57,214 @@ struct ConvArgs {
     void* out;            // MODE 0, 2: NHWC bf16 with CO channels; MODE 1: FP32 [b][y][x] (channel 0)
     const bf16* mask;     // MODE 2: NHWC bf16 with CO channels; output zeroed where mask <= 0
     const float* scale;   // MODE 1: optional per-sample factor
+    int* status;          // the handle's status word: RGS_ERR_TIMEOUT if the tensor-core wait ran out
     int H, W;
 };
 
+// ------------------------------------------------------------------ tcgen05 building blocks
+// Shared-memory matrix descriptor of a K-major operand without swizzle: core matrices of 8 rows x
+// 16 bytes stored contiguously (128 bytes), LBO = byte distance between K-adjacent core matrices,
+// SBO = between row-adjacent (8-row groups) ones; descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 32 (NC = 32) or 16 FP32 accumulator columns of TMEM lane (taddr's lane + thread's lane)
+template <int NC>
+__device__ __forceinline__ void tc_ld(uint32_t taddr, float (&v)[NC]) {
+    uint32_t r[NC];
+    if constexpr (NC == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// Shared memory of conv3x3_tc_kernel: three copies of the input halo (columns shifted by dx = 0, 1,
+// 2), the weights, the mbarrier and the TMEM address.
+template <int CS, int NP>
+struct ConvTcSmem {
+    static constexpr int C8 = CS / 8;
+    static constexpr int COPY = (TH + 2) * 2 * C8 * 128;        // bytes of one halo copy
+    static constexpr int A_BYTES = 3 * COPY;                    // one tile's halo copies (two buffers)
+    static constexpr int B_BYTES = 9 * (NP / 8) * C8 * 128;
+    static constexpr int BYTES = 2 * A_BYTES + B_BYTES + 16;
+};
+
+// 16-byte asynchronous copy global -> shared; bytes = 0 writes zeros (the source is not read).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc), "r"(bytes)
+                 : "memory");
+}
+
 // MODE 0: bias + ReLU, BF16 out.  MODE 1: bias, FP32 channel 0 out (times scale).  MODE 2: ReLU'
-// mask (backward for the activations), BF16 out.
-template <int CS, int NT, int MODE>
-__global__ void __launch_bounds__(128) conv3x3_mma_kernel(ConvArgs a) {
-    constexpr int HS = CS + 8;          // padded stride: fragment loads hit 32 distinct banks
-    constexpr int CO = NT * 8;
-    __shared__ __align__(16) bf16 sx[(TH + 2) * (TW + 2) * HS];
-    __shared__ __align__(16) bf16 sw[9 * CO * HS];
-    const int b = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+// mask (backward for the activations), BF16 out.  The 3x3 convolution of 8 x 16 pixel tiles as
+// an implicit GEMM on tcgen05: D (128 pixels x NP channels, FP32 in TMEM) = sum over the 9 taps
+// and the CS / 16 channel steps of A_tap (pixels x 16 input channels) B_tap^T (NP output channels
+// x 16 input channels), one M = 128, N = NP, K = 16 MMA each, issued by one thread.  A_tap is
+// addressed inside a halo copy: copy dx stores the halo rows hy = 0..9 as two octets of 8 pixels
+// (columns x0 - 1 + dx + 8 xo + 0..7) of 8-channel core matrices, so the pixels (y, x) of the
+// tile at tap (dy, dx) are the octets (y + dy) * 2 + xo: an 8-row-group stride of C8 * 128 bytes
+// from the start 2 dy C8 * 128.  NP: CO rounded up to 16 (zero weight rows).  The CTAs are
+// persistent over tiles: the weights are staged once; the halo of a tile is staged by
+// asynchronous copies (all of a thread's copies in flight at once) into one of two buffers while
+// the tensor core works on the previous tile, whose MMAs commit to an mbarrier (one phase per
+// tile) before the epilogue reads the accumulator from TMEM.
+template <int CS, int CO, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a, int B) {
+    constexpr int NP = CO < 16 ? 16 : CO;
+    using SM = ConvTcSmem<CS, NP>;
+    constexpr int C8 = SM::C8;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sB = smem + 2 * SM::A_BYTES;                        // halo buffers 0, 1 first
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * SM::A_BYTES + SM::B_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bf16* X = a.x + (size_t)b * a.H * a.W * CS;
-    for (int c = tid; c < (TH + 2) * (TW + 2) * (CS / 8); c += 128) {
-        const int pix = c / (CS / 8), ch = (c % (CS / 8)) * 8;
-        const int hy = pix / (TW + 2), hx = pix % (TW + 2);
-        const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-            v = *reinterpret_cast<const uint4*>(X + ((size_t)gy * a.W + gx) * CS + ch);
-        *reinterpret_cast<uint4*>(sx + pix * HS + ch) = v;
-    }
-    for (int c = tid; c < 9 * CO * (CS / 8); c += 128) {
-        const int row = c / (CS / 8), ch = (c % (CS / 8)) * 8;
-        *reinterpret_cast<uint4*>(sw + row * HS + ch) = *reinterpret_cast<const uint4*>(a.w + (size_t)row * CS + ch);
-    }
-    __syncthreads();
-    float acc[2][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-        for (int kc = 0; kc < CS; kc += 16) {
-            uint32_t afr[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const bf16* base = sx + ((warp * 2 + mt + dy) * (TW + 2) + dx) * HS + kc + 2 * t;
-                afr[mt][0] = ld32(base + g * HS);
-                afr[mt][1] = ld32(base + (g + 8) * HS);
-                afr[mt][2] = ld32(base + g * HS + 8);
-                afr[mt][3] = ld32(base + (g + 8) * HS + 8);
-            }
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const bf16* wb = sw + (tap * CO + nt * 8 + g) * HS + kc + 2 * t;
-                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], afr[mt], b0, b1);
-            }
+    const int tilesx = a.W / TW, tilesy = a.H / TH, ntiles = tilesx * tilesy * B;
+    // the halo copies of tile t into buffer buf: chunk (dx, hy, xo, c8, px) = 8 channels of one
+    // input pixel (zeros outside the grid), by asynchronous copies
+    auto stage_halo = [&](int t, int buf) {
+        const int b = t / (tilesx * tilesy), r = t % (tilesx * tilesy);
+        const int y0 = (r / tilesx) * TH, x0 = (r % tilesx) * TW;
+        const bf16* X = a.x + (size_t)b * a.H * a.W * CS;
+        unsigned char* sA = smem + buf * SM::A_BYTES;
+        for (int c = tid; c < 3 * (TH + 2) * 2 * C8 * 8; c += 128) {
+            const int px = c & 7, c8 = (c >> 3) % C8, oct = (c >> 3) / C8;    // oct = (dx, hy, xo)
+            const int xo = oct & 1, hy = (oct >> 1) % (TH + 2), dx = (oct >> 1) / (TH + 2);
+            const int gy = y0 - 1 + hy, gx = x0 - 1 + dx + 8 * xo + px;
+            const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+            cp_async16(sA + dx * SM::COPY + ((hy * 2 + xo) * C8 + c8) * 128 + px * 16,
+                       in ? X + ((size_t)gy * a.W + gx) * CS + c8 * 8 : X, in ? 16 : 0);
         }
+    };
+    // the weights, once: chunk (tap, n8, c8, row) = 8 input channels of output channel 8 n8 + row
+    for (int c = tid; c < 9 * (NP / 8) * C8 * 8; c += 128) {
+        const int row = c & 7, c8 = (c >> 3) % C8, tn = (c >> 3) / C8;      // tn = tap * (NP / 8) + n8
+        const int n8 = tn % (NP / 8), tap = tn / (NP / 8);
+        const int co = n8 * 8 + row;
+        cp_async16(sB + ((tn * C8) + c8) * 128 + row * 16, co < CO ? a.w + ((size_t)tap * CO + co) * CS + c8 * 8 : a.w,
+                   co < CO ? 16 : 0);
     }
+    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+    bool ok = true;
+    uint32_t phase = 0;
+    int buf = 0;
+    if (blockIdx.x < ntiles) stage_halo(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, phase ^= 1u, buf ^= 1) {
+        const int b = t / (tilesx * tilesy), r = t % (tilesx * tilesy);
+        const int y0 = (r / tilesx) * TH, x0 = (r % tilesx) * TW;
+        unsigned char* sA = smem + buf * SM::A_BYTES;
+        asm volatile("cp.async.wait_all;" ::: "memory");        // the weights and tile t's halo
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the operands, for the tensor core
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(sA), b0 = (uint32_t)__cvta_generic_to_shared(sB);
+            constexpr uint32_t idesc = tc_idesc_bf16(128, NP);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int y = y0 + warp * 2 + mt;
+                for (int kk = 0; kk < CS / 16; ++kk) {
+                    const uint64_t ad = tc_sdesc(a0 + dx * SM::COPY + 2 * dy * C8 * 128 + kk * 256, 128, C8 * 128);
+                    const uint64_t bd = tc_sdesc(b0 + tap * (NP / 8) * C8 * 128 + kk * 256, 128, C8 * 128);
+                    tc_mma(taddr, ad, bd, idesc, (tap | kk) != 0 ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                         : "memory");
+        }
+        // the next tile's halo into the other buffer, while the tensor core works on this one (that
+        // buffer's last reader, the MMAs of the previous tile, completed in the previous iteration)
+        if (t + (int)gridDim.x < ntiles) stage_halo(t + gridDim.x, buf ^ 1);
+        // bounded wait for this tile's MMAs; a wait that runs out records RGS_ERR_TIMEOUT and ends
+        // the CTA's tiles (decided for the whole CTA: every thread leaves the loop together)
+        uint32_t seen = 0;
+        for (int it = 0; it < (1 << 22) && !seen; ++it)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(seen) : "r"(mbar_a), "r"(phase) : "memory");
+        const bool done = __syncthreads_and((int)seen) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!done) {
+            if (tid == 0 && a.status) atomicCAS(a.status, 0, (int)RGS_ERR_TIMEOUT);
+            ok = false;
+        } else {
+            float acc[NP];
+            tc_ld<NP>(taddr + ((uint32_t)(warp * 32) << 16), acc);    // TMEM lanes 32 warp .. = pixels
+            const int p = warp * 32 + lane, y = y0 + p / TW, x = x0 + p % TW;
+            const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+            if constexpr (MODE == 1) {
+                const float sc = a.scale ? a.scale[b] : 1.f;
+                reinterpret_cast<float*>(a.out)[pix] = (acc[0] + a.bias[0]) * sc;
+            } else {
+                bf16* o = reinterpret_cast<bf16*>(a.out) + pix * CO;
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int co = nt * 8 + 2 * t;
+                for (int c = 0; c < CO; c += 8) {
+                    float v[8];
+                    if constexpr (MODE == 0) {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int x = x0 + g + 8 * half;
-                const size_t pix = ((size_t)b * a.H + y) * a.W + x;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (MODE == 0) {
-                    v0 = fmaxf(v0 + a.bias[co], 0.f);
-                    v1 = fmaxf(v1 + a.bias[co + 1], 0.f);
-                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(a.out) + pix * CO + co) =
-                        __floats2bfloat162_rn(v0, v1);
-                } else if (MODE == 1) {
-                    if (co == 0) {
-                        const float s = a.scale ? a.scale[b] : 1.f;
-                        reinterpret_cast<float*>(a.out)[pix] = (v0 + a.bias[0]) * s;
+                        for (int e = 0; e < 8; ++e) v[e] = fmaxf(acc[c + e] + a.bias[c + e], 0.f);
+                    } else {
+                        const uint4 mk = __ldg(reinterpret_cast<const uint4*>(a.mask + pix * CO + c));
+                        const bf16* m = reinterpret_cast<const bf16*>(&mk);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(m[e]) > 0.f ? acc[c + e] : 0.f;
                     }
-                } else {
-                    const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * CO + co);
-                    if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
-                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(a.out) + pix * CO + co) =
-                        __floats2bfloat162_rn(v0, v1);
+                    uint4 pk;
+                    __nv_bfloat162* q = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) q[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                    *reinterpret_cast<uint4*>(o + c) = pk;
                 }
             }
         }
+        // TMEM is reused by the next tile only after every thread has read it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr) : "memory");
 }
 
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const bf16* p) {
@@ -467,9 +585,20 @@ __global__ void init_kernel(float* __restrict__ p, int64_t off, int64_t nw, int6
 }
 
 template <int CS, int NT, int MODE>
-void launch_conv(rgs_context* ctx, const ConvArgs& a, int B) {
-    dim3 grid(a.W / TW, a.H / TH, B);
-    conv3x3_mma_kernel<CS, NT, MODE><<<grid, 128, 0, ctx->stream>>>(a);
+void launch_conv(rgs_context* ctx, const ConvArgs& a0, int B) {
+    constexpr int CO = NT * 8, NP = CO < 16 ? 16 : CO;
+    constexpr int smem = ConvTcSmem<CS, NP>::BYTES;
+    ConvArgs a = a0;
+    a.status = ctx->ctl.as<int>() + kStatusWord;
+    auto kern = conv3x3_tc_kernel<CS, CO, MODE>;
+    RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // one wave of resident CTAs: as many per SM as the shared memory holds, at most 8 (8 x 32 TMEM
+    // columns of the 512)
+    const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1024)));
+    const int ntiles = (a.W / TW) * (a.H / TH) * B;
+    const int grid = std::max(1, std::min(ntiles, per_sm * ctx->num_sms));
+    kern<<<grid, 128, smem, ctx->stream>>>(a, B);
     RGS_CUDA(cudaGetLastError());
     ctx->launches++;
 }
