@@ -238,7 +238,11 @@ RGS_API rgs_status rgs_arnoldi_basis(rgs_arnoldi a, void** Q, int64_t* ldq);
  * rgmres_solve: restarted randomized GMRES (Sec. 4.2, Eq. hls) on A x = b with
  * the RGS-Arnoldi basis; in each cycle y = argmin ||H z - r_11 e_1|| by Givens
  * rotations in FP64, x += Q y, and the true residual b - A x is recomputed in
- * FP64 (restarting is not in the paper, which runs one cycle).
+ * FP64 (restarting is not in the paper, which runs one cycle).  A cycle that
+ * leaves ||b - A x|| without a relative decrease of 2^-10 draws a new Theta (same
+ * kind, n and k; the r-th with seed + r * 0x9E3779B97F4A7C15 mod 2^64) for the
+ * following cycles (rgmres_info.sketch_refreshes).  With an SRHT sketch the
+ * products with A read it in SELL-32 form, built once per call (rgmres_info.sell).
  * cgs2_gmres_solve: the same restarted GMRES with an l2-orthonormal FP64 basis
  * built by CGS2 (projector (I - Q Q^T)^2, Sec. 1.2): the comparator.
  * b, x: device FP64 (x holds x0 on entry, the solution on exit).
