@@ -39,6 +39,7 @@ struct DevBuf {
         ptr = nullptr;
         bytes = 0;
         if (cudaMalloc(&ptr, want) != cudaSuccess) {
+            cudaGetLastError();            // not sticky: keep it from surfacing at a later launch check
             ptr = nullptr;
             throw RgsError{RGS_ERR_ALLOC, "cudaMalloc of " + std::to_string(want) + " bytes failed"};
         }

@@ -433,7 +433,16 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         SellView sview, sview_pc;
         const char* sell_env = std::getenv("RGS_SELL");
         const int dfm = sketch_is_df(&obj) ? 1 : 0;
-        if (s->kind == RGS_SKETCH_SRHT && !(sell_env && sell_env[0] == '0') && rgs_build_sell(h, *A, dfm, sell)) {
+        bool use_sell = false;
+        if (s->kind == RGS_SKETCH_SRHT && !(sell_env && sell_env[0] == '0')) {
+            try {                              // no room for the SELL-32 copy: the CSR product
+                use_sell = rgs_build_sell(h, *A, dfm, sell);
+            } catch (const RgsError& e) {
+                if (e.status != RGS_ERR_ALLOC) throw;
+                use_sell = false;
+            }
+        }
+        if (use_sell) {
             sview.nslices = sell.nslices;
             sview.off = sell.off.as<int64_t>();
             sview.col = sell.col.as<int32_t>();
