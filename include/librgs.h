@@ -52,7 +52,8 @@ typedef enum {
     RGS_ERR_TIMEOUT = 6,         /* a device-side grid barrier gave up waiting */
     RGS_ERR_NONFINITE = 7,       /* NaN or Inf met in a sketched norm */
     RGS_ERR_NOT_IMPLEMENTED = 8,
-    RGS_ERR_CERT_FAILED = 9      /* rgs_certify_embedding: omega_bar >= 1, no embedding certificate */
+    RGS_ERR_CERT_FAILED = 9,     /* rgs_certify_embedding: omega_bar >= 1, no embedding certificate */
+    RGS_ERR_CALLBACK = 10        /* a caller's preconditioner callback returned nonzero */
 } rgs_status;
 
 typedef enum { RGS_F64 = 0, RGS_F32 = 1, RGS_BF16 = 2 } rgs_dtype;
@@ -305,16 +306,41 @@ RGS_API rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double
  *                               the H x W grid of the unknowns; nonlinear, so flexible = 1 is
  *                               required and the solver keeps z_j = M(q_j) (flexible GMRES,
  *                               x = x0 + Z y).  params points to an rgs_learned_precond.
- * With the learned preconditioner set, a restart whose true residual is not below (1 - 2^-10)
- * times the previous one switches the rest of the solve to the unpreconditioned method
- * (rgmres_info.fallback_cycle); Jacobi is never switched off.
+ *   RGS_PRECOND_CALLBACK     -- the caller's M (an incomplete factorisation, say: Sec. 5.3 uses
+ *                               ILU(0)); params points to an rgs_callback_precond.  The solver calls
+ *                               apply(user, n, v, vtype, z, ztype, stream) from the calling thread
+ *                               between its launches; apply enqueues z = M(v) on stream (the
+ *                               handle's cudaStream_t) and returns 0, or nonzero to end the solve
+ *                               with RGS_ERR_CALLBACK.  v (read only) and z are device vectors of n
+ *                               entries, z never overlapping v; vtype is the basis storage type
+ *                               (RGS_F64 for the vector Q y below), ztype is RGS_F64 for an FP64
+ *                               basis and RGS_F32 otherwise.  flexible = 1 keeps every z_j = M(q_j)
+ *                               (n (restart + 1) entries of ztype; x = x0 + Z y; any M); flexible =
+ *                               0 is for a linear M: one z per step and x = x0 + M (Q y) after each
+ *                               cycle.  nonlinear = 1 puts M under the fallback rule below.
+ * With the learned preconditioner set (or a callback with nonlinear = 1), a restart whose true
+ * residual is not below (1 - 2^-10) times the previous one switches the rest of the solve to the
+ * unpreconditioned method (rgmres_info.fallback_cycle); Jacobi is never switched off.
  * The handle keeps the pointers in params (not copies): keep them valid while solving. */
-typedef enum { RGS_PRECOND_NONE = 0, RGS_PRECOND_JACOBI = 1, RGS_PRECOND_LEARNED_CONV = 2 } rgs_precond_kind;
+typedef enum {
+    RGS_PRECOND_NONE = 0,
+    RGS_PRECOND_JACOBI = 1,
+    RGS_PRECOND_LEARNED_CONV = 2,
+    RGS_PRECOND_CALLBACK = 3
+} rgs_precond_kind;
 typedef struct rgs_convnet_obj* rgs_convnet;
 typedef struct {
     rgs_convnet net;
     const double* logkappa;   /* device, H x W (row-major, x fastest): second input channel */
 } rgs_learned_precond;
+typedef int32_t (*rgs_precond_apply_fn)(void* user, int64_t n, const void* v, int32_t vtype, void* z,
+                                        int32_t ztype, void* stream);
+typedef struct {
+    rgs_precond_apply_fn apply;
+    void* user;               /* passed through unchanged */
+    int32_t nonlinear;        /* 1: the fallback rule applies to M */
+    int32_t reserved;         /* 0 */
+} rgs_callback_precond;
 RGS_API rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void* params,
                                              int32_t flexible);
 

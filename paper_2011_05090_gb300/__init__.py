@@ -41,6 +41,7 @@ RGS_ERR_TIMEOUT = 6
 RGS_ERR_NONFINITE = 7
 RGS_ERR_NOT_IMPLEMENTED = 8
 RGS_ERR_CERT_FAILED = 9
+RGS_ERR_CALLBACK = 10
 
 RGS_F64, RGS_F32, RGS_BF16 = 0, 1, 2
 RGS_SKETCH_GAUSSIAN, RGS_SKETCH_SRHT = 0, 1
@@ -52,7 +53,7 @@ RGS_FP32_FINE = 16              # rgs_qr: unique precision, FP32 transform sums 
 RGS_LS_RICHARDSON = 32          # rgs_qr: step 2 by two Richardson sweeps on the normal equations
 RGS_QR_FP64_FINE = RGS_FP64_FINE
 RGS_QR_FP64_SKETCH = RGS_FP64_FINE
-RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV = 0, 1, 2
+RGS_PRECOND_NONE, RGS_PRECOND_JACOBI, RGS_PRECOND_LEARNED_CONV, RGS_PRECOND_CALLBACK = 0, 1, 2, 3
 
 _DTYPE = {torch.float64: RGS_F64, torch.float32: RGS_F32, torch.bfloat16: RGS_BF16}
 _KIND = {"gaussian": RGS_SKETCH_GAUSSIAN, "srht": RGS_SKETCH_SRHT}
@@ -113,6 +114,16 @@ class Tuning(ctypes.Structure):
 
 class LearnedPrecond(ctypes.Structure):
     _fields_ = [("net", ctypes.c_void_p), ("logkappa", ctypes.c_void_p)]
+
+
+# int32_t apply(void* user, int64_t n, const void* v, int32_t vtype, void* z, int32_t ztype, void* stream)
+PrecondApplyFn = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p)
+
+
+class CallbackPrecond(ctypes.Structure):
+    _fields_ = [("apply", PrecondApplyFn), ("user", ctypes.c_void_p), ("nonlinear", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -423,11 +434,15 @@ def _gmres_result(st, info, hist, h):
            "history": [hist[i] for i in range(info.cycles + 1)], "fallback_cycle": info.fallback_cycle,
            "sell": bool(info.sell), "sketch_refreshes": info.sketch_refreshes}
     if st not in (RGS_OK, RGS_ERR_NOT_CONVERGED):
+        errors = getattr(h, "_precond_errors", None)
+        cause = errors[0] if st == RGS_ERR_CALLBACK and errors else None
+        if errors:
+            errors.clear()
         try:
             _check(st, h)
         except RgsError as e:
             e.info = res
-            raise
+            raise e from cause
     return res
 
 
@@ -569,12 +584,60 @@ def csr_to_device(rowptr, colind, val, device="cuda"):
 
 
 # ------------------------------------------------------------------ preconditioning
-def rgmres_set_preconditioner(h, kind, net=None, logkappa=None, flexible=False):
+class _DeviceVector:
+    """A device vector the library owns, seen as a torch tensor without a copy (torch takes no
+    read-only flag: the callback's contract says v is not written)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+def _device_tensor(ptr, n, dtype):
+    if dtype == RGS_BF16:      # no BF16 type string in the array interface: view the 16-bit words
+        return torch.as_tensor(_DeviceVector(ptr, n, "<i2"), device="cuda").view(torch.bfloat16)
+    return torch.as_tensor(_DeviceVector(ptr, n, {RGS_F64: "<f8", RGS_F32: "<f4"}[dtype]), device="cuda")
+
+
+def _precond_trampoline(fn, errors):
+    """The C callback around ``fn(v, z)``: v (read only) and z are torch views of the library's
+    device vectors, and fn runs with the handle's stream as torch's current stream.  An exception
+    is kept in ``errors`` and returned as a nonzero status (the solve then fails with
+    RGS_ERR_CALLBACK and the binding re-raises it)."""
+    def apply(user, n, v, vtype, z, ztype, stream):
+        try:
+            vt = _device_tensor(v, n, vtype)
+            zt = _device_tensor(z, n, ztype)
+            ts = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(ts):
+                fn(vt, zt)
+            return 0
+        except BaseException as e:          # noqa: BLE001 - carried back across the C frame
+            errors.append(e)
+            return 1
+    return PrecondApplyFn(apply)
+
+
+def rgmres_set_preconditioner(h, kind, net=None, logkappa=None, flexible=False, apply=None, nonlinear=False):
     """Select the right preconditioner of the following rgmres_solve calls on ``h``:
-    "none", "jacobi" or "learned" (a ConvNet and its log-kappa grid, FP64 on the device; flexible)."""
-    k = {"none": RGS_PRECOND_NONE, "jacobi": RGS_PRECOND_JACOBI, "learned": RGS_PRECOND_LEARNED_CONV}[kind]
+    "none", "jacobi", "learned" (a ConvNet and its log-kappa grid, FP64 on the device; flexible)
+    or "callback": ``apply(v, z)`` writes z = M(v) with torch operations on the current stream
+    (v of the basis type, or FP64 for the end-of-cycle vector Q y when not flexible; z FP64 for
+    an FP64 basis, else FP32).  ``flexible`` keeps every z; a linear M may run without it.
+    ``nonlinear`` puts M under the fallback rule of the learned preconditioner."""
+    k = {"none": RGS_PRECOND_NONE, "jacobi": RGS_PRECOND_JACOBI, "learned": RGS_PRECOND_LEARNED_CONV,
+         "callback": RGS_PRECOND_CALLBACK}[kind]
     params = None
-    if k == RGS_PRECOND_LEARNED_CONV:
+    if k == RGS_PRECOND_CALLBACK:
+        if apply is None:
+            raise ValueError("the callback preconditioner needs apply(v, z)")
+        errors = []
+        fnp = _precond_trampoline(apply, errors)
+        h._precond = CallbackPrecond(fnp, None, 1 if nonlinear else 0, 0)
+        h._precond_refs = (fnp, apply)          # the C function pointer must outlive the solves
+        h._precond_errors = errors
+        params = ctypes.byref(h._precond)
+    elif k == RGS_PRECOND_LEARNED_CONV:
         if logkappa.dtype != torch.float64 or not logkappa.is_cuda or not logkappa.is_contiguous():
             raise ValueError("logkappa must be a contiguous FP64 CUDA tensor")
         h._precond = LearnedPrecond(net.ptr, logkappa.data_ptr())

@@ -128,6 +128,7 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
     const int nbk = (m + kBucket - 1) / kBucket;
     struct Acc {
         double start = 0, work[4] = {0}, skew[4] = {0}, lat[4] = {0}, tail = 0, total = 0, psum_med = 0, psum_max = 0;
+        double item[4] = {0};   // first item: start -> sums, -> barrier, -> warp 0's totals, -> end of the items
         int n = 0, nq[4] = {0};
     };
     std::vector<Acc> acc(nbk);
@@ -155,6 +156,20 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
         }
         c.psum_med += median(w) * 1e-3;
         c.psum_max += *std::max_element(w.begin(), w.end()) * 1e-3;
+        for (int q = 0; q < 3; ++q) {                              // inside the first item (CTAs with one)
+            std::vector<double> u;
+            for (int b = 0; b < grid; ++b) {
+                const unsigned long long s1 = at(b, 11 + q), s0 = q == 0 ? at(b, 0) : at(b, 10 + q);
+                if (s1 != 0 && s0 != 0 && s1 >= s0) u.push_back((double)(s1 - s0));
+            }
+            if (!u.empty()) c.item[q] += median(u) * 1e-3;
+        }
+        {
+            std::vector<double> u;
+            for (int b = 0; b < grid; ++b)
+                if (at(b, 13) != 0 && at(b, 10) >= at(b, 13)) u.push_back((double)(at(b, 10) - at(b, 13)));
+            if (!u.empty()) c.item[3] += median(u) * 1e-3;
+        }
         for (int q = 0; q < 4; ++q) {
             if (at(0, 1 + 2 * q) == 0) break;                      // this launch had fewer barriers
             for (int b = 0; b < grid; ++b) {
@@ -176,8 +191,9 @@ void rgs_print_ls_trace(rgs_context* h, int m, int grid) {
         const Acc& c = acc[bk];
         if (c.n == 0) continue;
         std::fprintf(stderr, "[rgs trace] least squares, columns [%d,%d), %d CTAs (us): start spread %.2f; "
-                     "partial sums median %.2f, max %.2f", bk * kBucket, std::min(m, (bk + 1) * kBucket), grid,
-                     c.start / c.n, c.psum_med / c.n, c.psum_max / c.n);
+                     "partial sums median %.2f, max %.2f (first item: sums %.2f, barrier %.2f, totals %.2f, rest %.2f)",
+                     bk * kBucket, std::min(m, (bk + 1) * kBucket), grid, c.start / c.n, c.psum_med / c.n,
+                     c.psum_max / c.n, c.item[0] / c.n, c.item[1] / c.n, c.item[2] / c.n, c.item[3] / c.n);
         for (int q = 0; q < 4; ++q)
             if (c.nq[q] > 0)
                 std::fprintf(stderr, "; phase %d work %.2f, last arrival +%.2f, barrier %.2f", q, c.work[q] / c.nq[q],
@@ -200,6 +216,7 @@ const char* rgs_status_string(rgs_status s) {
         case RGS_ERR_NONFINITE: return "non-finite value";
         case RGS_ERR_NOT_IMPLEMENTED: return "not implemented";
         case RGS_ERR_CERT_FAILED: return "no embedding certificate (omega_bar >= 1)";
+        case RGS_ERR_CALLBACK: return "the preconditioner callback failed";
     }
     return "unknown status";
 }

@@ -73,6 +73,7 @@ struct rgs_context {
     int precond_flexible = 0;
     void* precond_net = nullptr;           // RGS_PRECOND_LEARNED_CONV: the network
     const double* precond_field = nullptr; // and its second input channel (log kappa, H x W)
+    rgs_callback_precond precond_cb{};     // RGS_PRECOND_CALLBACK: the caller's apply function
     DevBuf batch_theta;    // rgmres_solve_batched: shared BF16 Gaussian G (k x n)
     uint64_t batch_theta_seed = ~0ull;
     int batch_theta_k = 0;
@@ -416,6 +417,8 @@ void rgs_launch_residual(rgs_context* ctx, const rgs_csr& A, const double* x, co
 void rgs_launch_norm(rgs_context* ctx, int64_t n, const double* v, double* part, double* norm_out);
 void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype, int64_t ldq, const double* cy,
                            double* x, const int* ctl, const double* rowscale = nullptr);
+// x += z (z FP32 or FP64, n entries), skipped when the status word is set
+void rgs_launch_add_vector(rgs_context* ctx, int64_t n, const void* z, int ztype, double* x, const int* ctl);
 void rgs_launch_jacobi_setup(rgs_context* ctx, const rgs_csr& A, double* dinv, double* scaled_val);
 // convnet.cu: z = M(x) = ||x|| net(x / ||x||, log kappa) for one grid vector x (xtype), z FP32
 void rgs_convnet_apply_precond(rgs_context* ctx, void* net, const double* logkappa, const void* x, int xtype, float* z);
@@ -477,7 +480,8 @@ int rgs_ls_grid(const rgs_context* ctx);
 // RGS_TRACE: summary of the least-squares timestamps of launches 0..m-1 on stderr
 void rgs_print_ls_trace(rgs_context* h, int m, int grid);
 // least-squares trace per CTA: start, (arrival, departure) at each of up to four grid barriers, end,
-// end of phase 0's partial sums
-constexpr int kLsTraceSlots = 11;
+// end of phase 0's partial sums; inside the CTA's first phase-0 item: thread 0's sums done, shared
+// sums visible, warp 0's totals done
+constexpr int kLsTraceSlots = 14;
 void rgs_launch_certificates(rgs_context* ctx, const double* S, int k, int m, const double* R, int64_t ldr,
                              const double* P, double* out2 /* device: delta, delta_tilde */, double* work);

@@ -43,7 +43,9 @@ struct rgs_arnoldi_obj {
     DevBuf vdf;              // A's values split into double-float pairs
     DevBuf work;             // r (n), norm partials, scalars
     DevBuf jac;              // Jacobi: diag(A)^{-1} (n) and the values of A D^{-1} (nnz)
-    DevBuf Z;                // flexible preconditioning: z'_i = M(q'_i), n x mmax FP32
+    DevBuf Z;                // flexible preconditioning: z'_i = M(q'_i), n x mmax FP32 (a caller's
+                             // M: FP64 for an FP64 basis; one column when it is not flexible)
+    DevBuf pct;              // a caller's linear M, not flexible: Q y (FP64, n) at the end of a cycle
     const SellView* sell = nullptr;        // A in SELL-32 form for the fused product (rgmres_solve)
     unsigned long long* trace = nullptr;   // RGS_TRACE: least-squares timestamps of step i at
     size_t tstride = 0;                    // trace + i * tstride (the latest cycle's steps)
@@ -406,11 +408,26 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         // Right preconditioning A M, x = x0 + M (Q y) (Sec. 5.3 preconditions A_f P_f from the right).
         // Jacobi, M = D^{-1}: the Arnoldi operator is A D^{-1} (column-scaled values), and the
         // solution update applies D^{-1}.  Learned network (nonlinear): flexible GMRES, z'_i = M(q'_i)
-        // kept in Z, w' = A z'_i and x = x0 + Z y.
+        // kept in Z, w' = A z'_i and x = x0 + Z y.  A caller's M: the same when flexible, else
+        // one z per step and x = x0 + M (Q y).
         const int pk = h->precond_kind;
-        RGS_REQUIRE(pk == RGS_PRECOND_NONE || pk == RGS_PRECOND_JACOBI || pk == RGS_PRECOND_LEARNED_CONV,
+        RGS_REQUIRE(pk == RGS_PRECOND_NONE || pk == RGS_PRECOND_JACOBI || pk == RGS_PRECOND_LEARNED_CONV ||
+                        pk == RGS_PRECOND_CALLBACK,
                     "unknown preconditioner");
         const bool learned = pk == RGS_PRECOND_LEARNED_CONV;
+        const bool callback = pk == RGS_PRECOND_CALLBACK;
+        const bool cb_flex = callback && h->precond_flexible != 0;
+        const rgs_callback_precond cb = h->precond_cb;
+        const int ztype = obj.qtype == RGS_F64 ? RGS_F64 : RGS_F32;
+        auto apply_cb = [&](const void* v, int vtype, void* z) {
+            const int32_t rc = cb.apply(cb.user, s->n, v, vtype, z, ztype, (void*)h->stream);
+            if (rc != 0) throw RgsError{RGS_ERR_CALLBACK, "preconditioner callback returned " + std::to_string(rc)};
+        };
+        if (callback) {
+            RGS_REQUIRE(cb.apply != nullptr, "preconditioner callback not set");
+            obj.Z.ensure((size_t)dsize(ztype) * (size_t)obj.ldq * (cb_flex ? obj.mmax : 1));
+            if (!cb_flex) obj.pct.ensure(sizeof(double) * (size_t)s->n);
+        }
         rgs_csr Apc = *A;
         const double* dinv = nullptr;
         if (pk == RGS_PRECOND_JACOBI) {
@@ -467,6 +484,11 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
         int fallback_cycle = -1;
         // w' = A M q'_i (or A q'_i once the preconditioner is off), with its sketch
         auto product = [&](int i, bool sketch) -> int {
+            if (use_pc && callback) {
+                char* z = obj.Z.as<char>() + (cb_flex ? (size_t)dsize(ztype) * (size_t)i * obj.ldq : 0);
+                apply_cb(obj.Q.as<char>() + dsize(obj.qtype) * (size_t)i * obj.ldq, obj.qtype, z);
+                return launch_product(&obj, *A, i, z, ztype, sketch);
+            }
             if (use_pc && learned) {
                 float* z = obj.Z.as<float>() + (size_t)i * obj.ldq;
                 rgs_convnet_apply_precond(h, h->precond_net, h->precond_field,
@@ -571,7 +593,7 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
             // progress) turns it off; the unpreconditioned method finishes the solve.  A fixed linear
             // preconditioner (Jacobi) is kept: its slow cycles are the restarted method's, not its own.
             const bool stalled = cycles > 0 && !(rel < prev_rel * (1.0 - 0x1p-10));
-            if (use_pc && learned && stalled) {
+            if (use_pc && (learned || (callback && cb.nonlinear)) && stalled) {
                 use_pc = false;
                 fallback_cycle = cycles;
             } else if (stalled) {
@@ -605,7 +627,15 @@ rgs_status rgmres_solve(rgs_handle h, rgs_sketch s, const rgs_csr* A, const doub
                                   h->ctl.as<int>());
             if (use_pc && learned)
                 rgs_launch_sol_update(h, s->n, obj.Z.ptr, RGS_F32, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>());
-            else
+            else if (use_pc && cb_flex)
+                rgs_launch_sol_update(h, s->n, obj.Z.ptr, ztype, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>());
+            else if (use_pc && callback) {                 // x += M (Q y)
+                double* t = obj.pct.as<double>();
+                RGS_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * (size_t)s->n, h->stream));
+                rgs_launch_sol_update(h, s->n, obj.Q.ptr, obj.qtype, obj.ldq, cy_buf(&obj), t, h->ctl.as<int>());
+                apply_cb(t, RGS_F64, obj.Z.ptr);
+                rgs_launch_add_vector(h, s->n, obj.Z.ptr, ztype, x, h->ctl.as<int>());
+            } else
                 rgs_launch_sol_update(h, s->n, obj.Q.ptr, obj.qtype, obj.ldq, cy_buf(&obj), x, h->ctl.as<int>(),
                                       use_pc ? dinv : nullptr);
             ++cycles;
@@ -768,8 +798,16 @@ rgs_status cgs2_gmres_solve(rgs_handle h, const rgs_csr* A, const double* b, dou
 rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const void* params, int32_t flexible) {
     if (!h) return RGS_ERR_INVALID_ARG;
     return guarded(h, [&] {
-        RGS_REQUIRE(kind == RGS_PRECOND_NONE || kind == RGS_PRECOND_JACOBI || kind == RGS_PRECOND_LEARNED_CONV,
+        RGS_REQUIRE(kind == RGS_PRECOND_NONE || kind == RGS_PRECOND_JACOBI || kind == RGS_PRECOND_LEARNED_CONV ||
+                        kind == RGS_PRECOND_CALLBACK,
                     "unknown preconditioner kind");
+        rgs_callback_precond cb{};
+        if (kind == RGS_PRECOND_CALLBACK) {
+            RGS_REQUIRE(params != nullptr, "the callback preconditioner needs rgs_callback_precond parameters");
+            cb = *static_cast<const rgs_callback_precond*>(params);
+            RGS_REQUIRE(cb.apply != nullptr, "null apply function");
+            RGS_REQUIRE(flexible || !cb.nonlinear, "a nonlinear preconditioner needs flexible GMRES (flexible = 1)");
+        }
         if (kind == RGS_PRECOND_LEARNED_CONV) {
             RGS_REQUIRE(params != nullptr, "the learned preconditioner needs rgs_learned_precond parameters");
             RGS_REQUIRE(flexible, "a nonlinear preconditioner needs flexible GMRES (flexible = 1)");
@@ -781,6 +819,7 @@ rgs_status rgmres_set_preconditioner(rgs_handle h, rgs_precond_kind kind, const 
             h->precond_net = nullptr;
             h->precond_field = nullptr;
         }
+        h->precond_cb = cb;
         h->precond_kind = kind;
         h->precond_flexible = flexible;
     });

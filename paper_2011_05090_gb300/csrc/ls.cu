@@ -484,8 +484,10 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
             } else if (warp == 0 && l < k) {
                 part = A::from_d(a.p_vec[l]);
             }
+            if (tr && it == (int)blockIdx.x) tr[11] = globaltimer();   // this thread's sums
             if (sl == 0) shP[warp * 32 + rl] = part;
             __syncthreads();
+            if (tr && it == (int)blockIdx.x) tr[12] = globaltimer();
             if (warp == 0) {
                 const int lw = seg * R + lane;           // lanes 0..R-1: the segment's rows
                 const bool own = lane < R && lw < k;
@@ -513,6 +515,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                     if (vec == 0) nrm_s += sq; else nrm_p += sq;
                 }
             }
+            if (tr && it == (int)blockIdx.x) tr[13] = globaltimer();
             __syncthreads();                               // shP is reused by the next item
         }
         if (tr) tr[10] = globaltimer();

@@ -5,7 +5,8 @@
 //    pre-split into float pairs (the paper allows a coarser matvec than u_fine as long as its
 //    error stays O(u_crs), Sec. 4.1); with an FP64 basis everything is FP64.
 //  - residual_kernel: r = b - A x in FP64 with per-CTA partial sums of r^2 (restart residual).
-//  - sol_update_kernel: x += Q' cy (the GMRES solution update at the end of a cycle).
+//  - sol_update_kernel: x += Q' cy (the GMRES solution update at the end of a cycle);
+//    add_vector_kernel: x += z (a caller's preconditioner output, x = x0 + M (Q y)).
 //  - hess_solve_kernel: y from the Givens-rotated Hessenberg system (one warp).
 //  - multidot / axpy-style kernels for the CGS2 passes h = V^T w, w -= V h.
 #include "fwht.cuh"
@@ -369,6 +370,14 @@ __global__ void __launch_bounds__(256) sol_update_kernel(int64_t n, const TQ* __
     }
 }
 
+template <class TZ>
+__global__ void __launch_bounds__(256) add_vector_kernel(int64_t n, const TZ* __restrict__ z, double* __restrict__ x,
+                                                         const int* ctl) {
+    if (ctl[kStatusWord] != 0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)z[i];
+}
+
 // Back substitution on the rotated Hessenberg factor: Hr(0:j, 0:j) y = g(0:j), cy = sigma .* y.
 // One warp; j = ctl[kStopWord] if the cycle stopped early, else jmax.  Writes ctl[kStepsWord] = j.
 __global__ void hess_solve_kernel(const double* __restrict__ Hr, int ldh, const double* __restrict__ g,
@@ -678,6 +687,15 @@ void rgs_launch_sol_update(rgs_context* ctx, int64_t n, const void* Q, int qtype
     else
         sol_update_kernel<__nv_bfloat16><<<grid, 256, 0, ctx->stream>>>(n, (const __nv_bfloat16*)Q, ldq, cy, x, ctl,
                                                                          rowscale);
+    RGS_CUDA(cudaGetLastError());
+    ctx->launches++;
+}
+
+void rgs_launch_add_vector(rgs_context* ctx, int64_t n, const void* z, int ztype, double* x, const int* ctl) {
+    RGS_REQUIRE(ztype == RGS_F64 || ztype == RGS_F32, "z must be FP64 or FP32");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms));
+    if (ztype == RGS_F64) add_vector_kernel<double><<<grid, 256, 0, ctx->stream>>>(n, (const double*)z, x, ctl);
+    else add_vector_kernel<float><<<grid, 256, 0, ctx->stream>>>(n, (const float*)z, x, ctl);
     RGS_CUDA(cudaGetLastError());
     ctx->launches++;
 }

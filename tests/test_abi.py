@@ -86,9 +86,55 @@ def _header_constants():
 def test_binding_constants_match_the_header():
     consts = _header_constants()
     for must in ("RGS_OK", "RGS_ERR_BREAKDOWN", "RGS_F32", "RGS_SKETCH_SRHT", "RGS_QR_FP64_FINE",
-                 "RGS_QR_FP64_SKETCH", "RGS_PRECOND_LEARNED_CONV", "RGS_NOALLOC_SCRATCH_BYTES"):
+                 "RGS_QR_FP64_SKETCH", "RGS_PRECOND_LEARNED_CONV", "RGS_PRECOND_CALLBACK", "RGS_ERR_CALLBACK",
+                 "RGS_NOALLOC_SCRATCH_BYTES"):
         assert must in consts, must
     for name, val in consts.items():
         if hasattr(rgs, name):
             assert getattr(rgs, name) == val, name
     assert all(hasattr(rgs, n) for n in consts if n.startswith(("RGS_ERR_", "RGS_QR_", "RGS_SKETCH_")))
+
+
+_STRUCTS = [("rgs_qr_info", rgs.QRInfo), ("rgs_csr", rgs.CSR), ("rgmres_opts", rgs.GmresOpts),
+            ("rgmres_info", rgs.GmresInfo), ("rgmres_batch_opts", rgs.BatchOpts), ("rgs_tuning", rgs.Tuning),
+            ("rgs_learned_precond", rgs.LearnedPrecond), ("rgs_callback_precond", rgs.CallbackPrecond)]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (a C program
+    compiled against librgs.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "librgs.h"', "int main(void) {"]
+    for cname, py in _STRUCTS:
+        lines.append(f'    printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, timeout=120)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True, timeout=60).stdout.split("\n") if line)
+    for cname, py in _STRUCTS:
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, f"{cname}.{fname}"
+
+
+def test_precond_trampoline_turns_an_exception_into_a_status():
+    """The binding's C callback never lets a Python exception cross the C frame: it returns 1 and
+    keeps the exception for the solve's error (with or without a GPU)."""
+    errors = []
+
+    def fn(v, z):
+        raise ValueError("planted")
+
+    cb = rgs._precond_trampoline(fn, errors)
+    assert cb(None, 0, 0, rgs.RGS_F32, 0, rgs.RGS_F32, None) == 1
+    assert len(errors) == 1 and isinstance(errors[0], Exception)
