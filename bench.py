@@ -783,7 +783,8 @@ def run_ours(args):
         e_s = max_over_ranks(1e3 * sum(e_times) / len(e_times), world, "cuda") * 1e-3   # slowest rank
         e2e = {"value": world * total / e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * n * m,
                "d2h_bytes_per_step": 4 * n * m + 8 * m * m + 8 * m, "ms_per_step": 1e3 * e_s,
-               "ms_per_step_median": 1e3 * statistics.median(e_times), "steps": len(e_times)}
+               "ms_per_step_median": 1e3 * statistics.median(e_times), "steps": len(e_times),
+               "ms_steps": [round(1e3 * t, 1) for t in e_times]}
         del Wh, Qh
 
     # the same factorization with the other fine arithmetics: everything fine in FP64, and

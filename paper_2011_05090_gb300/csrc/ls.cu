@@ -697,15 +697,50 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         return;
     }
 
+    // The new reflector's scalars (one warp): totals SG, CR of phase 3's sums; alpha, beta, tau,
+    // vs and the solve's y_i.  They need nothing of phase 4, so while i <= 3G/2 warp 12 (of the
+    // fourth quad, which has no column there while i <= 3G) forms them during phase 4, hidden
+    // behind the column owners' dots, and the last phase loses the chain (about 1.2 us a launch
+    // at i < G).  With more columns per CTA the chain's FP64 instructions share the SM's FP64
+    // pipe with the dots and lengthen phase 4 by more than they save (measured from i = 300 at
+    // k = 2000); there warp 0 forms them in phase 5.  Same code, same roundings.
+    auto reflector_scalars = [&]() {
+        T alpha = zero, ypi0 = zero;
+        if (lane == 0) {                               // issued before the totals' round trip
+            alpha = A::ld(st.ys + i);
+            ypi0 = sol ? A::ld(st.yp + i) : zero;
+        }
+        T SG, CR;
+        warp_total2<A>(st.blk, 2, SG, CR);
+        if (lane == 0) {
+            T beta, tau, vs;
+            if (A::is_zero(SG)) {
+                beta = alpha; tau = zero; vs = zero;
+            } else {
+                const T nrm = A::sqrt_(A::add(A::mul(alpha, alpha), SG));
+                beta = A::nonneg(alpha) ? A::neg(nrm) : nrm;
+                tau = A::div(A::sub(beta, alpha), beta);
+                vs = A::div(A::one(), A::sub(alpha, beta));
+            }
+            scT[0] = beta; scT[1] = tau; scT[2] = vs;
+            scT[3] = sol ? A::sub(ypi0, A::mul(tau, A::add(ypi0, A::mul(CR, vs)))) : zero;
+        }
+    };
+    static_assert(NW == 16, "phase 4 runs four quads of four warps");
+    const bool early_scalars = 2 * i <= 3 * G;
+
     // ---- phase 4: per column j < i, the dots the new reflector needs that do not depend on beta:
     //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
     //   (and GMRES's rotation of H(:, i-1), by warp 0 of the last CTA)
     if (a.givens && i > 0 && blockIdx.x == G - 1 && tid < 32) givens_and_stop(st, a, r, ctl, false);
+    if (early_scalars && i == 0 && warp == 12) reflector_scalars();   // no column at all
     {
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
         for (int base = 0; base < i; base += G * (NW / 4)) {
             const int j = base + blockIdx.x + G * quad;
-            if (j < i) {
+            if (early_scalars && warp == 12) {             // quad 3 has no column: j >= 3G >= i
+                reflector_scalars();
+            } else if (j < i) {
                 const double* v = st.V + (size_t)j * k;
                 const int len = k - (i + 1), seg = (max(len, 0) + 3) / 4;
                 const int l0 = i + 1 + qw * seg, l1 = min(k, l0 + seg);
@@ -762,31 +797,10 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (!bar.sync(ctl, tr ? tr + 7 : nullptr)) return;
 
     // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    // Warp 0 forms the reflector's scalars (totals SG, CR; alpha, beta, tau, vs) while warps
-    // 1..15 compute, per column j < i, the two dots of T(j, i) = -tau (a_j + vs b_j) with
-    // a_j = sum_l T(j,l) V(i,l) and b_j = sum_l T(j,l) zp_l (l in [j, i)), which need neither.
-    if (warp == 0) {
-        T alpha = zero, ypi0 = zero;
-        if (lane == 0) {                               // issued before the totals' round trip
-            alpha = A::ld(st.ys + i);
-            ypi0 = sol ? A::ld(st.yp + i) : zero;
-        }
-        T SG, CR;
-        warp_total2<A>(st.blk, 2, SG, CR);
-        if (lane == 0) {
-            T beta, tau, vs;
-            if (A::is_zero(SG)) {
-                beta = alpha; tau = zero; vs = zero;
-            } else {
-                const T nrm = A::sqrt_(A::add(A::mul(alpha, alpha), SG));
-                beta = A::nonneg(alpha) ? A::neg(nrm) : nrm;
-                tau = A::div(A::sub(beta, alpha), beta);
-                vs = A::div(A::one(), A::sub(alpha, beta));
-            }
-            scT[0] = beta; scT[1] = tau; scT[2] = vs;
-            scT[3] = sol ? A::sub(ypi0, A::mul(tau, A::add(ypi0, A::mul(CR, vs)))) : zero;
-        }
-    }
+    // Warps 1..15 compute, per column j < i, the two dots of T(j, i) = -tau (a_j + vs b_j) with
+    // a_j = sum_l T(j,l) V(i,l) and b_j = sum_l T(j,l) zp_l (l in [j, i)), which need none of
+    // the reflector's scalars; warp 0 forms those here unless warp 12 did in phase 4.
+    if (warp == 0 && !early_scalars) reflector_scalars();
     const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
     auto tdots = [&](int j, T& da, T& db) {
         const double* tr = st.TT + (size_t)j * mm;
