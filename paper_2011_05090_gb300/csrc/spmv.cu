@@ -70,6 +70,13 @@ template <typename TX> __device__ __forceinline__ float xf(const TX* x, int c) {
     else return (float)x[c];
 }
 
+// x[c] through the read-only path (x is not written by the kernel that reads it)
+template <typename TX> __device__ __forceinline__ float xf_ro(const TX* x, int c) {
+    if constexpr (sizeof(TX) == 2)
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(x) + c)));
+    else return (float)__ldg(x + c);
+}
+
 // double-float product (ah + al) * b for an exact FP32 b (FMA gives the exact error of ah*b)
 __device__ __forceinline__ df df_mul_f(df a, float b) {
     const float p = a.h * b;
@@ -115,6 +122,10 @@ struct SpmvArith {
     __device__ static XV xload(const TX* x, int c) {
         if constexpr (DFM) return xf(x, c);
         else return (double)x[c];
+    }
+    __device__ static XV xload_ro(const TX* x, int c) {       // x not written by the kernel
+        if constexpr (DFM) return xf_ro(x, c);
+        else return (double)__ldg(x + c);
     }
     __device__ static V vload(const SpmvParams& p, int q) {
         if constexpr (DFM) return p.vdf[q];
@@ -193,6 +204,10 @@ __device__ __forceinline__ void tile_rows(const SpmvParams& p, const TX* x, int6
 // every load of entry t is one contiguous access and no row pointers are read.  Entries are
 // multiplied and added exactly as in tile_rows (first RB alternately into two chains, the rest
 // into the first); padding entries (value 0) add exact zeros, so the results are bit-identical.
+// A, its SELL copy and x are read-only here (w is another buffer), so every load takes the
+// read-only path and the four slices' offsets are read first and w is stored after the last
+// product: no store orders a later slice's loads behind an earlier slice's, and the slices'
+// load chains can overlap.
 template <typename TX, bool DFM>
 __device__ __forceinline__ void tile_rows_sell(const SpmvParams& p, const TX* x, int64_t rbase,
                                                typename std::conditional<DFM, df, double>::type z[4]) {
@@ -200,39 +215,56 @@ __device__ __forceinline__ void tile_rows_sell(const SpmvParams& p, const TX* x,
     using V = typename AR::V;
     using XV = typename AR::XV;
     const int lane = threadIdx.x & 31;
-    const V* sval = reinterpret_cast<const V*>(p.sval);
+    auto vld = [&](int64_t q) -> V {
+        if constexpr (DFM) {
+            const float2 t = __ldg(reinterpret_cast<const float2*>(p.sval) + q);
+            return df{t.x, t.y};
+        } else {
+            return __ldg(reinterpret_cast<const double*>(p.sval) + q);
+        }
+    };
+    int64_t q0[4];
+    int width[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int64_t s = (rbase + (int64_t)TILE_THREADS * e + (threadIdx.x & ~31)) >> 5;   // warp-uniform
-        V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
+        q0[e] = 0;
+        width[e] = 0;
         if (s < p.nslices) {
-            const int64_t q0 = __ldg(p.soff + s);
-            const int width = (int)((__ldg(p.soff + s + 1) - q0) >> 5);
-            int c[RB];
-            V v[RB];
-            XV xv[RB];
+            q0[e] = __ldg(p.soff + s);
+            width[e] = (int)((__ldg(p.soff + s + 1) - q0[e]) >> 5);
+        }
+    }
 #pragma unroll
-            for (int t = 0; t < RB; ++t)
-                if (t < width) {
-                    const int64_t q = q0 + 32 * t + lane;
-                    c[t] = __ldg(p.scol + q);
-                    v[t] = sval[q];
-                }
+    for (int e = 0; e < 4; ++e) {
+        V acc0 = FW<V>::zero(), acc1 = FW<V>::zero();
+        int c[RB];
+        V v[RB];
+        XV xv[RB];
 #pragma unroll
-            for (int t = 0; t < RB; ++t)
-                if (t < width) xv[t] = AR::xload(x, c[t]);
-#pragma unroll
-            for (int t = 0; t < RB; ++t)
-                if (t < width) {
-                    if (t & 1) acc1 = AR::madd(acc1, v[t], xv[t]);
-                    else acc0 = AR::madd(acc0, v[t], xv[t]);
-                }
-            for (int t = RB; t < width; ++t) {
-                const int64_t q = q0 + 32 * t + lane;
-                acc0 = AR::madd(acc0, sval[q], AR::xload(x, __ldg(p.scol + q)));
+        for (int t = 0; t < RB; ++t)
+            if (t < width[e]) {
+                const int64_t q = q0[e] + 32 * t + lane;
+                c[t] = __ldg(p.scol + q);
+                v[t] = vld(q);
             }
+#pragma unroll
+        for (int t = 0; t < RB; ++t)
+            if (t < width[e]) xv[t] = AR::xload_ro(x, c[t]);
+#pragma unroll
+        for (int t = 0; t < RB; ++t)
+            if (t < width[e]) {
+                if (t & 1) acc1 = AR::madd(acc1, v[t], xv[t]);
+                else acc0 = AR::madd(acc0, v[t], xv[t]);
+            }
+        for (int t = RB; t < width[e]; ++t) {
+            const int64_t q = q0[e] + 32 * t + lane;
+            acc0 = AR::madd(acc0, vld(q), AR::xload_ro(x, __ldg(p.scol + q)));
         }
         z[e] = FW<V>::add(acc0, acc1);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
         const int64_t r = rbase + threadIdx.x + (int64_t)TILE_THREADS * e;
         if (r < p.n) {
             if constexpr (DFM) {
