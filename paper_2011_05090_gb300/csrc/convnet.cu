@@ -1,11 +1,13 @@
 // The learned preconditioner: six 3x3 convolutions (2 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
 // between layers, zero padding) on H x W grids, with hand-written forward and backward kernels.
 //
-//  - conv3x3_tc_kernel: the convolution as an implicit GEMM (pixels x (tap, c_in) times
+//  - conv3x3_tma_kernel: the convolution as an implicit GEMM (pixels x (tap, c_in) times
 //    (tap, c_in) x c_out) on the tcgen05 tensor cores (BF16 operands from shared memory, FP32
-//    accumulator in TMEM, one M = 128 pixels x N = c_out x K = 16 MMA per tap and channel step).
-//    A CTA stages an 8 x 16 pixel tile's halo (three column-shifted copies, so that every tap's
-//    operand is a plain descriptor into them) and the layer's weights.  The same kernel computes
+//    accumulator in TMEM, one M = 128 pixels x N = c_out x K = 16 MMA per tap and channel step),
+//    each 16 x 8 pixel tile's halo brought in by TMA tensor copies (one per 8-channel chunk, zeros
+//    outside the grid); every tap's operand is a descriptor into the same halo.
+//  - conv3x3_tc_kernel: the same with 8 x 16 pixel tiles whose halos are staged by per-thread
+//    asynchronous copies (three column-shifted copies); used where no tensor map can be encoded.  The same kernel computes
 //    the backward pass for the activations: the gradient of a layer's input is the convolution of
 //    the output gradient with the taps flipped and c_in / c_out swapped, masked by ReLU'.
 //  - dweight_mma_kernel: weight and bias gradients (sums over all pixels of the batch) as
@@ -15,7 +17,10 @@
 // every update.
 #include "common.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -265,6 +270,218 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a, int B) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr) : "memory");
+}
+
+// ---- the convolution with TMA-staged halos
+// One 4-D tensor map per 8-channel chunk of the input (dims: 8 channels, W, H, B; strides 2 CS,
+// 2 CS W, 2 CS W H bytes): a tile's halo chunk is one cp.async.bulk.tensor of a box of 8 channels
+// x 10 columns x 18 rows, landing as rows of 16 bytes, pixel (h, w) at (10 h + w) * 16, with
+// zeros where the box leaves the grid.  The tile is 16 rows x 8 columns, so the 8-row groups of
+// the M = 128 pixels are 8 consecutive columns of one row: for tap (dy, dx) and channel step kk
+// the operand A is the descriptor at (10 dy + dx) * 16 into chunks 2 kk, 2 kk + 1, with an 8-row
+// group stride of 160 bytes and the chunk stride as K step (no shifted copies).  Thread 0 keeps
+// CONV_STAGES tiles' halos in flight, issues a tile's MMAs into one of two TMEM accumulators and
+// commits them to that accumulator's mbarrier; all threads read the other accumulator (the
+// previous tile) meanwhile.  A stage is refilled once the MMAs that read it have completed.  Same
+// MMAs in the same order as conv3x3_tc_kernel: bit-identical outputs.
+constexpr int TH2 = 16, TW2 = 8;                               // pixel tile (rows x columns)
+constexpr int HALO_H = TH2 + 2, HALO_W = TW2 + 2;
+constexpr int CHUNK_BYTES = HALO_H * HALO_W * 16;              // one chunk's box
+constexpr int CHUNK_STRIDE = (CHUNK_BYTES + 127) / 128 * 128;  // chunks 128-byte aligned
+constexpr int CONV_STAGES = 4;
+
+struct ConvMaps {
+    CUtensorMap m[4];                  // chunks 0 .. CS / 8 - 1
+};
+
+template <int CS, int NP>
+struct ConvTmaSmem {
+    static constexpr int C8 = CS / 8;
+    static constexpr int STAGE = C8 * CHUNK_STRIDE;
+    static constexpr int B_BYTES = 9 * (NP / 8) * C8 * 128;
+    static constexpr int BYTES = CONV_STAGES * STAGE + B_BYTES + 8 * (CONV_STAGES + 2) + 16;
+};
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_poll(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_limited(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_poll(mbar, parity)) return true;
+    return false;
+}
+
+template <int CS, int CO, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant__ ConvMaps maps, ConvArgs a, int B) {
+    constexpr int NP = CO < 16 ? 16 : CO;
+    using SM = ConvTmaSmem<CS, NP>;
+    constexpr int C8 = SM::C8, NS = CONV_STAGES;
+    constexpr int TCOLS = 2 * NP < 32 ? 32 : 2 * NP;             // two accumulators of NP columns
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sB = smem + NS * SM::STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + SM::B_BYTES);
+    uint64_t* mdone = full + NS;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 2);
+    int* abort_flag = reinterpret_cast<int*>(tslot + 1);       // a halo wait of thread 0 ran out
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tilesx = a.W / TW2, tilesy = (a.H + TH2 - 1) / TH2, ntiles = tilesx * tilesy * B;
+    const int G = gridDim.x;
+    const int nmine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+    const uint32_t full0 = (uint32_t)__cvta_generic_to_shared(full);
+    const uint32_t mdone0 = (uint32_t)__cvta_generic_to_shared(mdone);
+    const uint32_t stage0 = (uint32_t)__cvta_generic_to_shared(smem);
+    auto coords = [&](int j, int& b, int& y0, int& x0) {
+        const int t = (int)blockIdx.x + j * G;
+        b = t / (tilesx * tilesy);
+        const int r = t % (tilesx * tilesy);
+        y0 = (r / tilesx) * TH2;
+        x0 = (r % tilesx) * TW2;
+    };
+    // the weights, once (as in conv3x3_tc_kernel)
+    for (int c = tid; c < 9 * (NP / 8) * C8 * 8; c += 128) {
+        const int row = c & 7, c8 = (c >> 3) % C8, tn = (c >> 3) / C8;
+        const int n8 = tn % (NP / 8), tap = tn / (NP / 8);
+        const int co = n8 * 8 + row;
+        cp_async16(sB + ((tn * C8) + c8) * 128 + row * 16, co < CO ? a.w + ((size_t)tap * CO + co) * CS + c8 * 8 : a.w,
+                   co < CO ? 16 : 0);
+    }
+    if (tid == 0) {
+        for (int q = 0; q < NS + 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "n"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // the weights, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
+    // thread 0's bookkeeping: tiles whose halo copies were issued / seen landed, MMAs issued
+    int issued = 0, landed = 0, mmas = 0;
+    auto issue = [&](int j) {
+        if (j >= nmine) return;
+        int b, y0, x0;
+        coords(j, b, y0, x0);
+        const int s = j % NS;
+        mbar_arrive_expect_tx(full0 + 8 * s, (uint32_t)(C8 * CHUNK_BYTES));
+#pragma unroll
+        for (int c = 0; c < C8; ++c)
+            tma_load_4d(stage0 + s * SM::STAGE + c * CHUNK_STRIDE, &maps.m[c], 0, x0 - 1, y0 - 1, b, full0 + 8 * s);
+        issued = j + 1;
+    };
+    if (tid == 0)
+        for (int j = 0; j < NS; ++j) issue(j);
+    bool ok = true;
+    for (int j = 0; j <= nmine && ok; ++j) {
+        // tile j's MMAs into accumulator j % 2, once its halo has landed (thread 0)
+        if (tid == 0 && j < nmine) {
+            const int s = j % NS;
+            if (!mbar_wait_limited(full0 + 8 * s, (uint32_t)((j / NS) & 1))) {
+                *abort_flag = 1;
+            } else {
+                landed = j + 1;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = stage0 + s * SM::STAGE, b0 = (uint32_t)__cvta_generic_to_shared(sB);
+                const uint32_t dcol = taddr + (uint32_t)((j & 1) * NP);
+                constexpr uint32_t idesc = tc_idesc_bf16(128, NP);
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+                    for (int kk = 0; kk < CS / 16; ++kk) {
+                        const uint64_t ad = tc_sdesc(a0 + 2 * kk * CHUNK_STRIDE + (dy * HALO_W + dx) * 16, CHUNK_STRIDE,
+                                                     HALO_W * 16);
+                        const uint64_t bd = tc_sdesc(b0 + tap * (NP / 8) * C8 * 128 + kk * 256, 128, C8 * 128);
+                        tc_mma(dcol, ad, bd, idesc, (tap | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(mdone0 + 8 * (j & 1)) : "memory");
+                mmas = j + 1;
+            }
+        }
+        // the epilogue of tile j - 1 (all threads) from accumulator (j - 1) % 2
+        if (j >= 1) {
+            const int jp = j - 1;
+            const bool seen = mbar_wait_limited(mdone0 + 8 * (jp & 1), (uint32_t)((jp >> 1) & 1));
+            const bool done = __syncthreads_and((int)seen) != 0;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!done) {
+                if (tid == 0 && a.status) atomicCAS(a.status, 0, (int)RGS_ERR_TIMEOUT);
+                ok = false;
+            } else {
+                if (tid == 0) issue(jp + NS);            // its stage is free: the MMAs that read it are done
+                int b, y0, x0;
+                coords(jp, b, y0, x0);
+                float acc[NP];
+                tc_ld<NP>(taddr + (uint32_t)((jp & 1) * NP) + ((uint32_t)(warp * 32) << 16), acc);
+                const int m = warp * 32 + lane, y = y0 + m / TW2, x = x0 + m % TW2;
+                if (y < a.H) {
+                    const size_t pix = ((size_t)b * a.H + y) * a.W + x;
+                    if constexpr (MODE == 1) {
+                        const float sc = a.scale ? a.scale[b] : 1.f;
+                        reinterpret_cast<float*>(a.out)[pix] = (acc[0] + a.bias[0]) * sc;
+                    } else {
+                        bf16* o = reinterpret_cast<bf16*>(a.out) + pix * CO;
+#pragma unroll
+                        for (int c = 0; c < CO; c += 8) {
+                            float v[8];
+                            if constexpr (MODE == 0) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) v[e] = fmaxf(acc[c + e] + a.bias[c + e], 0.f);
+                            } else {
+                                const uint4 mk = __ldg(reinterpret_cast<const uint4*>(a.mask + pix * CO + c));
+                                const bf16* mm = reinterpret_cast<const bf16*>(&mk);
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(mm[e]) > 0.f ? acc[c + e] : 0.f;
+                            }
+                            uint4 pk;
+                            __nv_bfloat162* q = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) q[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                            *reinterpret_cast<uint4*>(o + c) = pk;
+                        }
+                    }
+                }
+            }
+        }
+        // accumulator (j - 1) % 2 takes tile j + 1's MMAs next: every thread has read it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(*abort_flag)) {
+            if (tid == 0 && a.status) atomicCAS(a.status, 0, (int)RGS_ERR_TIMEOUT);
+            ok = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!ok && tid == 0) {                               // copies and MMAs in flight end before the CTA does
+        for (int j = landed; j < issued; ++j) mbar_wait_limited(full0 + 8 * (j % NS), (uint32_t)((j / NS) & 1));
+        if (mmas > 0) mbar_wait_limited(mdone0 + 8 * ((mmas - 1) & 1), (uint32_t)(((mmas - 1) >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(TCOLS) : "memory");
 }
 
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const bf16* p) {
@@ -584,12 +801,66 @@ __global__ void init_kernel(float* __restrict__ p, int64_t off, int64_t nw, int6
     p[off + i] = (float)((2.0 * u - 1.0) * bound);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null if unavailable)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// The input's chunk maps: chunk c = channels 8c .. 8c + 7 of the NHWC BF16 tensor x (CS channels)
+bool encode_conv_maps(ConvMaps& m, const bf16* x, int CS, int W, int H, int B) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    for (int c = 0; c < CS / 8; ++c) {
+        const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {(cuuint64_t)CS * 2, (cuuint64_t)CS * 2 * W, (cuuint64_t)CS * 2 * W * H};
+        const cuuint32_t box[4] = {8, HALO_W, HALO_H, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (fn(&m.m[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + 8 * c), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 template <int CS, int NT, int MODE>
 void launch_conv(rgs_context* ctx, const ConvArgs& a0, int B) {
     constexpr int CO = NT * 8, NP = CO < 16 ? 16 : CO;
     constexpr int smem = ConvTcSmem<CS, NP>::BYTES;
     ConvArgs a = a0;
     a.status = ctx->ctl.as<int>() + kStatusWord;
+    // TMA-staged halos when the tensor maps can be encoded (RGS_CONV_TMA=0 in the environment:
+    // the halos staged by per-thread asynchronous copies)
+    const char* tma_env = std::getenv("RGS_CONV_TMA");
+    ConvMaps maps{};
+    if (!(tma_env && tma_env[0] == '0') && encode_conv_maps(maps, a.x, CS, a.W, a.H, B)) {
+        constexpr int tsmem = ConvTmaSmem<CS, NP>::BYTES;
+        auto kern = conv3x3_tma_kernel<CS, CO, MODE>;
+        RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem));
+        RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        // one wave: as many CTAs per SM as the shared memory holds (TMEM: 2 NP columns each)
+        const int per_sm = std::max(1, std::min(8, (227 * 1024) / (tsmem + 1024)));
+        const int ntiles = (a.W / TW2) * ((a.H + TH2 - 1) / TH2) * B;
+        const int grid = std::max(1, std::min(ntiles, per_sm * ctx->num_sms));
+        kern<<<grid, 128, tsmem, ctx->stream>>>(maps, a, B);
+        RGS_CUDA(cudaGetLastError());
+        ctx->launches++;
+        return;
+    }
     auto kern = conv3x3_tc_kernel<CS, CO, MODE>;
     RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RGS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));

@@ -91,6 +91,30 @@ def test_forward_matches_oracle(h, H, W, B):
     assert e_bf <= 6e-3 and e <= 3e-2
 
 
+@pytest.mark.parametrize("H,W,B", [(24, 48, 3), (64, 128, 2)])
+def test_tma_convolution_bit_identical_to_cp_async(h, H, W, B, monkeypatch):
+    """The convolutions with TMA-staged halos (the default) and with halos staged by per-thread
+    asynchronous copies (RGS_CONV_TMA=0) issue the same MMAs in the same order: the forward output
+    and the loss gradient agree bit for bit (H = 24: the second 16-row tile is half outside the
+    grid)."""
+    net = rgs.rgs_convnet_create(h, H, W, B, seed=1)
+    rgs.rgs_convnet_set_params(h, net, random_params(H + 2 * W))
+    x = dev(net_batch(B, H, W, 12), torch.float32)
+    t = dev(np.random.default_rng(13).standard_normal((B, H, W)), torch.float32)
+    out = {}
+    try:
+        for mode in ("tma", "cp"):
+            if mode == "cp":
+                monkeypatch.setenv("RGS_CONV_TMA", "0")
+            f = rgs.rgs_convnet_forward(h, net, x).clone()
+            L, g = rgs.rgs_convnet_loss_grad(h, net, x, t)
+            out[mode] = (f, L, g)
+    finally:
+        monkeypatch.delenv("RGS_CONV_TMA", raising=False)
+    assert torch.equal(out["tma"][0], out["cp"][0])
+    assert out["tma"][1] == out["cp"][1] and np.array_equal(out["tma"][2], out["cp"][2])
+
+
 def test_forward_batch_entries_are_independent(h):
     H, W = 16, 32
     net = rgs.rgs_convnet_create(h, H, W, 3, seed=2)
