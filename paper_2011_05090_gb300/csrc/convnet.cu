@@ -352,31 +352,6 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
         y0 = (r / tilesx) * TH2;
         x0 = (r % tilesx) * TW2;
     };
-    // the weights, once (as in conv3x3_tc_kernel)
-    for (int c = tid; c < 9 * (NP / 8) * C8 * 8; c += 128) {
-        const int row = c & 7, c8 = (c >> 3) % C8, tn = (c >> 3) / C8;
-        const int n8 = tn % (NP / 8), tap = tn / (NP / 8);
-        const int co = n8 * 8 + row;
-        cp_async16(sB + ((tn * C8) + c8) * 128 + row * 16, co < CO ? a.w + ((size_t)tap * CO + co) * CS + c8 * 8 : a.w,
-                   co < CO ? 16 : 0);
-    }
-    if (tid == 0) {
-        for (int q = 0; q < NS + 2; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * q) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *abort_flag = 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "n"(TCOLS) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // the weights, for the tensor core
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t taddr = *tslot;
     // thread 0's bookkeeping: tiles whose halo copies were issued / seen landed, MMAs issued
     int issued = 0, landed = 0, mmas = 0;
     auto issue = [&](int j) {
@@ -390,8 +365,33 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
             tma_load_4d(stage0 + s * SM::STAGE + c * CHUNK_STRIDE, &maps.m[c], 0, x0 - 1, y0 - 1, b, full0 + 8 * s);
         issued = j + 1;
     };
-    if (tid == 0)
+    // the barriers, and the first halos in flight while the weights are staged and TMEM allocated
+    if (tid == 0) {
+        for (int q = 0; q < NS + 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
         for (int j = 0; j < NS; ++j) issue(j);
+    }
+    // the weights, once (as in conv3x3_tc_kernel)
+    for (int c = tid; c < 9 * (NP / 8) * C8 * 8; c += 128) {
+        const int row = c & 7, c8 = (c >> 3) % C8, tn = (c >> 3) / C8;
+        const int n8 = tn % (NP / 8), tap = tn / (NP / 8);
+        const int co = n8 * 8 + row;
+        cp_async16(sB + ((tn * C8) + c8) * 128 + row * 16, co < CO ? a.w + ((size_t)tap * CO + co) * CS + c8 * 8 : a.w,
+                   co < CO ? 16 : 0);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "n"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // the weights, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = *tslot;
     bool ok = true;
     for (int j = 0; j <= nmine && ok; ++j) {
         // tile j's MMAs into accumulator j % 2, once its halo has landed (thread 0)
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(128) conv3x3_tma_kernel(const __grid_constant_
                 const uint32_t a0 = stage0 + s * SM::STAGE, b0 = (uint32_t)__cvta_generic_to_shared(sB);
                 const uint32_t dcol = taddr + (uint32_t)((j & 1) * NP);
                 constexpr uint32_t idesc = tc_idesc_bf16(128, NP);
-#pragma unroll 1
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
