@@ -440,7 +440,9 @@ struct LSState {
     double *sbuf, *pbuf, *ys, *yp;
     double *M;              // M = V T (column-major k x mmax): Q_H^T x = x - V (M^T x)
     double *u2s, *u2p;
-    double *zp, *d1, *d2;   // per-column dots of phase 4
+    double *N;              // N = V T^T (column-major k x mmax): the new T column's sums over rows below i
+    int* nfold;             // reflectors folded into N so far (phase 0 adds the newest once)
+    double *d1, *d2;        // per-column dots (scratch)
     double *blk;            // 4 * grid
     double *sigma, *pnorm, *coef;
     double *R;

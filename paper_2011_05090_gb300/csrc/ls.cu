@@ -8,8 +8,11 @@
 //   new reflector H_i from y_s(i:k)      (appends s_i, column i of R_S = [y_s(0:i); beta])
 //   x  = R_S^{-1} (H_i y_p)(0:i+1)       (the least-squares solution)
 //   T(0:i, i) = -tau_i T V^T v_i, R_S^{-1} gains the column -R_S^{-1} y_s(0:i) / beta,
-//   M(:, i) = V T(:, i) (formed at the start of the next launch).
-// One cooperative launch per column; phases are separated by bounded grid barriers.
+//   M(:, i) = V T(:, i) and N += v_i T(:, i)^T, N = V T^T (formed at the start of the next
+//   launch; with N, T V^T v_i's sums over the rows below i are dots with N's columns, so the
+//   new columns of T, R_S^{-1} and x are finished in the same phase as their other dots).
+// One cooperative launch per column; its four phases are separated by three bounded grid
+// barriers.
 //
 // Loads.  Vectors that every warp of the grid reads (T's new column, s', p, u, y, z) go through
 // L1: a grid barrier ends with a GPU-scope acquire, after which ordinary loads see every write
@@ -442,6 +445,17 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     if (tr) tr[0] = globaltimer();
     GridBarrier bar(ctl);
     const double pref = (app && tid == 0) ? st.pnorm[i] : 0.0;   // ||p_i||, for the breakdown test
+    const int nfold0 = *st.nfold;                                // reflectors in N before this launch
+    // N must hold reflectors 0 .. i-2 (or already i-1: a retried step); anything else (a launch
+    // that gave up between phase 0 and its first barrier) leaves it unusable: every CTA reads the
+    // same word and leaves before any write
+    if (app && !rich && i > 0 && nfold0 != i - 1 && nfold0 != i) {
+        if (gtid == 0 && ctl[kStatusWord] == 0 && ctl[kStopWord] == 0) {
+            atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_INVALID_ARG);
+            ctl[kDetailWord] = i;
+        }
+        return;
+    }
     if (tid == 0) {                                              // the partial sketches' scales
         scT[6] = A::from_d(a.s_scale);
         scT[7] = A::from_d(a.p_scale);
@@ -528,6 +542,32 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                 warp_row_dot2<A>(st.VT + (size_t)l * mm, tc, tc, min(i, l + 1), true, false, d, unused);
                 if (lane == 0) A::st(st.M + (size_t)(i - 1) * k + l, d);
             }
+            // N = V T^T (column-major k x mmax) gains reflector i - 1: N(:, j) += V(:, i-1) T(j, i-1)
+            // for j < i - 1, N(:, i-1) = V(:, i-1) T(i-1, i-1); V(:, i-1) vanishes above row i - 1.
+            // Once per reflector: nfold counts the reflectors in N (a step that is solved and then
+            // appended, or retried after a failed launch, reaches this with the same i again).
+            if (app && nfold0 == i - 1) {
+                const int r0 = (i - 1) & ~15;                 // item rows from a 16-row boundary
+                const int nch = (k - r0 + 255) / 256;
+                const double* vc = st.V + (size_t)(i - 1) * k;
+                for (int item = gwarp; item < i * nch; item += nwarps) {   // (column, 256 rows)
+                    const int j = item / nch, l0 = r0 + 256 * (item % nch);
+                    const T tj = A::ld(tc + j);
+                    double* nc = st.N + (size_t)j * k;
+                    T nv[8], vv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int l = l0 + 32 * q + lane;
+                        vv[q] = l < k ? A::ld(vc + l) : zero;
+                        nv[q] = (l < k && j < i - 1) ? A::ld(nc + l) : zero;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int l = l0 + 32 * q + lane;
+                        if (l < k) A::st(nc + l, A::add(nv[q], A::mul(vv[q], tj)));
+                    }
+                }
+            }
         }
         if (tid == 0) {
             if constexpr (f32) {
@@ -540,6 +580,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     }
     if (!bar.sync(ctl, tr ? tr + 1 : nullptr)) return;
+    if (app && !rich && gtid == 0) *st.nfold = i;
 
     // ---- phase 1: r_ii, s_i = s'/r_ii; u2 = M(:, 0:i)^T [s, p] = T^T V^T [s, p]
     // Warp 0 reads the squared norms' totals and forms the phase's scalars (FP64 square roots
@@ -698,12 +739,8 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     }
 
     // The new reflector's scalars (one warp): totals SG, CR of phase 3's sums; alpha, beta, tau,
-    // vs and the solve's y_i.  They need nothing of phase 4, so while i <= 3G/2 warp 12 (of the
-    // fourth quad, which has no column there while i <= 3G) forms them during phase 4, hidden
-    // behind the column owners' dots, and the last phase loses the chain (about 1.2 us a launch
-    // at i < G).  With more columns per CTA the chain's FP64 instructions share the SM's FP64
-    // pipe with the dots and lengthen phase 4 by more than they save (measured from i = 300 at
-    // k = 2000); there warp 0 forms them in phase 5.  Same code, same roundings.
+    // vs and the solve's y_i.  Warp 12 forms them at the start of phase 4 (the fourth quad has no
+    // column there while i <= 3G), behind the column owners' dots.
     auto reflector_scalars = [&]() {
         T alpha = zero, ypi0 = zero;
         if (lane == 0) {                               // issued before the totals' round trip
@@ -727,40 +764,50 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
         }
     };
     static_assert(NW == 16, "phase 4 runs four quads of four warps");
-    const bool early_scalars = 2 * i <= 3 * G;
 
-    // ---- phase 4: per column j < i, the dots the new reflector needs that do not depend on beta:
-    //   zp_j = sum_{l>i} V(l,j) ys_l,  d1_j = sum_{j<=l<i} Rinv(j,l) ys_l,  d2_j likewise with yp
-    //   (and GMRES's rotation of H(:, i-1), by warp 0 of the last CTA)
+    // ---- phase 4 (the last): the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x.  Per
+    //   column j < i, by the four warps of one quad: T(j, i) = -tau (a_j + vs b_j) with
+    //   a_j = sum_{j<=l<i} T(j,l) V(i,l) and b_j = sum_{l>i} N(l,j) ys_l (N = V T^T, kept by phase
+    //   0: b_j = sum_l T(j,l) zp_l with zp_l = sum_{r>i} V(r,l) ys_r, the same sum in the other
+    //   order, so no grid phase waits for the zp), and d1_j = sum_{j<=l<i} Rinv(j,l) ys_l (d2_j
+    //   likewise with yp) for R_S^{-1}(j, i) = -d1_j / beta and x_j; the quad's lane 0 finishes
+    //   the column.  GMRES: warp 0 of the last CTA rotates H(:, i-1).
     if (a.givens && i > 0 && blockIdx.x == G - 1 && tid < 32) givens_and_stop(st, a, r, ctl, false);
-    if (early_scalars && i == 0 && warp == 12) reflector_scalars();   // no column at all
+    if (warp == 12) reflector_scalars();               // read after the quads' first barrier
     {
+        // quad 3 splits its column over warps 13..15: warp 12 forms the scalars (and adds zeros)
         const int quad = tid >> 7, qw = (tid >> 5) & 3;
+        const int nq = quad == 3 ? 3 : 4, qi = quad == 3 ? qw - 1 : qw;
+        const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
         for (int base = 0; base < i; base += G * (NW / 4)) {
             const int j = base + blockIdx.x + G * quad;
-            if (early_scalars && warp == 12) {             // quad 3 has no column: j >= 3G >= i
-                reflector_scalars();
-            } else if (j < i) {
-                const double* v = st.V + (size_t)j * k;
-                const int len = k - (i + 1), seg = (max(len, 0) + 3) / 4;
-                const int l0 = i + 1 + qw * seg, l1 = min(k, l0 + seg);
-                Acc az = A::acc0(), a1 = A::acc0(), a2 = A::acc0();
+            if (j < i && qi < 0 && lane == 0) {
+                qs[(quad * 4 + qw) * 3] = zero;
+                qs[(quad * 4 + qw) * 3 + 1] = zero;
+                qs[(quad * 4 + qw) * 3 + 2] = zero;
+                shT[quad * 4 + qw] = zero;
+            } else if (j < i && qi >= 0) {
+                const double* nc = st.N + (size_t)j * k;
+                const int len = k - (i + 1), seg = (max(len, 0) + nq - 1) / nq;
+                const int l0 = i + 1 + qi * seg, l1 = min(k, l0 + seg);
+                Acc ab = A::acc0(), aa = A::acc0(), a1 = A::acc0(), a2 = A::acc0();
                 for (int lb = l0; lb < l1; lb += 32 * 8) {   // loads of 8 rows per lane first
-                    T vv[8], yv[8];
+                    T nv[8], yv[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int l = lb + 32 * q + lane;
-                        vv[q] = l < l1 ? A::ld(v + l) : zero;
+                        nv[q] = l < l1 ? A::ldcg(nc + l) : zero;    // N is written in this launch
                         yv[q] = l < l1 ? A::ld(st.ys + l) : zero;
                     }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) A::acc(az, vv[q], yv[q]);
+                    for (int q = 0; q < 8; ++q) A::acc(ab, nv[q], yv[q]);
                 }
                 const double* rr = st.RinvT + (size_t)j * mm;       // row j of R_S^{-1}
-                const int rlen = i - j, rseg = (rlen + 3) / 4;
-                const int r0 = j + qw * rseg, r1 = min(i, r0 + rseg);
+                const double* tt = st.TT + (size_t)j * mm;          // row j of T
+                const int rlen = i - j, rseg = (rlen + nq - 1) / nq;
+                const int r0 = j + qi * rseg, r1 = min(i, r0 + rseg);
                 for (int lb = r0; lb < r1; lb += 32 * 4) {
-                    T rv[4], y1[4], y2[4];
+                    T rv[4], y1[4], y2[4], tv[4], vv[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int l = lb + 32 * q + lane;
@@ -768,91 +815,56 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
                         rv[q] = ok ? A::ld(rr + l) : zero;
                         y1[q] = ok ? A::ld(st.ys + l) : zero;
                         y2[q] = (ok && sol) ? A::ld(st.yp + l) : zero;
+                        tv[q] = ok ? A::ld(tt + l) : zero;
+                        vv[q] = ok ? A::ld(vrow_i + l) : zero;
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         A::acc(a1, rv[q], y1[q]);
                         if (sol) A::acc(a2, rv[q], y2[q]);
+                        A::acc(aa, tv[q], vv[q]);
                     }
                 }
-                const T z = A::wsum(A::val(az));
+                const T bsum = A::wsum(A::val(ab));
+                const T asum = A::wsum(A::val(aa));
                 const T d1 = A::wsum(A::val(a1));
                 const T d2 = sol ? A::wsum(A::val(a2)) : zero;
                 if (lane == 0) {
-                    qs[(quad * 4 + qw) * 3] = z;
+                    qs[(quad * 4 + qw) * 3] = bsum;
                     qs[(quad * 4 + qw) * 3 + 1] = d1;
                     qs[(quad * 4 + qw) * 3 + 2] = d2;
+                    shT[quad * 4 + qw] = asum;
                 }
             }
             __syncthreads();
-            if (j < i && qw == 0 && lane == 0) {
+            const T beta = scT[0], tau = scT[1], vs = scT[2], ypi = scT[3];
+            if (j < i && qw == 0 && lane == 0 && !A::is_zero(beta)) {   // column j's entries of T, R_S^{-1}, x
                 const T* q4 = qs + quad * 12;
-                A::st(st.zp + j, A::add(A::add(q4[0], q4[3]), A::add(q4[6], q4[9])));
-                A::st(st.d1 + j, A::add(A::add(q4[1], q4[4]), A::add(q4[7], q4[10])));
-                A::st(st.d2 + j, A::add(A::add(q4[2], q4[5]), A::add(q4[8], q4[11])));
+                const T bj = A::add(A::add(q4[0], q4[3]), A::add(q4[6], q4[9]));
+                const T d1j = A::add(A::add(q4[1], q4[4]), A::add(q4[7], q4[10]));
+                const T d2j = A::add(A::add(q4[2], q4[5]), A::add(q4[8], q4[11]));
+                const T* s4 = shT + quad * 4;
+                const T aj = A::add(A::add(s4[0], s4[1]), A::add(s4[2], s4[3]));
+                const T t = A::neg(A::mul(tau, A::add(aj, A::mul(vs, bj))));
+                A::st(st.T + (size_t)i * mm + j, t);
+                A::st(st.TT + (size_t)j * mm + i, t);
+                const T cnew = A::neg(A::div(d1j, beta));            // R_S^{-1}(j, i)
+                A::st(st.RinvT + (size_t)j * mm + i, cnew);
+                if (sol) {
+                    const double xj = A::to_d(A::add(d2j, A::mul(cnew, ypi)));
+                    st.R[(size_t)a.xcol * st.ldr + j] = xj;
+                    st.coef[j] = xj * st.sigma[j];
+                }
             }
             __syncthreads();
         }
     }
-    if (!bar.sync(ctl, tr ? tr + 7 : nullptr)) return;
-
-    // ---- phase 5: the reflector H_i, V(:, i), T(0:i, i), R_S^{-1}(:, i) and x
-    // Warps 1..15 compute, per column j < i, the two dots of T(j, i) = -tau (a_j + vs b_j) with
-    // a_j = sum_l T(j,l) V(i,l) and b_j = sum_l T(j,l) zp_l (l in [j, i)), which need none of
-    // the reflector's scalars; warp 0 forms those here unless warp 12 did in phase 4.
-    if (warp == 0 && !early_scalars) reflector_scalars();
-    const double* vrow_i = st.VT + (size_t)i * mm;     // V(i, 0:i)
-    auto tdots = [&](int j, T& da, T& db) {
-        const double* tr = st.TT + (size_t)j * mm;
-        Acc ca[2] = {A::acc0(), A::acc0()}, cb[2] = {A::acc0(), A::acc0()};
-        for (int lb = j; lb < i; lb += 32 * 4) {       // loads of 4 entries per lane first
-            T tv[4], vv[4], zv[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int l = lb + 32 * q + lane;
-                const bool ok = l < i;
-                tv[q] = ok ? A::ld(tr + l) : zero;
-                vv[q] = ok ? A::ld(vrow_i + l) : zero;
-                zv[q] = ok ? A::ld(st.zp + l) : zero;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                A::acc(ca[q & 1], tv[q], vv[q]);
-                A::acc(cb[q & 1], tv[q], zv[q]);
-            }
-        }
-        da = A::wsum(A::add(A::val(ca[0]), A::val(ca[1])));
-        db = A::wsum(A::add(A::val(cb[0]), A::val(cb[1])));
-    };
-    const int gw1 = blockIdx.x + G * (warp - 1), nw1 = G * (NW - 1);
-    const bool first = warp >= 1 && gw1 < i;
-    T da0 = zero, db0 = zero;
-    if (first) tdots(gw1, da0, db0);
-    __syncthreads();
+    __syncthreads();                                   // the scalars, also when no column was done
     const T beta = scT[0], tau = scT[1], vs = scT[2], ypi = scT[3];
     if (A::is_zero(beta)) {
         if (gtid == 0) { atomicCAS(ctl + kStatusWord, 0, (int)RGS_ERR_BREAKDOWN); ctl[kDetailWord] = i; }
         return;
     }
-    auto finish = [&](int j, T da, T db) {           // lane 0: column j's entries of T, R_S^{-1}, x
-        const T t = A::neg(A::mul(tau, A::add(da, A::mul(vs, db))));
-        A::st(st.T + (size_t)i * mm + j, t);
-        A::st(st.TT + (size_t)j * mm + i, t);
-        const T cnew = A::neg(A::div(A::ld(st.d1 + j), beta));   // R_S^{-1}(j, i)
-        A::st(st.RinvT + (size_t)j * mm + i, cnew);
-        if (sol) {
-            const double xj = A::to_d(A::add(A::ld(st.d2 + j), A::mul(cnew, ypi)));
-            st.R[(size_t)a.xcol * st.ldr + j] = xj;
-            st.coef[j] = xj * st.sigma[j];
-        }
-    };
-    if (first && lane == 0) finish(gw1, da0, db0);
-    if (warp >= 1)
-        for (int j = gw1 + nw1; j < i; j += nw1) {
-            T da, db;
-            tdots(j, da, db);
-            if (lane == 0) finish(j, da, db);
-        }
     for (int l = gtid; l < k; l += nthreads) {
         const T vl = l < i ? zero : (l == i ? A::one() : A::mul(A::ld(st.ys + l), vs));
         A::st(st.V + (size_t)i * k + l, vl);
@@ -870,6 +882,7 @@ __global__ void __launch_bounds__(LT, 1) ls_kernel(LSState st, LSStep a) {
     }
     if (tr) tr[9] = globaltimer();
 }
+
 
 // Step 8 certificates: Delta_m = ||I - S^T S||_F, Delta~_m = ||P - S R||_F / ||P||_F.
 // Block t handles the columns b = t and b = m-1-t (equal total work per block): the entries
@@ -922,7 +935,8 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fin
     const size_t oV = take((size_t)k * mmax), oVT = take((size_t)k * mmax), oT = take((size_t)mmax * mmax),
                  oTT = take((size_t)mmax * mmax), oRi = take((size_t)mmax * mmax), oS = take((size_t)k * mmax),
                  osb = take(k), opb = take(k), oys = take(k), oyp = take(k), oM = take((size_t)k * mmax),
-                 ou2s = take(mmax), ou2p = take(mmax), ozp = take(mmax), od1 = take(mmax), od2 = take(mmax),
+                 ou2s = take(mmax), ou2p = take(mmax), oN = take((size_t)k * mmax), onf = take(1),
+                 od1 = take(mmax), od2 = take(mmax),
                  oblk = take((size_t)4 * grid), osg = take(mmax + 1),
                  opn = take(mmax + 2), oco = take(mmax + 1);
     buf.ensure(n * sizeof(double));
@@ -931,7 +945,7 @@ void rgs_ls_alloc(DevBuf& buf, int k, int mmax, int grid, int max_parts, int fin
     st->V = b + oV; st->VT = b + oVT; st->T = b + oT; st->TT = b + oTT; st->RinvT = b + oRi; st->S = b + oS;
     st->sbuf = b + osb; st->pbuf = b + opb; st->ys = b + oys; st->yp = b + oyp;
     st->M = b + oM; st->u2s = b + ou2s; st->u2p = b + ou2p;
-    st->zp = b + ozp; st->d1 = b + od1; st->d2 = b + od2;
+    st->N = b + oN; st->nfold = reinterpret_cast<int*>(b + onf); st->d1 = b + od1; st->d2 = b + od2;
     st->blk = b + oblk; st->sigma = b + osg; st->pnorm = b + opn;
     st->coef = b + oco;
 }
@@ -944,6 +958,7 @@ void rgs_ls_reset(rgs_context* ctx, const LSState& st) {
     RGS_CUDA(cudaMemsetAsync(st.TT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
     RGS_CUDA(cudaMemsetAsync(st.RinvT, 0, sizeof(double) * (size_t)st.mmax * st.mmax, ctx->stream));
     RGS_CUDA(cudaMemsetAsync(st.pnorm, 0, sizeof(double) * (size_t)(st.mmax + 2), ctx->stream));
+    RGS_CUDA(cudaMemsetAsync(st.nfold, 0, sizeof(int), ctx->stream));
 }
 
 int rgs_ls_grid(const rgs_context* ctx) {
